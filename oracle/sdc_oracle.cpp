@@ -1,0 +1,692 @@
+// Plain FP64 CPU oracle for the adaptive SDC step (test infrastructure).
+//
+// This file is the parity authority for the CUDA library.  It is slow on
+// purpose: single-threaded loops in the order the paper states the method, no
+// BLAS, no blocking, no fusion.  Only the test suite, the smoke check and the
+// benchmark's CPU-baseline leg load it; the library never does, and this file
+// shares no code, header or constant table with the library.
+//
+// What it computes (paper sections in brackets):
+//   * right Radau-IIA collocation nodes tau_1..tau_M with tau_M = 1, the
+//     cumulative quadrature matrix Q_mj = int_0^{tau_m} l_j, and the LU-trick
+//     lower-triangular preconditioner Qhat = U^T where Q^T = L U     [Sec. 3.1]
+//   * P1 finite elements: stiffness K, lumped mass m                 [Sec. 2.2]
+//   * Aliev-Panfilov current I_ion and gating rate R                [Sec. 5.1.1]
+//   * one SDC time step with operator-splitting sweeps (v then w) and
+//     nested algebraic active sets I_{k+1} = {i in I_k : |dv_i| >= TOL_drop}
+//                                                  [Sec. 3.2, eq. final-sdc; Sec. 4.2]
+//   * Jacobi-preconditioned CG on the restricted systems            [Sec. 4.2]
+//   * a dense Newton solve of the full collocation system (tiny meshes),
+//     the fixed point the SDC sweeps converge to                     [Sec. 3.1]
+//
+// Readings where the paper is ambiguous or garbled (each also listed in the
+// design notes):
+//   - Q is built on tau_1..tau_M only (standard Radau-IIA collocation); the
+//     node-to-node form S_i = Q_{i+1} - Q_i of eq. SDC Integration is equivalent.
+//   - the w correction of eq. final-sdc is read in its Newton-consistent form
+//     eps_m = (s_m + dt sum_{j<m} Qhat_mj dR_j eps_j) / (1 - dt Qhat_mm dR_m).
+//   - the predictor spreads the step's initial value to all nodes.
+//   - selection uses max over the M nodes of |dv_{m,i}| (v only).
+//   - the ionic load is lumped: b_i = m_i (I_ion(v_i, w_i) - I_stim,i).
+//
+// All parts are pinned by the CPU tests (Radau closed forms and exactness,
+// LU-trick nilpotency, SDC fixed point == direct collocation solve, Pade
+// stability function, observed time order, assembly stencils, conservation,
+// adaptivity invariants).
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// --------------------------------------------------------------------------
+// Collocation (Sec. 3.1)
+// --------------------------------------------------------------------------
+
+// Legendre polynomial P_n(x) by the three-term recurrence.
+long double legendre(int n, long double x) {
+    if (n == 0) return 1.0L;
+    long double p0 = 1.0L, p1 = x;
+    for (int k = 1; k < n; ++k) {
+        long double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+// Radau right polynomial on [-1, 1]: P_M(x) - P_{M-1}(x); its zeros map to the
+// Radau-IIA nodes by tau = (x + 1) / 2, and x = 1 is always one of them.
+long double radau_poly(int M, long double x) { return legendre(M, x) - legendre(M - 1, x); }
+
+// Nodes by sign-change bracketing on a fine grid, then bisection.
+bool radau_nodes(int M, std::vector<long double>& tau) {
+    tau.clear();
+    const int samples = 40000;
+    const long double lo = -1.0L, hi = 1.0L - 1e-3L;
+    long double xa = lo, fa = radau_poly(M, xa);
+    for (int s = 1; s <= samples; ++s) {
+        long double xb = lo + (hi - lo) * s / samples;
+        long double fb = radau_poly(M, xb);
+        if (fa == 0.0L) {
+            tau.push_back((xa + 1.0L) / 2.0L);
+        } else if ((fa < 0) != (fb < 0) && fb != 0.0L) {
+            long double a = xa, b = xb, f_a = fa;
+            for (int it = 0; it < 200; ++it) {
+                long double c = 0.5L * (a + b);
+                long double fc = radau_poly(M, c);
+                if (fc == 0.0L) { a = b = c; break; }
+                if ((fc < 0) == (f_a < 0)) { a = c; f_a = fc; } else { b = c; }
+            }
+            tau.push_back((0.5L * (a + b) + 1.0L) / 2.0L);
+        }
+        xa = xb;
+        fa = fb;
+    }
+    tau.push_back(1.0L);
+    return (int)tau.size() == M;
+}
+
+// Q[m][j] = integral over [0, tau_m] of the Lagrange polynomial l_j on tau_1..tau_M.
+void quadrature_matrix(const std::vector<long double>& tau, std::vector<long double>& Q) {
+    const int M = (int)tau.size();
+    Q.assign(M * M, 0.0L);
+    for (int j = 0; j < M; ++j) {
+        // monomial coefficients of l_j(s) = prod_{k != j} (s - tau_k) / (tau_j - tau_k)
+        std::vector<long double> c(1, 1.0L);
+        for (int k = 0; k < M; ++k) {
+            if (k == j) continue;
+            long double den = tau[j] - tau[k];
+            std::vector<long double> nc(c.size() + 1, 0.0L);
+            for (size_t p = 0; p < c.size(); ++p) {
+                nc[p + 1] += c[p] / den;
+                nc[p] -= c[p] * tau[k] / den;
+            }
+            c.swap(nc);
+        }
+        for (int m = 0; m < M; ++m) {
+            long double s = 0.0L, tp = tau[m];
+            for (size_t p = 0; p < c.size(); ++p) {
+                s += c[p] * tp / (long double)(p + 1);
+                tp *= tau[m];
+            }
+            Q[m * M + j] = s;
+        }
+    }
+}
+
+// LU trick: Q^T = L U (Doolittle, unit lower L, no pivoting); Qhat = U^T.
+bool lu_trick(int M, const std::vector<long double>& Q, std::vector<long double>& Qhat) {
+    std::vector<long double> A(M * M), L(M * M, 0.0L), U(M * M, 0.0L);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) A[i * M + j] = Q[j * M + i];
+    for (int i = 0; i < M; ++i) {
+        for (int j = i; j < M; ++j) {
+            long double s = A[i * M + j];
+            for (int k = 0; k < i; ++k) s -= L[i * M + k] * U[k * M + j];
+            U[i * M + j] = s;
+        }
+        if (std::fabs((double)U[i * M + i]) < 1e-14) return false;
+        L[i * M + i] = 1.0L;
+        for (int j = i + 1; j < M; ++j) {
+            long double s = A[j * M + i];
+            for (int k = 0; k < i; ++k) s -= L[j * M + k] * U[k * M + i];
+            L[j * M + i] = s / U[i * M + i];
+        }
+    }
+    Qhat.assign(M * M, 0.0L);
+    for (int m = 0; m < M; ++m)
+        for (int j = 0; j < M; ++j) Qhat[m * M + j] = U[j * M + m];
+    return true;
+}
+
+struct Collocation {
+    int M = 0;
+    std::vector<double> tau, Q, Qhat;  // row-major M x M
+};
+
+bool make_collocation(int M, Collocation& c) {
+    if (M < 1 || M > 8) return false;
+    std::vector<long double> tau, Q, Qh;
+    if (!radau_nodes(M, tau)) return false;
+    quadrature_matrix(tau, Q);
+    if (!lu_trick(M, Q, Qh)) return false;
+    c.M = M;
+    c.tau.assign(tau.begin(), tau.end());
+    c.Q.assign(Q.begin(), Q.end());
+    c.Qhat.assign(Qh.begin(), Qh.end());
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// Sparse matrix and P1 assembly (Sec. 2.2)
+// --------------------------------------------------------------------------
+
+struct Csr {
+    int n = 0;
+    std::vector<int> ptr, col;
+    std::vector<double> val;
+};
+
+struct System {
+    Csr K;                      // stiffness (includes the diagonal)
+    std::vector<double> mass;   // lumped mass (diagonal)
+};
+
+double det3(const double a[3][3]) {
+    return a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+           a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+           a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+}
+
+// K = sum_e sbar_e |e| G_e^T D_e G_e and m_i = sum_{e containing i} |e| / (d+1).
+// Duplicate contributions are summed in element order.
+bool assemble(int dim, int n_nodes, const double* xyz, int n_elems, const int* elems,
+              const double* sigma9, const double* elem_sigma9, const double* dof_scale,
+              System& sys) {
+    if (dim != 2 && dim != 3) return false;
+    const int nv = dim + 1;
+    std::vector<std::vector<std::pair<int, double>>> rows(n_nodes);
+    sys.mass.assign(n_nodes, 0.0);
+    for (int e = 0; e < n_elems; ++e) {
+        const int* vtx = elems + (size_t)e * nv;
+        for (int a = 0; a < nv; ++a)
+            if (vtx[a] < 0 || vtx[a] >= n_nodes) return false;
+        // Jacobian: column c = x_{c+1} - x_0
+        double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        for (int r = 0; r < dim; ++r)
+            for (int c = 0; c < dim; ++c)
+                J[r][c] = xyz[(size_t)vtx[c + 1] * dim + r] - xyz[(size_t)vtx[0] * dim + r];
+        double det = det3(J);
+        if (det == 0.0) return false;
+        double vol = std::fabs(det) / (dim == 2 ? 2.0 : 6.0);
+        // inverse by cofactors: inv[r][c] = cof[c][r] / det
+        double inv[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+                inv[r][c] = (J[r1][c1] * J[r2][c2] - J[r1][c2] * J[r2][c1]) / det;
+            }
+        // gradients of the barycentric coordinates: grad l_{c+1} = row c of inv
+        double g[4][3] = {{0}};
+        for (int c = 0; c < dim; ++c)
+            for (int r = 0; r < dim; ++r) g[c + 1][r] = inv[c][r];
+        for (int r = 0; r < dim; ++r) {
+            double s = 0.0;
+            for (int c = 1; c <= dim; ++c) s += g[c][r];
+            g[0][r] = -s;
+        }
+        const double* D = elem_sigma9 ? elem_sigma9 + (size_t)e * 9 : sigma9;
+        double sbar = 1.0;
+        if (dof_scale) {
+            double s = 0.0;
+            for (int a = 0; a < nv; ++a) s += dof_scale[vtx[a]];
+            sbar = s / nv;
+        }
+        for (int a = 0; a < nv; ++a) {
+            sys.mass[vtx[a]] += vol / nv;
+            for (int b = 0; b < nv; ++b) {
+                double s = 0.0;
+                for (int r = 0; r < dim; ++r)
+                    for (int c = 0; c < dim; ++c) s += g[a][r] * D[r * 3 + c] * g[b][c];
+                double kab = sbar * vol * s;
+                auto& row = rows[vtx[a]];
+                bool found = false;
+                for (auto& ent : row)
+                    if (ent.first == vtx[b]) { ent.second += kab; found = true; break; }
+                if (!found) row.push_back({vtx[b], kab});
+            }
+        }
+    }
+    sys.K.n = n_nodes;
+    sys.K.ptr.assign(n_nodes + 1, 0);
+    sys.K.col.clear();
+    sys.K.val.clear();
+    for (int i = 0; i < n_nodes; ++i) {
+        auto& row = rows[i];
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+                      return x.first < y.first;
+                  });
+        for (auto& ent : row) {
+            sys.K.col.push_back(ent.first);
+            sys.K.val.push_back(ent.second);
+        }
+        sys.K.ptr[i + 1] = (int)sys.K.col.size();
+    }
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// Aliev-Panfilov ionic model (Sec. 5.1.1)
+// --------------------------------------------------------------------------
+
+struct Ionic {
+    double ga, gs, a, eps, mu1, mu2, cw;
+};
+
+inline double ion_I(const Ionic& p, double v, double w) {
+    return p.ga * v * (v - p.a) * (v - 1.0) + v * w;
+}
+inline double ion_dIdv(const Ionic& p, double v, double w) {
+    return p.ga * (3.0 * v * v - 2.0 * (1.0 + p.a) * v + p.a) + w;
+}
+inline double ion_dIdw(const Ionic&, double v, double) { return v; }
+inline double ion_R(const Ionic& p, double v, double w) {
+    double E = p.eps + p.mu1 * w / (v + p.mu2);
+    double G = -w - p.gs * v * (v - p.a - 1.0);
+    return p.cw * E * G;
+}
+inline double ion_dRdv(const Ionic& p, double v, double w) {
+    double E = p.eps + p.mu1 * w / (v + p.mu2);
+    double G = -w - p.gs * v * (v - p.a - 1.0);
+    double dE = -p.mu1 * w / ((v + p.mu2) * (v + p.mu2));
+    double dG = -p.gs * (2.0 * v - p.a - 1.0);
+    return p.cw * (dE * G + E * dG);
+}
+inline double ion_dRdw(const Ionic& p, double v, double w) {
+    double E = p.eps + p.mu1 * w / (v + p.mu2);
+    double G = -w - p.gs * v * (v - p.a - 1.0);
+    double dE = p.mu1 / (v + p.mu2);
+    return p.cw * (dE * G - E);
+}
+
+// --------------------------------------------------------------------------
+// Status codes (same meaning as the library's, defined independently)
+// --------------------------------------------------------------------------
+enum { ORA_OK = 0, ORA_INVALID = -1, ORA_CG_NOCONV = -4, ORA_NONFINITE = -6, ORA_DOMAIN = -7 };
+
+// --------------------------------------------------------------------------
+// Jacobi PCG on A = diag(dA_off) + c K restricted to the active set (Sec. 4.2)
+// x, b are full-length; entries outside the active set are zero and stay zero.
+// dA holds the full diagonal of A for active rows.
+// --------------------------------------------------------------------------
+int pcg(const Csr& K, double c, const std::vector<double>& dA, const std::vector<int>& act,
+        const std::vector<double>& b, std::vector<double>& x,
+        double rtol, int maxit, int& iters, double& relres) {
+    const int n = K.n;
+    std::vector<double> r(n, 0.0), z(n, 0.0), p(n, 0.0), q(n, 0.0);
+    for (int i : act) {
+        x[i] = 0.0;
+        r[i] = b[i];
+        z[i] = r[i] / dA[i];
+        p[i] = z[i];
+    }
+    double rho = 0.0;
+    for (int i : act) rho += r[i] * z[i];
+    const double rho0 = rho;
+    iters = 0;
+    relres = 0.0;
+    if (rho0 == 0.0) return ORA_OK;
+    if (!std::isfinite(rho0)) return ORA_NONFINITE;
+    for (int it = 1; it <= maxit; ++it) {
+        // q = A p on the active rows; p is zero off the active set.
+        for (int i : act) {
+            double s = 0.0;
+            for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k) {
+                int j = K.col[k];
+                if (j == i) continue;
+                s += K.val[k] * p[j];
+            }
+            q[i] = dA[i] * p[i] + c * s;
+        }
+        double pq = 0.0;
+        for (int i : act) pq += p[i] * q[i];
+        double alpha = rho / pq;
+        for (int i : act) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            z[i] = r[i] / dA[i];
+        }
+        double rho_new = 0.0;
+        for (int i : act) rho_new += r[i] * z[i];
+        iters = it;
+        relres = std::sqrt(std::fabs(rho_new) / rho0);
+        if (!std::isfinite(rho_new)) return ORA_NONFINITE;
+        if (std::sqrt(rho_new) <= rtol * std::sqrt(rho0)) return ORA_OK;
+        double beta = rho_new / rho;
+        rho = rho_new;
+        for (int i : act) p[i] = z[i] + beta * p[i];
+    }
+    return ORA_CG_NOCONV;
+}
+
+double kdiag(const Csr& K, int i) {
+    for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k)
+        if (K.col[k] == i) return K.val[k];
+    return 0.0;
+}
+
+// (K x)_i over the full row (all neighbours, their current values)
+double krow(const Csr& K, int i, const double* x) {
+    double s = 0.0;
+    for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k) s += K.val[k] * x[K.col[k]];
+    return s;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C API (loaded with ctypes by the tests and the benchmark's CPU leg)
+// ==========================================================================
+
+extern "C" {
+
+typedef struct { double ga, gs, a, eps, mu1, mu2, cw; } ora_ionic;
+typedef struct { double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen; } ora_opts;
+#define ORA_MAX_SWEEPS 64
+#define ORA_MAX_M 8
+typedef struct {
+    int sweeps_run;
+    int n_active[ORA_MAX_SWEEPS];
+    int cg_iters[ORA_MAX_SWEEPS * ORA_MAX_M];
+    double cg_relres_max;
+    double min_margin;
+} ora_stats;
+
+int ora_collocation(int M, double* tau, double* Q, double* Qhat) {
+    Collocation c;
+    if (!make_collocation(M, c)) return ORA_INVALID;
+    for (int i = 0; i < M; ++i) tau[i] = c.tau[i];
+    for (int i = 0; i < M * M; ++i) {
+        Q[i] = c.Q[i];
+        Qhat[i] = c.Qhat[i];
+    }
+    return ORA_OK;
+}
+
+void ora_ionic_eval(const ora_ionic* ip, double v, double w, double* out6) {
+    Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
+    out6[0] = ion_I(p, v, w);
+    out6[1] = ion_dIdv(p, v, w);
+    out6[2] = ion_dIdw(p, v, w);
+    out6[3] = ion_R(p, v, w);
+    out6[4] = ion_dRdv(p, v, w);
+    out6[5] = ion_dRdw(p, v, w);
+}
+
+void* ora_create_fem(int dim, int n_nodes, const double* xyz, int n_elems, const int* elems,
+                     const double* sigma9, const double* elem_sigma9, const double* dof_scale) {
+    System* s = new System();
+    if (!assemble(dim, n_nodes, xyz, n_elems, elems, sigma9, elem_sigma9, dof_scale, *s)) {
+        delete s;
+        return nullptr;
+    }
+    return s;
+}
+
+void* ora_create_matrix(int n, const int* ptr, const int* col, const double* val,
+                        const double* mass) {
+    System* s = new System();
+    s->K.n = n;
+    s->K.ptr.assign(ptr, ptr + n + 1);
+    s->K.col.assign(col, col + ptr[n]);
+    s->K.val.assign(val, val + ptr[n]);
+    s->mass.assign(mass, mass + n);
+    return s;
+}
+
+int ora_n(void* h) { return ((System*)h)->K.n; }
+int ora_nnz(void* h) { return (int)((System*)h)->K.col.size(); }
+
+void ora_get_matrix(void* h, int* ptr, int* col, double* val, double* mass) {
+    System* s = (System*)h;
+    std::copy(s->K.ptr.begin(), s->K.ptr.end(), ptr);
+    std::copy(s->K.col.begin(), s->K.col.end(), col);
+    std::copy(s->K.val.begin(), s->K.val.end(), val);
+    std::copy(s->mass.begin(), s->mass.end(), mass);
+}
+
+void ora_destroy(void* h) { delete (System*)h; }
+
+// One SDC time step of length dt from (v, w) at the step start; on return
+// (v, w) hold the values at the last collocation node (tau_M = 1).
+// istim: per-node stimulus current for this step (NULL = none).
+// active_log (optional): concatenated ascending active lists of every sweep.
+// Vn, Wn (optional): all collocation-node values after the last sweep, [M][N].
+int ora_step(void* h, const ora_ionic* ip, int M, const double* istim, double* v, double* w,
+             double dt, int sweeps, double tol, const ora_opts* o, ora_stats* st,
+             int* active_log, double* Vn, double* Wn) {
+    System& S = *(System*)h;
+    const Csr& K = S.K;
+    const int N = K.n;
+    Collocation col;
+    if (!make_collocation(M, col) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 || dt <= 0)
+        return ORA_INVALID;
+    const std::vector<double>& Q = col.Q;
+    const std::vector<double>& Qh = col.Qhat;
+    Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
+    const double tol_drop = o->alpha * tol;
+
+    std::vector<double> v0(v, v + N), w0(w, w + N);
+    // collocation iterates V[m][i], W[m][i], spread predictor
+    std::vector<double> V((size_t)M * N), W((size_t)M * N);
+    for (int m = 0; m < M; ++m)
+        for (int i = 0; i < N; ++i) {
+            V[(size_t)m * N + i] = v0[i];
+            W[(size_t)m * N + i] = w0[i];
+        }
+    std::vector<int> act(N);
+    for (int i = 0; i < N; ++i) act[i] = i;
+    std::vector<double> f((size_t)M * N), J((size_t)M * N), r((size_t)M * N),
+        delta((size_t)M * N), b(N), dA(N), Kd(N);
+    for (int i = 0; i < N; ++i) Kd[i] = kdiag(K, i);
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->min_margin = INFINITY;
+    }
+    size_t log_pos = 0;
+    int status = ORA_OK;
+
+    for (int k = 0; k < sweeps; ++k) {
+        if (st) {
+            st->n_active[k] = (int)act.size();
+            st->sweeps_run = k + 1;
+        }
+        if (active_log) {
+            std::copy(act.begin(), act.end(), active_log + log_pos);
+            log_pos += act.size();
+        }
+        if (act.empty()) continue;
+        // residual of the collocation system at the current iterate (active rows only)
+        for (int m = 0; m < M; ++m)
+            for (int i : act) {
+                double vm = V[(size_t)m * N + i], wm = W[(size_t)m * N + i];
+                double s = istim ? istim[i] : 0.0;
+                f[(size_t)m * N + i] = -krow(K, i, &V[(size_t)m * N]) - S.mass[i] * (ion_I(p, vm, wm) - s);
+                J[(size_t)m * N + i] = o->reaction_implicit ? ion_dIdv(p, vm, wm) : 0.0;
+            }
+        for (int m = 0; m < M; ++m)
+            for (int i : act) {
+                double q = 0.0;
+                for (int j = 0; j < M; ++j) q += Q[m * M + j] * f[(size_t)j * N + i];
+                r[(size_t)m * N + i] = S.mass[i] * v0[i] + dt * q - S.mass[i] * V[(size_t)m * N + i];
+            }
+        std::fill(delta.begin(), delta.end(), 0.0);
+        // sequential node solves (lower-triangular Qhat)
+        for (int m = 0; m < M; ++m) {
+            for (int i : act) {
+                double corr = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    const double* dj = &delta[(size_t)j * N];
+                    corr += Qh[m * M + j] * (krow(K, i, dj) + S.mass[i] * J[(size_t)j * N + i] * dj[i]);
+                }
+                b[i] = r[(size_t)m * N + i] - dt * corr;
+            }
+            const double c = dt * Qh[m * M + m];
+            for (int i : act) {
+                dA[i] = S.mass[i] * (1.0 + c * J[(size_t)m * N + i]) + c * Kd[i];
+                if (!(dA[i] > 0.0)) return ORA_INVALID;
+            }
+            std::vector<double> x(N, 0.0);
+            int iters = 0;
+            double relres = 0.0;
+            int rc = pcg(K, c, dA, act, b, x, o->cg_rtol, o->cg_maxit, iters, relres);
+            if (st) {
+                st->cg_iters[k * ORA_MAX_M + m] = iters;
+                st->cg_relres_max = std::max(st->cg_relres_max, relres);
+            }
+            if (rc != ORA_OK) return rc;
+            for (int i : act) delta[(size_t)m * N + i] = x[i];
+        }
+        // v update on the active rows; inactive rows are held fixed
+        for (int m = 0; m < M; ++m)
+            for (int i : act) V[(size_t)m * N + i] += delta[(size_t)m * N + i];
+        // pointwise w sweep with the updated v and the old w
+        if (!o->w_frozen) {
+            for (int i : act) {
+                double g[ORA_MAX_M], d[ORA_MAX_M], s[ORA_MAX_M], eps[ORA_MAX_M];
+                for (int m = 0; m < M; ++m) {
+                    double vm = V[(size_t)m * N + i], wm = W[(size_t)m * N + i];
+                    if (vm + p.mu2 <= 0.0) return ORA_DOMAIN;
+                    g[m] = ion_R(p, vm, wm);
+                    d[m] = ion_dRdw(p, vm, wm);
+                }
+                for (int m = 0; m < M; ++m) {
+                    double q = 0.0;
+                    for (int j = 0; j < M; ++j) q += Q[m * M + j] * g[j];
+                    s[m] = w0[i] + dt * q - W[(size_t)m * N + i];
+                }
+                for (int m = 0; m < M; ++m) {
+                    double acc = s[m];
+                    for (int j = 0; j < m; ++j) acc += dt * Qh[m * M + j] * d[j] * eps[j];
+                    double den = 1.0 - dt * Qh[m * M + m] * d[m];
+                    if (!(den > 0.0)) return ORA_DOMAIN;
+                    eps[m] = acc / den;
+                }
+                for (int m = 0; m < M; ++m) W[(size_t)m * N + i] += eps[m];
+            }
+        }
+        // nested selection: keep i in I_k with max_m |dv_{m,i}| >= TOL_drop
+        std::vector<int> next;
+        for (int i : act) {
+            double amax = 0.0;
+            for (int m = 0; m < M; ++m) amax = std::max(amax, std::fabs(delta[(size_t)m * N + i]));
+            if (!std::isfinite(amax)) return ORA_NONFINITE;
+            if (st && tol_drop > 0.0) st->min_margin = std::min(st->min_margin, std::fabs(amax - tol_drop));
+            if (amax >= tol_drop) next.push_back(i);
+        }
+        act.swap(next);
+    }
+    for (int i = 0; i < N; ++i) {
+        v[i] = V[(size_t)(M - 1) * N + i];
+        w[i] = W[(size_t)(M - 1) * N + i];
+    }
+    if (Vn) std::copy(V.begin(), V.end(), Vn);
+    if (Wn) std::copy(W.begin(), W.end(), Wn);
+    return status;
+}
+
+// Dense Newton solve of the full collocation system (Sec. 3.1):
+//   m (v_m - v_0) = dt sum_j Q_mj f(v_j, w_j),   w_m - w_0 = dt sum_j Q_mj R(v_j, w_j)
+// for tiny systems only (2 N M unknowns, dense LU with partial pivoting).
+int ora_collocation_solve(void* h, const ora_ionic* ip, int M, const double* istim, double* v,
+                          double* w, double dt, double* Vn, double* Wn, int* newton_iters) {
+    System& S = *(System*)h;
+    const Csr& K = S.K;
+    const int N = K.n;
+    const int U = 2 * N * M;
+    if (U > 4000) return ORA_INVALID;
+    Collocation col;
+    if (!make_collocation(M, col)) return ORA_INVALID;
+    const std::vector<double>& Q = col.Q;
+    Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
+    std::vector<double> v0(v, v + N), w0(w, w + N);
+    std::vector<double> Z(U);
+    auto iv = [&](int m, int i) { return m * N + i; };
+    auto iw = [&](int m, int i) { return N * M + m * N + i; };
+    for (int m = 0; m < M; ++m)
+        for (int i = 0; i < N; ++i) {
+            Z[iv(m, i)] = v0[i];
+            Z[iw(m, i)] = w0[i];
+        }
+    std::vector<double> G(U), A((size_t)U * U), dz(U);
+    std::vector<int> piv(U);
+    int it;
+    for (it = 0; it < 50; ++it) {
+        // residual
+        for (int m = 0; m < M; ++m)
+            for (int i = 0; i < N; ++i) {
+                double qv = 0.0, qw = 0.0;
+                for (int j = 0; j < M; ++j) {
+                    double vj = Z[iv(j, i)], wj = Z[iw(j, i)];
+                    double Kv = 0.0;
+                    for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k) Kv += K.val[k] * Z[iv(j, K.col[k])];
+                    double fj = -Kv - S.mass[i] * (ion_I(p, vj, wj) - (istim ? istim[i] : 0.0));
+                    qv += Q[m * M + j] * fj;
+                    qw += Q[m * M + j] * ion_R(p, vj, wj);
+                }
+                G[iv(m, i)] = S.mass[i] * (Z[iv(m, i)] - v0[i]) - dt * qv;
+                G[iw(m, i)] = (Z[iw(m, i)] - w0[i]) - dt * qw;
+            }
+        // Jacobian
+        std::fill(A.begin(), A.end(), 0.0);
+        for (int m = 0; m < M; ++m)
+            for (int i = 0; i < N; ++i) {
+                size_t rv = (size_t)iv(m, i) * U, rw = (size_t)iw(m, i) * U;
+                A[rv + iv(m, i)] += S.mass[i];
+                A[rw + iw(m, i)] += 1.0;
+                for (int j = 0; j < M; ++j) {
+                    double vj = Z[iv(j, i)], wj = Z[iw(j, i)];
+                    double q = dt * Q[m * M + j];
+                    for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k) A[rv + iv(j, K.col[k])] += q * K.val[k];
+                    A[rv + iv(j, i)] += q * S.mass[i] * ion_dIdv(p, vj, wj);
+                    A[rv + iw(j, i)] += q * S.mass[i] * ion_dIdw(p, vj, wj);
+                    A[rw + iv(j, i)] -= q * ion_dRdv(p, vj, wj);
+                    A[rw + iw(j, i)] -= q * ion_dRdw(p, vj, wj);
+                }
+            }
+        // LU with partial pivoting, solve A dz = -G
+        for (int c = 0; c < U; ++c) {
+            int best = c;
+            for (int r2 = c + 1; r2 < U; ++r2)
+                if (std::fabs(A[(size_t)r2 * U + c]) > std::fabs(A[(size_t)best * U + c])) best = r2;
+            piv[c] = best;
+            if (best != c) {
+                for (int k = 0; k < U; ++k) std::swap(A[(size_t)c * U + k], A[(size_t)best * U + k]);
+            }
+            double d = A[(size_t)c * U + c];
+            if (d == 0.0) return ORA_INVALID;
+            for (int r2 = c + 1; r2 < U; ++r2) {
+                double l = A[(size_t)r2 * U + c] / d;
+                A[(size_t)r2 * U + c] = l;
+                if (l != 0.0)
+                    for (int k = c + 1; k < U; ++k) A[(size_t)r2 * U + k] -= l * A[(size_t)c * U + k];
+            }
+        }
+        for (int i = 0; i < U; ++i) dz[i] = -G[i];
+        for (int c = 0; c < U; ++c) {
+            if (piv[c] != c) std::swap(dz[c], dz[piv[c]]);
+            for (int r2 = c + 1; r2 < U; ++r2) dz[r2] -= A[(size_t)r2 * U + c] * dz[c];
+        }
+        for (int c = U - 1; c >= 0; --c) {
+            double s = dz[c];
+            for (int k = c + 1; k < U; ++k) s -= A[(size_t)c * U + k] * dz[k];
+            dz[c] = s / A[(size_t)c * U + c];
+        }
+        double nrm = 0.0, zn = 1.0;
+        for (int i = 0; i < U; ++i) {
+            Z[i] += dz[i];
+            nrm = std::max(nrm, std::fabs(dz[i]));
+            zn = std::max(zn, std::fabs(Z[i]));
+        }
+        if (nrm <= 1e-15 * zn) { ++it; break; }
+    }
+    if (newton_iters) *newton_iters = it;
+    for (int i = 0; i < N; ++i) {
+        v[i] = Z[iv(M - 1, i)];
+        w[i] = Z[iw(M - 1, i)];
+    }
+    if (Vn)
+        for (int m = 0; m < M; ++m)
+            for (int i = 0; i < N; ++i) Vn[(size_t)m * N + i] = Z[iv(m, i)];
+    if (Wn)
+        for (int m = 0; m < M; ++m)
+            for (int i = 0; i < N; ++i) Wn[(size_t)m * N + i] = Z[iw(m, i)];
+    return ORA_OK;
+}
+
+}  // extern "C"
