@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of adaptive SDC on the 3D monodomain slab (201x71x31 nodes,
+442,401 dofs, M = 4 Radau nodes, dt = 0.05 ms, 5 sweeps, TOL = 1e-5, 1 ms
+corner stimulus) on one GB300, through the library's C ABI.
+
+One benchmark step = one SDC time step (all sweeps, all node solves, the
+selection and extraction of the nested active sets).  The K timed steps are the
+first K steps of the trajectory from t = 0 (K = 1000 covers the workload's
+50 ms).  Between timed steps L2 is flushed by writing a 256 MiB buffer; each
+step is timed with CUDA events on the library's stream.
+
+Printed as one JSON line: steps/s (value), active-dof sweeps/s, the plain-SDC
+run at the same dt with its speedup and both errors against a 12-sweep
+reference, the live roofline of the dominant kernel (restricted PCG), the
+end-to-end rate through the host-buffer entry point, the CPU oracle timed on a
+bounded sample of the same trajectory, and the SM clocks seen meanwhile.
+
+--impl reference times the CPU oracle alone (single thread) on the same
+workload and prints the same line with "impl": "reference".
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "SDC steps/s, 3D slab 201x71x31 (adaptive TOL=1e-5)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5"], default="w1")
+    ap.add_argument("--ref-sweeps", type=int, default=12)
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/reference/e2e runs")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    return {"w1": W.w1_slab, "w1l": W.w1l_slab, "w0": W.w0_square, "w5": W.w5_tissue}[name]()
+
+
+def config_of(wl, K):
+    return {"workload": wl.name, "n_dofs": wl.n, "M": wl.M, "dt_ms": wl.dt, "sweeps": wl.sweeps,
+            "TOL": wl.tol, "alpha": wl.alpha, "cg_rtol": wl.cg_rtol,
+            "simulated_ms": round(K * wl.dt, 6),
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_id):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", device_id, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        sm, mx, reasons = [], [], set()
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(self.NAMES, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.tmp.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_steps(wl, states, budget_s):
+    """Time single oracle steps from the given (step index, v, w) states until the
+    budget is used.  Returns (steps done, seconds, per-step results)."""
+    import oracle
+    S = oracle.System.from_mesh(wl.mesh, wl.sigma, wl.dof_scale)
+    done, secs, outs = 0, 0.0, []
+    for (n, v, w) in states:
+        t0 = time.perf_counter()
+        r = S.step(wl.ionic, wl.M, v, w, wl.dt, wl.sweeps, wl.tol, alpha=wl.alpha,
+                   cg_rtol=wl.cg_rtol, istim=wl.stim_vector(n * wl.dt))
+        secs += time.perf_counter() - t0
+        done += 1
+        outs.append((n, r))
+        if r["status"] != 0:
+            raise RuntimeError("oracle step failed with status %d" % r["status"])
+        if secs >= budget_s:
+            break
+    return done, secs, outs
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    wl = make_workload(args.workload)
+    import oracle
+    S = oracle.System.from_mesh(wl.mesh, wl.sigma, wl.dof_scale)
+    v, w = wl.v0.copy(), wl.w0.copy()
+    # warm-up: W oracle steps on a copy of the initial state (untimed)
+    wv, ww = v.copy(), w.copy()
+    for n in range(min(args.warmup, 1)):
+        r = S.step(wl.ionic, wl.M, wv, ww, wl.dt, wl.sweeps, wl.tol, alpha=wl.alpha,
+                   cg_rtol=wl.cg_rtol, istim=wl.stim_vector(n * wl.dt))
+    budget = max(10.0, min(120.0, args.cpu_budget * 3))
+    done, secs, nact = 0, 0.0, 0
+    while done < args.steps and secs < budget:
+        t0 = time.perf_counter()
+        r = S.step(wl.ionic, wl.M, v, w, wl.dt, wl.sweeps, wl.tol, alpha=wl.alpha,
+                   cg_rtol=wl.cg_rtol, istim=wl.stim_vector(done * wl.dt))
+        secs += time.perf_counter() - t0
+        if r["status"] != 0:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle step failed: %d"
+                              % r["status"]}))
+            return 0
+        v, w = r["v"], r["w"]
+        nact += sum(r["stats"].n_active[:wl.sweeps])
+        done += 1
+    value = done / secs
+    sample = ("first %d of the %d requested steps from t = 0 (single-threaded FP64 oracle, "
+              "time budget %.0f s)" % (done, args.steps, budget))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / done, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, done),
+            "active_dof_sweeps_per_s": nact / secs,
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def pcg_bytes(st, M, sweeps):
+    """Algorithmic bytes of the restricted PCG solves of one step: per iteration
+    and active row 12 zbar + 104 B (zbar = stored entries per row incl. the
+    diagonal; FP64 values, int32 indices, fused vector traffic)."""
+    b = 0.0
+    for k in range(st.sweeps_run):
+        n = st.n_active[k]
+        if n == 0:
+            continue
+        nnz = st.nnz_active[k] + n
+        per_iter = 12.0 * nnz + 104.0 * n
+        for m in range(M):
+            b += st.cg_iters[k][m] * per_iter
+    return b
+
+
+def run_gb300(args):
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Context, default_options
+
+    wl = make_workload(args.workload)
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream(dev)
+    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha)
+    ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
+    v0 = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
+    w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def trajectory(tol, sweeps, steps, timed):
+        v, w = v0.clone(), w0.clone()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)] if timed else None
+        agg = {"active_dof_sweeps": 0, "pcg_ms": 0.0, "pcg_launches": 0, "pcg_bytes": 0.0,
+               "launches": 0, "phase_ms": np.zeros(5)}
+        for n in range(steps):
+            if timed:
+                flush.fill_(n)
+                ev[n][0].record(stream)
+            st = ctx.step(v, w, n * wl.dt, wl.dt, sweeps, tol)
+            if timed:
+                ev[n][1].record(stream)
+            agg["active_dof_sweeps"] += sum(st.n_active[:st.sweeps_run])
+            agg["pcg_ms"] += st.phase_ms[1]
+            agg["pcg_launches"] += st.phase_launches[1]
+            agg["pcg_bytes"] += pcg_bytes(st, wl.M, sweeps)
+            agg["launches"] += st.kernel_launches
+            agg["phase_ms"] += np.array(st.phase_ms[:5])
+        torch.cuda.synchronize(dev)
+        total_ms = sum(a.elapsed_time(b) for a, b in ev) if timed else None
+        return v, w, total_ms, agg
+
+    # warm-up (untimed, discarded)
+    trajectory(wl.tol, wl.sweeps, Wm, timed=False)
+    props = torch.cuda.get_device_properties(dev)
+    dev_id = str(getattr(props, "uuid", "")) or str(local)
+    if dev_id and not dev_id.startswith("GPU-") and len(dev_id) > 8:
+        dev_id = "GPU-" + dev_id
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dev_id)
+    va, wa, ms_adapt, agg_a = trajectory(wl.tol, wl.sweeps, K, timed=True)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms_adapt = max_over_ranks(ms_adapt, world)
+    value = world * K / (ms_adapt / 1e3)
+
+    extras = {}
+    if not args.no_extras:
+        vp, wp, ms_plain, agg_p = trajectory(0.0, wl.sweeps, K, timed=True)
+        vr, _, _, _ = trajectory(0.0, args.ref_sweeps, K, timed=False)
+        ref = vr.cpu().numpy()
+        err_a = float(np.abs(va.cpu().numpy() - ref).max())
+        err_p = float(np.abs(vp.cpu().numpy() - ref).max())
+        extras = {"plain": {"value": K / (ms_plain / 1e3), "unit": "steps/s",
+                            "ms_per_step": ms_plain / K,
+                            "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_plain / 1e3)},
+                  "speedup_vs_plain": ms_plain / ms_adapt,
+                  "err_vs_ref": {"adaptive": err_a, "plain": err_p,
+                                 "reference": "plain SDC, %d sweeps, same dt" % args.ref_sweeps,
+                                 "norm": "max |v(t_K) - v_ref(t_K)|"}}
+
+    # end to end through the host-buffer entry point (pinned host arrays)
+    samples = sorted({s for s in (0, K // 5, 2 * K // 5, 3 * K // 5, 4 * K // 5) if s + 1 < K})
+    snaps = {}
+    hv_t = torch.tensor(wl.v0, dtype=torch.float64).pin_memory()
+    hw_t = torch.tensor(wl.w0, dtype=torch.float64).pin_memory()
+    hv, hw = hv_t.numpy(), hw_t.numpy()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    e2e_s = 0.0
+    for n in range(K):
+        if n in samples or n - 1 in samples:
+            snaps[n] = (hv.copy(), hw.copy())      # outside the timed call
+        t0 = time.perf_counter()
+        ctx.step_host(hv, hw, n * wl.dt, wl.dt, wl.sweeps, wl.tol)
+        e2e_s += time.perf_counter() - t0
+    e2e = {"value": world * K / max_over_ranks(e2e_s, world), "unit": "steps/s",
+           "h2d_bytes_per_step": 2 * 8 * wl.n, "d2h_bytes_per_step": 2 * 8 * wl.n,
+           "api": "sdc_step_host (pinned host v, w)"}
+
+    # roofline of the dominant kernel: restricted PCG, live CUDA-event times
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    pcg_s = agg_a["pcg_ms"] / 1e3
+    launches = max(1, agg_a["pcg_launches"])
+    achieved = agg_a["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
+    roofline = {"kernel": "k_pcg (restricted Jacobi-PCG, one cooperative launch per node solve)",
+                "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks
+                else "fallback 6.8 TB/s",
+                "traffic": None,
+                "algorithmic_bytes_per_launch": agg_a["pcg_bytes"] / launches,
+                "avg_launch_ms": agg_a["pcg_ms"] / launches,
+                "launches": agg_a["pcg_launches"],
+                "share_of_step": agg_a["pcg_ms"] / ms_adapt}
+
+    cpu = None
+    parity = None
+    if rank == 0 and not args.no_cpu_baseline:
+        states = [(s, snaps[s][0], snaps[s][1]) for s in samples if s in snaps]
+        done, secs, outs = oracle_steps(wl, states, args.cpu_budget)
+        cpu = {"value": done / secs, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": "%d single steps of the same trajectory, started from the GPU states at "
+                         "steps %s (single-threaded FP64 oracle)"
+                         % (done, [s for s, _ in outs])}
+        diffs = []
+        for s, r in outs:
+            if s + 1 in snaps:
+                gv = snaps[s + 1][0]
+                diffs.append(float(np.abs(gv - r["v"]).max() / max(1.0, np.abs(r["v"]).max())))
+        parity = {"max_rel_diff_v_vs_oracle": max(diffs) if diffs else None, "steps": len(diffs)}
+
+    phase = dict(zip(("residual", "pcg", "update", "select", "extract"),
+                     (agg_a["phase_ms"] / K).round(4).tolist()))
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": ms_adapt / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, K),
+            "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_adapt / 1e3),
+            **extras,
+            "phase_ms_per_step": phase,
+            "roofline": roofline, "cpu_baseline": cpu, "oracle_parity_on_sample": parity,
+            "e2e": e2e, "clocks": clk, "gpu_launches": agg_a["launches"]}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * sdc.h - C ABI of the GB300 (sm_103a) adaptive spectral deferred correction
+ * library for P1 finite-element monodomain reaction-diffusion systems with
+ * Aliev-Panfilov kinetics.
+ *
+ * The problem (Sec. 2.2, eq. abstract monodomain; Sec. 3, eq. abstract ODE):
+ *     m .* v' = -K v - m .* (I_ion(v, w) - I_stim),     w' = R(v, w)
+ * with K the P1 stiffness matrix of div(sigma grad v) under homogeneous
+ * Neumann conditions and m the lumped mass.  One time step is a Radau-IIA
+ * collocation step (Sec. 3.1) approximated by LU-trick SDC sweeps with the
+ * v-then-w operator splitting of eq. final-sdc (Sec. 3.2).  After each sweep
+ * only the dofs whose voltage correction reaches TOL_drop = alpha * TOL stay
+ * active; later sweeps solve the restricted systems on those nested index sets
+ * with Jacobi-preconditioned CG, holding the dropped dofs fixed (Sec. 4.2).
+ *
+ * Conventions for every call:
+ *   - Host arrays passed to sdc_create / sdc_set_stimulus are copied; the caller
+ *     keeps ownership and may free them on return.
+ *   - Device arrays (prefix d_) are caller-owned FP64 device memory on the
+ *     context's device; the library never frees them.
+ *   - All device work is issued on the stream given to sdc_create.  Calls that
+ *     read results back (sdc_step, sdc_step_host) synchronise that stream before
+ *     they return.
+ *   - Every call returns an sdc_status.  On failure no output is guaranteed to
+ *     be meaningful and sdc_last_error(ctx) gives a one-line reason.  Invalid
+ *     arguments are rejected with SDC_E_INVALID before any device work starts.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef SDC_GB300_H
+#define SDC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SDC_MAX_M 8        /* collocation nodes per step */
+#define SDC_MAX_SWEEPS 64  /* SDC sweeps per step */
+
+/* Kernel phases of a step, as reported in sdc_stats. */
+#define SDC_PHASE_RESIDUAL 0  /* spread, collocation residual + ionic model, final copy */
+#define SDC_PHASE_PCG 1       /* restricted Jacobi-PCG solves (one launch per node)    */
+#define SDC_PHASE_UPDATE 2    /* v update, w sweep, selection flags                    */
+#define SDC_PHASE_SELECT 3    /* stable compaction of the next active set              */
+#define SDC_PHASE_EXTRACT 4   /* restricted submatrix extraction                       */
+#define SDC_N_PHASES 5
+
+typedef struct sdc_ctx sdc_ctx;
+
+typedef enum {
+    SDC_OK = 0,
+    SDC_E_INVALID = -1,   /* bad argument; nothing was launched */
+    SDC_E_CUDA = -2,      /* a CUDA runtime call failed */
+    SDC_E_NOMEM = -3,     /* device allocation failed */
+    SDC_E_CG_NOCONV = -4, /* CG reached cg_maxit without meeting cg_rtol */
+    SDC_E_TIMEOUT = -5,   /* a device-side wait exceeded its spin budget */
+    SDC_E_NONFINITE = -6, /* NaN or Inf in a residual or correction */
+    SDC_E_DOMAIN = -7     /* gating rate pole v + mu2 <= 0, or a non-positive pivot */
+} sdc_status;
+
+/* P1 simplex mesh (Sec. 2.2).  Host arrays, copied at sdc_create.
+ *   dim        2 (triangles) or 3 (tetrahedra)
+ *   xyz        n_nodes * dim coordinates, node-major
+ *   elem_ptr   n_elems + 1 offsets into elem_node; every element must list
+ *              exactly dim + 1 distinct nodes
+ *   sigma      global conductivity tensor, 9 doubles row-major (the leading
+ *              dim x dim block is used); ignored where elem_sigma is given
+ *   elem_sigma NULL or n_elems * 9 per-element tensors
+ *   dof_scale  NULL or n_nodes per-node conductivity scale s; element e uses
+ *              the mean of s over its vertices                                 */
+typedef struct {
+    int dim;
+    int n_nodes;
+    const double* xyz;
+    int n_elems;
+    const int* elem_ptr;
+    const int* elem_node;
+    const double* sigma;
+    const double* elem_sigma;
+    const double* dof_scale;
+} sdc_mesh;
+
+/* Aliev-Panfilov model (Sec. 5.1.1):
+ *   I_ion(v, w) = ga v (v - a)(v - 1) + v w
+ *   R(v, w)     = cw (eps + mu1 w / (v + mu2)) (-w - gs v (v - a - 1))
+ * The paper's values use cw = 1/4; the standard 1996 form uses cw = 1.         */
+typedef struct {
+    double ga, gs, a, eps, mu1, mu2, cw;
+} sdc_ionic;
+
+typedef struct {
+    double alpha;          /* TOL_drop = alpha * TOL (Sec. 4.2); default 0.1                  */
+    double cg_rtol;        /* stop when sqrt(r'z) <= cg_rtol sqrt(r0'z0); default 1e-10        */
+    int cg_maxit;          /* default 2000                                                    */
+    int reaction_implicit; /* 1: lumped dI/dv on the diagonal of every node system (Sec. 3.2) */
+    int w_frozen;          /* 1: w is held at its initial value (no gating dynamics)          */
+    double drop_rel;       /* assembly: off-diagonal K_ij with |K_ij| <= drop_rel sqrt(K_ii K_jj)
+                              are rounding residue of cancelling element terms and are not
+                              stored; default 1e-12, 0 keeps every structural entry           */
+    long long spin_budget; /* SM clock cycles a device-side barrier may wait; default 4e9     */
+    int cg_block_size;     /* threads per CG block (64..1024, multiple of 32); default 256    */
+    int cg_max_blocks;     /* 0: one cooperative grid filling every SM                        */
+    int profile;           /* 1: bracket every kernel launch with CUDA events on the context's
+                              stream and report device time per phase in sdc_stats; default 0 */
+    int inject_fault;      /* testing hook, default 0.  1: in every CG launch the last block
+                              leaves without arriving at the first grid barrier, so the other
+                              blocks' bounded waits run out and the step returns SDC_E_TIMEOUT */
+} sdc_options;
+
+/* Per-step statistics (valid when sdc_step returns).                              */
+typedef struct {
+    int sweeps_run;
+    int n_active[SDC_MAX_SWEEPS];          /* |I_k| for k = 0 .. sweeps_run-1              */
+    long long nnz_active[SDC_MAX_SWEEPS];  /* stored off-diagonal entries of K[I_k, I_k]   */
+    int cg_iters[SDC_MAX_SWEEPS][SDC_MAX_M];
+    double cg_relres_max;                  /* max final sqrt(r'z / r0'z0) over all solves */
+    double min_margin;                     /* min over selections of |max_m|dv| - TOL_drop| */
+    int kernel_launches;                   /* kernels this step launched                    */
+    /* per phase SDC_PHASE_*: launches, and device ms when the profile option is set */
+    int phase_launches[SDC_N_PHASES];
+    double phase_ms[SDC_N_PHASES];
+} sdc_stats;
+
+/* Fill defaults (values above). */
+void sdc_default_options(sdc_options* opt);
+/* Standard Aliev-Panfilov parameters: ga = gs = 8, a = 0.15, eps = 0.002,
+ * mu1 = 0.2, mu2 = 0.3, cw = 1. */
+void sdc_default_ionic(sdc_ionic* ion);
+
+/* Radau-IIA collocation data (Sec. 3.1): right Radau nodes tau[M] on [0, 1]
+ * with tau[M-1] = 1; cumulative quadrature Q[m*M + j] = integral over
+ * [0, tau_m] of the Lagrange polynomial l_j on tau_1..tau_M; LU-trick
+ * preconditioner Qhat = U^T where Q^T = L U (Doolittle), lower triangular
+ * (Sec. 3.1, after eq. SDC).  Host-only; 1 <= M <= 8. */
+sdc_status sdc_radau(int M, double* tau, double* Q, double* Qhat);
+
+/* Create a context: copies the mesh, assembles K and m on the device
+ * (Sec. 2.2), and allocates every device buffer a step needs for up to
+ * n_nodes active dofs.  stream: a cudaStream_t (NULL = legacy default stream)
+ * of the current device.  Returns SDC_E_INVALID for a malformed mesh or
+ * M outside [1, 8]; SDC_E_NOMEM when device memory is short.
+ * On failure *out is NULL. */
+sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
+                      const sdc_options* opt, void* stream);
+
+/* Stimulus current I_stim = amp on the listed nodes for every step whose start
+ * time t satisfies t_on <= t < t_off (constant over the step).  nodes: host,
+ * n entries in [0, n_nodes).  Replaces any previous stimulus; n = 0 clears. */
+sdc_status sdc_set_stimulus(sdc_ctx* ctx, const int* nodes, int n, double amp, double t_on,
+                            double t_off);
+
+/* One SDC time step [t, t + dt] (Sec. 3.2 eq. final-sdc with the nested
+ * index sets of Sec. 4.2).
+ *   d_v, d_w  device, n_nodes doubles each: the state at t on entry, the state
+ *             at t + dt (last Radau node) on return; updated in place
+ *   sweeps    number of sweeps K (1 .. 64); the first sweep uses every dof
+ *   TOL       SDC tolerance >= 0; TOL_drop = alpha * TOL, TOL = 0 is plain SDC
+ *   stats     NULL or filled on return
+ * Synchronises the context's stream.  Errors: SDC_E_CG_NOCONV, SDC_E_TIMEOUT,
+ * SDC_E_NONFINITE, SDC_E_DOMAIN (the state is then partially updated). */
+sdc_status sdc_step(sdc_ctx* ctx, double* d_v, double* d_w, double t, double dt, int sweeps,
+                    double TOL, sdc_stats* stats);
+
+/* sdc_step on HOST arrays h_v, h_w (n_nodes doubles each, preferably pinned):
+ * copies them to context-owned device buffers, steps, and copies the result
+ * back before returning. */
+sdc_status sdc_step_host(sdc_ctx* ctx, double* h_v, double* h_w, double t, double dt, int sweeps,
+                         double TOL, sdc_stats* stats);
+
+/* Collocation-node values of the last step, d_V and d_W device arrays of
+ * M * n_nodes doubles laid out [m][node]. */
+sdc_status sdc_get_nodes(const sdc_ctx* ctx, double* d_V, double* d_W);
+
+/* Active index list I_k of sweep k of the last step, ascending, copied to the
+ * host array h_idx (capacity n_nodes).  *n receives |I_k|. */
+sdc_status sdc_get_active(const sdc_ctx* ctx, int sweep, int* h_idx, int* n);
+
+/* Sizes of the assembled system: node count and stored entries of K
+ * (diagonal included, after the drop_rel filter). */
+sdc_status sdc_get_info(const sdc_ctx* ctx, int* n_nodes, long long* nnz, int* max_row_offdiag);
+
+/* The assembled K as host CSR (rows ascending, columns ascending, diagonal
+ * included) and the lumped mass m; arrays sized by sdc_get_info. */
+sdc_status sdc_get_matrix(const sdc_ctx* ctx, int* row_ptr, int* col, double* val, double* mass);
+
+/* One-line description of the last failure on ctx (never NULL). */
+const char* sdc_last_error(const sdc_ctx* ctx);
+const char* sdc_status_string(int status);
+
+/* Free every device and host resource of ctx (NULL is ignored). */
+void sdc_destroy(sdc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDC_GB300_H */

@@ -1,0 +1,230 @@
+"""ctypes binding of libsdc_gb300.so: the C ABI of include/sdc.h, same names.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  There is no fallback: if the shared library is missing, every
+call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsdc_gb300.so")
+
+SDC_MAX_M = 8
+SDC_MAX_SWEEPS = 64
+SDC_N_PHASES = 5
+PHASES = ("residual", "pcg", "update", "select", "extract")
+SDC_OK, SDC_E_INVALID, SDC_E_CUDA, SDC_E_NOMEM = 0, -1, -2, -3
+SDC_E_CG_NOCONV, SDC_E_TIMEOUT, SDC_E_NONFINITE, SDC_E_DOMAIN = -4, -5, -6, -7
+
+
+class sdc_mesh(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int), ("xyz", C.POINTER(C.c_double)),
+                ("n_elems", C.c_int), ("elem_ptr", C.POINTER(C.c_int)),
+                ("elem_node", C.POINTER(C.c_int)), ("sigma", C.POINTER(C.c_double)),
+                ("elem_sigma", C.POINTER(C.c_double)), ("dof_scale", C.POINTER(C.c_double))]
+
+
+class sdc_ionic(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("ga", "gs", "a", "eps", "mu1", "mu2", "cw")]
+
+
+class sdc_options(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
+                ("reaction_implicit", C.c_int), ("w_frozen", C.c_int), ("drop_rel", C.c_double),
+                ("spin_budget", C.c_longlong), ("cg_block_size", C.c_int),
+                ("cg_max_blocks", C.c_int), ("profile", C.c_int), ("inject_fault", C.c_int)]
+
+
+class sdc_stats(C.Structure):
+    _fields_ = [("sweeps_run", C.c_int), ("n_active", C.c_int * SDC_MAX_SWEEPS),
+                ("nnz_active", C.c_longlong * SDC_MAX_SWEEPS),
+                ("cg_iters", (C.c_int * SDC_MAX_M) * SDC_MAX_SWEEPS),
+                ("cg_relres_max", C.c_double), ("min_margin", C.c_double),
+                ("kernel_launches", C.c_int), ("phase_launches", C.c_int * SDC_N_PHASES),
+                ("phase_ms", C.c_double * SDC_N_PHASES)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_vp = C.c_void_p
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "sdc_default_options": (None, [C.POINTER(sdc_options)]),
+    "sdc_default_ionic": (None, [C.POINTER(sdc_ionic)]),
+    "sdc_radau": (C.c_int, [C.c_int, _dp, _dp, _dp]),
+    "sdc_create": (C.c_int, [C.POINTER(_vp), C.POINTER(sdc_mesh), C.POINTER(sdc_ionic), C.c_int,
+                             C.POINTER(sdc_options), _vp]),
+    "sdc_set_stimulus": (C.c_int, [_vp, _ip, C.c_int, C.c_double, C.c_double, C.c_double]),
+    "sdc_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                           C.POINTER(sdc_stats)]),
+    "sdc_step_host": (C.c_int, [_vp, _dp, _dp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                C.POINTER(sdc_stats)]),
+    "sdc_get_nodes": (C.c_int, [_vp, _vp, _vp]),
+    "sdc_get_active": (C.c_int, [_vp, C.c_int, _ip, _ip]),
+    "sdc_get_info": (C.c_int, [_vp, _ip, C.POINTER(C.c_longlong), _ip]),
+    "sdc_get_matrix": (C.c_int, [_vp, _ip, _ip, _dp, _dp]),
+    "sdc_last_error": (C.c_char_p, [_vp]),
+    "sdc_status_string": (C.c_char_p, [C.c_int]),
+    "sdc_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libsdc_gb300.so is not built (%s); run __graft_entry__.build()"
+                               % LIB_PATH)
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class SdcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (load().sdc_status_string(status).decode(), status, message))
+        self.status = status
+
+
+def _check(status, ctx=None):
+    if status != SDC_OK:
+        msg = load().sdc_last_error(ctx).decode()
+        raise SdcError(status, msg)
+
+
+def default_options(**kw) -> sdc_options:
+    o = sdc_options()
+    load().sdc_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ionic_struct(p: dict) -> sdc_ionic:
+    return sdc_ionic(*(float(p[k]) for k in ("ga", "gs", "a", "eps", "mu1", "mu2", "cw")))
+
+
+def radau(M: int):
+    tau, Q, Qh = np.zeros(M), np.zeros((M, M)), np.zeros((M, M))
+    _check(load().sdc_radau(M, tau.ctypes.data_as(_dp), Q.ctypes.data_as(_dp),
+                            Qh.ctypes.data_as(_dp)))
+    return tau, Q, Qh
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor (or an int address)."""
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+class Context:
+    """One sdc_ctx.  Mesh arrays are copied by the library at creation."""
+
+    def __init__(self, dim, xyz, elems, sigma=None, elem_sigma=None, dof_scale=None,
+                 ionic=None, M=3, options=None, stream=0):
+        L = load()
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        elems = np.ascontiguousarray(elems, dtype=np.int32)
+        ne, nv = elems.shape
+        eptr = np.arange(0, (ne + 1) * nv, nv, dtype=np.int32)
+        sig = None if sigma is None else np.ascontiguousarray(np.asarray(sigma).reshape(9), np.float64)
+        es = None if elem_sigma is None else np.ascontiguousarray(
+            np.asarray(elem_sigma).reshape(-1, 9), np.float64)
+        ds = None if dof_scale is None else np.ascontiguousarray(dof_scale, np.float64)
+        self._keep = (xyz, elems, eptr, sig, es, ds)
+        dp = lambda a: None if a is None else a.ctypes.data_as(_dp)
+        mesh = sdc_mesh(dim, xyz.shape[0], dp(xyz), ne, eptr.ctypes.data_as(_ip),
+                        elems.ctypes.data_as(_ip), dp(sig), dp(es), dp(ds))
+        ion = sdc_ionic()
+        if ionic is None:
+            L.sdc_default_ionic(C.byref(ion))
+        else:
+            ion = ionic_struct(ionic)
+        opts = options if options is not None else default_options()
+        h = _vp()
+        _check(L.sdc_create(C.byref(h), C.byref(mesh), C.byref(ion), int(M), C.byref(opts),
+                            _vp(stream)))
+        self._h = h
+        self.M = int(M)
+        self.n = int(xyz.shape[0])
+
+    @classmethod
+    def from_workload(cls, wl, options=None, stream=0):
+        ctx = cls(wl.mesh.dim, wl.mesh.xyz, wl.mesh.elems, sigma=wl.sigma,
+                  elem_sigma=wl.mesh.elem_sigma, dof_scale=wl.dof_scale, ionic=wl.ionic, M=wl.M,
+                  options=options, stream=stream)
+        if wl.stim_nodes.size:
+            ctx.set_stimulus(wl.stim_nodes, wl.stim_amp, wl.stim_t_on, wl.stim_t_off)
+        return ctx
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sdc_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stimulus(self, nodes, amp, t_on, t_off):
+        nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+        _check(load().sdc_set_stimulus(self._h, nodes.ctypes.data_as(_ip), nodes.size, amp,
+                                       t_on, t_off), self._h)
+
+    def step(self, v, w, t, dt, sweeps, tol, want_stats=True):
+        """One step on device tensors v, w (FP64, n entries each, updated in place)."""
+        st = sdc_stats() if want_stats else None
+        _check(load().sdc_step(self._h, _vp(_ptr(v)), _vp(_ptr(w)), float(t), float(dt),
+                               int(sweeps), float(tol), C.byref(st) if st is not None else None),
+               self._h)
+        return st
+
+    def step_host(self, v, w, t, dt, sweeps, tol, want_stats=False):
+        """One step on host numpy arrays v, w (updated in place)."""
+        assert v.dtype == np.float64 and w.dtype == np.float64
+        assert v.flags.c_contiguous and w.flags.c_contiguous
+        st = sdc_stats() if want_stats else None
+        _check(load().sdc_step_host(self._h, v.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
+                                    float(t), float(dt), int(sweeps), float(tol),
+                                    C.byref(st) if st is not None else None), self._h)
+        return st
+
+    def nodes(self, V, W):
+        _check(load().sdc_get_nodes(self._h, _vp(_ptr(V)), _vp(_ptr(W))), self._h)
+
+    def active(self, sweep):
+        n = C.c_int(0)
+        _check(load().sdc_get_active(self._h, sweep, None, C.byref(n)), self._h)
+        out = np.zeros(max(1, n.value), np.int32)
+        _check(load().sdc_get_active(self._h, sweep, out.ctypes.data_as(_ip), C.byref(n)), self._h)
+        return out[:n.value]
+
+    def info(self):
+        n, nnz, w = C.c_int(0), C.c_longlong(0), C.c_int(0)
+        _check(load().sdc_get_info(self._h, C.byref(n), C.byref(nnz), C.byref(w)), self._h)
+        return n.value, nnz.value, w.value
+
+    def matrix(self):
+        n, nnz, _ = self.info()
+        rp, ci = np.zeros(n + 1, np.int32), np.zeros(nnz, np.int32)
+        val, mass = np.zeros(nnz), np.zeros(n)
+        _check(load().sdc_get_matrix(self._h, rp.ctypes.data_as(_ip), ci.ctypes.data_as(_ip),
+                                     val.ctypes.data_as(_dp), mass.ctypes.data_as(_dp)), self._h)
+        return rp, ci, val, mass

@@ -1,0 +1,543 @@
+// C ABI entry points and the host side of one SDC step (Sec. 3.2 eq. final-sdc,
+// Sec. 4.2 nested index sets).  Device work is issued on the context's stream;
+// the host reads back one integer per sweep (|I_{k+1}|, which sizes the next
+// launches) together with the error flag.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sdc_internal.h"
+
+using namespace sdc;
+
+struct sdc_ctx {
+    int N = 0, M = 0, dim = 0;
+    cudaStream_t stream = nullptr;
+    sdc_ionic ion_c{};
+    Ionic ion{};
+    sdc_options opt{};
+    Coll co{};
+    double tau[kMaxM] = {};
+    AssemblyOut K;
+    double* stim = nullptr;       // per-node amplitude (device) or null
+    double stim_t_on = 0.0, stim_t_off = 0.0;
+    StepBuffers B;
+    std::vector<int*> act;        // act[k]: active list of sweep k >= 1 (device)
+    std::vector<int> n_act;       // |I_k| of the last step
+    int last_sweeps = 0;
+    int pcg_block = 256, pcg_blocks = 0;
+    int* h_pin = nullptr;         // pinned: [0] count, [1] err
+    std::vector<cudaEvent_t> events;   // profiling event pool
+    bool stepped = false;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+sdc_status fail(sdc_ctx* c, sdc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return st;
+}
+
+sdc_status cuda_fail(sdc_ctx* c, const char* where) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, SDC_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+template <class T>
+bool dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)) == cudaSuccess;
+}
+
+void free_ell(Ell& e) {
+    cudaFree(e.val);
+    cudaFree(e.col);
+    cudaFree(e.len);
+    e = Ell();
+}
+
+int alloc_buffers(sdc_ctx* c) {
+    StepBuffers& B = c->B;
+    const int N = c->N, M = c->M;
+    B.N = N;
+    B.M = M;
+    B.ld = (N + 31) / 32 * 32;
+    const size_t ld = B.ld;
+    const int nbu = (N + kUpdateBlock - 1) / kUpdateBlock;
+    c->pcg_block = c->opt.cg_block_size;
+    c->pcg_blocks = pcg_max_blocks(c->pcg_block);
+    if (c->opt.cg_max_blocks > 0) c->pcg_blocks = std::min(c->pcg_blocks, c->opt.cg_max_blocks);
+    if (c->pcg_blocks < 1) return SDC_E_CUDA;
+    B.max_blocks = c->pcg_blocks;
+    bool ok = dalloc(&B.V, (size_t)N * M) && dalloc(&B.W, (size_t)N * M) &&
+              dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
+              dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.z, ld) &&
+              dalloc(&B.p, ld) && dalloc(&B.q, ld) && dalloc(&B.dA, ld) &&
+              dalloc(&B.part, 2 * (size_t)B.max_blocks) && dalloc(&B.flag, ld) &&
+              dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
+              dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
+              dalloc(&B.wtmp, N);
+    for (int b = 0; b < 2 && ok; ++b) {
+        Ell& A = B.A[b];
+        A.ld = B.ld;
+        A.width = c->K.K.width;
+        ok = dalloc(&A.val, (size_t)A.width * ld) && dalloc(&A.col, (size_t)A.width * ld) &&
+             dalloc(&A.len, ld);
+    }
+    if (!ok) return SDC_E_NOMEM;
+    if (cudaMallocHost(&c->h_pin, 4 * sizeof(int)) != cudaSuccess) return SDC_E_NOMEM;
+    cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), c->stream);
+    return SDC_OK;
+}
+
+void free_all(sdc_ctx* c) {
+    StepBuffers& B = c->B;
+    double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.part,
+                    B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
+    for (double* p : dp) cudaFree(p);
+    int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff};
+    for (int* p : ip) cudaFree(p);
+    cudaFree(B.sc);
+    free_ell(B.A[0]);
+    free_ell(B.A[1]);
+    free_ell(c->K.K);
+    for (int* p : c->act) cudaFree(p);
+    c->act.clear();
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    c->h_pin = nullptr;
+}
+
+bool finite_all(const double* a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!(a[i] == a[i]) || a[i] - a[i] != 0.0) return false;
+    return true;
+}
+
+// Read the error flag and the next active count; resets the flag.
+int sync_sweep(sdc_ctx* c, int& count) {
+    cudaMemcpyAsync(&c->h_pin[0], &c->B.sc->count, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(&c->h_pin[1], &c->B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SDC_E_CUDA;
+    count = c->h_pin[0];
+    return c->h_pin[1];
+}
+
+}  // namespace
+
+extern "C" {
+
+void sdc_default_options(sdc_options* o) {
+    if (!o) return;
+    o->alpha = 0.1;
+    o->cg_rtol = 1e-10;
+    o->cg_maxit = 2000;
+    o->reaction_implicit = 1;
+    o->w_frozen = 0;
+    o->drop_rel = 1e-12;
+    o->spin_budget = 4000000000LL;
+    o->cg_block_size = 256;
+    o->cg_max_blocks = 0;
+    o->profile = 0;
+    o->inject_fault = 0;
+}
+
+void sdc_default_ionic(sdc_ionic* p) {
+    if (!p) return;
+    p->ga = 8.0;
+    p->gs = 8.0;
+    p->a = 0.15;
+    p->eps = 0.002;
+    p->mu1 = 0.2;
+    p->mu2 = 0.3;
+    p->cw = 1.0;
+}
+
+const char* sdc_status_string(int s) {
+    switch (s) {
+        case SDC_OK: return "ok";
+        case SDC_E_INVALID: return "invalid argument";
+        case SDC_E_CUDA: return "CUDA error";
+        case SDC_E_NOMEM: return "out of device memory";
+        case SDC_E_CG_NOCONV: return "CG did not converge";
+        case SDC_E_TIMEOUT: return "device wait timed out";
+        case SDC_E_NONFINITE: return "non-finite value";
+        case SDC_E_DOMAIN: return "outside the model's domain";
+        default: return "unknown status";
+    }
+}
+
+const char* sdc_last_error(const sdc_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+sdc_status sdc_radau(int M, double* tau, double* Q, double* Qhat) {
+    if (!tau || !Q || !Qhat || M < 1 || M > kMaxM) return SDC_E_INVALID;
+    return radau_collocation(M, tau, Q, Qhat) ? SDC_OK : SDC_E_INVALID;
+}
+
+sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
+                      const sdc_options* opt, void* stream) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, SDC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !ionic) return fail(nullptr, SDC_E_INVALID, "mesh or ionic is NULL");
+    if (M < 1 || M > kMaxM) return fail(nullptr, SDC_E_INVALID, "M = %d outside [1, 8]", M);
+    if (mesh->dim != 2 && mesh->dim != 3)
+        return fail(nullptr, SDC_E_INVALID, "dim = %d (2 or 3)", mesh->dim);
+    if (mesh->n_nodes < 1 || mesh->n_elems < 1 || !mesh->xyz || !mesh->elem_ptr || !mesh->elem_node)
+        return fail(nullptr, SDC_E_INVALID, "empty mesh or NULL mesh arrays");
+    if (!mesh->sigma && !mesh->elem_sigma)
+        return fail(nullptr, SDC_E_INVALID, "neither sigma nor elem_sigma given");
+    const int nv = mesh->dim + 1;
+    for (int e = 0; e < mesh->n_elems; ++e) {
+        if (mesh->elem_ptr[e + 1] - mesh->elem_ptr[e] != nv)
+            return fail(nullptr, SDC_E_INVALID, "element %d has %d nodes (P1 simplex needs %d)", e,
+                        mesh->elem_ptr[e + 1] - mesh->elem_ptr[e], nv);
+        for (int a = 0; a < nv; ++a) {
+            const int v = mesh->elem_node[mesh->elem_ptr[e] + a];
+            if (v < 0 || v >= mesh->n_nodes)
+                return fail(nullptr, SDC_E_INVALID, "element %d references node %d", e, v);
+            for (int b = 0; b < a; ++b)
+                if (mesh->elem_node[mesh->elem_ptr[e] + b] == v)
+                    return fail(nullptr, SDC_E_INVALID, "element %d repeats node %d", e, v);
+        }
+    }
+    if (!finite_all(mesh->xyz, mesh->n_nodes * mesh->dim))
+        return fail(nullptr, SDC_E_INVALID, "non-finite coordinates");
+    sdc_options o;
+    sdc_default_options(&o);
+    if (opt) o = *opt;
+    if (!(o.alpha >= 0.0) || !(o.cg_rtol > 0.0) || o.cg_maxit < 1 || !(o.drop_rel >= 0.0) ||
+        o.spin_budget < 1 || o.cg_block_size < 64 || o.cg_block_size > 1024 ||
+        o.cg_block_size % 32 != 0 || o.cg_max_blocks < 0 || o.inject_fault < 0 ||
+        o.inject_fault > 1)
+        return fail(nullptr, SDC_E_INVALID, "invalid options");
+    if (!(ionic->mu2 > 0.0) && !o.w_frozen)
+        return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
+
+    sdc_ctx* c = new sdc_ctx();
+    c->N = mesh->n_nodes;
+    c->M = M;
+    c->dim = mesh->dim;
+    c->stream = (cudaStream_t)stream;
+    c->ion_c = *ionic;
+    c->ion = Ionic{ionic->ga, ionic->gs, ionic->a, ionic->eps, ionic->mu1, ionic->mu2, ionic->cw};
+    c->opt = o;
+    double Q[kMaxM * kMaxM], Qh[kMaxM * kMaxM];
+    if (!radau_collocation(M, c->tau, Q, Qh)) {
+        delete c;
+        return fail(nullptr, SDC_E_INVALID, "collocation setup failed for M = %d", M);
+    }
+    c->co.M = M;
+    for (int m = 0; m < kMaxM; ++m)
+        for (int j = 0; j < kMaxM; ++j) {
+            c->co.Q[m * kMaxM + j] = (m < M && j < M) ? Q[m * M + j] : 0.0;
+            c->co.Qh[m * kMaxM + j] = (m < M && j < M) ? Qh[m * M + j] : 0.0;
+        }
+    std::string why;
+    int rc = assemble_device(*mesh, o.drop_rel, c->stream, c->K, why);
+    if (rc != SDC_OK) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, (sdc_status)rc, "%s", why.c_str());
+    }
+    rc = alloc_buffers(c);
+    if (rc != SDC_OK) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, (sdc_status)rc, "device buffer allocation failed");
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        sdc_status st = cuda_fail(nullptr, "sdc_create");
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return SDC_OK;
+}
+
+sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, double t_on,
+                            double t_off) {
+    if (!c) return SDC_E_INVALID;
+    if (n < 0 || (n > 0 && !nodes)) return fail(c, SDC_E_INVALID, "bad stimulus node list");
+    for (int i = 0; i < n; ++i)
+        if (nodes[i] < 0 || nodes[i] >= c->N)
+            return fail(c, SDC_E_INVALID, "stimulus node %d out of range", nodes[i]);
+    if (!std::isfinite(amp)) return fail(c, SDC_E_INVALID, "non-finite stimulus amplitude");
+    cudaFree(c->stim);
+    c->stim = nullptr;
+    if (n == 0) return SDC_OK;
+    std::vector<double> h(c->N, 0.0);
+    for (int i = 0; i < n; ++i) h[nodes[i]] = amp;
+    if (!dalloc(&c->stim, c->N)) return fail(c, SDC_E_NOMEM, "stimulus allocation failed");
+    if (cudaMemcpyAsync(c->stim, h.data(), c->N * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(c, "sdc_set_stimulus");
+    c->stim_t_on = t_on;
+    c->stim_t_off = t_off;
+    return SDC_OK;
+}
+
+sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                    double TOL, sdc_stats* stats) {
+    if (!c) return SDC_E_INVALID;
+    if (!d_v || !d_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDC_E_INVALID, "dt must be positive");
+    if (sweeps < 1 || sweeps > SDC_MAX_SWEEPS)
+        return fail(c, SDC_E_INVALID, "sweeps = %d outside [1, %d]", sweeps, SDC_MAX_SWEEPS);
+    if (!(TOL >= 0.0)) return fail(c, SDC_E_INVALID, "TOL must be >= 0");
+    StepBuffers& B = c->B;
+    const int N = c->N, M = c->M;
+    cudaStream_t s = c->stream;
+    const double tol_drop = c->opt.alpha * TOL;
+    const double stim_on = (c->stim && c->stim_t_on <= t && t < c->stim_t_off) ? 1.0 : 0.0;
+    while ((int)c->act.size() < sweeps) {
+        int* p = nullptr;
+        if (!dalloc(&p, N)) return fail(c, SDC_E_NOMEM, "active-list allocation failed");
+        c->act.push_back(p);
+    }
+    c->n_act.assign(sweeps, 0);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+
+    // kernel phases: launch counts always, device time with the profile option
+    const bool prof = c->opt.profile != 0;
+    struct Mark { int phase; int a, b; };
+    std::vector<Mark> marks;
+    int ev_used = 0;
+    int launches[SDC_N_PHASES] = {0, 0, 0, 0, 0};
+    auto next_event = [&]() -> int {
+        if (ev_used == (int)c->events.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->events.push_back(e);
+        }
+        return ev_used++;
+    };
+    auto run = [&](int phase, int nk, auto&& fn) {
+        int a = -1;
+        if (prof) {
+            a = next_event();
+            cudaEventRecord(c->events[a], s);
+        }
+        fn();
+        if (prof) {
+            const int b = next_event();
+            cudaEventRecord(c->events[b], s);
+            marks.push_back({phase, a, b});
+        }
+        launches[phase] += nk;
+    };
+
+    // reset scalars: error flag, CG statistics, margin
+    cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), s);
+    const double big = 1.7976931348623157e308;
+    cudaMemcpyAsync(&B.sc->margin, &big, sizeof(double), cudaMemcpyHostToDevice, s);
+    run(SDC_PHASE_RESIDUAL, 1, [&] { launch_spread(N, M, d_v, d_w, B.V, B.W, s); });
+
+    int n = N;
+    const int* act = nullptr;      // identity for the first sweep
+    const Ell* A = &c->K.K;
+    long long nnz = c->K.nnz - N;
+    int cur = 0;                   // ping-pong index of the restricted matrix
+    int status = SDC_OK;
+    int k = 0;
+    for (k = 0; k < sweeps; ++k) {
+        c->n_act[k] = n;
+        if (stats) {
+            stats->n_active[k] = n;
+            stats->nnz_active[k] = nnz;
+            stats->sweeps_run = k + 1;
+        }
+        if (n == 0) continue;
+        run(SDC_PHASE_RESIDUAL, 1, [&] {
+            launch_residual(M, n, act, c->K.K, c->K.kdiag, c->K.mass, c->stim, stim_on, B.V, B.W,
+                            d_v, dt, c->ion, c->co, c->opt.reaction_implicit, B, s);
+        });
+        for (int m = 0; m < M && status == SDC_OK; ++m) {
+            run(SDC_PHASE_PCG, 1, [&] {
+                if (launch_pcg(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit,
+                               c->opt.spin_budget, k, c->pcg_block, c->pcg_blocks,
+                               c->opt.inject_fault, B, s) != SDC_OK)
+                    status = cuda_fail(c, "cooperative CG launch");
+            });
+        }
+        if (status != SDC_OK) break;
+        run(SDC_PHASE_UPDATE, 1, [&] {
+            launch_update(M, n, act, d_w, dt, c->ion, c->co, tol_drop, c->opt.w_frozen, B, s);
+        });
+        int* next = (k + 1 < sweeps) ? c->act[k + 1] : c->act[0];
+        run(SDC_PHASE_SELECT, 2, [&] { launch_select(n, act, next, B, s); });
+        int n_next = 0;
+        int e = sync_sweep(c, n_next);
+        if (e != SDC_OK) {
+            status = e == SDC_E_CUDA ? cuda_fail(c, "sweep") : fail(c, (sdc_status)e,
+                     "sweep %d: %s", k, sdc_status_string(e));
+            break;
+        }
+        if (k + 1 < sweeps && n_next > 0) {
+            Ell& An = B.A[cur];
+            run(SDC_PHASE_EXTRACT, 1, [&] { launch_extract(n, *A, B.map, An, B, s); });
+            unsigned long long hn = 0;
+            cudaMemcpyAsync(&hn, &B.sc->nnz, sizeof(hn), cudaMemcpyDeviceToHost, s);
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                status = cuda_fail(c, "extract");
+                break;
+            }
+            nnz = (long long)hn;
+            A = &An;
+            cur ^= 1;
+        }
+        act = (k + 1 < sweeps) ? c->act[k + 1] : nullptr;
+        n = n_next;
+    }
+    if (status == SDC_OK) {
+        run(SDC_PHASE_RESIDUAL, 1, [&] { launch_final(N, M, B.V, B.W, d_v, d_w, s); });
+        if (cudaStreamSynchronize(s) != cudaSuccess) status = cuda_fail(c, "sdc_step");
+    }
+    c->last_sweeps = sweeps;
+    c->stepped = true;
+    if (stats) {
+        std::vector<int> it(SDC_MAX_SWEEPS * kMaxM);
+        std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM);
+        double mg = 0.0;
+        cudaMemcpyAsync(it.data(), B.sc->cg_iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(rr.data(), B.sc->cg_relres, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        for (int kk = 0; kk < sweeps; ++kk)
+            for (int m = 0; m < M; ++m) {
+                stats->cg_iters[kk][m] = it[kk * kMaxM + m];
+                stats->cg_relres_max = std::max(stats->cg_relres_max, rr[kk * kMaxM + m]);
+            }
+        stats->min_margin = mg >= big ? INFINITY : mg;
+        stats->kernel_launches = 0;
+        for (int ph = 0; ph < SDC_N_PHASES; ++ph) {
+            stats->phase_launches[ph] = launches[ph];
+            stats->kernel_launches += launches[ph];
+            stats->phase_ms[ph] = 0.0;
+        }
+        for (const Mark& mk : marks) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, c->events[mk.a], c->events[mk.b]) == cudaSuccess)
+                stats->phase_ms[mk.phase] += ms;
+        }
+    }
+    return (sdc_status)status;
+}
+
+sdc_status sdc_step_host(sdc_ctx* c, double* h_v, double* h_w, double t, double dt, int sweeps,
+                         double TOL, sdc_stats* stats) {
+    if (!c) return SDC_E_INVALID;
+    if (!h_v || !h_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
+    const size_t bytes = (size_t)c->N * sizeof(double);
+    if (cudaMemcpyAsync(c->B.vtmp, h_v, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(c->B.wtmp, h_w, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return cuda_fail(c, "sdc_step_host upload");
+    sdc_status st = sdc_step(c, c->B.vtmp, c->B.wtmp, t, dt, sweeps, TOL, stats);
+    if (st != SDC_OK) return st;
+    if (cudaMemcpyAsync(h_v, c->B.vtmp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h_w, c->B.wtmp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(c, "sdc_step_host download");
+    return SDC_OK;
+}
+
+sdc_status sdc_get_nodes(const sdc_ctx* cc, double* d_V, double* d_W) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    if (!c) return SDC_E_INVALID;
+    if (!d_V || !d_W) return fail(c, SDC_E_INVALID, "NULL output");
+    launch_nodes_out(c->N, c->M, c->B.V, c->B.W, d_V, d_W, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "sdc_get_nodes");
+    return SDC_OK;
+}
+
+sdc_status sdc_get_active(const sdc_ctx* cc, int sweep, int* h_idx, int* n) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    if (!c) return SDC_E_INVALID;
+    if (!c->stepped || sweep < 0 || sweep >= c->last_sweeps || !n)
+        return fail(c, SDC_E_INVALID, "no active list for sweep %d", sweep);
+    const int cnt = c->n_act[sweep];
+    *n = cnt;
+    if (!h_idx || cnt == 0) return SDC_OK;
+    if (sweep == 0) {
+        for (int i = 0; i < cnt; ++i) h_idx[i] = i;
+        return SDC_OK;
+    }
+    if (cudaMemcpyAsync(h_idx, c->act[sweep], (size_t)cnt * sizeof(int), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(c, "sdc_get_active");
+    return SDC_OK;
+}
+
+sdc_status sdc_get_info(const sdc_ctx* c, int* n_nodes, long long* nnz, int* max_row_offdiag) {
+    if (!c) return SDC_E_INVALID;
+    if (n_nodes) *n_nodes = c->N;
+    if (nnz) *nnz = c->K.nnz;
+    if (max_row_offdiag) *max_row_offdiag = c->K.K.width;
+    return SDC_OK;
+}
+
+sdc_status sdc_get_matrix(const sdc_ctx* cc, int* row_ptr, int* col, double* val, double* mass) {
+    sdc_ctx* c = const_cast<sdc_ctx*>(cc);
+    if (!c) return SDC_E_INVALID;
+    if (!row_ptr || !col || !val || !mass) return fail(c, SDC_E_INVALID, "NULL output");
+    const int N = c->N;
+    const Ell& E = c->K.K;
+    std::vector<double> ev((size_t)E.width * E.ld), kd(N);
+    std::vector<int> ec((size_t)E.width * E.ld), el(E.ld);
+    cudaStream_t s = c->stream;
+    cudaMemcpyAsync(ev.data(), E.val, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(ec.data(), E.col, ec.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(el.data(), E.len, el.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(kd.data(), c->K.kdiag, N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(mass, c->K.mass, N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, "sdc_get_matrix");
+    long long pos = 0;
+    row_ptr[0] = 0;
+    for (int i = 0; i < N; ++i) {
+        // merge the diagonal into the ascending off-diagonal columns
+        bool diag_done = false;
+        for (int t = 0; t < el[i]; ++t) {
+            const int j = ec[(size_t)t * E.ld + i];
+            if (!diag_done && j > i) {
+                col[pos] = i;
+                val[pos++] = kd[i];
+                diag_done = true;
+            }
+            col[pos] = j;
+            val[pos++] = ev[(size_t)t * E.ld + i];
+        }
+        if (!diag_done) {
+            col[pos] = i;
+            val[pos++] = kd[i];
+        }
+        row_ptr[i + 1] = (int)pos;
+    }
+    return SDC_OK;
+}
+
+void sdc_destroy(sdc_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the library's translation units (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sdc.h"
+
+namespace sdc {
+
+constexpr int kMaxM = SDC_MAX_M;
+constexpr int kUpdateBlock = 256;   // block size of the update / scatter kernels
+
+// Aliev-Panfilov parameters as passed to kernels (Sec. 5.1.1).
+struct Ionic {
+    double ga, gs, a, eps, mu1, mu2, cw;
+};
+
+// Collocation matrices, fixed stride kMaxM, passed by value to kernels.
+struct Coll {
+    int M;
+    double Q[kMaxM * kMaxM];
+    double Qh[kMaxM * kMaxM];
+};
+
+// Device scalars of one context (one allocation).
+struct DevScalars {
+    int count;                 // |I_{k+1}| written by the scan kernel
+    int err;                   // first error code raised by any kernel (0 = none)
+    unsigned bar;              // grid-barrier arrival counter of the running CG launch
+    int pad;
+    unsigned long long nnz;    // stored off-diagonals of the newest restricted matrix
+    double margin;             // min |max_m |dv| - TOL_drop| of the newest selection
+    int cg_iters[SDC_MAX_SWEEPS * kMaxM];
+    double cg_relres[SDC_MAX_SWEEPS * kMaxM];
+};
+
+// ELL-R matrix in column-major slots: entry t of row i at [t * ld + i],
+// row i holds len[i] entries.  Used for off-diagonal parts only.
+struct Ell {
+    double* val = nullptr;
+    int* col = nullptr;
+    int* len = nullptr;
+    int ld = 0;
+    int width = 0;
+};
+
+// ---- collocation (radau.cpp) ----
+bool radau_collocation(int M, double* tau, double* Q, double* Qhat);
+
+// ---- assembly (assembly.cu) ----
+struct AssemblyOut {
+    Ell K;                 // off-diagonal part of K (device)
+    double* kdiag = nullptr;
+    double* mass = nullptr;
+    long long nnz = 0;     // stored entries including the diagonal
+};
+int assemble_device(const sdc_mesh& mesh, double drop_rel, cudaStream_t s, AssemblyOut& out,
+                    std::string& why);
+
+// ---- step kernels (step.cu) ----
+struct StepBuffers {
+    int N = 0, M = 0, ld = 0;
+    double* V = nullptr;      // [N][M] node-interleaved collocation iterates of v
+    double* W = nullptr;      // [N][M] same for w
+    double* R = nullptr;      // [M][ld] residual / right-hand sides (compact rows)
+    double* J = nullptr;      // [M][ld] dI/dv at the iterate
+    double* D = nullptr;      // [M][ld] corrections dv
+    double* mc = nullptr;     // [ld] lumped mass of the active rows
+    double* kdc = nullptr;    // [ld] K_ii of the active rows
+    double* r = nullptr;      // CG vectors [ld]
+    double* z = nullptr;
+    double* p = nullptr;
+    double* q = nullptr;
+    double* dA = nullptr;
+    double* part = nullptr;   // 2 * max_blocks partial sums
+    int max_blocks = 0;
+    int* flag = nullptr;      // [ld]
+    int* map = nullptr;       // [ld] old compact row -> new compact row or -1
+    int* blockcnt = nullptr;  // per update block
+    int* blockoff = nullptr;
+    double* blockmarg = nullptr;
+    Ell A[2];                 // restricted off-diagonal matrices (ping-pong)
+    DevScalars* sc = nullptr;
+    double* vtmp = nullptr;   // host-call staging [N]
+    double* wtmp = nullptr;
+};
+
+void launch_spread(int N, int M, const double* v0, const double* w0, double* V, double* W,
+                   cudaStream_t s);
+void launch_final(int N, int M, const double* V, const double* W, double* v, double* w,
+                  cudaStream_t s);
+void launch_nodes_out(int N, int M, const double* V, const double* W, double* Vout, double* Wout,
+                      cudaStream_t s);
+void launch_residual(int M, int n, const int* act, const Ell& K, const double* kdiag,
+                     const double* mass, const double* stim, double stim_on, const double* V,
+                     const double* W, const double* v0, double dt, const Ionic& ion,
+                     const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
+int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
+               long long budget, int sweep, int block, int max_blocks, int inject_fault,
+               StepBuffers& B, cudaStream_t s);
+void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
+                   const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s);
+void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s);
+void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepBuffers& B,
+                    cudaStream_t s);
+int pcg_max_blocks(int block);
+
+}  // namespace sdc

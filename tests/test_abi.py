@@ -1,0 +1,72 @@
+"""CPU checks of the C ABI: the library loads, exports every entry point that
+include/sdc.h declares, and its host-side collocation data agrees with the
+oracle's.  No device work is started here."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(sdc_[a-z_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_07206_gb300 import build as b
+    b.build()
+    from paper_2311_07206_gb300 import binding
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2311_07206_gb300 import binding
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in binding.SIGNATURES, "binding lacks " + n
+
+
+def test_default_options(lib):
+    from paper_2311_07206_gb300 import default_options
+    o = default_options()
+    assert o.alpha == 0.1 and o.cg_rtol == 1e-10 and o.reaction_implicit == 1
+    assert o.w_frozen == 0 and o.inject_fault == 0 and o.cg_block_size == 256
+
+
+@pytest.mark.parametrize("M", range(1, 9))
+def test_library_collocation_matches_oracle(lib, M):
+    from paper_2311_07206_gb300 import radau
+    t1, Q1, H1 = radau(M)
+    t2, Q2, H2 = oracle.collocation(M)
+    np.testing.assert_allclose(t1, t2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(Q1, Q2, rtol=0, atol=4e-15)
+    np.testing.assert_allclose(H1, H2, rtol=0, atol=4e-14)
+
+
+def test_collocation_rejects_bad_M(lib):
+    from paper_2311_07206_gb300 import SdcError, radau
+    for M in (0, 9):
+        with pytest.raises(SdcError):
+            radau(M)
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2311_07206_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        binding.load()
