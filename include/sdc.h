@@ -97,8 +97,16 @@ typedef struct {
                               are rounding residue of cancelling element terms and are not
                               stored; default 1e-12, 0 keeps every structural entry           */
     long long spin_budget; /* SM clock cycles a device-side barrier may wait; default 4e9     */
-    int cg_block_size;     /* threads per CG block (64..1024, multiple of 32); default 256    */
-    int cg_max_blocks;     /* 0: one cooperative grid filling every SM                        */
+    int cg_block_size;     /* threads per block of the global-vector CG (64..1024, multiple
+                              of 32); default 256                                             */
+    int cg_smem_block_size;/* threads per block of the shared-memory and cluster CG; default 512 */
+    int cg_cluster_max;    /* largest cluster (CTAs) for the cluster CG, 1..16; default 16      */
+    int cg_max_blocks;     /* 0: no limit on the cooperative CG grid                          */
+    int cg_variant;        /* 0: automatic; 1: vectors in global memory; 2: per-block vectors
+                              in shared memory whenever |I_k| <= 4096 * SM count             */
+    int cg_rows_per_block; /* shared-memory variant: target rows per block (0 = 512)          */
+    int cg_cluster_rows;   /* solves with |I_k| <= this run on one thread-block cluster
+                              (16 CTAs, distributed shared memory); default 20000, 0 = never */
     int profile;           /* 1: bracket every kernel launch with CUDA events on the context's
                               stream and report device time per phase in sdc_stats; default 0 */
     int inject_fault;      /* testing hook, default 0.  1: in every CG launch the last block
@@ -118,6 +126,7 @@ typedef struct {
     /* per phase SDC_PHASE_*: launches, and device ms when the profile option is set */
     int phase_launches[SDC_N_PHASES];
     double phase_ms[SDC_N_PHASES];
+    double cg_ms[SDC_MAX_SWEEPS][SDC_MAX_M];  /* device ms per node solve (profile option) */
 } sdc_stats;
 
 /* Fill defaults (values above). */

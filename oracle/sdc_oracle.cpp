@@ -519,6 +519,7 @@ int ora_step(void* h, const ora_ionic* ip, int M, const double* istim, double* v
             const double c = dt * Qh[m * M + m];
             for (int i : act) {
                 dA[i] = S.mass[i] * (1.0 + c * J[(size_t)m * N + i]) + c * Kd[i];
+                if (!std::isfinite(dA[i])) return ORA_NONFINITE;
                 if (!(dA[i] > 0.0)) return ORA_DOMAIN;
             }
             std::vector<double> x(N, 0.0);

@@ -38,7 +38,10 @@ class sdc_options(C.Structure):
     _fields_ = [("alpha", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("reaction_implicit", C.c_int), ("w_frozen", C.c_int), ("drop_rel", C.c_double),
                 ("spin_budget", C.c_longlong), ("cg_block_size", C.c_int),
-                ("cg_max_blocks", C.c_int), ("profile", C.c_int), ("inject_fault", C.c_int)]
+                ("cg_smem_block_size", C.c_int), ("cg_cluster_max", C.c_int),
+                ("cg_max_blocks", C.c_int), ("cg_variant", C.c_int),
+                ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
+                ("profile", C.c_int), ("inject_fault", C.c_int)]
 
 
 class sdc_stats(C.Structure):
@@ -47,7 +50,8 @@ class sdc_stats(C.Structure):
                 ("cg_iters", (C.c_int * SDC_MAX_M) * SDC_MAX_SWEEPS),
                 ("cg_relres_max", C.c_double), ("min_margin", C.c_double),
                 ("kernel_launches", C.c_int), ("phase_launches", C.c_int * SDC_N_PHASES),
-                ("phase_ms", C.c_double * SDC_N_PHASES)]
+                ("phase_ms", C.c_double * SDC_N_PHASES),
+                ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS)]
 
 
 _dp = C.POINTER(C.c_double)

@@ -30,7 +30,7 @@ struct sdc_ctx {
     std::vector<int*> act;        // act[k]: active list of sweep k >= 1 (device)
     std::vector<int> n_act;       // |I_k| of the last step
     int last_sweeps = 0;
-    int pcg_block = 256, pcg_blocks = 0;
+    PcgConfig pcg;
     int* h_pin = nullptr;         // pinned: [0] count, [1] err
     std::vector<cudaEvent_t> events;   // profiling event pool
     bool stepped = false;
@@ -76,15 +76,26 @@ int alloc_buffers(sdc_ctx* c) {
     B.ld = (N + 31) / 32 * 32;
     const size_t ld = B.ld;
     const int nbu = (N + kUpdateBlock - 1) / kUpdateBlock;
-    c->pcg_block = c->opt.cg_block_size;
-    c->pcg_blocks = pcg_max_blocks(c->pcg_block);
-    if (c->opt.cg_max_blocks > 0) c->pcg_blocks = std::min(c->pcg_blocks, c->opt.cg_max_blocks);
-    if (c->pcg_blocks < 1) return SDC_E_CUDA;
-    B.max_blocks = c->pcg_blocks;
+    PcgConfig& P = c->pcg;
+    P.block = c->opt.cg_block_size;
+    P.max_blocks_general = pcg_max_blocks(P.block);
+    if (c->opt.cg_max_blocks > 0)
+        P.max_blocks_general = std::min(P.max_blocks_general, c->opt.cg_max_blocks);
+    P.sms = pcg_sm_count();
+    P.max_blocks = c->opt.cg_max_blocks;
+    P.rows_per_block = c->opt.cg_rows_per_block;
+    P.variant = c->opt.cg_variant;
+    P.smem_block = c->opt.cg_smem_block_size;
+    P.cluster = std::min(pcg_cluster_size(P.smem_block), c->opt.cg_cluster_max);
+    P.cluster_rows = c->opt.cg_cluster_rows;
+    P.inject_fault = c->opt.inject_fault;
+    P.budget = c->opt.spin_budget;
+    if (P.max_blocks_general < 1 || P.sms < 1) return SDC_E_CUDA;
+    B.max_blocks = std::max(P.max_blocks_general, P.sms);
     bool ok = dalloc(&B.V, (size_t)N * M) && dalloc(&B.W, (size_t)N * M) &&
               dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
               dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.z, ld) &&
-              dalloc(&B.p, ld) && dalloc(&B.q, ld) && dalloc(&B.dA, ld) &&
+              dalloc(&B.p, ld) && dalloc(&B.q, ld) && dalloc(&B.dA, ld) && dalloc(&B.idA, ld) &&
               dalloc(&B.part, 2 * (size_t)B.max_blocks) && dalloc(&B.flag, ld) &&
               dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
               dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
@@ -104,7 +115,7 @@ int alloc_buffers(sdc_ctx* c) {
 
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
-    double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.part,
+    double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.idA, B.part,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
     int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff};
@@ -150,7 +161,12 @@ void sdc_default_options(sdc_options* o) {
     o->drop_rel = 1e-12;
     o->spin_budget = 4000000000LL;
     o->cg_block_size = 256;
+    o->cg_smem_block_size = 512;
+    o->cg_cluster_max = 16;
     o->cg_max_blocks = 0;
+    o->cg_variant = 0;
+    o->cg_rows_per_block = 0;
+    o->cg_cluster_rows = 20000;
     o->profile = 0;
     o->inject_fault = 0;
 }
@@ -223,8 +239,11 @@ sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ioni
     if (opt) o = *opt;
     if (!(o.alpha >= 0.0) || !(o.cg_rtol > 0.0) || o.cg_maxit < 1 || !(o.drop_rel >= 0.0) ||
         o.spin_budget < 1 || o.cg_block_size < 64 || o.cg_block_size > 1024 ||
-        o.cg_block_size % 32 != 0 || o.cg_max_blocks < 0 || o.inject_fault < 0 ||
-        o.inject_fault > 1)
+        o.cg_block_size % 32 != 0 || o.cg_max_blocks < 0 || o.cg_smem_block_size < 64 ||
+        o.cg_smem_block_size > 1024 || o.cg_smem_block_size % 32 != 0 || o.cg_cluster_max < 1 ||
+        o.cg_cluster_max > 16 || o.inject_fault < 0 ||
+        o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
+        o.cg_cluster_rows < 0)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
@@ -317,7 +336,7 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
 
     // kernel phases: launch counts always, device time with the profile option
     const bool prof = c->opt.profile != 0;
-    struct Mark { int phase; int a, b; };
+    struct Mark { int phase; int a, b; int k, m; };
     std::vector<Mark> marks;
     int ev_used = 0;
     int launches[SDC_N_PHASES] = {0, 0, 0, 0, 0};
@@ -329,6 +348,7 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         }
         return ev_used++;
     };
+    int cur_k = -1, cur_m = -1;
     auto run = [&](int phase, int nk, auto&& fn) {
         int a = -1;
         if (prof) {
@@ -339,7 +359,7 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         if (prof) {
             const int b = next_event();
             cudaEventRecord(c->events[b], s);
-            marks.push_back({phase, a, b});
+            marks.push_back({phase, a, b, cur_k, cur_m});
         }
         launches[phase] += nk;
     };
@@ -370,10 +390,11 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
                             d_v, dt, c->ion, c->co, c->opt.reaction_implicit, B, s);
         });
         for (int m = 0; m < M && status == SDC_OK; ++m) {
+            cur_k = k;
+            cur_m = m;
             run(SDC_PHASE_PCG, 1, [&] {
-                if (launch_pcg(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit,
-                               c->opt.spin_budget, k, c->pcg_block, c->pcg_blocks,
-                               c->opt.inject_fault, B, s) != SDC_OK)
+                if (launch_pcg(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit, k, c->pcg,
+                               B, s) != SDC_OK)
                     status = cuda_fail(c, "cooperative CG launch");
             });
         }
@@ -434,8 +455,10 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         }
         for (const Mark& mk : marks) {
             float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, c->events[mk.a], c->events[mk.b]) == cudaSuccess)
+            if (cudaEventElapsedTime(&ms, c->events[mk.a], c->events[mk.b]) == cudaSuccess) {
                 stats->phase_ms[mk.phase] += ms;
+                if (mk.phase == SDC_PHASE_PCG) stats->cg_ms[mk.k][mk.m] = ms;
+            }
         }
     }
     return (sdc_status)status;

@@ -37,30 +37,23 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
-// Every block calls this the same number of times; `epoch` counts arrivals the
-// caller expects (gridDim.x per call).  A wait longer than `budget` SM cycles
-// raises SDC_E_TIMEOUT and returns false in every thread of the block, so the
-// kernel can leave without touching further memory.
-__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned& epoch, long long budget,
-                                          int* err) {
-    epoch += gridDim.x;
-    __syncthreads();
-    int ok = 1;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bar, 1u);
-        const long long t0 = clock64();
-        while (ld_acquire_gpu(bar) < epoch) {
-            if (clock64() - t0 > budget) {
-                raise_error(err, SDC_E_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(32);
+// Called by ONE thread per block after a __syncthreads that follows the block's
+// writes, and followed by a __syncthreads: arrives with a release reduction
+// (cumulative over the writes the CTA barrier ordered before it) and waits with
+// acquire loads until `epoch` arrivals are counted, so every thread of the
+// block sees every block's writes after the closing CTA barrier.
+// A wait longer than `budget` SM cycles raises SDC_E_TIMEOUT and returns 0.
+__device__ __forceinline__ int barrier_arrive_wait(unsigned* bar, unsigned epoch, long long budget,
+                                                   int* err) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(bar) < epoch) {
+        if (clock64() - t0 > budget) {
+            raise_error(err, SDC_E_TIMEOUT);
+            return 0;
         }
-        __threadfence();
     }
-    return __syncthreads_and(ok) != 0;
+    return 1;
 }
 
 // ---- deterministic reductions --------------------------------------------------
@@ -90,14 +83,55 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
-// Sum of the G per-block partials written before the last grid barrier.  Every
-// warp computes the same value in the same order (bitwise identical in every
-// block), read through L2 so no stale L1 line is used.
-__device__ __forceinline__ double sum_partials(const double* part, int G) {
+// Grid-wide sum of one double per thread, fused with a grid barrier, for a
+// part where FP64 issue slots are scarce.  Each thread stores its value in
+// red[threadIdx.x]; warp 0 adds the block's values (one lane per 32-stride
+// column, then a shuffle tree), lane 0 publishes the block total to
+// part[blockIdx.x] and waits at the barrier, warp 0 adds the G block totals in
+// index order (bitwise identical in every block), and lane 0 alone runs
+// `on_total(total)`, which derives the iteration's scalars and stores them in
+// shared memory.  A closing CTA barrier makes them visible to the block.
+// Returns false after a barrier timeout.  red: blockDim.x doubles; flag: an
+// int in shared memory.
+template <class F>
+__device__ __forceinline__ bool grid_reduce(double v, double* red, double* part, unsigned* bar,
+                                            unsigned& epoch, long long budget, int* err,
+                                            int* ok_flag, F&& on_total) {
     const int lane = threadIdx.x & 31;
-    double s = 0.0;
-    for (int i = lane; i < G; i += 32) s += __ldcg(part + i);
-    return warp_sum(s);
+    red[threadIdx.x] = v;
+    __syncthreads();
+    epoch += gridDim.x;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = lane; i < (int)blockDim.x; i += 32) s += red[i];
+        s = warp_sum(s);
+        int ok = 1;
+        if (lane == 0) {
+            part[blockIdx.x] = s;
+            ok = barrier_arrive_wait(bar, epoch, budget, err);
+        }
+        __syncwarp();
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+            double t = 0.0;
+            for (int i = lane; i < (int)gridDim.x; i += 32) t += __ldcg(part + i);
+            t = warp_sum(t);
+            if (lane == 0) on_total(t);
+        }
+        if (lane == 0) *ok_flag = ok;
+    }
+    __syncthreads();
+    return *ok_flag != 0;
+}
+
+// Plain grid barrier with the same conventions (flag: an int in shared memory).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, long long budget,
+                                             int* err, int* ok_flag) {
+    epoch += gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) *ok_flag = barrier_arrive_wait(bar, epoch, budget, err);
+    __syncthreads();
+    return *ok_flag != 0;
 }
 
 }  // namespace sdc

@@ -75,6 +75,7 @@ struct StepBuffers {
     double* p = nullptr;
     double* q = nullptr;
     double* dA = nullptr;
+    double* idA = nullptr;
     double* part = nullptr;   // 2 * max_blocks partial sums
     int max_blocks = 0;
     int* flag = nullptr;      // [ld]
@@ -98,9 +99,27 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const double* mass, const double* stim, double stim_on, const double* V,
                      const double* W, const double* v0, double dt, const Ionic& ion,
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
+// Launch configuration of the restricted PCG solves.
+constexpr int kSmemRows = 3968;     // rows per block of the shared-memory variant
+struct PcgConfig {
+    int block = 256;                // block size of the general variant
+    int max_blocks_general = 0;     // cooperative grid limit of the general variant
+    int smem_block = 1024;          // block size of the shared-memory variant
+    int sms = 0;                    // SM count (one shared-memory block per SM at most)
+    int max_blocks = 0;             // user limit on the shared-memory grid (0 = none)
+    int rows_per_block = 0;         // target rows per shared-memory block (0 = default)
+    int variant = 0;                // 0 auto, 1 general only, 2 shared memory when it fits
+    int cluster = 0;                // CTAs of the cluster variant (0 = unavailable)
+    int cluster_rows = 0;           // use the cluster variant for n <= cluster_rows
+    int cluster_rows_per_cta = 64;  // rows per CTA below which fewer CTAs are used
+    int big_rows = 300000;          // shared-memory variant uses 1024 threads from here on
+    int inject_fault = 0;
+    long long budget = 0;
+};
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
-               long long budget, int sweep, int block, int max_blocks, int inject_fault,
-               StepBuffers& B, cudaStream_t s);
+               int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
+int pcg_sm_count();
+int pcg_cluster_size(int block);
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
                    const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s);
 void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s);

@@ -14,6 +14,8 @@
 
 #include <cfloat>
 
+#include <cooperative_groups.h>
+
 #include "device_common.cuh"
 #include "sdc_internal.h"
 
@@ -112,7 +114,8 @@ struct CgParams {
     double* z;
     double* p;
     double* q;
-    double* dA;
+    double* dA;          // diagonal of the node system
+    double* idA;         // its reciprocal (Jacobi preconditioner)
     double* part;
     unsigned* bar;
     int* err;
@@ -127,110 +130,162 @@ struct CgParams {
     double* R;
     double qh[kMaxM];    // Qhat[m'][m], m' = 0..M-1
     int inject_fault;    // testing hook: the last block skips the first barrier
+    int L;               // rows per block (shared-memory variant)
 };
 
-// Jacobi-PCG on the restricted node system, whole solve in one cooperative
-// launch.  Rows are processed grid-stride; each thread owns the same rows in
-// every phase.  Per iteration: q = A p with p.q (barrier), x/r/z updates with
-// r.z (barrier), p = z + beta p (barrier).  Partial sums are reduced in a fixed
-// order by every block, so all blocks take identical decisions.
-__global__ void __launch_bounds__(1024) k_pcg(CgParams P) {
-    __shared__ double sh[32];
+// Shared per-block scalars of a CG solve.  Lane 0 of warp 0 derives them from
+// each grid-wide sum (one FP64 division / square root per block, not per
+// thread: the FP64 pipe is the scarce unit on this part).
+struct CgShared {
+    double red[1024];   // per-thread partial sums
+    double alpha, beta, rho, rho0, thresh, rzmax, rn;
+    int ok, state;      // state: 0 iterating, 1 converged, 2 non-finite
+};
+
+// The stopping test sqrt(r.z) <= rtol sqrt(r0.z0) is evaluated as
+// r.z <= rzmax with rzmax the largest double whose correctly rounded square
+// root does not exceed the threshold (sqrt is monotone), found once per solve:
+// the same decision without a square root per iteration.
+__device__ __forceinline__ double largest_with_sqrt_at_most(double thresh) {
+    double r = thresh * thresh;
+    for (int k = 0; k < 64 && !(sqrt(r) <= thresh); ++k) r = nextafter(r, 0.0);
+    for (int k = 0; k < 64; ++k) {
+        const double up = nextafter(r, INFINITY);
+        if (!(sqrt(up) <= thresh)) break;
+        r = up;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void cg_after_rho0(CgShared& S, double tot, double rtol) {
+    S.rho0 = tot;
+    S.rho = tot;
+    S.rn = tot;
+    S.thresh = rtol * sqrt(tot);
+    S.rzmax = largest_with_sqrt_at_most(S.thresh);
+    S.state = !isfinite(tot) ? 2 : (tot == 0.0 ? 1 : 0);
+}
+__device__ __forceinline__ void cg_after_pq(CgShared& S, double pq) { S.alpha = S.rho / pq; }
+__device__ __forceinline__ void cg_after_rz(CgShared& S, double rn) {
+    S.rn = rn;
+    if (!isfinite(rn)) {
+        S.state = 2;
+    } else if (rn >= 0.0 && rn <= S.rzmax) {
+        S.state = 1;
+    } else {
+        S.beta = rn / S.rho;
+        S.rho = rn;
+    }
+}
+// final relative preconditioned residual sqrt(r.z / r0.z0)
+__device__ __forceinline__ double cg_relres(const CgShared& S) {
+    return S.rho0 > 0.0 ? sqrt(fabs(S.rn) / S.rho0) : 0.0;
+}
+
+// Jacobi-PCG on the restricted node system (diagonal preconditioner), whole
+// solve in one cooperative launch, vectors in global memory (any size).
+//
+// The iteration is the standard preconditioned CG, arranged with two grid-wide
+// synchronisation points per iteration: the matrix is applied to z = D^-1 r,
+// and p and q = A p follow from p = z + beta p, q = A z + beta q (the same
+// iterates in exact arithmetic as q = A p; rounding differs only in the order
+// of the additions).  Per iteration:
+//   phase A: s = A z (gathers z of neighbouring rows), p, q updates, p.q
+//            -> grid sum, alpha = rho / p.q
+//   phase B: x += alpha p, r -= alpha q, z = D^-1 r (published), r.z
+//            -> grid sum, convergence test, beta
+// Rows are processed grid-stride; each thread owns the same rows in every
+// phase.  Block totals are added in a fixed order by every block, so all
+// blocks take identical decisions.
+__global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
+    __shared__ CgShared S;
     const int G = gridDim.x;
     const int stride = G * blockDim.x;
     const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int ld = P.ld;
+    const double c = P.c;
     unsigned epoch = 0;
     int buf = 0;
 
     double part = 0.0;
     for (int i = i0; i < P.n; i += stride) {
-        const double d = P.mc[i] * (1.0 + P.c * P.J[i]) + P.c * P.kdc[i];
-        if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
         P.dA[i] = d;
+        P.idA[i] = id;
         const double r = P.b[i];
-        const double z = r / d;
+        const double z = r * id;
         P.r[i] = r;
-        P.p[i] = z;
+        P.z[i] = z;
+        P.p[i] = 0.0;
+        P.q[i] = 0.0;
         P.x[i] = 0.0;
         part += r * z;
     }
-    double s = block_sum(part, sh);
-    if (threadIdx.x == 0) P.part[buf * G + blockIdx.x] = s;
     if (P.inject_fault && blockIdx.x == G - 1) {
         // leave without arriving: every other block's bounded wait runs out
         if (G == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
         return;
     }
-    if (!grid_sync(P.bar, epoch, P.budget, P.err)) return;
-    const double rho0 = sum_partials(P.part + buf * G, G);
-    buf ^= 1;
-
-    int it = 0;
-    double relres = 0.0;
-    bool done = (rho0 == 0.0);
-    if (!isfinite(rho0)) {
-        if (i0 == 0) raise_error(P.err, SDC_E_NONFINITE);
+    if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                     [&](double t) { cg_after_rho0(S, t, P.rtol); }))
         return;
-    }
-    const double thresh = P.rtol * sqrt(rho0);
-    double rho = rho0;
-    while (!done) {
+    buf ^= 1;
+    int it = 0;
+    double beta = 0.0;
+    while (S.state == 0) {
         if (it >= P.maxit) {
             if (i0 == 0) raise_error(P.err, SDC_E_CG_NOCONV);
             break;
         }
         ++it;
-        // q = A p, p.q
+        // s = A z; p = z + beta p; q = s + beta q; p.q
         part = 0.0;
         for (int i = i0; i < P.n; i += stride) {
             const int len = P.alen[i];
             double acc = 0.0;
             for (int t = 0; t < len; ++t)
-                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.p + P.acol[(size_t)t * ld + i]);
-            const double pi = __ldcg(P.p + i);
-            const double qi = P.dA[i] * pi + P.c * acc;
+                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.z + P.acol[(size_t)t * ld + i]);
+            const double zi = __ldcg(P.z + i);
+            const double si = P.dA[i] * zi + c * acc;
+            const double pi = zi + beta * P.p[i];
+            const double qi = si + beta * P.q[i];
+            P.p[i] = pi;
             P.q[i] = qi;
             part += pi * qi;
         }
-        s = block_sum(part, sh);
-        if (threadIdx.x == 0) P.part[buf * G + blockIdx.x] = s;
-        if (!grid_sync(P.bar, epoch, P.budget, P.err)) return;
-        const double pq = sum_partials(P.part + buf * G, G);
+        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                         [&](double t) { cg_after_pq(S, t); }))
+            return;
         buf ^= 1;
-        const double alpha = rho / pq;
-        // x += alpha p, r -= alpha q, z = r / diag, r.z
+        const double alpha = S.alpha;
+        // x += alpha p, r -= alpha q, z = D^-1 r, r.z
         part = 0.0;
         for (int i = i0; i < P.n; i += stride) {
-            const double pi = __ldcg(P.p + i);
-            P.x[i] += alpha * pi;
+            P.x[i] += alpha * P.p[i];
             const double r = P.r[i] - alpha * P.q[i];
             P.r[i] = r;
-            const double z = r / P.dA[i];
+            const double z = r * P.idA[i];
             P.z[i] = z;
             part += r * z;
         }
-        s = block_sum(part, sh);
-        if (threadIdx.x == 0) P.part[buf * G + blockIdx.x] = s;
-        if (!grid_sync(P.bar, epoch, P.budget, P.err)) return;
-        const double rho_new = sum_partials(P.part + buf * G, G);
-        buf ^= 1;
-        relres = sqrt(fabs(rho_new) / rho0);
-        if (!isfinite(rho_new)) {
-            if (i0 == 0) raise_error(P.err, SDC_E_NONFINITE);
+        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                         [&](double t) { cg_after_rz(S, t); }))
             return;
-        }
-        if (sqrt(rho_new) <= thresh) break;
-        const double beta = rho_new / rho;
-        rho = rho_new;
-        for (int i = i0; i < P.n; i += stride) P.p[i] = P.z[i] + beta * __ldcg(P.p + i);
-        if (!grid_sync(P.bar, epoch, P.budget, P.err)) return;
+        buf ^= 1;
+        beta = S.beta;
+    }
+    if (S.state == 2) {
+        if (i0 == 0) raise_error(P.err, SDC_E_NONFINITE);
+        return;
     }
     if (i0 == 0) {
         *P.iters_out = it;
-        *P.relres_out = relres;
+        *P.relres_out = cg_relres(S);
     }
-    // x is complete in every block: the last barrier followed its update.
+    // x is complete in every block: the last grid sum followed its update.
     if (P.m + 1 < P.M) {
         for (int i = i0; i < P.n; i += stride) {
             const int len = P.alen[i];
@@ -243,6 +298,278 @@ __global__ void __launch_bounds__(1024) k_pcg(CgParams P) {
                 P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
         }
     }
+}
+
+// Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
+// block b owns the contiguous rows [b L, b L + L); their x, r, z, p, q,
+// diagonal and reciprocal diagonal stay in shared memory for the whole solve.
+// Only z is published to global memory (coalesced) for the neighbours'
+// gathers; the matrix is read through the read-only path.
+__global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    const int G = gridDim.x, B = blockDim.x, t = threadIdx.x;
+    const int L = P.L, ld = P.ld;
+    const int r0 = blockIdx.x * L;
+    const int nl = max(0, min(P.n - r0, L));
+    double* __restrict__ sx = sm;
+    double* __restrict__ sr = sm + L;
+    double* __restrict__ sz = sm + 2 * L;
+    double* __restrict__ sp = sm + 3 * L;
+    double* __restrict__ sq = sm + 4 * L;
+    double* __restrict__ sd = sm + 5 * L;
+    double* __restrict__ si = sm + 6 * L;
+    double* __restrict__ zg = P.z;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    unsigned epoch = 0;
+    int buf = 0;
+
+    double part = 0.0;
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
+        sd[l] = d;
+        si[l] = id;
+        const double r = P.b[i];
+        const double z = r * id;
+        sr[l] = r;
+        sz[l] = z;
+        zg[i] = z;
+        sp[l] = 0.0;
+        sq[l] = 0.0;
+        sx[l] = 0.0;
+        part += r * z;
+    }
+    if (P.inject_fault && blockIdx.x == G - 1) {
+        if (G == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                     [&](double tot) { cg_after_rho0(S, tot, P.rtol); }))
+        return;
+    buf ^= 1;
+    int it = 0;
+    double beta = 0.0;
+    while (S.state == 0) {
+        if (it >= P.maxit) {
+            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        part = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(zg + __ldg(acol + (size_t)k * ld + i));
+            const double zi = sz[l];
+            const double s_i = sd[l] * zi + c * acc;
+            const double pi = zi + beta * sp[l];
+            const double qi = s_i + beta * sq[l];
+            sp[l] = pi;
+            sq[l] = qi;
+            part += pi * qi;
+        }
+        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                         [&](double tot) { cg_after_pq(S, tot); }))
+            return;
+        buf ^= 1;
+        const double alpha = S.alpha;
+        part = 0.0;
+        for (int l = t; l < nl; l += B) {
+            sx[l] += alpha * sp[l];
+            const double r = sr[l] - alpha * sq[l];
+            sr[l] = r;
+            const double z = r * si[l];
+            sz[l] = z;
+            zg[r0 + l] = z;
+            part += r * z;
+        }
+        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
+                         [&](double tot) { cg_after_rz(S, tot); }))
+            return;
+        buf ^= 1;
+        beta = S.beta;
+    }
+    if (S.state == 2) {
+        if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+    }
+    for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
+    if (P.m + 1 < P.M) {
+        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            const double xi = sx[l];
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(P.x + __ldg(acol + (size_t)k * ld + i));
+            const double corr = P.kdc[i] * xi + acc + P.mc[i] * P.J[i] * xi;
+            for (int mm = P.m + 1; mm < P.M; ++mm)
+                P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
+        }
+    }
+}
+
+// Thread-block-cluster variant for small active sets (n <= C * L rows, one
+// cluster of C CTAs).  The same iteration as k_pcg_smem; z and x of other CTAs
+// are read from their shared memory (distributed shared memory), block totals
+// are exchanged through shared memory, and the hardware cluster barrier
+// replaces the global arrival counter, so the iteration loop touches no global
+// memory besides the (read-only) matrix.  Every CTA takes the same decisions
+// (same totals, same order) and leaves only after a final cluster barrier, so
+// no CTA reads the shared memory of one that has exited.
+__global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    __shared__ double cpart[2];
+    __shared__ double* zr[16];
+    __shared__ double* xr[16];
+    __shared__ double* pr[16];
+    const int B = blockDim.x, t = threadIdx.x;
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int L = P.L, ld = P.ld;
+    const int r0 = rank * L;
+    const int nl = max(0, min(P.n - r0, L));
+    const int nact = min(B, nl);
+    double* __restrict__ sx = sm;
+    double* __restrict__ sr = sm + L;
+    double* __restrict__ sz = sm + 2 * L;
+    double* __restrict__ sp = sm + 3 * L;
+    double* __restrict__ sq = sm + 4 * L;
+    double* __restrict__ sd = sm + 5 * L;
+    double* __restrict__ si = sm + 6 * L;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    if (t < C) {
+        zr[t] = cl.map_shared_rank(sz, t);
+        xr[t] = cl.map_shared_rank(sx, t);
+        pr[t] = cl.map_shared_rank(cpart, t);
+    }
+    int buf = 0;
+    // cluster-wide sum; lane 0 of warp 0 derives the scalars from the total
+    auto reduce = [&](double v, auto&& on_total) {
+        S.red[t] = v;
+        __syncthreads();
+        if (t < 32) {
+            double s = 0.0;
+            for (int i = t; i < nact; i += 32) s += S.red[i];
+            s = warp_sum(s);
+            if (t == 0) cpart[buf] = s;
+        }
+        cl.sync();
+        if (t < 32) {
+            double tot = t < C ? pr[t][buf] : 0.0;
+            tot = warp_sum(tot);
+            if (t == 0) on_total(tot);
+        }
+        buf ^= 1;
+        __syncthreads();
+    };
+
+    double part = 0.0;
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
+        sd[l] = d;
+        si[l] = id;
+        const double r = P.b[i];
+        const double z = r * id;
+        sr[l] = r;
+        sz[l] = z;
+        sp[l] = 0.0;
+        sq[l] = 0.0;
+        sx[l] = 0.0;
+        part += r * z;
+    }
+    reduce(part, [&](double tot) { cg_after_rho0(S, tot, P.rtol); });
+    int it = 0;
+    double beta = 0.0;
+    while (S.state == 0) {
+        if (it >= P.maxit) {
+            if (rank == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        part = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k) {
+                const int j = __ldg(acol + (size_t)k * ld + i);
+                const int owner = j / L;
+                acc += __ldg(aval + (size_t)k * ld + i) * zr[owner][j - owner * L];
+            }
+            const double zi = sz[l];
+            const double s_i = sd[l] * zi + c * acc;
+            const double pi = zi + beta * sp[l];
+            const double qi = s_i + beta * sq[l];
+            sp[l] = pi;
+            sq[l] = qi;
+            part += pi * qi;
+        }
+        reduce(part, [&](double tot) { cg_after_pq(S, tot); });
+        const double alpha = S.alpha;
+        part = 0.0;
+        for (int l = t; l < nl; l += B) {
+            sx[l] += alpha * sp[l];
+            const double r = sr[l] - alpha * sq[l];
+            sr[l] = r;
+            const double z = r * si[l];
+            sz[l] = z;
+            part += r * z;
+        }
+        reduce(part, [&](double tot) { cg_after_rz(S, tot); });
+        beta = S.beta;
+    }
+    if (S.state == 2) {
+        if (rank == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+    } else {
+        if (rank == 0 && t == 0) {
+            *P.iters_out = it;
+            *P.relres_out = cg_relres(S);
+        }
+        for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
+        if (P.m + 1 < P.M) {
+            cl.sync();   // every CTA's x is final
+            for (int l = t; l < nl; l += B) {
+                const int i = r0 + l;
+                const int len = __ldg(alen + i);
+                const double xi = sx[l];
+                double acc = 0.0;
+                for (int k = 0; k < len; ++k) {
+                    const int j = __ldg(acol + (size_t)k * ld + i);
+                    const int owner = j / L;
+                    acc += __ldg(aval + (size_t)k * ld + i) * xr[owner][j - owner * L];
+                }
+                const double corr = P.kdc[i] * xi + acc + P.mc[i] * P.J[i] * xi;
+                for (int mm = P.m + 1; mm < P.M; ++mm)
+                    P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
+            }
+        }
+    }
+    cl.sync();   // nobody leaves while another CTA may still read its shared memory
 }
 
 template <int M>
@@ -467,9 +794,40 @@ int pcg_max_blocks(int block) {
     return sms * per;
 }
 
+int pcg_cluster_size(int block) {
+    cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(7 * kSmemRows * sizeof(double)));
+    cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int C = 16; C >= 2; C /= 2) {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(C);
+        lc.blockDim = dim3(block);
+        lc.dynamicSmemBytes = (size_t)7 * kSmemRows * sizeof(double);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_pcg_cluster, &lc) == cudaSuccess &&
+            nclusters >= 1)
+            return C;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+int pcg_sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
-               long long budget, int sweep, int block, int max_blocks, int inject_fault,
-               StepBuffers& B, cudaStream_t s) {
+               int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
     CgParams P;
     P.n = n;
     P.ld = B.ld;
@@ -487,12 +845,13 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.p = B.p;
     P.q = B.q;
     P.dA = B.dA;
+    P.idA = B.idA;
     P.part = B.part;
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
     P.rtol = rtol;
     P.maxit = maxit;
-    P.budget = budget;
+    P.budget = cfg.budget;
     P.iters_out = &B.sc->cg_iters[sweep * kMaxM + m];
     P.relres_out = &B.sc->cg_relres[sweep * kMaxM + m];
     P.m = m;
@@ -500,13 +859,67 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.dt = dt;
     P.R = B.R;
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = j < co.M ? co.Qh[j * kMaxM + m] : 0.0;
-    P.inject_fault = inject_fault;
-    int grid = std::min(max_blocks, nblk(n, block));
-    if (grid < 1) grid = 1;
+    P.inject_fault = cfg.inject_fault;
+    P.L = 0;
     cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
     void* args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(block), args,
-                                                0, s);
+    // cluster variant: one cluster of cfg.cluster CTAs for small active sets
+    if (cfg.variant != 1 && cfg.cluster > 0 && !cfg.inject_fault && n <= cfg.cluster_rows &&
+        n <= cfg.cluster * kSmemRows) {
+        static bool cattr_set = false;
+        if (!cattr_set) {
+            cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(7 * kSmemRows * sizeof(double)));
+            cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cattr_set = true;
+        }
+        // enough CTAs for the FP64 work, never more rows per CTA than fit
+        int C = std::min(cfg.cluster, std::max(nblk(n, cfg.cluster_rows_per_cta), nblk(n, kSmemRows)));
+        C = std::max(C, 1);
+        P.L = nblk(n, C);
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(C);
+        lc.blockDim = dim3(cfg.smem_block);
+        lc.dynamicSmemBytes = (size_t)7 * P.L * sizeof(double);
+        lc.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&lc, k_pcg_cluster, P);
+        return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+    }
+    // shared-memory variant: one block per SM at most, each owning <= kSmemRows rows
+    const bool smem_ok = cfg.variant != 1 && n <= cfg.sms * kSmemRows;
+    if (smem_ok && cfg.variant != 1) {
+        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+        int grid = std::max(nblk(n, kSmemRows), nblk(n, rpb));
+        grid = std::min(grid, cfg.sms);
+        if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
+        grid = std::max(grid, nblk(n, kSmemRows));
+        grid = std::max(grid, 1);
+        P.L = nblk(n, grid);
+        const size_t smem = (size_t)7 * P.L * sizeof(double);
+        // the largest systems keep every SM's FP64 pipe busy with 32 warps;
+        // smaller ones favour shorter block-level reductions
+        const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_pcg_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(7 * kSmemRows * sizeof(double)));
+            attr_set = true;
+        }
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_smem, dim3(grid),
+                                                    dim3(blk), args, smem, s);
+        return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+    }
+    int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));
+    if (grid < 1) grid = 1;
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(cfg.block),
+                                                args, 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 
