@@ -191,6 +191,26 @@ sdc_status sdc_get_info(const sdc_ctx* ctx, int* n_nodes, long long* nnz, int* m
  * included) and the lumped mass m; arrays sized by sdc_get_info. */
 sdc_status sdc_get_matrix(const sdc_ctx* ctx, int* row_ptr, int* col, double* val, double* mass);
 
+/* One node system of eq. final-sdc solved on its own (Sec. 3.2; Jacobi-PCG as
+ * in Sec. 4.2):
+ *     (diag(mass .* (1 + c J)) + c K) x = b,
+ * by preconditioned CG from x = 0 with the diagonal preconditioner, stopping
+ * when sqrt(r'z) <= rtol sqrt(r0'z0).  K is given by its diagonal d_kdiag[n]
+ * and its off-diagonal part in column-major ELL slots: row i holds
+ * d_len[i] <= width entries, entry t at d_val[t * ld + i], column
+ * d_col[t * ld + i] in [0, n); ld >= n.  Every array is caller-owned device
+ * memory of the current device; d_x receives the solution.  The workspace
+ * (6 n doubles plus a few per SM) is allocated and freed inside the call, which
+ * synchronises `stream` (a cudaStream_t, NULL = legacy default).  iters and
+ * relres (host, may be NULL) receive the iteration count and the final
+ * sqrt(r'z / r0'z0).  Errors: SDC_E_INVALID (nothing launched),
+ * SDC_E_NOMEM, SDC_E_CG_NOCONV, SDC_E_NONFINITE, SDC_E_DOMAIN (a non-positive
+ * diagonal); details from sdc_last_error(NULL) on the calling thread. */
+sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int* d_len, int ld,
+                         int width, const double* d_kdiag, const double* d_mass, const double* d_J,
+                         double c, const double* d_b, double* d_x, double rtol, int maxit,
+                         int* iters, double* relres, void* stream);
+
 /* One-line description of the last failure on ctx (never NULL). */
 const char* sdc_last_error(const sdc_ctx* ctx);
 const char* sdc_status_string(int status);

@@ -74,6 +74,8 @@ SIGNATURES = {
     "sdc_get_active": (C.c_int, [_vp, C.c_int, _ip, _ip]),
     "sdc_get_info": (C.c_int, [_vp, _ip, C.POINTER(C.c_longlong), _ip]),
     "sdc_get_matrix": (C.c_int, [_vp, _ip, _ip, _dp, _dp]),
+    "sdc_pcg_solve": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp,
+                                C.c_double, _vp, _vp, C.c_double, C.c_int, _ip, _dp, _vp]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_status_string": (C.c_char_p, [C.c_int]),
     "sdc_destroy": (None, [_vp]),
@@ -232,3 +234,43 @@ class Context:
         _check(load().sdc_get_matrix(self._h, rp.ctypes.data_as(_ip), ci.ctypes.data_as(_ip),
                                      val.ctypes.data_as(_dp), mass.ctypes.data_as(_dp)), self._h)
         return rp, ci, val, mass
+
+
+def csr_to_ell(rp, ci, val, n):
+    """Split a CSR matrix into its diagonal and column-major ELL off-diagonal
+    slots (marshalling for sdc_pcg_solve).  Returns kdiag, ell_val, ell_col,
+    ell_len, ld, width."""
+    rp = np.asarray(rp)
+    ci = np.asarray(ci)
+    val = np.asarray(val, dtype=np.float64)
+    kdiag = np.zeros(n)
+    rows = []
+    width = 0
+    for i in range(n):
+        cols = ci[rp[i]:rp[i + 1]]
+        vals = val[rp[i]:rp[i + 1]]
+        off = cols != i
+        kdiag[i] = vals[~off].sum()
+        rows.append((cols[off], vals[off]))
+        width = max(width, int(off.sum()))
+    ld = (n + 31) // 32 * 32
+    ev = np.zeros((max(width, 1), ld))
+    ec = np.zeros((max(width, 1), ld), dtype=np.int32)
+    el = np.zeros(n, dtype=np.int32)
+    for i, (cols, vals) in enumerate(rows):
+        el[i] = len(cols)
+        ev[:len(cols), i] = vals
+        ec[:len(cols), i] = cols
+    return kdiag, ev, ec, el, ld, width
+
+
+def pcg_solve(n, ell_val, ell_col, ell_len, ld, width, kdiag, mass, J, c, b, x, rtol=1e-10,
+              maxit=10000, stream=0):
+    """sdc_pcg_solve on device tensors (or integer device addresses)."""
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    _check(load().sdc_pcg_solve(int(n), _vp(_ptr(ell_val)), _vp(_ptr(ell_col)), _vp(_ptr(ell_len)),
+                                int(ld), int(width), _vp(_ptr(kdiag)), _vp(_ptr(mass)),
+                                _vp(_ptr(J)), float(c), _vp(_ptr(b)), _vp(_ptr(x)), float(rtol),
+                                int(maxit), C.byref(it), C.byref(rr), _vp(stream)))
+    return it.value, rr.value

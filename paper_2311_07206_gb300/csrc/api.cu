@@ -556,6 +556,60 @@ sdc_status sdc_get_matrix(const sdc_ctx* cc, int* row_ptr, int* col, double* val
     return SDC_OK;
 }
 
+sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int* d_len, int ld,
+                         int width, const double* d_kdiag, const double* d_mass, const double* d_J,
+                         double c, const double* d_b, double* d_x, double rtol, int maxit,
+                         int* iters, double* relres, void* stream) {
+    g_create_error.clear();
+    if (n < 1 || ld < n || width < 0 || !d_len || !d_kdiag || !d_mass || !d_J || !d_b || !d_x ||
+        (width > 0 && (!d_val || !d_col)) || !(rtol > 0.0) || maxit < 1 || !std::isfinite(c))
+        return fail(nullptr, SDC_E_INVALID, "sdc_pcg_solve: invalid arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int block = 256;
+    const int maxb = pcg_max_blocks(block);
+    // workspace: 6 vectors, 2 * maxb partial sums, then the scalars
+    const size_t nd = (size_t)6 * n + 2 * (size_t)maxb + 2;
+    char* ws = nullptr;
+    if (cudaMalloc(&ws, nd * sizeof(double) + 64) != cudaSuccess)
+        return fail(nullptr, SDC_E_NOMEM, "sdc_pcg_solve: workspace allocation failed");
+    double* v = (double*)ws;
+    PcgScratch w;
+    w.r = v; w.z = v + n; w.p = v + 2 * (size_t)n; w.q = v + 3 * (size_t)n;
+    w.dA = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.part = v + 6 * (size_t)n;
+    w.max_blocks = maxb;
+    w.relres = v + 6 * (size_t)n + 2 * (size_t)maxb;
+    unsigned* sc = (unsigned*)(w.relres + 1);
+    w.bar = sc;
+    w.err = (int*)(sc + 1);
+    w.iters = (int*)(sc + 2);
+    Ell A;
+    A.val = const_cast<double*>(d_val);
+    A.col = const_cast<int*>(d_col);
+    A.len = const_cast<int*>(d_len);
+    A.ld = ld;
+    A.width = width;
+    int status = SDC_OK;
+    int h[3] = {0, 0, 0};
+    double hr = 0.0;
+    cudaMemsetAsync(w.relres, 0, sizeof(double) + 3 * sizeof(unsigned), s);
+    if (launch_pcg_standalone(n, A, d_kdiag, d_mass, d_J, c, d_b, d_x, rtol, maxit, 4000000000LL,
+                              block, w, s) != SDC_OK) {
+        status = cuda_fail(nullptr, "sdc_pcg_solve launch");
+    } else {
+        cudaMemcpyAsync(h, sc, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hr, w.relres, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            status = cuda_fail(nullptr, "sdc_pcg_solve");
+        } else if (h[1] != 0) {
+            status = fail(nullptr, (sdc_status)h[1], "sdc_pcg_solve: %s", sdc_status_string(h[1]));
+        }
+    }
+    if (iters) *iters = h[2];
+    if (relres) *relres = hr;
+    cudaFree(ws);
+    return (sdc_status)status;
+}
+
 void sdc_destroy(sdc_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);

@@ -119,6 +119,24 @@ struct PcgConfig {
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
                int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
 int pcg_sm_count();
+
+// Workspace of one standalone PCG solve (caller-provided device memory).
+// r, z, p, q, dA, idA: n doubles each; part: 2 * max_blocks doubles;
+// bar, err, iters, relres: one value each, bar and err zero before the launch.
+struct PcgScratch {
+    double *r, *z, *p, *q, *dA, *idA, *part;
+    int max_blocks;
+    unsigned* bar;
+    int* err;
+    int* iters;
+    double* relres;
+};
+// Jacobi-PCG on (diag(mass (1 + c J)) + c K)[n x n] with the off-diagonal part
+// of K in A (ELL-R) and its diagonal in kdiag, using the global-vector kernel.
+int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double* mass,
+                          const double* J, double c, const double* b, double* x, double rtol,
+                          int maxit, long long budget, int block, const PcgScratch& w,
+                          cudaStream_t s);
 int pcg_cluster_size(int block);
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
                    const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s);

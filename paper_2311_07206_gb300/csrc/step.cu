@@ -923,6 +923,51 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 
+int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double* mass,
+                          const double* J, double c, const double* b, double* x, double rtol,
+                          int maxit, long long budget, int block, const PcgScratch& w,
+                          cudaStream_t s) {
+    CgParams P;
+    P.n = n;
+    P.ld = A.ld;
+    P.aval = A.val;
+    P.acol = A.col;
+    P.alen = A.len;
+    P.mc = mass;
+    P.kdc = kdiag;
+    P.J = J;
+    P.c = c;
+    P.b = b;
+    P.x = x;
+    P.r = w.r;
+    P.z = w.z;
+    P.p = w.p;
+    P.q = w.q;
+    P.dA = w.dA;
+    P.idA = w.idA;
+    P.part = w.part;
+    P.bar = w.bar;
+    P.err = w.err;
+    P.rtol = rtol;
+    P.maxit = maxit;
+    P.budget = budget;
+    P.iters_out = w.iters;
+    P.relres_out = w.relres;
+    P.m = 0;
+    P.M = 1;            // no coupling into later nodes
+    P.dt = 0.0;
+    P.R = nullptr;
+    for (int j = 0; j < kMaxM; ++j) P.qh[j] = 0.0;
+    P.inject_fault = 0;
+    P.L = 0;
+    int grid = std::min(std::min(w.max_blocks, pcg_max_blocks(block)), nblk(n, block));
+    if (grid < 1) grid = 1;
+    void* args[] = {&P};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(block), args,
+                                                0, s);
+    return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+}
+
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
                    const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s) {
     dispatch_M(M, [&](auto mc) {
