@@ -211,6 +211,28 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
                          double c, const double* d_b, double* d_x, double rtol, int maxit,
                          int* iters, double* relres, void* stream);
 
+/* Largest n accepted by sdc_pcg_solve_noalloc. */
+#define SDC_PCG_NOALLOC_MAX_ROWS 65536
+
+/* sdc_pcg_solve for callers that cannot allocate device memory (the paper has
+ * no counterpart; this is a service of the library).  Same arguments, results
+ * and errors as sdc_pcg_solve, but no device memory is allocated or freed:
+ * the workspace is a static array of the library, reserved (about 3.2 MB) on
+ * every GPU that loads the library until the process exits.
+ *   - n <= SDC_PCG_NOALLOC_MAX_ROWS, else SDC_E_INVALID with a message from
+ *     sdc_last_error(NULL), and nothing is launched.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture starts on the device.
+ *   - Every call on a device uses the same array; calls that overlap on the GPU
+ *     (other streams, other host threads) race.  Serialise them.
+ * Meant for host frameworks that hand out all device memory from their own
+ * pool, and for time-critical loops where cudaMalloc/cudaFree may block. */
+sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const int* d_col, const int* d_len,
+                                 int ld, int width, const double* d_kdiag, const double* d_mass,
+                                 const double* d_J, double c, const double* d_b, double* d_x,
+                                 double rtol, int maxit, int* iters, double* relres, void* stream);
+
 /* One-line description of the last failure on ctx (never NULL). */
 const char* sdc_last_error(const sdc_ctx* ctx);
 const char* sdc_status_string(int status);

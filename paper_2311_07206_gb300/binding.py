@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libsdc_gb300.so")
 SDC_MAX_M = 8
 SDC_MAX_SWEEPS = 64
 SDC_N_PHASES = 5
+SDC_PCG_NOALLOC_MAX_ROWS = 65536
 PHASES = ("residual", "pcg", "update", "select", "extract")
 SDC_OK, SDC_E_INVALID, SDC_E_CUDA, SDC_E_NOMEM = 0, -1, -2, -3
 SDC_E_CG_NOCONV, SDC_E_TIMEOUT, SDC_E_NONFINITE, SDC_E_DOMAIN = -4, -5, -6, -7
@@ -76,6 +77,9 @@ SIGNATURES = {
     "sdc_get_matrix": (C.c_int, [_vp, _ip, _ip, _dp, _dp]),
     "sdc_pcg_solve": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp,
                                 C.c_double, _vp, _vp, C.c_double, C.c_int, _ip, _dp, _vp]),
+    "sdc_pcg_solve_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp,
+                                        _vp, C.c_double, _vp, _vp, C.c_double, C.c_int, _ip, _dp,
+                                        _vp]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_status_string": (C.c_char_p, [C.c_int]),
     "sdc_destroy": (None, [_vp]),
@@ -273,4 +277,19 @@ def pcg_solve(n, ell_val, ell_col, ell_len, ld, width, kdiag, mass, J, c, b, x, 
                                 int(ld), int(width), _vp(_ptr(kdiag)), _vp(_ptr(mass)),
                                 _vp(_ptr(J)), float(c), _vp(_ptr(b)), _vp(_ptr(x)), float(rtol),
                                 int(maxit), C.byref(it), C.byref(rr), _vp(stream)))
+    return it.value, rr.value
+
+
+def pcg_solve_noalloc(n, ell_val, ell_col, ell_len, ld, width, kdiag, mass, J, c, b, x,
+                      rtol=1e-10, maxit=10000, stream=0):
+    """sdc_pcg_solve_noalloc: the same solve, workspace in the library's static
+    device array (no device allocation; n <= SDC_PCG_NOALLOC_MAX_ROWS; calls
+    that overlap on the GPU race)."""
+    it = C.c_int(0)
+    rr = C.c_double(0.0)
+    _check(load().sdc_pcg_solve_noalloc(int(n), _vp(_ptr(ell_val)), _vp(_ptr(ell_col)),
+                                        _vp(_ptr(ell_len)), int(ld), int(width), _vp(_ptr(kdiag)),
+                                        _vp(_ptr(mass)), _vp(_ptr(J)), float(c), _vp(_ptr(b)),
+                                        _vp(_ptr(x)), float(rtol), int(maxit), C.byref(it),
+                                        C.byref(rr), _vp(stream)))
     return it.value, rr.value

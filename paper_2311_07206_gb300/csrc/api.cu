@@ -41,6 +41,14 @@ namespace {
 
 thread_local std::string g_create_error;
 
+}  // namespace
+
+namespace sdc {
+void set_thread_error(const char* msg) { g_create_error = msg; }
+}  // namespace sdc
+
+namespace {
+
 sdc_status fail(sdc_ctx* c, sdc_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;

@@ -1,0 +1,130 @@
+// sdc_pcg_solve_noalloc: the node-system solve of sdc_pcg_solve for callers
+// that must not allocate device memory themselves or through this library.
+//
+// Typical such callers: a host application or simulation framework that owns
+// every byte of device memory through its own pool and forbids raw cudaMalloc
+// (it would bypass the pool's budget or fragment it), and time-critical loops
+// in which cudaMalloc/cudaFree may block or synchronise the device.  They pass
+// inputs and outputs as usual; the solver's workspace (six vectors, per-block
+// partial sums, the barrier counter and status words) lives in the file-scope
+// array below instead of a per-call allocation.
+//
+// Costs and limits of that choice:
+//   * every GPU that loads the library reserves the array (about 3.2 MB) until
+//     the process exits;
+//   * n is limited to SDC_PCG_NOALLOC_MAX_ROWS rows;
+//   * all calls on a device share the one array and it keeps the last call's
+//     contents, so calls that overlap on the GPU (two streams, two host
+//     threads) race and corrupt each other; serialise them;
+//   * host code cannot use the array's name as a device address, so the first
+//     call on each device looks the address up (cudaGetSymbolAddress, with that
+//     device current) and caches it; make that first call before any stream
+//     capture is started on the device.
+
+#include <cstdio>
+#include <mutex>
+
+#include "sdc_internal.h"
+
+namespace {
+
+constexpr int kMaxRows = SDC_PCG_NOALLOC_MAX_ROWS;
+constexpr int kMaxBlocks = 4096;   // partial-sum slots per buffer
+constexpr size_t kVecDoubles = 6 * (size_t)kMaxRows;
+constexpr size_t kScalarDoubles = 4;   // relres, then barrier counter, error, iterations
+constexpr size_t kScratchDoubles = kVecDoubles + 2 * (size_t)kMaxBlocks + kScalarDoubles;
+
+static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_scratch_addr[kMaxDevices] = {};
+
+sdc_status reject(sdc_status st, const char* msg) {
+    sdc::set_thread_error(msg);
+    return st;
+}
+
+}  // namespace
+
+extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const int* d_col,
+                                            const int* d_len, int ld, int width,
+                                            const double* d_kdiag, const double* d_mass,
+                                            const double* d_J, double c, const double* d_b,
+                                            double* d_x, double rtol, int maxit, int* iters,
+                                            double* relres, void* stream) {
+    sdc::set_thread_error("");
+    if (n > kMaxRows) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "sdc_pcg_solve_noalloc: n = %d exceeds the static workspace of %d rows", n,
+                 kMaxRows);
+        return reject(SDC_E_INVALID, buf);
+    }
+    if (n < 1 || ld < n || width < 0 || !d_len || !d_kdiag || !d_mass || !d_J || !d_b || !d_x ||
+        (width > 0 && (!d_val || !d_col)) || !(rtol > 0.0) || maxit < 1 || !(c - c == 0.0))
+        return reject(SDC_E_INVALID, "sdc_pcg_solve_noalloc: invalid arguments");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return reject(SDC_E_CUDA, "sdc_pcg_solve_noalloc: no current device");
+    if (dev < 0 || dev >= kMaxDevices)
+        return reject(SDC_E_INVALID, "sdc_pcg_solve_noalloc: device ordinal out of range");
+    double* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!g_scratch_addr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
+            if (e != cudaSuccess || !p) {
+                char buf[200];
+                snprintf(buf, sizeof buf,
+                         "sdc_pcg_solve_noalloc: cudaGetSymbolAddress failed: %s",
+                         cudaGetErrorString(e));
+                return reject(SDC_E_CUDA, buf);
+            }
+            g_scratch_addr[dev] = (double*)p;
+        }
+        base = g_scratch_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    sdc::PcgScratch w;
+    w.r = base;
+    w.z = base + (size_t)n;
+    w.p = base + 2 * (size_t)n;
+    w.q = base + 3 * (size_t)n;
+    w.dA = base + 4 * (size_t)n;
+    w.idA = base + 5 * (size_t)n;
+    w.part = base + kVecDoubles;
+    w.max_blocks = kMaxBlocks;
+    w.relres = base + kVecDoubles + 2 * (size_t)kMaxBlocks;
+    unsigned* sc = (unsigned*)(w.relres + 1);
+    w.bar = sc;
+    w.err = (int*)(sc + 1);
+    w.iters = (int*)(sc + 2);
+    sdc::Ell A;
+    A.val = const_cast<double*>(d_val);
+    A.col = const_cast<int*>(d_col);
+    A.len = const_cast<int*>(d_len);
+    A.ld = ld;
+    A.width = width;
+    // the barrier counter, error word and outputs must start at zero on every call
+    if (cudaMemsetAsync(w.relres, 0, kScalarDoubles * sizeof(double), s) != cudaSuccess)
+        return reject(SDC_E_CUDA, "sdc_pcg_solve_noalloc: clearing the status words failed");
+    if (sdc::launch_pcg_standalone(n, A, d_kdiag, d_mass, d_J, c, d_b, d_x, rtol, maxit,
+                                   4000000000LL, 256, w, s) != SDC_OK)
+        return reject(SDC_E_CUDA, "sdc_pcg_solve_noalloc: launch failed");
+    int h[3] = {0, 0, 0};
+    double hr = 0.0;
+    if (cudaMemcpyAsync(h, sc, 3 * sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&hr, w.relres, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return reject(SDC_E_CUDA, "sdc_pcg_solve_noalloc: reading the status failed");
+    if (iters) *iters = h[2];
+    if (relres) *relres = hr;
+    if (h[1] != 0) {
+        char buf[120];
+        snprintf(buf, sizeof buf, "sdc_pcg_solve_noalloc: %s", sdc_status_string(h[1]));
+        return reject((sdc_status)h[1], buf);
+    }
+    return SDC_OK;
+}

@@ -119,6 +119,8 @@ struct PcgConfig {
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
                int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
 int pcg_sm_count();
+// Message returned by sdc_last_error(NULL) on the calling thread.
+void set_thread_error(const char* msg);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
 // r, z, p, q, dA, idA: n doubles each; part: 2 * max_blocks doubles;
