@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5"], default="w1")
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w3"], default="w1",
+                    help="w3: 96-instance batch, batched launches vs per-instance launches")
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -401,10 +402,93 @@ def run_gb300(args):
     return 0
 
 
+def run_batch(args):
+    """96 2D instances (sides log-uniform in [64, 512], D ~ U[0.5, 2]): one
+    batched step of all instances vs the same steps as per-instance launches."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Batch, Context, default_options
+
+    insts = W.batch_instances()
+    wl0 = insts[0]
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream(dev)
+    opts = default_options(profile=0)
+    batch = Batch(insts, options=opts, stream=stream.cuda_stream)
+    solos = [Context.from_workload(wl, options=opts, stream=stream.cuda_stream) for wl in insts]
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    v0 = np.concatenate([wl.v0 for wl in insts])
+    w0 = np.concatenate([wl.w0 for wl in insts])
+
+    def run_batched(steps, timed):
+        v, w = t64(v0), t64(w0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)] if timed else []
+        ads = 0
+        for n in range(steps):
+            if timed:
+                ev[n][0].record(stream)
+            st = batch.step(v, w, n * wl0.dt, wl0.dt, wl0.sweeps, wl0.tol)
+            if timed:
+                ev[n][1].record(stream)
+            ads += sum(st.n_active[:st.sweeps_run])
+        torch.cuda.synchronize(dev)
+        return v, (sum(a.elapsed_time(b) for a, b in ev) if timed else None), ads
+
+    def run_solo(steps, timed):
+        vs = [t64(wl.v0) for wl in insts]
+        ws = [t64(wl.w0) for wl in insts]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for n in range(steps):
+            for b, wl in enumerate(insts):
+                solos[b].step(vs[b], ws[b], n * wl.dt, wl.dt, wl.sweeps, wl.tol, want_stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return vs, (e0.elapsed_time(e1) if timed else None)
+
+    run_batched(Wm, False)
+    run_solo(Wm, False)
+    barrier(world)
+    clocks = Clocks(str(local))
+    vb, ms_b, ads = run_batched(K, True)
+    clk = clocks.stop()
+    vs, ms_s = run_solo(K, True)
+    vbh = vb.cpu().numpy()
+    diff = max(float(np.abs(vbh[batch.offsets[b]:batch.offsets[b + 1]] - vs[b].cpu().numpy()).max())
+               for b in range(len(insts)))
+    ms_b = max_over_ranks(ms_b, world)
+    line = {"metric": "batched SDC steps/s, 96 2D instances (one step = every instance)",
+            "value": world * K / (ms_b / 1e3), "unit": "steps/s", "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": ms_b / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch_96_2d_instances", "n_dofs": int(batch.n),
+                       "instances": len(insts), "M": wl0.M, "dt_ms": wl0.dt,
+                       "sweeps": wl0.sweeps, "TOL": wl0.tol, "l2": "inputs larger than L2"},
+            "instance_steps_per_s": world * K * len(insts) / (ms_b / 1e3),
+            "active_dof_sweeps_per_s": world * ads / (ms_b / 1e3),
+            "per_instance_launches": {"value": K / (ms_s / 1e3), "unit": "steps/s",
+                                      "ms_per_step": ms_s / K},
+            "speedup_vs_per_instance": ms_s / ms_b,
+            "max_abs_diff_batched_vs_per_instance": diff,
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    for c in solos:
+        c.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "w3":
+        return run_batch(args)
     return run_gb300(args)
 
 

@@ -211,6 +211,49 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
                          double c, const double* d_b, double* d_x, double rtol, int maxit,
                          int* iters, double* relres, void* stream);
 
+/* ---- Batches: many independent instances advanced by the same launches ----
+ *
+ * A batch stacks instances (meshes of the same dimension, each with its own
+ * conductivity, stimulus and size) as disjoint diagonal blocks of one system.
+ * Every kernel of the step runs once for the whole batch; the node solves run
+ * one independent Jacobi-PCG per instance inside one cooperative launch (own
+ * reductions, own stopping test, own iteration count), so each instance
+ * follows the same iteration as a solo context up to the rounding order of
+ * its dot products.  All instances share M, the ionic parameters, the options,
+ * dt, the number of sweeps, TOL and one stimulus window. */
+typedef struct sdc_batch sdc_batch;
+
+/* meshes: n_instances meshes (host, copied).  Instance b owns the dofs
+ * offsets[b] .. offsets[b+1]-1 of the batch state (see sdc_batch_info), in its
+ * own node order. */
+sdc_status sdc_batch_create(sdc_batch** out, const sdc_mesh* meshes, int n_instances,
+                            const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream);
+
+/* n_instances and offsets[n_instances + 1] (host; either may be NULL). */
+sdc_status sdc_batch_info(const sdc_batch* batch, int* n_instances, int* offsets);
+
+/* Stimulus amp on the listed nodes (instance-local numbering) of one
+ * instance; every instance must use the same window [t_on, t_off). */
+sdc_status sdc_batch_set_stimulus(sdc_batch* batch, int instance, const int* nodes, int n,
+                                  double amp, double t_on, double t_off);
+
+/* One step of every instance: d_v, d_w hold the concatenated states
+ * (offsets[n_instances] doubles each).  stats aggregates the batch
+ * (n_active summed, cg_iters the maximum over instances). */
+sdc_status sdc_batch_step(sdc_batch* batch, double* d_v, double* d_w, double t, double dt,
+                          int sweeps, double TOL, sdc_stats* stats);
+
+/* Per-instance statistics of sweep `sweep` of the last step: n_active[n_instances]
+ * and cg_iters[M][n_instances] (host; either may be NULL). */
+sdc_status sdc_batch_instance_stats(const sdc_batch* batch, int sweep, int* n_active,
+                                    int* cg_iters);
+
+/* The batch's underlying context (for sdc_get_nodes, sdc_get_active,
+ * sdc_get_matrix on the stacked system); owned by the batch. */
+sdc_ctx* sdc_batch_context(sdc_batch* batch);
+
+void sdc_batch_destroy(sdc_batch* batch);
+
 /* Largest n accepted by sdc_pcg_solve_noalloc. */
 #define SDC_PCG_NOALLOC_MAX_ROWS 65536
 

@@ -8,6 +8,7 @@ does, and raises if the library has not been built.
 """
 
 from .binding import (  # noqa: F401
+    Batch,
     Context,
     SdcError,
     default_options,
@@ -16,4 +17,4 @@ from .binding import (  # noqa: F401
     sdc_stats,
 )
 
-__all__ = ["Context", "SdcError", "default_options", "load", "radau", "sdc_stats"]
+__all__ = ["Batch", "Context", "SdcError", "default_options", "load", "radau", "sdc_stats"]

@@ -80,6 +80,16 @@ SIGNATURES = {
     "sdc_pcg_solve_noalloc": (C.c_int, [C.c_int, _vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp,
                                         _vp, C.c_double, _vp, _vp, C.c_double, C.c_int, _ip, _dp,
                                         _vp]),
+    "sdc_batch_create": (C.c_int, [C.POINTER(_vp), _vp, C.c_int, C.POINTER(sdc_ionic), C.c_int,
+                                   C.POINTER(sdc_options), _vp]),
+    "sdc_batch_info": (C.c_int, [_vp, _ip, _ip]),
+    "sdc_batch_set_stimulus": (C.c_int, [_vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double,
+                                         C.c_double]),
+    "sdc_batch_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                 C.POINTER(sdc_stats)]),
+    "sdc_batch_instance_stats": (C.c_int, [_vp, C.c_int, _ip, _ip]),
+    "sdc_batch_context": (_vp, [_vp]),
+    "sdc_batch_destroy": (None, [_vp]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_status_string": (C.c_char_p, [C.c_int]),
     "sdc_destroy": (None, [_vp]),
@@ -293,3 +303,80 @@ def pcg_solve_noalloc(n, ell_val, ell_col, ell_len, ld, width, kdiag, mass, J, c
                                         _vp(_ptr(x)), float(rtol), int(maxit), C.byref(it),
                                         C.byref(rr), _vp(stream)))
     return it.value, rr.value
+
+
+class Batch:
+    """One sdc_batch: instances stacked as disjoint diagonal blocks."""
+
+    def __init__(self, workloads, options=None, stream=0):
+        L = load()
+        wl0 = workloads[0]
+        keep = []
+        meshes = (sdc_mesh * len(workloads))()
+        for b, wl in enumerate(workloads):
+            if wl.M != wl0.M or wl.ionic != wl0.ionic:
+                raise ValueError("batch instances share M and the ionic parameters")
+            xyz = np.ascontiguousarray(wl.mesh.xyz, dtype=np.float64)
+            el = np.ascontiguousarray(wl.mesh.elems, dtype=np.int32)
+            ne, nv = el.shape
+            ep = np.arange(0, (ne + 1) * nv, nv, dtype=np.int32)
+            sig = np.ascontiguousarray(np.asarray(wl.sigma).reshape(9), np.float64)
+            es = None if wl.mesh.elem_sigma is None else np.ascontiguousarray(
+                wl.mesh.elem_sigma.reshape(-1, 9), np.float64)
+            ds = None if wl.dof_scale is None else np.ascontiguousarray(wl.dof_scale, np.float64)
+            keep.append((xyz, el, ep, sig, es, ds))
+            dp = lambda a: None if a is None else a.ctypes.data_as(_dp)
+            meshes[b] = sdc_mesh(wl.mesh.dim, xyz.shape[0], dp(xyz), ne, ep.ctypes.data_as(_ip),
+                                 el.ctypes.data_as(_ip), dp(sig), dp(es), dp(ds))
+        opts = options if options is not None else default_options()
+        h = _vp()
+        _check(L.sdc_batch_create(C.byref(h), meshes, len(workloads), C.byref(ionic_struct(wl0.ionic)),
+                                  wl0.M, C.byref(opts), _vp(stream)))
+        self._h = h
+        self.M = wl0.M
+        self.count = len(workloads)
+        off = np.zeros(self.count + 1, np.int32)
+        _check(L.sdc_batch_info(self._h, None, off.ctypes.data_as(_ip)))
+        self.offsets = off
+        self.n = int(off[-1])
+        for b, wl in enumerate(workloads):
+            if wl.stim_nodes.size:
+                nodes = np.ascontiguousarray(wl.stim_nodes, np.int32)
+                _check(L.sdc_batch_set_stimulus(self._h, b, nodes.ctypes.data_as(_ip), nodes.size,
+                                                wl.stim_amp, wl.stim_t_on, wl.stim_t_off),
+                       L.sdc_batch_context(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.sdc_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, v, w, t, dt, sweeps, tol):
+        st = sdc_stats()
+        _check(load().sdc_batch_step(self._h, _vp(_ptr(v)), _vp(_ptr(w)), float(t), float(dt),
+                                     int(sweeps), float(tol), C.byref(st)),
+               load().sdc_batch_context(self._h))
+        return st
+
+    def instance_stats(self, sweep):
+        na = np.zeros(self.count, np.int32)
+        it = np.zeros((self.M, self.count), np.int32)
+        _check(load().sdc_batch_instance_stats(self._h, sweep, na.ctypes.data_as(_ip),
+                                               it.ctypes.data_as(_ip)),
+               load().sdc_batch_context(self._h))
+        return na, it
+
+    def active(self, sweep):
+        """Active list of the stacked system for a sweep of the last step."""
+        ctx = load().sdc_batch_context(self._h)
+        n = C.c_int(0)
+        _check(load().sdc_get_active(ctx, sweep, None, C.byref(n)), ctx)
+        out = np.zeros(max(1, n.value), np.int32)
+        _check(load().sdc_get_active(ctx, sweep, out.ctypes.data_as(_ip), C.byref(n)), ctx)
+        return out[:n.value]

@@ -33,6 +33,10 @@ struct sdc_ctx {
     PcgConfig pcg;
     int* h_pin = nullptr;         // pinned: [0] count, [1] err
     std::vector<cudaEvent_t> events;   // profiling event pool
+    std::vector<int> inst_off;    // batched contexts: first dof of each instance (+ total)
+    std::vector<int> seg_bounds;  // instance boundaries in the current active list
+    std::vector<int> inst_active; // [sweep][instance] active dofs of the last step
+    int* h_bounds = nullptr;      // pinned staging of the boundaries
     bool stepped = false;
     std::string err;
 };
@@ -104,7 +108,7 @@ int alloc_buffers(sdc_ctx* c) {
               dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
               dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.z, ld) &&
               dalloc(&B.p, ld) && dalloc(&B.q, ld) && dalloc(&B.dA, ld) && dalloc(&B.idA, ld) &&
-              dalloc(&B.part, 2 * (size_t)B.max_blocks) && dalloc(&B.flag, ld) &&
+              dalloc(&B.flag, ld) &&
               dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
               dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
               dalloc(&B.wtmp, N);
@@ -115,6 +119,23 @@ int alloc_buffers(sdc_ctx* c) {
         ok = dalloc(&A.val, (size_t)A.width * ld) && dalloc(&A.col, (size_t)A.width * ld) &&
              dalloc(&A.len, ld);
     }
+    if (ok && !c->inst_off.empty()) {
+        const int nseg = (int)c->inst_off.size() - 1;
+        B.nseg = nseg;
+        P.max_blocks_batch = pcg_batch_max_blocks(P.block);
+        if (c->opt.cg_max_blocks > 0)
+            P.max_blocks_batch = std::min(P.max_blocks_batch, c->opt.cg_max_blocks);
+        B.max_blocks = std::max(B.max_blocks, P.max_blocks_batch);
+        ok = dalloc(&B.inst_off, nseg + 1) && dalloc(&B.bounds, nseg + 1) &&
+             dalloc(&B.segtab, 5 * (size_t)P.max_blocks_batch) && dalloc(&B.bars, nseg) &&
+             dalloc(&B.seg_iters, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
+             dalloc(&B.seg_relres, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
+             cudaMallocHost(&c->h_bounds, (nseg + 1) * sizeof(int)) == cudaSuccess;
+        if (ok)
+            cudaMemcpyAsync(B.inst_off, c->inst_off.data(), (nseg + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, c->stream);
+    }
+    if (ok) ok = dalloc(&B.part, 2 * (size_t)B.max_blocks);
     if (!ok) return SDC_E_NOMEM;
     if (cudaMallocHost(&c->h_pin, 4 * sizeof(int)) != cudaSuccess) return SDC_E_NOMEM;
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), c->stream);
@@ -126,8 +147,13 @@ void free_all(sdc_ctx* c) {
     double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.idA, B.part,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
-    int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff};
+    int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff, B.inst_off, B.bounds, B.segtab,
+                 B.seg_iters};
     for (int* p : ip) cudaFree(p);
+    cudaFree(B.bars);
+    cudaFree(B.seg_relres);
+    if (c->h_bounds) cudaFreeHost(c->h_bounds);
+    c->h_bounds = nullptr;
     cudaFree(B.sc);
     free_ell(B.A[0]);
     free_ell(B.A[1]);
@@ -213,8 +239,12 @@ sdc_status sdc_radau(int M, double* tau, double* Q, double* Qhat) {
     return radau_collocation(M, tau, Q, Qhat) ? SDC_OK : SDC_E_INVALID;
 }
 
-sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
-                      const sdc_options* opt, void* stream) {
+}  // extern "C"
+
+namespace {
+
+sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
+                       const sdc_options* opt, void* stream, const std::vector<int>* inst_off) {
     g_create_error.clear();
     if (!out) return fail(nullptr, SDC_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -264,6 +294,7 @@ sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ioni
     c->ion_c = *ionic;
     c->ion = Ionic{ionic->ga, ionic->gs, ionic->a, ionic->eps, ionic->mu1, ionic->mu2, ionic->cw};
     c->opt = o;
+    if (inst_off) c->inst_off = *inst_off;
     double Q[kMaxM * kMaxM], Qh[kMaxM * kMaxM];
     if (!radau_collocation(M, c->tau, Q, Qh)) {
         delete c;
@@ -296,6 +327,15 @@ sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ioni
     }
     *out = c;
     return SDC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
+                      const sdc_options* opt, void* stream) {
+    return create_impl(out, mesh, ionic, M, opt, stream, nullptr);
 }
 
 sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, double t_on,
@@ -340,6 +380,7 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         c->act.push_back(p);
     }
     c->n_act.assign(sweeps, 0);
+    if (B.nseg > 0) c->inst_active.assign((size_t)sweeps * B.nseg, 0);
     if (stats) std::memset(stats, 0, sizeof(*stats));
 
     // kernel phases: launch counts always, device time with the profile option
@@ -374,6 +415,11 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
 
     // reset scalars: error flag, CG statistics, margin
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), s);
+    if (B.nseg > 0) {
+        const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * B.nseg;
+        cudaMemsetAsync(B.seg_iters, 0, cnt * sizeof(int), s);
+        cudaMemsetAsync(B.seg_relres, 0, cnt * sizeof(double), s);
+    }
     const double big = 1.7976931348623157e308;
     cudaMemcpyAsync(&B.sc->margin, &big, sizeof(double), cudaMemcpyHostToDevice, s);
     run(SDC_PHASE_RESIDUAL, 1, [&] { launch_spread(N, M, d_v, d_w, B.V, B.W, s); });
@@ -397,13 +443,22 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
             launch_residual(M, n, act, c->K.K, c->K.kdiag, c->K.mass, c->stim, stim_on, B.V, B.W,
                             d_v, dt, c->ion, c->co, c->opt.reaction_implicit, B, s);
         });
+        const bool batched = B.nseg > 0;
+        if (batched) {
+            if (k == 0) c->seg_bounds = c->inst_off;
+            for (int g = 0; g < B.nseg; ++g)
+                c->inst_active[(size_t)k * B.nseg + g] = c->seg_bounds[g + 1] - c->seg_bounds[g];
+        }
         for (int m = 0; m < M && status == SDC_OK; ++m) {
             cur_k = k;
             cur_m = m;
             run(SDC_PHASE_PCG, 1, [&] {
-                if (launch_pcg(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit, k, c->pcg,
-                               B, s) != SDC_OK)
-                    status = cuda_fail(c, "cooperative CG launch");
+                const int rc = batched
+                    ? launch_pcg_batch(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit, k,
+                                       c->pcg, c->seg_bounds, B, s)
+                    : launch_pcg(n, *A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit, k, c->pcg,
+                                 B, s);
+                if (rc != SDC_OK) status = cuda_fail(c, "cooperative CG launch");
             });
         }
         if (status != SDC_OK) break;
@@ -412,8 +467,15 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         });
         int* next = (k + 1 < sweeps) ? c->act[k + 1] : c->act[0];
         run(SDC_PHASE_SELECT, 2, [&] { launch_select(n, act, next, B, s); });
+        if (batched) {
+            launch_seg_bounds(next, &B.sc->count, B, s);
+            launches[SDC_PHASE_SELECT] += 1;
+            cudaMemcpyAsync(c->h_bounds, B.bounds, (B.nseg + 1) * sizeof(int),
+                            cudaMemcpyDeviceToHost, s);
+        }
         int n_next = 0;
         int e = sync_sweep(c, n_next);
+        if (batched) c->seg_bounds.assign(c->h_bounds, c->h_bounds + B.nseg + 1);
         if (e != SDC_OK) {
             status = e == SDC_E_CUDA ? cuda_fail(c, "sweep") : fail(c, (sdc_status)e,
                      "sweep %d: %s", k, sdc_status_string(e));
@@ -449,6 +511,26 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         cudaMemcpyAsync(rr.data(), B.sc->cg_relres, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        if (B.nseg > 0) {
+            const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * B.nseg;
+            std::vector<int> si(cnt);
+            std::vector<double> sr(cnt);
+            cudaMemcpyAsync(si.data(), B.seg_iters, cnt * sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(sr.data(), B.seg_relres, cnt * sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            for (int kk = 0; kk < sweeps; ++kk)
+                for (int m = 0; m < M; ++m) {
+                    int mx = 0;
+                    double mr = 0.0;
+                    for (int g = 0; g < B.nseg; ++g) {
+                        const size_t at = (size_t)(kk * kMaxM + m) * B.nseg + g;
+                        mx = std::max(mx, si[at]);
+                        mr = std::max(mr, sr[at]);
+                    }
+                    it[kk * kMaxM + m] = mx;
+                    rr[kk * kMaxM + m] = mr;
+                }
+        }
         for (int kk = 0; kk < sweeps; ++kk)
             for (int m = 0; m < M; ++m) {
                 stats->cg_iters[kk][m] = it[kk * kMaxM + m];
@@ -616,6 +698,160 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     if (relres) *relres = hr;
     cudaFree(ws);
     return (sdc_status)status;
+}
+
+}  // extern "C"
+
+struct sdc_batch {
+    sdc_ctx* ctx = nullptr;
+    std::vector<int> off;        // first dof of each instance, then the total
+    std::vector<double> amp;     // per-dof stimulus amplitude of the union
+    double t_on = 0.0, t_off = 0.0;
+    bool has_window = false;
+};
+
+extern "C" {
+
+sdc_status sdc_batch_create(sdc_batch** out, const sdc_mesh* meshes, int n_instances,
+                            const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, SDC_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!meshes || n_instances < 1) return fail(nullptr, SDC_E_INVALID, "no instances");
+    const int dim = meshes[0].dim;
+    long long nodes = 0, elems = 0;
+    for (int b = 0; b < n_instances; ++b) {
+        const sdc_mesh& m = meshes[b];
+        if (m.dim != dim)
+            return fail(nullptr, SDC_E_INVALID, "instance %d: all instances need dim %d", b, dim);
+        if (m.n_nodes < 1 || m.n_elems < 1 || !m.xyz || !m.elem_ptr || !m.elem_node ||
+            (!m.sigma && !m.elem_sigma))
+            return fail(nullptr, SDC_E_INVALID, "instance %d: empty mesh or NULL arrays", b);
+        nodes += m.n_nodes;
+        elems += m.n_elems;
+    }
+    if (nodes > 0x7fffffffLL || elems > 0x7fffffffLL / (dim + 1))
+        return fail(nullptr, SDC_E_INVALID, "batch too large for 32-bit indices");
+    // union mesh: instances stacked as disjoint diagonal blocks
+    std::vector<double> xyz, esig, scale;
+    std::vector<int> eptr(1, 0), enode;
+    std::vector<int> off(1, 0);
+    xyz.reserve((size_t)nodes * dim);
+    esig.reserve((size_t)elems * 9);
+    scale.reserve((size_t)nodes);
+    enode.reserve((size_t)elems * (dim + 1));
+    for (int b = 0; b < n_instances; ++b) {
+        const sdc_mesh& m = meshes[b];
+        const int base = off.back();
+        xyz.insert(xyz.end(), m.xyz, m.xyz + (size_t)m.n_nodes * dim);
+        for (int e = 0; e < m.n_elems; ++e) {
+            for (int k = m.elem_ptr[e]; k < m.elem_ptr[e + 1]; ++k) {
+                const int v = m.elem_node[k];
+                enode.push_back(v >= 0 && v < m.n_nodes ? base + v : -1);
+            }
+            eptr.push_back((int)enode.size());
+            const double* sg = m.elem_sigma ? m.elem_sigma + (size_t)e * 9 : m.sigma;
+            esig.insert(esig.end(), sg, sg + 9);
+        }
+        for (int i = 0; i < m.n_nodes; ++i) scale.push_back(m.dof_scale ? m.dof_scale[i] : 1.0);
+        off.push_back(base + m.n_nodes);
+    }
+    sdc_mesh U;
+    U.dim = dim;
+    U.n_nodes = (int)nodes;
+    U.xyz = xyz.data();
+    U.n_elems = (int)elems;
+    U.elem_ptr = eptr.data();
+    U.elem_node = enode.data();
+    U.sigma = nullptr;
+    U.elem_sigma = esig.data();
+    U.dof_scale = scale.data();
+    sdc_ctx* c = nullptr;
+    sdc_status st = create_impl(&c, &U, ionic, M, opt, stream, &off);
+    if (st != SDC_OK) return st;
+    sdc_batch* bt = new sdc_batch();
+    bt->ctx = c;
+    bt->off = off;
+    bt->amp.assign((size_t)nodes, 0.0);
+    *out = bt;
+    return SDC_OK;
+}
+
+sdc_status sdc_batch_info(const sdc_batch* bt, int* n_instances, int* offsets) {
+    if (!bt) return SDC_E_INVALID;
+    if (n_instances) *n_instances = (int)bt->off.size() - 1;
+    if (offsets) std::copy(bt->off.begin(), bt->off.end(), offsets);
+    return SDC_OK;
+}
+
+sdc_status sdc_batch_set_stimulus(sdc_batch* bt, int instance, const int* nodes, int n, double amp,
+                                  double t_on, double t_off) {
+    if (!bt) return SDC_E_INVALID;
+    sdc_ctx* c = bt->ctx;
+    const int ninst = (int)bt->off.size() - 1;
+    if (instance < 0 || instance >= ninst)
+        return fail(c, SDC_E_INVALID, "instance %d out of range", instance);
+    if (n < 0 || (n > 0 && !nodes) || !std::isfinite(amp))
+        return fail(c, SDC_E_INVALID, "bad stimulus");
+    if (n > 0 && bt->has_window && (t_on != bt->t_on || t_off != bt->t_off))
+        return fail(c, SDC_E_INVALID, "every instance of a batch shares one stimulus window");
+    const int base = bt->off[instance], size = bt->off[instance + 1] - base;
+    for (int i = 0; i < n; ++i)
+        if (nodes[i] < 0 || nodes[i] >= size)
+            return fail(c, SDC_E_INVALID, "stimulus node %d out of range", nodes[i]);
+    std::fill(bt->amp.begin() + base, bt->amp.begin() + base + size, 0.0);
+    for (int i = 0; i < n; ++i) bt->amp[base + nodes[i]] = amp;
+    if (n > 0) {
+        bt->t_on = t_on;
+        bt->t_off = t_off;
+        bt->has_window = true;
+    }
+    std::vector<int> idx;
+    for (size_t i = 0; i < bt->amp.size(); ++i)
+        if (bt->amp[i] != 0.0) idx.push_back((int)i);
+    if (idx.empty()) return sdc_set_stimulus(c, nullptr, 0, 0.0, 0.0, 0.0);
+    sdc_status st = sdc_set_stimulus(c, idx.data(), (int)idx.size(), 1.0, bt->t_on, bt->t_off);
+    if (st != SDC_OK) return st;
+    // per-dof amplitudes (the context stores amplitude * on/off per dof)
+    if (cudaMemcpyAsync(c->stim, bt->amp.data(), bt->amp.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return cuda_fail(c, "sdc_batch_set_stimulus");
+    return SDC_OK;
+}
+
+sdc_status sdc_batch_step(sdc_batch* bt, double* d_v, double* d_w, double t, double dt, int sweeps,
+                          double TOL, sdc_stats* stats) {
+    if (!bt) return SDC_E_INVALID;
+    return sdc_step(bt->ctx, d_v, d_w, t, dt, sweeps, TOL, stats);
+}
+
+sdc_status sdc_batch_instance_stats(const sdc_batch* bt, int sweep, int* n_active, int* cg_iters) {
+    if (!bt) return SDC_E_INVALID;
+    sdc_ctx* c = bt->ctx;
+    const int nseg = (int)bt->off.size() - 1;
+    if (!c->stepped || sweep < 0 || sweep >= c->last_sweeps)
+        return fail(c, SDC_E_INVALID, "no statistics for sweep %d", sweep);
+    if (n_active)
+        for (int g = 0; g < nseg; ++g) n_active[g] = c->inst_active[(size_t)sweep * nseg + g];
+    if (cg_iters) {
+        std::vector<int> si((size_t)c->M * nseg);
+        for (int m = 0; m < c->M; ++m)
+            if (cudaMemcpy(si.data() + (size_t)m * nseg,
+                           c->B.seg_iters + (size_t)(sweep * kMaxM + m) * nseg, nseg * sizeof(int),
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                return cuda_fail(c, "sdc_batch_instance_stats");
+        std::copy(si.begin(), si.end(), cg_iters);
+    }
+    return SDC_OK;
+}
+
+sdc_ctx* sdc_batch_context(sdc_batch* bt) { return bt ? bt->ctx : nullptr; }
+
+void sdc_batch_destroy(sdc_batch* bt) {
+    if (!bt) return;
+    sdc_destroy(bt->ctx);
+    delete bt;
 }
 
 void sdc_destroy(sdc_ctx* c) {

@@ -93,28 +93,31 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // shared memory.  A closing CTA barrier makes them visible to the block.
 // Returns false after a barrier timeout.  red: blockDim.x doubles; flag: an
 // int in shared memory.
+// The participating blocks are the `nblk` blocks of a group (the whole grid,
+// or one instance's share of a batched launch); `bidx` is this block's index
+// in the group, part[0..nblk) its partial-sum slots and bar its counter.
 template <class F>
-__device__ __forceinline__ bool grid_reduce(double v, double* red, double* part, unsigned* bar,
-                                            unsigned& epoch, long long budget, int* err,
-                                            int* ok_flag, F&& on_total) {
+__device__ __forceinline__ bool group_reduce(double v, double* red, double* part, unsigned* bar,
+                                             int nblk, int bidx, unsigned& epoch, long long budget,
+                                             int* err, int* ok_flag, F&& on_total) {
     const int lane = threadIdx.x & 31;
     red[threadIdx.x] = v;
     __syncthreads();
-    epoch += gridDim.x;
+    epoch += nblk;
     if (threadIdx.x < 32) {
         double s = 0.0;
         for (int i = lane; i < (int)blockDim.x; i += 32) s += red[i];
         s = warp_sum(s);
         int ok = 1;
         if (lane == 0) {
-            part[blockIdx.x] = s;
+            part[bidx] = s;
             ok = barrier_arrive_wait(bar, epoch, budget, err);
         }
         __syncwarp();
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (ok) {
             double t = 0.0;
-            for (int i = lane; i < (int)gridDim.x; i += 32) t += __ldcg(part + i);
+            for (int i = lane; i < nblk; i += 32) t += __ldcg(part + i);
             t = warp_sum(t);
             if (lane == 0) on_total(t);
         }
@@ -124,14 +127,28 @@ __device__ __forceinline__ bool grid_reduce(double v, double* red, double* part,
     return *ok_flag != 0;
 }
 
-// Plain grid barrier with the same conventions (flag: an int in shared memory).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, long long budget,
-                                             int* err, int* ok_flag) {
-    epoch += gridDim.x;
+template <class F>
+__device__ __forceinline__ bool grid_reduce(double v, double* red, double* part, unsigned* bar,
+                                            unsigned& epoch, long long budget, int* err,
+                                            int* ok_flag, F&& on_total) {
+    return group_reduce(v, red, part, bar, (int)gridDim.x, (int)blockIdx.x, epoch, budget, err,
+                        ok_flag, on_total);
+}
+
+// Plain barrier of a block group with the same conventions (flag: an int in
+// shared memory).
+__device__ __forceinline__ bool group_barrier(unsigned* bar, int nblk, unsigned& epoch,
+                                              long long budget, int* err, int* ok_flag) {
+    epoch += nblk;
     __syncthreads();
     if (threadIdx.x == 0) *ok_flag = barrier_arrive_wait(bar, epoch, budget, err);
     __syncthreads();
     return *ok_flag != 0;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, long long budget,
+                                             int* err, int* ok_flag) {
+    return group_barrier(bar, (int)gridDim.x, epoch, budget, err, ok_flag);
 }
 
 }  // namespace sdc

@@ -87,6 +87,14 @@ struct StepBuffers {
     DevScalars* sc = nullptr;
     double* vtmp = nullptr;   // host-call staging [N]
     double* wtmp = nullptr;
+    // batched contexts: nseg instances, contiguous in the dof numbering
+    int nseg = 0;
+    int* inst_off = nullptr;      // [nseg + 1] first dof of each instance
+    int* bounds = nullptr;        // [nseg + 1] instance boundaries in the current active list
+    int* segtab = nullptr;        // per-block group table of the batched PCG launch
+    unsigned* bars = nullptr;     // [nseg] barrier counters
+    int* seg_iters = nullptr;     // [SDC_MAX_SWEEPS * kMaxM * nseg]
+    double* seg_relres = nullptr; // same shape
 };
 
 void launch_spread(int N, int M, const double* v0, const double* w0, double* V, double* W,
@@ -113,6 +121,8 @@ struct PcgConfig {
     int cluster_rows = 0;           // use the cluster variant for n <= cluster_rows
     int cluster_rows_per_cta = 64;  // rows per CTA below which fewer CTAs are used
     int big_rows = 300000;          // shared-memory variant uses 1024 threads from here on
+    int max_blocks_batch = 0;       // cooperative grid limit of the batched variant
+    int batch_rows_per_block = 1024;
     int inject_fault = 0;
     long long budget = 0;
 };
@@ -121,6 +131,14 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
 int pcg_sm_count();
 // Message returned by sdc_last_error(NULL) on the calling thread.
 void set_thread_error(const char* msg);
+
+// Batched PCG: independent solves of the instances whose compact rows are
+// [bounds[s], bounds[s+1]); empty instances are skipped.
+int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
+                     int maxit, int sweep, const PcgConfig& cfg, const std::vector<int>& bounds,
+                     StepBuffers& B, cudaStream_t s);
+void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s);
+int pcg_batch_max_blocks(int block);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
 // r, z, p, q, dA, idA: n doubles each; part: 2 * max_blocks doubles;

@@ -99,6 +99,13 @@ __global__ void k_residual(int n, const int* __restrict__ act, const double* __r
     kdc[p] = kd;
 }
 
+// One block's share of a batched PCG launch.
+struct SegBlock {
+    int row0, row1;   // compact rows of the instance
+    int blk0, nblk;   // the instance's first block and block count
+    int seg;          // instance index
+};
+
 struct CgParams {
     int n, ld;
     const double* aval;
@@ -197,18 +204,22 @@ __device__ __forceinline__ double cg_relres(const CgShared& S) {
 // Rows are processed grid-stride; each thread owns the same rows in every
 // phase.  Block totals are added in a fixed order by every block, so all
 // blocks take identical decisions.
-__global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
-    __shared__ CgShared S;
-    const int G = gridDim.x;
-    const int stride = G * blockDim.x;
-    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+// One group of `nblk` blocks solves rows [row0, row1): the whole launch, or
+// one instance of a batched launch.  `part` points at the group's first
+// partial-sum slot of buffer 0; buffer 1 is `pstride` doubles further.
+__device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int row0, int row1,
+                                          int nblk, int bidx, unsigned* bar, double* part,
+                                          int pstride, int* iters_out, double* relres_out) {
+    const int stride = nblk * blockDim.x;
+    const int i0 = row0 + bidx * blockDim.x + threadIdx.x;
+    const bool lead = (bidx == 0 && threadIdx.x == 0);
     const int ld = P.ld;
     const double c = P.c;
     unsigned epoch = 0;
     int buf = 0;
 
-    double part = 0.0;
-    for (int i = i0; i < P.n; i += stride) {
+    double acc_part = 0.0;
+    for (int i = i0; i < row1; i += stride) {
         const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
         if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
         else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
@@ -222,28 +233,28 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
         P.p[i] = 0.0;
         P.q[i] = 0.0;
         P.x[i] = 0.0;
-        part += r * z;
+        acc_part += r * z;
     }
-    if (P.inject_fault && blockIdx.x == G - 1) {
+    if (P.inject_fault && bidx == nblk - 1) {
         // leave without arriving: every other block's bounded wait runs out
-        if (G == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        if (nblk == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
         return;
     }
-    if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                     [&](double t) { cg_after_rho0(S, t, P.rtol); }))
+    if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
+                      P.err, &S.ok, [&](double t) { cg_after_rho0(S, t, P.rtol); }))
         return;
     buf ^= 1;
     int it = 0;
     double beta = 0.0;
     while (S.state == 0) {
         if (it >= P.maxit) {
-            if (i0 == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
             break;
         }
         ++it;
         // s = A z; p = z + beta p; q = s + beta q; p.q
-        part = 0.0;
-        for (int i = i0; i < P.n; i += stride) {
+        acc_part = 0.0;
+        for (int i = i0; i < row1; i += stride) {
             const int len = P.alen[i];
             double acc = 0.0;
             for (int t = 0; t < len; ++t)
@@ -254,40 +265,40 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
             const double qi = si + beta * P.q[i];
             P.p[i] = pi;
             P.q[i] = qi;
-            part += pi * qi;
+            acc_part += pi * qi;
         }
-        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                         [&](double t) { cg_after_pq(S, t); }))
+        if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
+                          P.err, &S.ok, [&](double t) { cg_after_pq(S, t); }))
             return;
         buf ^= 1;
         const double alpha = S.alpha;
         // x += alpha p, r -= alpha q, z = D^-1 r, r.z
-        part = 0.0;
-        for (int i = i0; i < P.n; i += stride) {
+        acc_part = 0.0;
+        for (int i = i0; i < row1; i += stride) {
             P.x[i] += alpha * P.p[i];
             const double r = P.r[i] - alpha * P.q[i];
             P.r[i] = r;
             const double z = r * P.idA[i];
             P.z[i] = z;
-            part += r * z;
+            acc_part += r * z;
         }
-        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                         [&](double t) { cg_after_rz(S, t); }))
+        if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
+                          P.err, &S.ok, [&](double t) { cg_after_rz(S, t); }))
             return;
         buf ^= 1;
         beta = S.beta;
     }
     if (S.state == 2) {
-        if (i0 == 0) raise_error(P.err, SDC_E_NONFINITE);
+        if (lead) raise_error(P.err, SDC_E_NONFINITE);
         return;
     }
-    if (i0 == 0) {
-        *P.iters_out = it;
-        *P.relres_out = cg_relres(S);
+    if (lead) {
+        *iters_out = it;
+        *relres_out = cg_relres(S);
     }
-    // x is complete in every block: the last grid sum followed its update.
+    // x is complete in every block of the group: the last group sum followed its update.
     if (P.m + 1 < P.M) {
-        for (int i = i0; i < P.n; i += stride) {
+        for (int i = i0; i < row1; i += stride) {
             const int len = P.alen[i];
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
@@ -298,6 +309,43 @@ __global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
                 P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
         }
     }
+}
+
+__global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
+    __shared__ CgShared S;
+    pcg_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar, P.part, (int)gridDim.x,
+              P.iters_out, P.relres_out);
+}
+
+// Batched variant: independent solves of the instances of a batch (disjoint
+// diagonal blocks of the system) in one cooperative launch.  Block b works on
+// the group tab[b] describes: that instance's compact rows, its own barrier
+// counter and partial-sum slots, its own iteration count.  Groups never wait
+// for each other, so a converged instance's blocks leave early.
+__global__ void __launch_bounds__(1024, 1) k_pcg_batch(CgParams P, const SegBlock* __restrict__ tab,
+                                                        unsigned* __restrict__ bars,
+                                                        int* __restrict__ seg_iters,
+                                                        double* __restrict__ seg_relres) {
+    __shared__ CgShared S;
+    const SegBlock g = tab[blockIdx.x];
+    pcg_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
+              P.part + g.blk0, (int)gridDim.x, seg_iters + g.seg, seg_relres + g.seg);
+}
+
+// Compact boundaries of the batch instances in a sorted active list:
+// bounds[s] = first position p with act[p] >= inst_off[s] (lower bound).
+__global__ void k_seg_bounds(const int* __restrict__ count, const int* __restrict__ act, int nseg,
+                             const int* __restrict__ inst_off, int* __restrict__ bounds) {
+    const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sidx > nseg) return;
+    const int n = *count;
+    const int key = inst_off[sidx];
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (act[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    bounds[sidx] = lo;
 }
 
 // Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
@@ -921,6 +969,98 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(cfg.block),
                                                 args, 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+}
+
+int pcg_batch_max_blocks(int block) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batch, block, 0);
+    return sms * per;
+}
+
+void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s) {
+    k_seg_bounds<<<nblk(B.nseg + 1, 128), 128, 0, s>>>(count, act, B.nseg, B.inst_off, B.bounds);
+}
+
+int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
+                     int maxit, int sweep, const PcgConfig& cfg, const std::vector<int>& bounds,
+                     StepBuffers& B, cudaStream_t s) {
+    const int nseg = (int)bounds.size() - 1;
+    const int Gmax = cfg.max_blocks_batch;
+    // blocks per instance: proportional to its active rows, at least one
+    std::vector<int> want(nseg, 0);
+    long long total = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const int r = bounds[g + 1] - bounds[g];
+        if (r > 0) want[g] = std::max(1, nblk(r, cfg.batch_rows_per_block));
+        total += want[g];
+    }
+    if (total > Gmax) {
+        const double f = (double)Gmax / (double)total;
+        for (int g = 0; g < nseg; ++g)
+            if (want[g] > 0) want[g] = std::max(1, (int)(want[g] * f));
+    }
+    CgParams P;
+    P.n = n;
+    P.ld = B.ld;
+    P.aval = A.val;
+    P.acol = A.col;
+    P.alen = A.len;
+    P.mc = B.mc;
+    P.kdc = B.kdc;
+    P.J = B.J + (size_t)m * B.ld;
+    P.c = dt * co.Qh[m * kMaxM + m];
+    P.b = B.R + (size_t)m * B.ld;
+    P.x = B.D + (size_t)m * B.ld;
+    P.r = B.r;
+    P.z = B.z;
+    P.p = B.p;
+    P.q = B.q;
+    P.dA = B.dA;
+    P.idA = B.idA;
+    P.part = B.part;
+    P.bar = nullptr;
+    P.err = &B.sc->err;
+    P.rtol = rtol;
+    P.maxit = maxit;
+    P.budget = cfg.budget;
+    P.iters_out = nullptr;
+    P.relres_out = nullptr;
+    P.m = m;
+    P.M = co.M;
+    P.dt = dt;
+    P.R = B.R;
+    for (int j = 0; j < kMaxM; ++j) P.qh[j] = j < co.M ? co.Qh[j * kMaxM + m] : 0.0;
+    P.inject_fault = 0;
+    P.L = 0;
+    int* seg_iters = B.seg_iters + (size_t)(sweep * kMaxM + m) * nseg;
+    double* seg_relres = B.seg_relres + (size_t)(sweep * kMaxM + m) * nseg;
+    cudaMemsetAsync(B.bars, 0, nseg * sizeof(unsigned), s);
+    // waves of instances whose blocks fit in one cooperative grid
+    std::vector<SegBlock> tab;
+    int g = 0;
+    while (g < nseg) {
+        tab.clear();
+        while (g < nseg) {
+            if (want[g] == 0) { ++g; continue; }
+            if (!tab.empty() && (int)tab.size() + want[g] > Gmax) break;
+            const int blk0 = (int)tab.size();
+            const int nb = std::min(want[g], Gmax);
+            for (int b = 0; b < nb; ++b) tab.push_back({bounds[g], bounds[g + 1], blk0, nb, g});
+            ++g;
+        }
+        if (tab.empty()) break;
+        if (cudaMemcpyAsync(B.segtab, tab.data(), tab.size() * sizeof(SegBlock),
+                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return SDC_E_CUDA;
+        const SegBlock* dtab = reinterpret_cast<const SegBlock*>(B.segtab);
+        void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3((int)tab.size()),
+                                                    dim3(cfg.block), args, 0, s);
+        if (e != cudaSuccess) return SDC_E_CUDA;
+    }
+    return SDC_OK;
 }
 
 int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double* mass,
