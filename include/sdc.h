@@ -29,6 +29,8 @@
 #ifndef SDC_GB300_H
 #define SDC_GB300_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -210,6 +212,55 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
                          int width, const double* d_kdiag, const double* d_mass, const double* d_J,
                          double c, const double* d_b, double* d_x, double rtol, int maxit,
                          int* iters, double* relres, void* stream);
+
+/* ---- Differentiation: tape, replay and the discrete adjoint of a step ----
+ *
+ * With the nested index sets of a step held fixed, the step is a smooth map
+ * (v0, w0; s, ga, gs, a) -> (v, w) once every node solve is read as the exact
+ * solution of its linear system.  A tape records what the reverse pass needs:
+ * the collocation-node values after every sweep and the active lists. */
+#define SDC_TAPE_OFF 0
+#define SDC_TAPE_RECORD 1   /* sdc_step_taped fills the tape                     */
+#define SDC_TAPE_REPLAY 2   /* sdc_step_taped takes its active sets from the tape */
+
+typedef struct {
+    int mode;
+    int sweeps;                      /* sweeps recorded (set by RECORD)                     */
+    double* d_V;                     /* device, sweeps * n_nodes * M doubles (caller-owned) */
+    double* d_W;                     /* same                                                */
+    int* d_act;                      /* device, sweeps * n_nodes ints: list of sweep k >= 1 */
+    int n_active[SDC_MAX_SWEEPS];    /* |I_k|, host                                         */
+} sdc_tape;
+
+/* Bytes of device memory a tape of `sweeps` sweeps needs (d_V + d_W + d_act). */
+size_t sdc_tape_bytes(const sdc_ctx* ctx, int sweeps);
+
+/* sdc_step with a tape: RECORD stores the state after each sweep and the active
+ * lists; REPLAY runs the step with the recorded active sets instead of
+ * selecting new ones (the tape's sweeps must equal `sweeps`); TOL then only
+ * matters for the statistics.  A NULL tape or mode OFF is sdc_step. */
+sdc_status sdc_step_taped(sdc_ctx* ctx, double* d_v, double* d_w, double t, double dt, int sweeps,
+                          double TOL, sdc_stats* stats, sdc_tape* tape);
+
+/* Discrete adjoint of the step recorded on `tape` (Sec. 3.2 eq. final-sdc,
+ * Sec. 4.2, active sets fixed).  Given the adjoints d_lam_v, d_lam_w of the
+ * step's outputs, writes the adjoints d_lam_v0, d_lam_w0 of its inputs d_v0,
+ * d_w0 (the state the recorded step started from, device), adds dL/ds to
+ * d_grad_scale (device, n_nodes; may be NULL), s being the per-node
+ * conductivity scale, and adds dL/d(ga, gs, a) to grad_ionic[3] (host; may be
+ * NULL).  The reverse node solves use the forward's Jacobi-PCG with the
+ * context's cg_rtol.  Synchronises the stream.  Not available for batches. */
+sdc_status sdc_step_adjoint(sdc_ctx* ctx, const sdc_tape* tape, const double* d_v0,
+                            const double* d_w0, double dt, const double* d_lam_v,
+                            const double* d_lam_w, double* d_lam_v0, double* d_lam_w0,
+                            double* d_grad_scale, double* grad_ionic);
+
+/* Re-assemble K for a new per-node conductivity scale (host, n_nodes positive
+ * values; NULL = all ones) on the context's mesh. */
+sdc_status sdc_set_dof_scale(sdc_ctx* ctx, const double* h_scale);
+
+/* Replace the ionic parameters of a context. */
+sdc_status sdc_set_ionic(sdc_ctx* ctx, const sdc_ionic* ionic);
 
 /* ---- Batches: many independent instances advanced by the same launches ----
  *

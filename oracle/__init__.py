@@ -69,6 +69,9 @@ def lib():
         L.ora_destroy.argtypes = [C.c_void_p]
         L.ora_step.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp, C.c_double,
                                C.c_int, C.c_double, C.POINTER(_Opts), C.POINTER(Stats), _ip, _dp, _dp]
+        L.ora_step_forced.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
+                                      C.c_double, C.c_int, C.c_double, C.POINTER(_Opts),
+                                      C.POINTER(Stats), _ip, _dp, _dp, _ip, _ip]
         L.ora_collocation_solve.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
                                             C.c_double, _dp, _dp, _ip]
         _lib = L
@@ -184,6 +187,30 @@ class System:
         if want_nodes:
             out["V"], out["W"] = Vn, Wn
         return out
+
+    def step_forced(self, ionic: dict, M: int, v, w, dt: float, sweeps: int, active_lists,
+                    cg_rtol: float = 1e-10, cg_maxit: int = 10000, istim=None,
+                    reaction_implicit: bool = True, w_frozen: bool = False):
+        """One SDC step whose active sets are given (active_lists[k] for sweeps
+        k >= 1; the first sweep covers every dof) instead of selected."""
+        n = self.n
+        v = np.array(v, dtype=np.float64, copy=True)
+        w = np.array(w, dtype=np.float64, copy=True)
+        counts = np.zeros(max(1, sweeps), np.int32)
+        counts[0] = n
+        lists = []
+        for k in range(1, sweeps):
+            lk = np.ascontiguousarray(active_lists[k], dtype=np.int32)
+            counts[k] = lk.size
+            lists.append(lk)
+        flat = np.concatenate(lists) if lists else np.zeros(1, np.int32)
+        flat = np.ascontiguousarray(flat, dtype=np.int32)
+        st = Stats()
+        opts = _Opts(0.1, cg_rtol, cg_maxit, int(reaction_implicit), int(w_frozen))
+        rc = lib().ora_step_forced(self._h, C.byref(_ionic(ionic)), M, _d(_f64(istim)), _d(v),
+                                   _d(w), dt, sweeps, 0.0, C.byref(opts), C.byref(st), None, None,
+                                   None, _i(counts), _i(flat))
+        return dict(v=v, w=w, status=rc, stats=st)
 
     def collocation_solve(self, ionic: dict, M: int, v, w, dt: float, istim=None):
         """Dense Newton solution of the full collocation system (tiny meshes)."""

@@ -447,9 +447,25 @@ void ora_destroy(void* h) { delete (System*)h; }
 // istim: per-node stimulus current for this step (NULL = none).
 // active_log (optional): concatenated ascending active lists of every sweep.
 // Vn, Wn (optional): all collocation-node values after the last sweep, [M][N].
+// forced_counts / forced_lists (optional, for derivative checks): the active
+// sets to use instead of selecting them, |I_k| = forced_counts[k], the lists of
+// sweeps 1..sweeps-1 concatenated in forced_lists (I_0 is every dof).
+int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, double* v, double* w,
+                    double dt, int sweeps, double tol, const ora_opts* o, ora_stats* st,
+                    int* active_log, double* Vn, double* Wn, const int* forced_counts,
+                    const int* forced_lists);
+
 int ora_step(void* h, const ora_ionic* ip, int M, const double* istim, double* v, double* w,
              double dt, int sweeps, double tol, const ora_opts* o, ora_stats* st,
              int* active_log, double* Vn, double* Wn) {
+    return ora_step_forced(h, ip, M, istim, v, w, dt, sweeps, tol, o, st, active_log, Vn, Wn,
+                           nullptr, nullptr);
+}
+
+int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, double* v, double* w,
+                    double dt, int sweeps, double tol, const ora_opts* o, ora_stats* st,
+                    int* active_log, double* Vn, double* Wn, const int* forced_counts,
+                    const int* forced_lists) {
     System& S = *(System*)h;
     const Csr& K = S.K;
     const int N = K.n;
@@ -569,6 +585,15 @@ int ora_step(void* h, const ora_ionic* ip, int M, const double* istim, double* v
             if (!std::isfinite(amax)) return ORA_NONFINITE;
             if (st && tol_drop > 0.0) st->min_margin = std::min(st->min_margin, std::fabs(amax - tol_drop));
             if (amax >= tol_drop) next.push_back(i);
+        }
+        if (forced_counts) {
+            // replace the selection by the given set of the next sweep
+            next.clear();
+            if (k + 1 < sweeps) {
+                size_t off = 0;
+                for (int kk = 1; kk <= k; ++kk) off += (size_t)forced_counts[kk];
+                next.assign(forced_lists + off, forced_lists + off + forced_counts[k + 1]);
+            }
         }
         act.swap(next);
     }

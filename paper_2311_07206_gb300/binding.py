@@ -55,6 +55,13 @@ class sdc_stats(C.Structure):
                 ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS)]
 
 
+class sdc_tape(C.Structure):
+    _fields_ = [("mode", C.c_int), ("sweeps", C.c_int), ("d_V", C.c_void_p), ("d_W", C.c_void_p),
+                ("d_act", C.c_void_p), ("n_active", C.c_int * SDC_MAX_SWEEPS)]
+
+
+SDC_TAPE_OFF, SDC_TAPE_RECORD, SDC_TAPE_REPLAY = 0, 1, 2
+
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 _vp = C.c_void_p
@@ -90,6 +97,13 @@ SIGNATURES = {
     "sdc_batch_instance_stats": (C.c_int, [_vp, C.c_int, _ip, _ip]),
     "sdc_batch_context": (_vp, [_vp]),
     "sdc_batch_destroy": (None, [_vp]),
+    "sdc_tape_bytes": (C.c_size_t, [_vp, C.c_int]),
+    "sdc_step_taped": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                                 C.POINTER(sdc_stats), C.POINTER(sdc_tape)]),
+    "sdc_step_adjoint": (C.c_int, [_vp, C.POINTER(sdc_tape), _vp, _vp, C.c_double, _vp, _vp, _vp,
+                                   _vp, _vp, _dp]),
+    "sdc_set_dof_scale": (C.c_int, [_vp, _dp]),
+    "sdc_set_ionic": (C.c_int, [_vp, C.POINTER(sdc_ionic)]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_status_string": (C.c_char_p, [C.c_int]),
     "sdc_destroy": (None, [_vp]),
@@ -225,6 +239,46 @@ class Context:
                                     float(t), float(dt), int(sweeps), float(tol),
                                     C.byref(st) if st is not None else None), self._h)
         return st
+
+    # ---- differentiation ----------------------------------------------------
+    def new_tape(self, sweeps, device):
+        """A tape (device buffers owned by torch tensors kept on the object)."""
+        import torch
+        tp = sdc_tape()
+        tp.mode = SDC_TAPE_RECORD
+        tp.sweeps = 0
+        tp._V = torch.empty(sweeps * self.n * self.M, dtype=torch.float64, device=device)
+        tp._W = torch.empty_like(tp._V)
+        tp._act = torch.zeros(max(1, sweeps * self.n), dtype=torch.int32, device=device)
+        tp.d_V, tp.d_W, tp.d_act = tp._V.data_ptr(), tp._W.data_ptr(), tp._act.data_ptr()
+        return tp
+
+    def step_taped(self, v, w, t, dt, sweeps, tol, tape, mode=SDC_TAPE_RECORD, want_stats=False):
+        tape.mode = mode
+        st = sdc_stats() if want_stats else None
+        _check(load().sdc_step_taped(self._h, _vp(_ptr(v)), _vp(_ptr(w)), float(t), float(dt),
+                                     int(sweeps), float(tol),
+                                     C.byref(st) if st is not None else None, C.byref(tape)),
+               self._h)
+        return st
+
+    def adjoint(self, tape, v0, w0, dt, lam_v, lam_w, lam_v0, lam_w0, grad_scale=None,
+                grad_ionic=None):
+        """Adjoint of the step on `tape`; grad_ionic: numpy float64[3] accumulated."""
+        gi = grad_ionic.ctypes.data_as(_dp) if grad_ionic is not None else None
+        _check(load().sdc_step_adjoint(self._h, C.byref(tape), _vp(_ptr(v0)), _vp(_ptr(w0)),
+                                       float(dt), _vp(_ptr(lam_v)), _vp(_ptr(lam_w)),
+                                       _vp(_ptr(lam_v0)), _vp(_ptr(lam_w0)),
+                                       _vp(_ptr(grad_scale)) if grad_scale is not None else None,
+                                       gi), self._h)
+
+    def set_dof_scale(self, scale):
+        sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
+        _check(load().sdc_set_dof_scale(self._h, None if sc is None else sc.ctypes.data_as(_dp)),
+               self._h)
+
+    def set_ionic(self, ionic):
+        _check(load().sdc_set_ionic(self._h, C.byref(ionic_struct(ionic))), self._h)
 
     def nodes(self, V, W):
         _check(load().sdc_get_nodes(self._h, _vp(_ptr(V)), _vp(_ptr(W))), self._h)

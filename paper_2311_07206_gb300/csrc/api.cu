@@ -37,6 +37,7 @@ struct sdc_ctx {
     std::vector<int> seg_bounds;  // instance boundaries in the current active list
     std::vector<int> inst_active; // [sweep][instance] active dofs of the last step
     int* h_bounds = nullptr;      // pinned staging of the boundaries
+    AdjointBuffers AW;            // adjoint workspace, allocated on first use
     bool stepped = false;
     std::string err;
 };
@@ -142,6 +143,8 @@ int alloc_buffers(sdc_ctx* c) {
     return SDC_OK;
 }
 
+void free_adjoint(AdjointBuffers& W);
+
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
     double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.idA, B.part,
@@ -158,12 +161,43 @@ void free_all(sdc_ctx* c) {
     free_ell(B.A[0]);
     free_ell(B.A[1]);
     free_ell(c->K.K);
+    free_mesh_dev(c->K.mesh);
+    free_adjoint(c->AW);
     for (int* p : c->act) cudaFree(p);
     c->act.clear();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     if (c->h_pin) cudaFreeHost(c->h_pin);
     c->h_pin = nullptr;
+}
+
+bool ensure_pos(sdc_ctx* c) {
+    if (c->AW.pos) return true;
+    if (!dalloc(&c->AW.pos, c->N)) return false;
+    cudaMemsetAsync(c->AW.pos, 0xff, (size_t)c->N * sizeof(int), c->stream);   // all -1
+    return true;
+}
+
+bool ensure_adjoint(sdc_ctx* c) {
+    AdjointBuffers& W = c->AW;
+    if (W.Vb) return true;
+    const size_t NM = (size_t)c->N * c->M, MLD = (size_t)c->M * c->B.ld;
+    return ensure_pos(c) && dalloc(&W.Vb, NM) && dalloc(&W.Wb, NM) && dalloc(&W.V0, NM) &&
+           dalloc(&W.W0, NM) && dalloc(&W.X, MLD) && dalloc(&W.Jb, MLD) &&
+           dalloc(&W.bfull, NM) && dalloc(&W.vkfull, NM) && dalloc(&W.ffull, NM) &&
+           dalloc(&W.ge, (size_t)c->K.mesh.n_elems) &&
+           dalloc(&W.part3, 3 * (size_t)((c->N + 255) / 256)) && dalloc(&W.iacc, 3) &&
+           dalloc(&W.iters, (size_t)SDC_MAX_SWEEPS * kMaxM) &&
+           dalloc(&W.relres, (size_t)SDC_MAX_SWEEPS * kMaxM);
+}
+
+void free_adjoint(AdjointBuffers& W) {
+    double* dp[] = {W.Vb, W.Wb, W.V0, W.W0, W.X, W.Jb, W.bfull, W.vkfull, W.ffull, W.ge,
+                    W.part3, W.iacc, W.relres};
+    for (double* p : dp) cudaFree(p);
+    cudaFree(W.pos);
+    cudaFree(W.iters);
+    W = AdjointBuffers();
 }
 
 bool finite_all(const double* a, int n) {
@@ -361,8 +395,48 @@ sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, dou
     return SDC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                     double TOL, sdc_stats* stats, sdc_tape* tape);
+}
+
+extern "C" {
+
 sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
                     double TOL, sdc_stats* stats) {
+    return step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats, nullptr);
+}
+
+sdc_status sdc_step_taped(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                          double TOL, sdc_stats* stats, sdc_tape* tape) {
+    if (!c) return SDC_E_INVALID;
+    if (tape && tape->mode != SDC_TAPE_OFF) {
+        if (tape->mode != SDC_TAPE_RECORD && tape->mode != SDC_TAPE_REPLAY)
+            return fail(c, SDC_E_INVALID, "unknown tape mode %d", tape->mode);
+        if (!tape->d_V || !tape->d_W || (sweeps > 1 && !tape->d_act))
+            return fail(c, SDC_E_INVALID, "tape buffers missing");
+        if (tape->mode == SDC_TAPE_REPLAY) {
+            if (tape->sweeps != sweeps)
+                return fail(c, SDC_E_INVALID, "replay: tape holds %d sweeps, step asks %d",
+                            tape->sweeps, sweeps);
+            if (tape->n_active[0] != c->N)
+                return fail(c, SDC_E_INVALID, "replay: first sweep must cover every dof");
+            for (int k = 1; k < sweeps; ++k)
+                if (tape->n_active[k] < 0 || tape->n_active[k] > tape->n_active[k - 1])
+                    return fail(c, SDC_E_INVALID, "replay: active sets are not nested");
+        }
+    }
+    return step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats,
+                     tape && tape->mode != SDC_TAPE_OFF ? tape : nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                     double TOL, sdc_stats* stats, sdc_tape* tape) {
     if (!c) return SDC_E_INVALID;
     if (!d_v || !d_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDC_E_INVALID, "dt must be positive");
@@ -438,7 +512,16 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
             stats->nnz_active[k] = nnz;
             stats->sweeps_run = k + 1;
         }
-        if (n == 0) continue;
+        if (n == 0) {
+            if (tape && tape->mode == SDC_TAPE_RECORD) {
+                tape->n_active[k] = 0;
+                cudaMemcpyAsync(tape->d_V + (size_t)k * N * M, B.V, (size_t)N * M * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(tape->d_W + (size_t)k * N * M, B.W, (size_t)N * M * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s);
+            }
+            continue;
+        }
         run(SDC_PHASE_RESIDUAL, 1, [&] {
             launch_residual(M, n, act, c->K.K, c->K.kdiag, c->K.mass, c->stim, stim_on, B.V, B.W,
                             d_v, dt, c->ion, c->co, c->opt.reaction_implicit, B, s);
@@ -466,7 +549,32 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
             launch_update(M, n, act, d_w, dt, c->ion, c->co, tol_drop, c->opt.w_frozen, B, s);
         });
         int* next = (k + 1 < sweeps) ? c->act[k + 1] : c->act[0];
-        run(SDC_PHASE_SELECT, 2, [&] { launch_select(n, act, next, B, s); });
+        const bool replay = tape && tape->mode == SDC_TAPE_REPLAY;
+        if (!replay) {
+            run(SDC_PHASE_SELECT, 2, [&] { launch_select(n, act, next, B, s); });
+        } else {
+            // the next set comes from the tape; the old->new row map from a position table
+            const int nn = (k + 1 < sweeps) ? tape->n_active[k + 1] : 0;
+            if (!ensure_pos(c)) {
+                status = fail(c, SDC_E_NOMEM, "replay: position table allocation failed");
+                break;
+            }
+            if (nn > 0)
+                cudaMemcpyAsync(next, tape->d_act + (size_t)(k + 1) * N, (size_t)nn * sizeof(int),
+                                cudaMemcpyDeviceToDevice, s);
+            launch_pos_set(nn, next, c->AW.pos, 0, s);
+            launch_replay_map(n, act, c->AW.pos, B.map, s);
+            launch_pos_set(nn, next, c->AW.pos, 1, s);
+            cudaMemcpyAsync(&B.sc->count, &tape->n_active[k + 1 < sweeps ? k + 1 : 0], sizeof(int),
+                            cudaMemcpyHostToDevice, s);
+            launches[SDC_PHASE_SELECT] += 3;
+        }
+        if (tape && tape->mode == SDC_TAPE_RECORD) {
+            cudaMemcpyAsync(tape->d_V + (size_t)k * N * M, B.V, (size_t)N * M * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(tape->d_W + (size_t)k * N * M, B.W, (size_t)N * M * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+        }
         if (batched) {
             launch_seg_bounds(next, &B.sc->count, B, s);
             launches[SDC_PHASE_SELECT] += 1;
@@ -476,6 +584,12 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
         int n_next = 0;
         int e = sync_sweep(c, n_next);
         if (batched) c->seg_bounds.assign(c->h_bounds, c->h_bounds + B.nseg + 1);
+        if (tape && tape->mode == SDC_TAPE_RECORD && e == SDC_OK) {
+            tape->n_active[k] = n;
+            if (k + 1 < sweeps && n_next > 0)
+                cudaMemcpyAsync(tape->d_act + (size_t)(k + 1) * N, next,
+                                (size_t)n_next * sizeof(int), cudaMemcpyDeviceToDevice, s);
+        }
         if (e != SDC_OK) {
             status = e == SDC_E_CUDA ? cuda_fail(c, "sweep") : fail(c, (sdc_status)e,
                      "sweep %d: %s", k, sdc_status_string(e));
@@ -503,6 +617,10 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
     }
     c->last_sweeps = sweeps;
     c->stepped = true;
+    if (tape && tape->mode == SDC_TAPE_RECORD) {
+        tape->sweeps = sweeps;
+        cudaStreamSynchronize(s);
+    }
     if (stats) {
         std::vector<int> it(SDC_MAX_SWEEPS * kMaxM);
         std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM);
@@ -553,6 +671,9 @@ sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, i
     }
     return (sdc_status)status;
 }
+}  // namespace
+
+extern "C" {
 
 sdc_status sdc_step_host(sdc_ctx* c, double* h_v, double* h_w, double t, double dt, int sweeps,
                          double TOL, sdc_stats* stats) {
@@ -852,6 +973,89 @@ void sdc_batch_destroy(sdc_batch* bt) {
     if (!bt) return;
     sdc_destroy(bt->ctx);
     delete bt;
+}
+
+size_t sdc_tape_bytes(const sdc_ctx* c, int sweeps) {
+    if (!c || sweeps < 1) return 0;
+    return (size_t)2 * sweeps * c->N * c->M * sizeof(double) + (size_t)sweeps * c->N * sizeof(int);
+}
+
+sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0,
+                            const double* d_w0, double dt, const double* d_lam_v,
+                            const double* d_lam_w, double* d_lam_v0, double* d_lam_w0,
+                            double* d_grad_scale, double* grad_ionic) {
+    if (!c) return SDC_E_INVALID;
+    if (!tape || tape->sweeps < 1 || tape->sweeps > SDC_MAX_SWEEPS || !tape->d_V || !tape->d_W ||
+        (tape->sweeps > 1 && !tape->d_act))
+        return fail(c, SDC_E_INVALID, "sdc_step_adjoint: missing or empty tape");
+    if (!d_v0 || !d_w0 || !d_lam_v || !d_lam_w || !d_lam_v0 || !d_lam_w0)
+        return fail(c, SDC_E_INVALID, "sdc_step_adjoint: NULL array");
+    if (!(dt > 0.0)) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: dt must be positive");
+    if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available for batches");
+    if (tape->n_active[0] != c->N)
+        return fail(c, SDC_E_INVALID, "sdc_step_adjoint: the first sweep must cover every dof");
+    if (!ensure_adjoint(c)) return fail(c, SDC_E_NOMEM, "adjoint workspace allocation failed");
+    cudaStream_t s = c->stream;
+    AdjointArgs a;
+    a.mesh = &c->K.mesh;
+    a.K = &c->K.K;
+    a.kdiag = c->K.kdiag;
+    a.mass = c->K.mass;
+    a.lam_v = d_lam_v;
+    a.lam_w = d_lam_w;
+    a.lam_v0 = d_lam_v0;
+    a.lam_w0 = d_lam_w0;
+    a.v0 = d_v0;
+    a.w0 = d_w0;
+    a.grad_scale = d_grad_scale;
+    a.tape_V = tape->d_V;
+    a.tape_W = tape->d_W;
+    a.tape_act = tape->d_act;
+    a.n_active = tape->n_active;
+    a.sweeps = tape->sweeps;
+    a.dt = dt;
+    a.ion = c->ion;
+    a.co = c->co;
+    a.reaction_implicit = c->opt.reaction_implicit;
+    a.w_frozen = c->opt.w_frozen;
+    a.rtol = c->opt.cg_rtol;
+    a.maxit = c->opt.cg_maxit;
+    a.cfg = &c->pcg;
+    cudaMemsetAsync(c->B.sc, 0, sizeof(DevScalars), s);
+    const int st = adjoint_step(a, c->B, c->AW, s);
+    if (st != SDC_OK) return cuda_fail(c, "sdc_step_adjoint");
+    double acc[3] = {0, 0, 0};
+    int herr = 0;
+    cudaMemcpyAsync(acc, c->AW.iacc, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&herr, &c->B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, "sdc_step_adjoint");
+    if (herr != 0)
+        return fail(c, (sdc_status)herr, "sdc_step_adjoint: %s", sdc_status_string(herr));
+    if (grad_ionic)
+        for (int i = 0; i < 3; ++i) grad_ionic[i] += acc[i];
+    return SDC_OK;
+}
+
+sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
+    if (!c) return SDC_E_INVALID;
+    if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: not available for batches");
+    if (h_scale)
+        for (int i = 0; i < c->N; ++i)
+            if (!std::isfinite(h_scale[i]) || !(h_scale[i] > 0.0))
+                return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: scale %d not positive", i);
+    std::string why;
+    const int rc = reassemble_device(c->K, h_scale, c->opt.drop_rel, c->stream, why);
+    if (rc != SDC_OK) return fail(c, (sdc_status)rc, "%s", why.c_str());
+    return SDC_OK;
+}
+
+sdc_status sdc_set_ionic(sdc_ctx* c, const sdc_ionic* ionic) {
+    if (!c || !ionic) return SDC_E_INVALID;
+    if (!(ionic->mu2 > 0.0) && !c->opt.w_frozen)
+        return fail(c, SDC_E_INVALID, "mu2 must be positive");
+    c->ion_c = *ionic;
+    c->ion = Ionic{ionic->ga, ionic->gs, ionic->a, ionic->eps, ionic->mu1, ionic->mu2, ionic->cw};
+    return SDC_OK;
 }
 
 void sdc_destroy(sdc_ctx* c) {

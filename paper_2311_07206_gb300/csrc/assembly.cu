@@ -38,43 +38,12 @@ __global__ void k_assemble_rows(int N, int dim, const double* __restrict__ xyz,
         const int e = n2e[k];
         const int a = n2e_loc[k];
         const int* vt = elem + (size_t)e * nv;
-        double x0[3] = {0, 0, 0};
-        for (int c = 0; c < dim; ++c) x0[c] = xyz[(size_t)vt[0] * dim + c];
-        // edge matrix E: column c = x_{c+1} - x_0 ; gradients = rows of E^{-1}
-        double E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-        for (int c = 0; c < dim; ++c)
-            for (int r = 0; r < dim; ++r) E[r][c] = xyz[(size_t)vt[c + 1] * dim + r] - x0[r];
-        double grad[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        double det;
-        if (dim == 2) {
-            det = E[0][0] * E[1][1] - E[0][1] * E[1][0];
-            const double id = 1.0 / det;
-            // inverse [[E11, -E01], [-E10, E00]] / det
-            grad[1][0] = E[1][1] * id;  grad[1][1] = -E[0][1] * id;
-            grad[2][0] = -E[1][0] * id; grad[2][1] = E[0][0] * id;
-        } else {
-            const double c00 = E[1][1] * E[2][2] - E[1][2] * E[2][1];
-            const double c01 = E[1][2] * E[2][0] - E[1][0] * E[2][2];
-            const double c02 = E[1][0] * E[2][1] - E[1][1] * E[2][0];
-            det = E[0][0] * c00 + E[0][1] * c01 + E[0][2] * c02;
-            const double id = 1.0 / det;
-            // (E^{-1})_{rc} = adj(E)_{rc} / det, adj = cofactor^T
-            grad[1][0] = c00 * id;
-            grad[1][1] = (E[0][2] * E[2][1] - E[0][1] * E[2][2]) * id;
-            grad[1][2] = (E[0][1] * E[1][2] - E[0][2] * E[1][1]) * id;
-            grad[2][0] = c01 * id;
-            grad[2][1] = (E[0][0] * E[2][2] - E[0][2] * E[2][0]) * id;
-            grad[2][2] = (E[0][2] * E[1][0] - E[0][0] * E[1][2]) * id;
-            grad[3][0] = c02 * id;
-            grad[3][1] = (E[0][1] * E[2][0] - E[0][0] * E[2][1]) * id;
-            grad[3][2] = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) * id;
-        }
-        if (det == 0.0 || !isfinite(det)) {
+        double grad[4][3];
+        double vol;
+        if (!p1_gradients(dim, xyz, vt, grad, vol)) {
             raise_error(err, SDC_E_INVALID);
             return;
         }
-        for (int c = 0; c < dim; ++c) grad[0][c] = -(grad[1][c] + grad[2][c] + grad[3][c]);
-        const double vol = fabs(det) / (dim == 2 ? 2.0 : 6.0);
         const double* D = esig9 ? esig9 + (size_t)e * 9 : sigma9;
         double sbar = 1.0;
         if (scale) {
@@ -279,9 +248,83 @@ int assemble_device(const sdc_mesh& mesh, double drop_rel, cudaStream_t s, Assem
     } else if (why.empty()) {
         why = "assembly: device allocation or copy failed";
     }
-    cudaFree(d_xyz); cudaFree(d_sig); cudaFree(d_esig); cudaFree(d_scale); cudaFree(d_val);
-    cudaFree(d_elem); cudaFree(d_n2e_ptr); cudaFree(d_n2e); cudaFree(d_n2e_loc);
-    cudaFree(d_rp); cudaFree(d_ci); cudaFree(d_err); cudaFree(d_cnt);
+    MeshDev& md = out.mesh;
+    md.dim = dim;
+    md.n_nodes = N;
+    md.n_elems = NE;
+    md.nnz_pattern = nnz;
+    md.xyz = d_xyz; md.sig = d_sig; md.esig = d_esig; md.scale = d_scale;
+    md.elem = d_elem; md.n2e_ptr = d_n2e_ptr; md.n2e = d_n2e; md.n2e_loc = d_n2e_loc;
+    md.rp = d_rp; md.ci = d_ci;
+    if (rc != SDC_OK) free_mesh_dev(md);
+    cudaFree(d_val); cudaFree(d_err); cudaFree(d_cnt);
+    return rc;
+}
+
+void free_mesh_dev(MeshDev& m) {
+    cudaFree(m.xyz); cudaFree(m.sig); cudaFree(m.esig); cudaFree(m.scale);
+    cudaFree(m.elem); cudaFree(m.n2e_ptr); cudaFree(m.n2e); cudaFree(m.n2e_loc);
+    cudaFree(m.rp); cudaFree(m.ci);
+    m = MeshDev();
+}
+
+int reassemble_device(AssemblyOut& out, const double* h_scale, double drop_rel, cudaStream_t s,
+                      std::string& why) {
+    MeshDev& md = out.mesh;
+    const int N = md.n_nodes;
+    if (!md.rp) {
+        why = "re-assembly: mesh not kept";
+        return SDC_E_INVALID;
+    }
+    if (h_scale) {
+        if (!md.scale && cudaMalloc(&md.scale, N * sizeof(double)) != cudaSuccess) return SDC_E_NOMEM;
+        cudaMemcpyAsync(md.scale, h_scale, N * sizeof(double), cudaMemcpyHostToDevice, s);
+    } else if (md.scale) {
+        cudaFree(md.scale);
+        md.scale = nullptr;
+    }
+    double* d_val = nullptr;
+    int *d_err = nullptr, *d_cnt = nullptr;
+    if (cudaMalloc(&d_val, md.nnz_pattern * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&d_cnt, N * sizeof(int)) != cudaSuccess) {
+        cudaFree(d_val); cudaFree(d_err); cudaFree(d_cnt);
+        return SDC_E_NOMEM;
+    }
+    int rc = SDC_OK;
+    cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    const int bs = 128, gs = (N + bs - 1) / bs;
+    k_assemble_rows<<<gs, bs, 0, s>>>(N, md.dim, md.xyz, md.elem, md.n2e_ptr, md.n2e, md.n2e_loc,
+                                      md.sig, md.esig, md.scale, md.rp, md.ci, d_val, out.mass,
+                                      d_err);
+    k_diag<<<gs, bs, 0, s>>>(N, md.rp, md.ci, d_val, out.kdiag);
+    k_ell_count<<<gs, bs, 0, s>>>(N, md.rp, md.ci, d_val, out.kdiag, drop_rel, d_cnt);
+    std::vector<int> cnt(N);
+    int herr = 0;
+    cudaMemcpyAsync(cnt.data(), d_cnt, N * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = SDC_E_CUDA;
+        why = std::string("re-assembly: ") + cudaGetErrorString(cudaGetLastError());
+    } else if (herr != 0) {
+        rc = SDC_E_INVALID;
+        why = "re-assembly: degenerate element";
+    } else {
+        long long kept = 0;
+        int maxw = 0;
+        for (int c : cnt) { maxw = std::max(maxw, c); kept += c; }
+        if (maxw > out.K.width) {
+            rc = SDC_E_INVALID;
+            why = "re-assembly: the new scale stores more off-diagonals per row than the context";
+        } else {
+            out.nnz = kept + N;
+            cudaMemsetAsync(out.K.len, 0, (size_t)out.K.ld * sizeof(int), s);
+            k_ell_fill<<<gs, bs, 0, s>>>(N, md.rp, md.ci, d_val, out.kdiag, drop_rel, out.K.ld,
+                                          out.K.val, out.K.col, out.K.len);
+            if (cudaStreamSynchronize(s) != cudaSuccess) rc = SDC_E_CUDA;
+        }
+    }
+    cudaFree(d_val); cudaFree(d_err); cudaFree(d_cnt);
     return rc;
 }
 

@@ -27,6 +27,49 @@ __device__ __forceinline__ void ap_R_dRdw(const Ionic& p, double v, double w, do
     dRdw = p.cw * (p.mu1 * inv * G - E);
 }
 
+// ---- P1 element geometry (Sec. 2.2) -------------------------------------------
+// Gradients of the barycentric coordinates of simplex e and its measure.
+// Returns false for a degenerate element.  grad[a][c], a = 0..dim.
+__device__ __forceinline__ bool p1_gradients(int dim, const double* __restrict__ xyz,
+                                             const int* vt, double grad[4][3], double& vol) {
+    double x0[3] = {0, 0, 0};
+    for (int c = 0; c < dim; ++c) x0[c] = xyz[(size_t)vt[0] * dim + c];
+    // edge matrix E: column c = x_{c+1} - x_0 ; gradients = rows of E^{-1}
+    double E[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int c = 0; c < dim; ++c)
+        for (int r = 0; r < dim; ++r) E[r][c] = xyz[(size_t)vt[c + 1] * dim + r] - x0[r];
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) grad[a][c] = 0.0;
+    double det;
+    if (dim == 2) {
+        det = E[0][0] * E[1][1] - E[0][1] * E[1][0];
+        const double id = 1.0 / det;
+        // inverse [[E11, -E01], [-E10, E00]] / det
+        grad[1][0] = E[1][1] * id;  grad[1][1] = -E[0][1] * id;
+        grad[2][0] = -E[1][0] * id; grad[2][1] = E[0][0] * id;
+    } else {
+        const double c00 = E[1][1] * E[2][2] - E[1][2] * E[2][1];
+        const double c01 = E[1][2] * E[2][0] - E[1][0] * E[2][2];
+        const double c02 = E[1][0] * E[2][1] - E[1][1] * E[2][0];
+        det = E[0][0] * c00 + E[0][1] * c01 + E[0][2] * c02;
+        const double id = 1.0 / det;
+        // (E^{-1})_{rc} = adj(E)_{rc} / det, adj = cofactor^T
+        grad[1][0] = c00 * id;
+        grad[1][1] = (E[0][2] * E[2][1] - E[0][1] * E[2][2]) * id;
+        grad[1][2] = (E[0][1] * E[1][2] - E[0][2] * E[1][1]) * id;
+        grad[2][0] = c01 * id;
+        grad[2][1] = (E[0][0] * E[2][2] - E[0][2] * E[2][0]) * id;
+        grad[2][2] = (E[0][2] * E[1][0] - E[0][0] * E[1][2]) * id;
+        grad[3][0] = c02 * id;
+        grad[3][1] = (E[0][1] * E[2][0] - E[0][0] * E[2][1]) * id;
+        grad[3][2] = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) * id;
+    }
+    if (det == 0.0 || !isfinite(det)) return false;
+    for (int c = 0; c < dim; ++c) grad[0][c] = -(grad[1][c] + grad[2][c] + grad[3][c]);
+    vol = fabs(det) / (dim == 2 ? 2.0 : 6.0);
+    return true;
+}
+
 // ---- error flag: first error wins ---------------------------------------------
 __device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
 

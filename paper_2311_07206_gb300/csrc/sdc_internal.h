@@ -51,14 +51,35 @@ struct Ell {
 bool radau_collocation(int M, double* tau, double* Q, double* Qhat);
 
 // ---- assembly (assembly.cu) ----
+// The mesh as kept on the device (re-assembly, conductivity gradients).
+struct MeshDev {
+    int dim = 0, n_nodes = 0, n_elems = 0;
+    long long nnz_pattern = 0;
+    double* xyz = nullptr;     // n_nodes * dim
+    double* sig = nullptr;     // 9, global tensor
+    double* esig = nullptr;    // n_elems * 9 or null
+    double* scale = nullptr;   // n_nodes or null (all ones)
+    int* elem = nullptr;       // n_elems * (dim + 1)
+    int* n2e_ptr = nullptr;    // node -> element lists, ascending element order
+    int* n2e = nullptr;
+    int* n2e_loc = nullptr;    // the node's local index in that element
+    int* rp = nullptr;         // CSR pattern of K
+    int* ci = nullptr;
+};
 struct AssemblyOut {
     Ell K;                 // off-diagonal part of K (device)
     double* kdiag = nullptr;
     double* mass = nullptr;
     long long nnz = 0;     // stored entries including the diagonal
+    MeshDev mesh;
 };
 int assemble_device(const sdc_mesh& mesh, double drop_rel, cudaStream_t s, AssemblyOut& out,
                     std::string& why);
+// Recompute K's values for a new per-node conductivity scale (host array, or
+// null for all ones) on the kept pattern; fails if the stored width would grow.
+int reassemble_device(AssemblyOut& out, const double* h_scale, double drop_rel, cudaStream_t s,
+                      std::string& why);
+void free_mesh_dev(MeshDev& m);
 
 // ---- step kernels (step.cu) ----
 struct StepBuffers {
@@ -132,6 +153,23 @@ int pcg_sm_count();
 // Message returned by sdc_last_error(NULL) on the calling thread.
 void set_thread_error(const char* msg);
 
+// One node solve with caller-chosen right-hand side, solution, J and
+// coupling targets (the reverse sweep of the adjoint uses it).
+struct PcgRole {
+    const double* b;
+    double* x;
+    const double* J;        // J of the solved node, compact
+    const double* Jall;     // [M][ld] J of every node (targets use their own)
+    double* R;              // [M][ld] coupling targets
+    int epi_lo, epi_hi, epi_target_J;
+    double qh[kMaxM];
+    double c;               // dt * Qhat_mm of the solved node
+    int* iters_out;
+    double* relres_out;
+};
+int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,
+                    int maxit, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
+
 // Batched PCG: independent solves of the instances whose compact rows are
 // [bounds[s], bounds[s+1]); empty instances are skipped.
 int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
@@ -139,6 +177,48 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
                      StepBuffers& B, cudaStream_t s);
 void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s);
 int pcg_batch_max_blocks(int block);
+
+// ---- adjoint (adjoint.cu) ----
+struct AdjointArgs {
+    const MeshDev* mesh;
+    const Ell* K;
+    const double* kdiag;
+    const double* mass;
+    const double* lam_v;   // adjoints of the step's outputs
+    const double* lam_w;
+    double* lam_v0;        // adjoints of the step's inputs (written)
+    double* lam_w0;
+    const double* v0;      // the step's inputs
+    const double* w0;
+    double* grad_scale;    // += dL/ds per node, or null
+    const double* tape_V;  // [sweeps][N * M] state after each sweep
+    const double* tape_W;
+    const int* tape_act;   // [sweeps][N] active list of sweep k (k >= 1)
+    const int* n_active;   // host [sweeps]
+    int sweeps;
+    double dt;
+    Ionic ion;
+    Coll co;
+    int reaction_implicit, w_frozen;
+    double rtol;
+    int maxit;
+    const PcgConfig* cfg;
+};
+struct AdjointBuffers {
+    double *Vb = nullptr, *Wb = nullptr, *V0 = nullptr, *W0 = nullptr;
+    double *X = nullptr, *Jb = nullptr;                       // [M][ld]
+    double *bfull = nullptr, *vkfull = nullptr, *ffull = nullptr;   // [M][N]
+    double *ge = nullptr;                                     // [n_elems]
+    double *part3 = nullptr, *iacc = nullptr;                 // block partials, 3 accumulators
+    int* pos = nullptr;                                       // [N], -1 outside a list
+    int* iters = nullptr;                                     // [SDC_MAX_SWEEPS * kMaxM]
+    double* relres = nullptr;
+};
+int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaStream_t s);
+void launch_pos_set(int n, const int* act, int* pos, int reset, cudaStream_t s);
+void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, Ell& out,
+                           cudaStream_t s);
+void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
 // r, z, p, q, dA, idA: n doubles each; part: 2 * max_blocks doubles;

@@ -135,10 +135,25 @@ struct CgParams {
     int m, M;
     double dt;
     double* R;
-    double qh[kMaxM];    // Qhat[m'][m], m' = 0..M-1
+    double qh[kMaxM];    // coupling coefficient per target node
+    // targets [epi_lo, epi_hi): R[t] -= dt qh[t] (K x + mass J' x), with J' this
+    // node's J (forward sweep, targets after m) or the target's own J taken from
+    // Jall (reverse sweep, targets before m)
+    int epi_lo, epi_hi, epi_target_J;
+    const double* Jall;
     int inject_fault;    // testing hook: the last block skips the first barrier
     int L;               // rows per block (shared-memory variant)
 };
+
+// LU-trick coupling of one solved row into the right-hand sides of other nodes.
+__device__ __forceinline__ void cg_couple_row(const CgParams& P, int i, double xi, double kx) {
+    const double base = P.kdc[i] * xi + kx;
+    for (int t = P.epi_lo; t < P.epi_hi; ++t) {
+        const double Jt = P.epi_target_J ? P.Jall[(size_t)t * P.ld + i] : P.J[i];
+        P.R[(size_t)t * P.ld + i] -= P.dt * P.qh[t] * (base + P.mc[i] * Jt * xi);
+    }
+}
+
 
 // Shared per-block scalars of a CG solve.  Lane 0 of warp 0 derives them from
 // each grid-wide sum (one FP64 division / square root per block, not per
@@ -297,16 +312,14 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         *relres_out = cg_relres(S);
     }
     // x is complete in every block of the group: the last group sum followed its update.
-    if (P.m + 1 < P.M) {
+    if (P.epi_lo < P.epi_hi) {
         for (int i = i0; i < row1; i += stride) {
             const int len = P.alen[i];
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
             for (int t = 0; t < len; ++t)
                 acc += P.aval[(size_t)t * ld + i] * __ldcg(P.x + P.acol[(size_t)t * ld + i]);
-            const double corr = P.kdc[i] * xi + acc + P.mc[i] * P.J[i] * xi;
-            for (int mm = P.m + 1; mm < P.M; ++mm)
-                P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
+            cg_couple_row(P, i, xi, acc);
         }
     }
 }
@@ -455,7 +468,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
         *P.relres_out = cg_relres(S);
     }
     for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
-    if (P.m + 1 < P.M) {
+    if (P.epi_lo < P.epi_hi) {
         if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
@@ -464,9 +477,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
                 acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(P.x + __ldg(acol + (size_t)k * ld + i));
-            const double corr = P.kdc[i] * xi + acc + P.mc[i] * P.J[i] * xi;
-            for (int mm = P.m + 1; mm < P.M; ++mm)
-                P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
+            cg_couple_row(P, i, xi, acc);
         }
     }
 }
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
             *P.relres_out = cg_relres(S);
         }
         for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
-        if (P.m + 1 < P.M) {
+        if (P.epi_lo < P.epi_hi) {
             cl.sync();   // every CTA's x is final
             for (int l = t; l < nl; l += B) {
                 const int i = r0 + l;
@@ -611,9 +622,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
                     const int owner = j / L;
                     acc += __ldg(aval + (size_t)k * ld + i) * xr[owner][j - owner * L];
                 }
-                const double corr = P.kdc[i] * xi + acc + P.mc[i] * P.J[i] * xi;
-                for (int mm = P.m + 1; mm < P.M; ++mm)
-                    P.R[(size_t)mm * ld + i] -= P.dt * P.qh[mm] * corr;
+                cg_couple_row(P, i, xi, acc);
             }
         }
     }
@@ -834,6 +843,8 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
     });
 }
 
+int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
+
 int pcg_max_blocks(int block) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -904,11 +915,64 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.relres_out = &B.sc->cg_relres[sweep * kMaxM + m];
     P.m = m;
     P.M = co.M;
+    P.epi_lo = m + 1;
+    P.epi_hi = co.M;
+    P.epi_target_J = 0;
+    P.Jall = B.J;
     P.dt = dt;
     P.R = B.R;
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = j < co.M ? co.Qh[j * kMaxM + m] : 0.0;
     P.inject_fault = cfg.inject_fault;
     P.L = 0;
+    return launch_pcg_params(P, cfg, B, s);
+}
+
+int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,
+                    int maxit, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
+    CgParams P;
+    P.n = n;
+    P.ld = B.ld;
+    P.aval = A.val;
+    P.acol = A.col;
+    P.alen = A.len;
+    P.mc = B.mc;
+    P.kdc = B.kdc;
+    P.J = role.J;
+    P.c = role.c;
+    P.b = role.b;
+    P.x = role.x;
+    P.r = B.r;
+    P.z = B.z;
+    P.p = B.p;
+    P.q = B.q;
+    P.dA = B.dA;
+    P.idA = B.idA;
+    P.part = B.part;
+    P.bar = &B.sc->bar;
+    P.err = &B.sc->err;
+    P.rtol = rtol;
+    P.maxit = maxit;
+    P.budget = cfg.budget;
+    P.iters_out = role.iters_out;
+    P.relres_out = role.relres_out;
+    P.m = 0;
+    P.M = M;
+    P.epi_lo = role.epi_lo;
+    P.epi_hi = role.epi_hi;
+    P.epi_target_J = role.epi_target_J;
+    P.Jall = role.Jall;
+    P.dt = dt;
+    P.R = role.R;
+    for (int j = 0; j < kMaxM; ++j) P.qh[j] = role.qh[j];
+    P.inject_fault = 0;
+    P.L = 0;
+    PcgConfig c2 = cfg;
+    c2.inject_fault = 0;
+    return launch_pcg_params(P, c2, B, s);
+}
+
+int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
+    const int n = P.n;
     cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
     void* args[] = {&P};
     // cluster variant: one cluster of cfg.cluster CTAs for small active sets
@@ -1029,6 +1093,10 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.relres_out = nullptr;
     P.m = m;
     P.M = co.M;
+    P.epi_lo = m + 1;
+    P.epi_hi = co.M;
+    P.epi_target_J = 0;
+    P.Jall = B.J;
     P.dt = dt;
     P.R = B.R;
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = j < co.M ? co.Qh[j * kMaxM + m] : 0.0;
@@ -1094,7 +1162,11 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.iters_out = w.iters;
     P.relres_out = w.relres;
     P.m = 0;
-    P.M = 1;            // no coupling into later nodes
+    P.M = 1;            // no coupling into other nodes
+    P.epi_lo = 0;
+    P.epi_hi = 0;
+    P.epi_target_J = 0;
+    P.Jall = nullptr;
     P.dt = 0.0;
     P.R = nullptr;
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = 0.0;
