@@ -48,8 +48,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w3"], default="w1",
-                    help="w3: 96-instance batch, batched launches vs per-instance launches")
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w3", "w4"], default="w1",
+                    help="w3: 96-instance batch, batched launches vs per-instance launches; "
+                         "w4: gradient by the discrete adjoint vs finite differences")
+    ap.add_argument("--fd-directions", type=int, default=16)
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -483,12 +485,111 @@ def run_batch(args):
     return 0
 
 
+def run_grad(args):
+    """W4 (101x36x16 slab, M = 3, 200 steps): gradient of the probe loss with
+    respect to the per-node conductivity scale and (k, a) by the discrete
+    adjoint with checkpoints every 20 steps, checked against central
+    differences on random directions with the active sets replayed."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Context, default_options
+    from paper_2311_07206_gb300.autodiff import TrajectoryLoss, _set_params, replayed_loss
+
+    wl = W.w4_slab()
+    steps = min(args.steps, wl.steps)
+    ck = 20
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context.from_workload(wl, options=default_options(cg_rtol=1e-12),
+                                stream=stream.cuda_stream)
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    probes = t64(wl.meta["probes"]).long()
+    k0, a0 = wl.ionic["ga"], wl.ionic["a"]
+    s_init = wl.dof_scale.copy()
+    # target: the run with s = 1 and the nominal (k, a)
+    _set_params(ctx, wl, t64(np.ones(wl.n)), k0, a0)
+    v, w = t64(wl.v0), t64(wl.w0)
+    targets = []
+    for n in range(steps):
+        ctx.step(v, w, n * wl.dt, wl.dt, wl.sweeps, wl.tol, want_stats=False)
+        targets.append(v[probes].clone())
+    for _ in range(max(1, args.warmup)):
+        sc = t64(s_init).requires_grad_(True)
+        ka = t64([k0, a0]).requires_grad_(True)
+        TrajectoryLoss.apply(sc, ka, ctx, wl, min(steps, ck), probes, targets, ck).backward()
+    torch.cuda.synchronize(dev)
+    sc = t64(s_init).requires_grad_(True)
+    ka = t64([k0, a0]).requires_grad_(True)
+    t0 = time.perf_counter()
+    L = TrajectoryLoss.apply(sc, ka, ctx, wl, steps, probes, targets, ck)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    gs, gka = sc.grad.cpu().numpy(), ka.grad.cpu().numpy()
+    # finite differences with the forward's active sets replayed
+    _set_params(ctx, wl, t64(s_init), k0, a0)
+    v0, w0 = t64(wl.v0), t64(wl.w0)
+    tapes = []
+    v, w = v0.clone(), w0.clone()
+    for n in range(steps):
+        tp = ctx.new_tape(wl.sweeps, dev)
+        ctx.step_taped(v, w, n * wl.dt, wl.dt, wl.sweeps, wl.tol, tp)
+        tapes.append(tp)
+    rng = np.random.default_rng(SEED_FD)
+    errs = []
+    h = 1e-5 * float(np.linalg.norm(s_init))
+    tf0 = time.perf_counter()
+    for _ in range(args.fd_directions):
+        d = rng.standard_normal(wl.n)
+        d /= np.linalg.norm(d)
+        lp, lm = [], []
+        for sgn, out in ((1, lp), (-1, lm)):
+            _set_params(ctx, wl, t64(s_init + sgn * h * d), k0, a0)
+            out.append(replayed_loss(ctx, wl, v0, w0, steps, probes, targets, tapes))
+        fd = (lp[0] - lm[0]) / (2 * h)
+        ad = float(gs @ d)
+        errs.append(abs(fd - ad) / max(abs(fd), abs(ad), 1e-300))
+    tf1 = time.perf_counter()
+    del tapes
+    line = {"metric": "adjoint gradient evaluations/s, W4 slab 101x36x16 (200 steps)",
+            "value": 1.0 / (t2 - t0), "unit": "gradients/s", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * (t2 - t0) / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "n_dofs": wl.n, "M": wl.M, "dt_ms": wl.dt,
+                       "sweeps": wl.sweeps, "TOL": wl.tol, "checkpoint_every": ck,
+                       "probes": int(probes.numel()), "cg_rtol": 1e-12},
+            "loss": L.item(), "forward_s": t1 - t0, "backward_s": t2 - t1,
+            "grad_norm_scale": float(np.linalg.norm(gs)), "grad_k_a": gka.tolist(),
+            "fd_check": {"directions": args.fd_directions, "step": h,
+                         "max_rel_err": max(errs) if errs else None,
+                         "median_rel_err": float(np.median(errs)) if errs else None,
+                         "masks": "replayed from the forward", "seconds": tf1 - tf0}}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+SEED_FD = 2311_07206 + 40
+
+
 def main():
     args = parse()
+    if args.impl == "reference" and args.workload in ("w3", "w4"):
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the reference arm times the oracle on the slab workload only"}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "w3":
         return run_batch(args)
+    if args.workload == "w4":
+        return run_grad(args)
     return run_gb300(args)
 
 
