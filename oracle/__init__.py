@@ -72,6 +72,9 @@ def lib():
         L.ora_step_forced.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
                                       C.c_double, C.c_int, C.c_double, C.POINTER(_Opts),
                                       C.POINTER(Stats), _ip, _dp, _dp, _ip, _ip]
+        L.ora_step_emi.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_double, C.c_double, C.c_int,
+                                   C.c_int, _ip, _ip, _dp, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
+                                   C.c_double, C.POINTER(_Opts), C.POINTER(Stats), _ip]
         L.ora_collocation_solve.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
                                             C.c_double, _dp, _dp, _ip]
         _lib = L
@@ -211,6 +214,34 @@ class System:
                                    _d(w), dt, sweeps, 0.0, C.byref(opts), C.byref(st), None, None,
                                    None, _i(counts), _i(flat))
         return dict(v=v, w=w, status=rc, stats=st)
+
+    def step_emi(self, wl, u, w, sweeps=None, tol=None, cg_rtol=None, w_frozen=False,
+                 want_log=False):
+        """One SDC step of a cell-by-cell workload (K of this system = the
+        subdomain stiffness; pairs, Robin and membrane data from `wl`)."""
+        n = self.n
+        sweeps = wl.sweeps if sweeps is None else sweeps
+        tol = wl.tol if tol is None else tol
+        cg_rtol = wl.cg_rtol if cg_rtol is None else cg_rtol
+        u = np.array(u, dtype=np.float64, copy=True)
+        w = np.array(w, dtype=np.float64, copy=True)
+        st = Stats()
+        opts = _Opts(wl.alpha, cg_rtol, 100000, 1, int(w_frozen))
+        log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
+        rob = _f64(wl.robin)
+        pk, pl, pa, pkd = _i32(wl.pair_k), _i32(wl.pair_l), _f64(wl.pair_area), _i32(wl.pair_kind)
+        rc = lib().ora_step_emi(self._h, C.byref(_ionic(wl.ionic)), wl.Cm, wl.g_gap, wl.M,
+                                wl.n_pairs, _i(pk), _i(pl), _d(pa), _i(pkd), _d(rob), _d(u),
+                                _d(w), wl.dt, sweeps, tol, C.byref(opts), C.byref(st), _i(log))
+        out = dict(u=u, w=w, status=rc, stats=st)
+        if want_log:
+            lists, pos = [], 0
+            for k in range(st.sweeps_run):
+                c = st.n_active[k]
+                lists.append(log[pos:pos + c].copy())
+                pos += c
+            out["active"] = lists
+        return out
 
     def collocation_solve(self, ionic: dict, M: int, v, w, dt: float, istim=None):
         """Dense Newton solution of the full collocation system (tiny meshes)."""

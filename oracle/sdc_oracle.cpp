@@ -354,6 +354,49 @@ int pcg(const Csr& K, double c, const std::vector<double>& dA, const std::vector
     return ORA_CG_NOCONV;
 }
 
+// Jacobi PCG with the operator given as a function y = A x on the active rows
+// (x is zero off the active set), same iteration and stopping rule as pcg().
+template <class Op>
+int pcg_op(int n, Op apply, const std::vector<double>& diag, const std::vector<int>& act,
+           const std::vector<double>& b, std::vector<double>& x, double rtol, int maxit,
+           int& iters, double& relres) {
+    std::vector<double> r(n, 0.0), z(n, 0.0), p(n, 0.0), q(n, 0.0);
+    for (int i : act) {
+        x[i] = 0.0;
+        r[i] = b[i];
+        z[i] = r[i] / diag[i];
+        p[i] = z[i];
+    }
+    double rho = 0.0;
+    for (int i : act) rho += r[i] * z[i];
+    const double rho0 = rho;
+    iters = 0;
+    relres = 0.0;
+    if (rho0 == 0.0) return ORA_OK;
+    if (!std::isfinite(rho0)) return ORA_NONFINITE;
+    for (int it = 1; it <= maxit; ++it) {
+        apply(p, q);
+        double pq = 0.0;
+        for (int i : act) pq += p[i] * q[i];
+        double alpha = rho / pq;
+        for (int i : act) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            z[i] = r[i] / diag[i];
+        }
+        double rho_new = 0.0;
+        for (int i : act) rho_new += r[i] * z[i];
+        iters = it;
+        relres = std::sqrt(std::fabs(rho_new) / rho0);
+        if (!std::isfinite(rho_new)) return ORA_NONFINITE;
+        if (std::sqrt(rho_new) <= rtol * std::sqrt(rho0)) return ORA_OK;
+        double beta = rho_new / rho;
+        rho = rho_new;
+        for (int i : act) p[i] = z[i] + beta * p[i];
+    }
+    return ORA_CG_NOCONV;
+}
+
 double kdiag(const Csr& K, int i) {
     for (int k = K.ptr[i]; k < K.ptr[i + 1]; ++k)
         if (K.col[k] == i) return K.val[k];
@@ -604,6 +647,186 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
     if (Vn) std::copy(V.begin(), V.end(), Vn);
     if (Wn) std::copy(W.begin(), W.end(), Wn);
     return status;
+}
+
+// One SDC step of the cell-by-cell (EMI) system (Sec. 2.1, eq. abstract reaction
+// diffusion / abstract gating) in the abstract form B u' = -A u - b(u, w) of
+// Sec. 3:
+//   A = K + diag(robin)                 (stiffness of every subdomain, Robin term)
+//   B = sum_p area_p Cm (e_k - e_l)(e_k - e_l)^T              (membrane capacitance)
+//   b = sum_p area_p I_p(u_k - u_l, w_p) (e_k - e_l),  I_p = I_ion (kind 0) or g_gap v (kind 1)
+//   w_p' = R(u_k - u_l, w_p) on the cell-ECS pairs (kind 0).
+// The sweep is that of ora_step with B in place of the lumped mass and the
+// pair Jacobian sum_p area_p dI_p/dv (e_k - e_l)(e_k - e_l)^T in place of the
+// lumped ionic Jacobian; the gating sweep runs over the pairs with an active
+// endpoint; selection uses |du| of every potential dof.
+int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, int n_pairs,
+                 const int* pk, const int* pl, const double* parea, const int* pkind,
+                 const double* robin, double* u, double* w, double dt, int sweeps, double tol,
+                 const ora_opts* o, ora_stats* st, int* active_log) {
+    System& S = *(System*)h;
+    const Csr& K = S.K;
+    const int N = K.n, NP = n_pairs;
+    Collocation col;
+    if (!make_collocation(M, col) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 || dt <= 0)
+        return ORA_INVALID;
+    const std::vector<double>& Q = col.Q;
+    const std::vector<double>& Qh = col.Qhat;
+    Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
+    const double tol_drop = o->alpha * tol;
+    // pairs incident to each node, with the sign of the node in v = u_k - u_l
+    std::vector<std::vector<std::pair<int, int>>> inc(N);
+    for (int q = 0; q < NP; ++q) {
+        inc[pk[q]].push_back({q, +1});
+        inc[pl[q]].push_back({q, -1});
+    }
+    auto partner = [&](int q, int i) { return pk[q] == i ? pl[q] : pk[q]; };
+    std::vector<double> u0(u, u + N), w0(w, w + NP);
+    std::vector<double> U((size_t)M * N), Wp((size_t)M * NP);
+    for (int m = 0; m < M; ++m) {
+        for (int i = 0; i < N; ++i) U[(size_t)m * N + i] = u0[i];
+        for (int q = 0; q < NP; ++q) Wp[(size_t)m * NP + q] = w0[q];
+    }
+    std::vector<int> act(N);
+    for (int i = 0; i < N; ++i) act[i] = i;
+    std::vector<char> on(N, 1);
+    std::vector<double> Ip((size_t)M * NP), Jp((size_t)M * NP), f((size_t)M * N), r((size_t)M * N),
+        delta((size_t)M * N), b(N), diag(N), Kd(N);
+    for (int i = 0; i < N; ++i) Kd[i] = kdiag(K, i) + (robin ? robin[i] : 0.0);
+    if (st) {
+        std::memset(st, 0, sizeof(*st));
+        st->min_margin = INFINITY;
+    }
+    size_t log_pos = 0;
+    // (A x)_i over the full row: K plus the Robin diagonal
+    auto arow = [&](int i, const double* x) {
+        return krow(K, i, x) + (robin ? robin[i] : 0.0) * x[i];
+    };
+    for (int k = 0; k < sweeps; ++k) {
+        if (st) {
+            st->n_active[k] = (int)act.size();
+            st->sweeps_run = k + 1;
+        }
+        if (active_log) {
+            std::copy(act.begin(), act.end(), active_log + log_pos);
+            log_pos += act.size();
+        }
+        if (act.empty()) continue;
+        for (int m = 0; m < M; ++m)
+            for (int q = 0; q < NP; ++q) {
+                const double v = U[(size_t)m * N + pk[q]] - U[(size_t)m * N + pl[q]];
+                const double wq = Wp[(size_t)m * NP + q];
+                if (pkind[q] == 0) {
+                    Ip[(size_t)m * NP + q] = ion_I(p, v, wq);
+                    Jp[(size_t)m * NP + q] = o->reaction_implicit ? ion_dIdv(p, v, wq) : 0.0;
+                } else {
+                    Ip[(size_t)m * NP + q] = g_gap * v;
+                    Jp[(size_t)m * NP + q] = o->reaction_implicit ? g_gap : 0.0;
+                }
+            }
+        for (int m = 0; m < M; ++m)
+            for (int i : act) {
+                double s = -arow(i, &U[(size_t)m * N]);
+                for (auto& e : inc[i]) s -= e.second * parea[e.first] * Ip[(size_t)m * NP + e.first];
+                f[(size_t)m * N + i] = s;
+            }
+        for (int m = 0; m < M; ++m)
+            for (int i : act) {
+                double bt = 0.0;
+                for (auto& e : inc[i]) {
+                    const int j = partner(e.first, i);
+                    bt += parea[e.first] * Cm *
+                          ((u0[i] - u0[j]) - (U[(size_t)m * N + i] - U[(size_t)m * N + j]));
+                }
+                double qs = 0.0;
+                for (int j = 0; j < M; ++j) qs += Q[m * M + j] * f[(size_t)j * N + i];
+                r[(size_t)m * N + i] = bt + dt * qs;
+            }
+        std::fill(delta.begin(), delta.end(), 0.0);
+        for (int m = 0; m < M; ++m) {
+            for (int i : act) {
+                double corr = 0.0;
+                for (int j = 0; j < m; ++j) {
+                    const double* dj = &delta[(size_t)j * N];
+                    double pj = 0.0;
+                    for (auto& e : inc[i])
+                        pj += parea[e.first] * Jp[(size_t)j * NP + e.first] *
+                              (dj[i] - dj[partner(e.first, i)]);
+                    corr += Qh[m * M + j] * (arow(i, dj) + pj);
+                }
+                b[i] = r[(size_t)m * N + i] - dt * corr;
+            }
+            const double c = dt * Qh[m * M + m];
+            for (int i : act) {
+                double d = c * Kd[i];
+                for (auto& e : inc[i]) d += parea[e.first] * (Cm + c * Jp[(size_t)m * NP + e.first]);
+                diag[i] = d;
+                if (!std::isfinite(d)) return ORA_NONFINITE;
+                if (!(d > 0.0)) return ORA_DOMAIN;
+            }
+            auto apply = [&](const std::vector<double>& x, std::vector<double>& y) {
+                for (int i : act) {
+                    double s = c * arow(i, x.data());
+                    for (auto& e : inc[i])
+                        s += parea[e.first] * (Cm + c * Jp[(size_t)m * NP + e.first]) *
+                             (x[i] - x[partner(e.first, i)]);
+                    y[i] = s;
+                }
+            };
+            std::vector<double> x(N, 0.0);
+            int iters = 0;
+            double relres = 0.0;
+            const int rc = pcg_op(N, apply, diag, act, b, x, o->cg_rtol, o->cg_maxit, iters, relres);
+            if (st) {
+                st->cg_iters[k * ORA_MAX_M + m] = iters;
+                st->cg_relres_max = std::max(st->cg_relres_max, relres);
+            }
+            if (rc != ORA_OK) return rc;
+            for (int i : act) delta[(size_t)m * N + i] = x[i];
+        }
+        for (int m = 0; m < M; ++m)
+            for (int i : act) U[(size_t)m * N + i] += delta[(size_t)m * N + i];
+        if (!o->w_frozen) {
+            for (int q = 0; q < NP; ++q) {
+                if (pkind[q] != 0 || !(on[pk[q]] || on[pl[q]])) continue;
+                double g[ORA_MAX_M], d[ORA_MAX_M], s[ORA_MAX_M], eps[ORA_MAX_M];
+                for (int m = 0; m < M; ++m) {
+                    const double v = U[(size_t)m * N + pk[q]] - U[(size_t)m * N + pl[q]];
+                    const double wq = Wp[(size_t)m * NP + q];
+                    if (v + p.mu2 <= 0.0) return ORA_DOMAIN;
+                    g[m] = ion_R(p, v, wq);
+                    d[m] = ion_dRdw(p, v, wq);
+                }
+                for (int m = 0; m < M; ++m) {
+                    double qs = 0.0;
+                    for (int j = 0; j < M; ++j) qs += Q[m * M + j] * g[j];
+                    s[m] = w0[q] + dt * qs - Wp[(size_t)m * NP + q];
+                }
+                for (int m = 0; m < M; ++m) {
+                    double acc = s[m];
+                    for (int j = 0; j < m; ++j) acc += dt * Qh[m * M + j] * d[j] * eps[j];
+                    const double den = 1.0 - dt * Qh[m * M + m] * d[m];
+                    if (!(den > 0.0)) return ORA_DOMAIN;
+                    eps[m] = acc / den;
+                }
+                for (int m = 0; m < M; ++m) Wp[(size_t)m * NP + q] += eps[m];
+            }
+        }
+        std::vector<int> next;
+        for (int i : act) {
+            double amax = 0.0;
+            for (int m = 0; m < M; ++m) amax = std::max(amax, std::fabs(delta[(size_t)m * N + i]));
+            if (!std::isfinite(amax)) return ORA_NONFINITE;
+            if (st && tol_drop > 0.0) st->min_margin = std::min(st->min_margin, std::fabs(amax - tol_drop));
+            if (amax >= tol_drop) next.push_back(i);
+        }
+        for (int i : act) on[i] = 0;
+        for (int i : next) on[i] = 1;
+        act.swap(next);
+    }
+    for (int i = 0; i < N; ++i) u[i] = U[(size_t)(M - 1) * N + i];
+    for (int q = 0; q < NP; ++q) w[q] = Wp[(size_t)(M - 1) * NP + q];
+    return ORA_OK;
 }
 
 // Dense Newton solve of the full collocation system (Sec. 3.1):
