@@ -305,6 +305,51 @@ sdc_ctx* sdc_batch_context(sdc_batch* batch);
 
 void sdc_batch_destroy(sdc_batch* batch);
 
+/* ---- Cell-by-cell (EMI) model: membranes resolved between subdomains ----
+ *
+ * Sec. 2.1 (eqs. of the cell-by-cell model) in the abstract form of Sec. 3:
+ *     B u' = -(K + diag(robin)) u - b(u, w),     w_p' = R(u_k - u_l, w_p)
+ * with one potential dof per (mesh vertex, subdomain), K the P1 stiffness of
+ * every subdomain (the mesh's elements carry their subdomain's conductivity
+ * and use the dofs of that subdomain), and the membranes lumped onto dof
+ * pairs p = (k, l) of area A_p:
+ *     B = sum_p A_p Cm (e_k - e_l)(e_k - e_l)^T,
+ *     b = sum_p A_p I_p(u_k - u_l, w_p) (e_k - e_l),
+ *     I_p = I_ion of the Aliev-Panfilov model (kind 0, cell-bath membrane, k
+ *           on the cell side) or g_gap v (kind 1, gap junction between cells).
+ * The step is the SDC sweep of sdc_step with B in place of the lumped mass
+ * and sum_p A_p dI_p/dv (e_k - e_l)(e_k - e_l)^T in place of the lumped
+ * ionic Jacobian; the gating sweep runs over the kind-0 pairs with at least
+ * one active end.  Host arrays, copied at sdc_create_emi:
+ *   n_pairs              number of pairs (>= 1)
+ *   pair_k, pair_l       dofs of each pair, distinct, in [0, n_nodes)
+ *   pair_area            lumped membrane measure A_p > 0
+ *   pair_kind            0 or 1
+ *   robin                NULL or n_nodes values >= 0 (Robin coefficient times
+ *                        the lumped boundary measure of each dof)
+ *   Cm > 0, g_gap >= 0                                                           */
+typedef struct {
+    int n_pairs;
+    const int* pair_k;
+    const int* pair_l;
+    const double* pair_area;
+    const int* pair_kind;
+    const double* robin;
+    double Cm;
+    double g_gap;
+} sdc_emi;
+
+/* Create a context for the cell-by-cell model.  mesh as for sdc_create
+ * (elem_sigma normally per element); its lumped mass is not used.  On such a
+ * context sdc_step and sdc_step_host take d_v = the n_nodes potentials u and
+ * d_w = the n_pairs gating values (entries of kind-1 pairs are left as
+ * given); sdc_get_nodes writes M * n_nodes potentials and M * n_pairs gating
+ * values, both [m][index].  Not available on such a context: tapes, the
+ * adjoint, stimuli, sdc_set_dof_scale (SDC_E_INVALID).  The profile option
+ * counts launches per phase but records no device times. */
+sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* emi,
+                          const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream);
+
 /* Largest n accepted by sdc_pcg_solve_noalloc. */
 #define SDC_PCG_NOALLOC_MAX_ROWS 65536
 

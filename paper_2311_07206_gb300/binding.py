@@ -60,6 +60,13 @@ class sdc_tape(C.Structure):
                 ("d_act", C.c_void_p), ("n_active", C.c_int * SDC_MAX_SWEEPS)]
 
 
+class sdc_emi(C.Structure):
+    _fields_ = [("n_pairs", C.c_int), ("pair_k", C.POINTER(C.c_int)),
+                ("pair_l", C.POINTER(C.c_int)), ("pair_area", C.POINTER(C.c_double)),
+                ("pair_kind", C.POINTER(C.c_int)), ("robin", C.POINTER(C.c_double)),
+                ("Cm", C.c_double), ("g_gap", C.c_double)]
+
+
 SDC_TAPE_OFF, SDC_TAPE_RECORD, SDC_TAPE_REPLAY = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
@@ -73,6 +80,8 @@ SIGNATURES = {
     "sdc_radau": (C.c_int, [C.c_int, _dp, _dp, _dp]),
     "sdc_create": (C.c_int, [C.POINTER(_vp), C.POINTER(sdc_mesh), C.POINTER(sdc_ionic), C.c_int,
                              C.POINTER(sdc_options), _vp]),
+    "sdc_create_emi": (C.c_int, [C.POINTER(_vp), C.POINTER(sdc_mesh), C.POINTER(sdc_emi),
+                                 C.POINTER(sdc_ionic), C.c_int, C.POINTER(sdc_options), _vp]),
     "sdc_set_stimulus": (C.c_int, [_vp, _ip, C.c_int, C.c_double, C.c_double, C.c_double]),
     "sdc_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
                            C.POINTER(sdc_stats)]),
@@ -170,7 +179,7 @@ class Context:
     """One sdc_ctx.  Mesh arrays are copied by the library at creation."""
 
     def __init__(self, dim, xyz, elems, sigma=None, elem_sigma=None, dof_scale=None,
-                 ionic=None, M=3, options=None, stream=0):
+                 ionic=None, M=3, options=None, stream=0, emi=None):
         L = load()
         xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         elems = np.ascontiguousarray(elems, dtype=np.int32)
@@ -191,8 +200,24 @@ class Context:
             ion = ionic_struct(ionic)
         opts = options if options is not None else default_options()
         h = _vp()
-        _check(L.sdc_create(C.byref(h), C.byref(mesh), C.byref(ion), int(M), C.byref(opts),
-                            _vp(stream)))
+        self.n_pairs = 0
+        if emi is None:
+            _check(L.sdc_create(C.byref(h), C.byref(mesh), C.byref(ion), int(M), C.byref(opts),
+                                _vp(stream)))
+        else:
+            pk = np.ascontiguousarray(emi["pair_k"], np.int32)
+            pl = np.ascontiguousarray(emi["pair_l"], np.int32)
+            pa = np.ascontiguousarray(emi["pair_area"], np.float64)
+            pkind = np.ascontiguousarray(emi["pair_kind"], np.int32)
+            rb = emi.get("robin")
+            rb = None if rb is None else np.ascontiguousarray(rb, np.float64)
+            self._keep_emi = (pk, pl, pa, pkind, rb)
+            e = sdc_emi(pk.size, pk.ctypes.data_as(_ip), pl.ctypes.data_as(_ip),
+                        pa.ctypes.data_as(_dp), pkind.ctypes.data_as(_ip), dp(rb),
+                        float(emi["Cm"]), float(emi["g_gap"]))
+            _check(L.sdc_create_emi(C.byref(h), C.byref(mesh), C.byref(e), C.byref(ion), int(M),
+                                    C.byref(opts), _vp(stream)))
+            self.n_pairs = int(pk.size)
         self._h = h
         self.M = int(M)
         self.n = int(xyz.shape[0])
@@ -205,6 +230,15 @@ class Context:
         if wl.stim_nodes.size:
             ctx.set_stimulus(wl.stim_nodes, wl.stim_amp, wl.stim_t_on, wl.stim_t_off)
         return ctx
+
+    @classmethod
+    def from_emi(cls, wl, options=None, stream=0):
+        """Cell-by-cell context of an EMI workload (state: n potentials, n_pairs gating)."""
+        emi = dict(pair_k=wl.pair_k, pair_l=wl.pair_l, pair_area=wl.pair_area,
+                   pair_kind=wl.pair_kind, robin=wl.robin, Cm=wl.Cm, g_gap=wl.g_gap)
+        return cls(wl.mesh.dim, wl.mesh.xyz, wl.mesh.elems, sigma=np.eye(3),
+                   elem_sigma=wl.mesh.elem_sigma, ionic=wl.ionic, M=wl.M, options=options,
+                   stream=stream, emi=emi)
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -399,6 +433,15 @@ class Batch:
                 _check(L.sdc_batch_set_stimulus(self._h, b, nodes.ctypes.data_as(_ip), nodes.size,
                                                 wl.stim_amp, wl.stim_t_on, wl.stim_t_off),
                        L.sdc_batch_context(self._h))
+
+    @classmethod
+    def from_emi(cls, wl, options=None, stream=0):
+        """Cell-by-cell context of an EMI workload (state: n potentials, n_pairs gating)."""
+        emi = dict(pair_k=wl.pair_k, pair_l=wl.pair_l, pair_area=wl.pair_area,
+                   pair_kind=wl.pair_kind, robin=wl.robin, Cm=wl.Cm, g_gap=wl.g_gap)
+        return cls(wl.mesh.dim, wl.mesh.xyz, wl.mesh.elems, sigma=np.eye(3),
+                   elem_sigma=wl.mesh.elem_sigma, ionic=wl.ionic, M=wl.M, options=options,
+                   stream=stream, emi=emi)
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:

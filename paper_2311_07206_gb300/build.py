@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsdc_gb300.so")
-SOURCES = ["api.cu", "assembly.cu", "step.cu", "adjoint.cu", "noalloc.cu", "radau.cpp"]
+SOURCES = ["api.cu", "assembly.cu", "step.cu", "adjoint.cu", "emi.cu", "noalloc.cu", "radau.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr"]

@@ -38,6 +38,8 @@ struct sdc_ctx {
     std::vector<int> inst_active; // [sweep][instance] active dofs of the last step
     int* h_bounds = nullptr;      // pinned staging of the boundaries
     AdjointBuffers AW;            // adjoint workspace, allocated on first use
+    bool is_emi = false;          // cell-by-cell model (sdc_create_emi)
+    EmiDev emi;
     bool stepped = false;
     std::string err;
 };
@@ -163,6 +165,7 @@ void free_all(sdc_ctx* c) {
     free_ell(c->K.K);
     free_mesh_dev(c->K.mesh);
     free_adjoint(c->AW);
+    emi_free(c->emi);
     for (int* p : c->act) cudaFree(p);
     c->act.clear();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -278,7 +281,8 @@ sdc_status sdc_radau(int M, double* tau, double* Q, double* Qhat) {
 namespace {
 
 sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
-                       const sdc_options* opt, void* stream, const std::vector<int>* inst_off) {
+                       const sdc_options* opt, void* stream, const std::vector<int>* inst_off,
+                       const sdc_emi* emi = nullptr) {
     g_create_error.clear();
     if (!out) return fail(nullptr, SDC_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -319,6 +323,27 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
+    if (emi) {
+        if (emi->n_pairs < 1 || !emi->pair_k || !emi->pair_l || !emi->pair_area || !emi->pair_kind)
+            return fail(nullptr, SDC_E_INVALID, "EMI: no pairs or NULL pair arrays");
+        if (!(emi->Cm > 0.0) || !std::isfinite(emi->Cm) || !(emi->g_gap >= 0.0) ||
+            !std::isfinite(emi->g_gap))
+            return fail(nullptr, SDC_E_INVALID, "EMI: Cm must be positive, g_gap >= 0");
+        for (int p = 0; p < emi->n_pairs; ++p) {
+            const int k = emi->pair_k[p], l = emi->pair_l[p];
+            if (k < 0 || k >= mesh->n_nodes || l < 0 || l >= mesh->n_nodes || k == l)
+                return fail(nullptr, SDC_E_INVALID, "EMI: pair %d joins dofs %d and %d", p, k, l);
+            if (!(emi->pair_area[p] > 0.0) || !std::isfinite(emi->pair_area[p]))
+                return fail(nullptr, SDC_E_INVALID, "EMI: pair %d area not positive", p);
+            if (emi->pair_kind[p] != 0 && emi->pair_kind[p] != 1)
+                return fail(nullptr, SDC_E_INVALID, "EMI: pair %d kind %d (0 or 1)", p,
+                            emi->pair_kind[p]);
+        }
+        if (emi->robin)
+            for (int i = 0; i < mesh->n_nodes; ++i)
+                if (!(emi->robin[i] >= 0.0) || !std::isfinite(emi->robin[i]))
+                    return fail(nullptr, SDC_E_INVALID, "EMI: robin[%d] negative or non-finite", i);
+    }
 
     sdc_ctx* c = new sdc_ctx();
     c->N = mesh->n_nodes;
@@ -353,6 +378,15 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         delete c;
         return fail(nullptr, (sdc_status)rc, "device buffer allocation failed");
     }
+    if (emi) {
+        c->is_emi = true;
+        rc = emi_setup(*emi, c->N, M, c->K.K.width, c->B.ld, c->stream, c->emi, why);
+        if (rc != SDC_OK) {
+            free_all(c);
+            delete c;
+            return fail(nullptr, (sdc_status)rc, "%s", why.c_str());
+        }
+    }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         sdc_status st = cuda_fail(nullptr, "sdc_create");
         free_all(c);
@@ -372,9 +406,20 @@ sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ioni
     return create_impl(out, mesh, ionic, M, opt, stream, nullptr);
 }
 
+sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* emi,
+                          const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream) {
+    if (!emi) {
+        g_create_error = "emi is NULL";
+        if (out) *out = nullptr;
+        return SDC_E_INVALID;
+    }
+    return create_impl(out, mesh, ionic, M, opt, stream, nullptr, emi);
+}
+
 sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, double t_on,
                             double t_off) {
     if (!c) return SDC_E_INVALID;
+    if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_set_stimulus: not available for EMI contexts");
     if (n < 0 || (n > 0 && !nodes)) return fail(c, SDC_E_INVALID, "bad stimulus node list");
     for (int i = 0; i < n; ++i)
         if (nodes[i] < 0 || nodes[i] >= c->N)
@@ -456,6 +501,15 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     c->n_act.assign(sweeps, 0);
     if (B.nseg > 0) c->inst_active.assign((size_t)sweeps * B.nseg, 0);
     if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (c->is_emi) {
+        if (tape) return fail(c, SDC_E_INVALID, "tapes are not available for EMI contexts");
+        EmiStepArgs ea{N, M, s, &c->K, &B, &c->emi, &c->act, &c->n_act, &c->pcg, &c->opt, &c->co,
+                       &c->ion, c->h_pin, &c->err};
+        const int st = emi_step(ea, d_v, d_w, dt, sweeps, TOL, stats);
+        c->last_sweeps = sweeps;
+        c->stepped = true;
+        return (sdc_status)st;
+    }
 
     // kernel phases: launch counts always, device time with the profile option
     const bool prof = c->opt.profile != 0;
@@ -680,13 +734,15 @@ sdc_status sdc_step_host(sdc_ctx* c, double* h_v, double* h_w, double t, double 
     if (!c) return SDC_E_INVALID;
     if (!h_v || !h_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
     const size_t bytes = (size_t)c->N * sizeof(double);
+    const size_t wbytes = c->is_emi ? (size_t)c->emi.np * sizeof(double) : bytes;
+    double* wdev = c->is_emi ? c->emi.wstage : c->B.wtmp;
     if (cudaMemcpyAsync(c->B.vtmp, h_v, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(c->B.wtmp, h_w, bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        cudaMemcpyAsync(wdev, h_w, wbytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return cuda_fail(c, "sdc_step_host upload");
-    sdc_status st = sdc_step(c, c->B.vtmp, c->B.wtmp, t, dt, sweeps, TOL, stats);
+    sdc_status st = sdc_step(c, c->B.vtmp, wdev, t, dt, sweeps, TOL, stats);
     if (st != SDC_OK) return st;
     if (cudaMemcpyAsync(h_v, c->B.vtmp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaMemcpyAsync(h_w, c->B.wtmp, bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h_w, wdev, wbytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return cuda_fail(c, "sdc_step_host download");
     return SDC_OK;
@@ -696,7 +752,8 @@ sdc_status sdc_get_nodes(const sdc_ctx* cc, double* d_V, double* d_W) {
     sdc_ctx* c = const_cast<sdc_ctx*>(cc);
     if (!c) return SDC_E_INVALID;
     if (!d_V || !d_W) return fail(c, SDC_E_INVALID, "NULL output");
-    launch_nodes_out(c->N, c->M, c->B.V, c->B.W, d_V, d_W, c->stream);
+    if (c->is_emi) emi_nodes_out(c->emi, c->N, c->M, c->B.V, d_V, d_W, c->stream);
+    else launch_nodes_out(c->N, c->M, c->B.V, c->B.W, d_V, d_W, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "sdc_get_nodes");
     return SDC_OK;
 }
@@ -992,6 +1049,7 @@ sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0
         return fail(c, SDC_E_INVALID, "sdc_step_adjoint: NULL array");
     if (!(dt > 0.0)) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: dt must be positive");
     if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available for batches");
+    if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available for EMI contexts");
     if (tape->n_active[0] != c->N)
         return fail(c, SDC_E_INVALID, "sdc_step_adjoint: the first sweep must cover every dof");
     if (!ensure_adjoint(c)) return fail(c, SDC_E_NOMEM, "adjoint workspace allocation failed");
@@ -1039,6 +1097,7 @@ sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0
 sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
     if (!c) return SDC_E_INVALID;
     if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: not available for batches");
+    if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: not available for EMI contexts");
     if (h_scale)
         for (int i = 0; i < c->N; ++i)
             if (!std::isfinite(h_scale[i]) || !(h_scale[i] > 0.0))

@@ -245,4 +245,44 @@ void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepB
                     cudaStream_t s);
 int pcg_max_blocks(int block);
 
+// ---- cell-by-cell (EMI) model (emi.cu) ----
+struct EmiDev {
+    int np = 0;                 // pairs
+    int max_inc = 0;            // most pairs at one dof
+    double Cm = 1.0, g_gap = 0.0;
+    int *pk = nullptr, *pl = nullptr, *pkind = nullptr;
+    double* parea = nullptr;
+    double* robin = nullptr;    // [N] or null
+    int *np_ptr = nullptr, *np_pid = nullptr, *np_part = nullptr, *np_sign = nullptr;  // dof -> pairs
+    double *Wp = nullptr;       // [np][M] gating at the collocation nodes
+    double *Ip = nullptr, *Jp = nullptr;   // [M][np] pair current and its dI/dv
+    Ell A;                      // node-solve operator B + c (K + D_m) restricted (ld = B.ld)
+    int* pos = nullptr;         // [N] compact row of a dof in the current list, -1 outside
+    double* wstage = nullptr;   // [np] host-call staging
+};
+// Copies the pair data (host arrays validated by the caller) and allocates
+// the EMI buffers.
+int emi_setup(const sdc_emi& emi, int N, int M, int k_width, int ld, cudaStream_t s, EmiDev& E,
+              std::string& why);
+void emi_free(EmiDev& E);
+struct EmiStepArgs {
+    int N, M;
+    cudaStream_t s;
+    const AssemblyOut* K;
+    StepBuffers* B;
+    EmiDev* E;
+    std::vector<int*>* act;     // device lists, act[k] for sweep k >= 1, act[0] scratch
+    std::vector<int>* n_act;
+    const PcgConfig* pcg;
+    const sdc_options* opt;
+    const Coll* co;
+    const Ionic* ion;
+    int* h_pin;                 // pinned: [0] count, [1] err
+    std::string* err;
+};
+int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int sweeps, double TOL,
+             sdc_stats* stats);
+void emi_nodes_out(const EmiDev& E, int N, int M, const double* V, double* d_V, double* d_W,
+                   cudaStream_t s);
+
 }  // namespace sdc

@@ -70,3 +70,30 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         binding.load()
+
+
+@pytest.mark.parametrize("bad", ["self_pair", "kind", "area", "Cm", "robin", "range"])
+def test_emi_create_rejects_bad_pairs_before_device_work(lib, bad):
+    """sdc_create_emi validates the pair data on the host and returns
+    SDC_E_INVALID before any device call (so this runs without a GPU)."""
+    from paper_2311_07206_gb300 import Context, SdcError
+    from workloads.emi import emi_tiny
+    wl = emi_tiny("two_cells")
+    emi = dict(pair_k=wl.pair_k.copy(), pair_l=wl.pair_l.copy(), pair_area=wl.pair_area.copy(),
+               pair_kind=wl.pair_kind.copy(), robin=wl.robin.copy(), Cm=wl.Cm, g_gap=wl.g_gap)
+    if bad == "self_pair":
+        emi["pair_l"][3] = emi["pair_k"][3]
+    elif bad == "kind":
+        emi["pair_kind"][0] = 2
+    elif bad == "area":
+        emi["pair_area"][1] = 0.0
+    elif bad == "Cm":
+        emi["Cm"] = -1.0
+    elif bad == "robin":
+        emi["robin"][5] = np.nan
+    else:
+        emi["pair_k"][2] = wl.n
+    with pytest.raises(SdcError) as e:
+        Context(3, wl.mesh.xyz, wl.mesh.elems, sigma=np.eye(3), elem_sigma=wl.mesh.elem_sigma,
+                ionic=wl.ionic, M=wl.M, emi=emi)
+    assert e.value.status == -1 and "EMI" in str(e.value)

@@ -1,0 +1,133 @@
+"""GPU parity of the cell-by-cell (EMI) step (Sec. 2.1 in the abstract form of
+Sec. 3, sweep of Sec. 3.2, nested sets of Sec. 4.2) against the oracle's
+EMI step, through the C ABI.
+
+Each GPU step starts from the oracle's state.  Tolerance 1e-10 relative in
+the max norm for the potentials and the per-pair gating, active index lists
+identical, CG iteration counts within one.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads.emi import emi_tiny
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_07206_gb300 import build as b
+    b.build()
+    return torch, torch.device("cuda:0")
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(1.0, np.abs(b).max())
+
+
+def _ctx(wl, torch, dev, **opts):
+    from paper_2311_07206_gb300 import Context, default_options
+    return Context.from_emi(wl, options=default_options(**opts),
+                            stream=torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _run(wl, torch, dev, steps, tol, sweeps=None, w_frozen=False, **opts):
+    sweeps = wl.sweeps if sweeps is None else sweeps
+    ctx = _ctx(wl, torch, dev, w_frozen=int(w_frozen), **opts)
+    S = oracle.System.from_mesh(wl.mesh)
+    u, w = wl.u0.copy(), wl.w0.copy()
+    shrank = False
+    for n in range(steps):
+        du = torch.tensor(u, dtype=torch.float64, device=dev)
+        dw = torch.tensor(w, dtype=torch.float64, device=dev)
+        st = ctx.step(du, dw, n * wl.dt, wl.dt, sweeps, tol)
+        r = S.step_emi(wl, u, w, sweeps=sweeps, tol=tol, w_frozen=w_frozen, want_log=True)
+        assert r["status"] == 0
+        gu, gw = du.cpu().numpy(), dw.cpu().numpy()
+        assert _relmax(gu, r["u"]) <= RTOL, n
+        assert _relmax(gw, r["w"]) <= RTOL, n
+        assert list(st.n_active[:sweeps]) == list(r["stats"].n_active[:sweeps])
+        for k in range(sweeps):
+            if r["stats"].n_active[k]:
+                assert np.array_equal(ctx.active(k), r["active"][k]), "sweep %d" % k
+            for m in range(wl.M):
+                assert abs(st.cg_iters[k][m] - r["stats"].cg_iters[k * 8 + m]) <= 1
+        shrank |= st.n_active[sweeps - 1] < wl.n
+        # kind-1 (gap junction) pairs carry no gating: left as given
+        gap = wl.pair_kind == 1
+        assert np.array_equal(gw[gap], w[gap])
+        u, w = r["u"], r["w"]
+    ctx.close()
+    return shrank
+
+
+@pytest.mark.parametrize("kind", ["two_cells", "grid"])
+@pytest.mark.parametrize("variant,cluster", [(0, 20000), (2, 0), (1, 0)])
+def test_emi_step_parity_adaptive(torch_dev, kind, variant, cluster):
+    torch, dev = torch_dev
+    wl = emi_tiny(kind)
+    shrank = _run(wl, torch, dev, 3, wl.tol, cg_variant=variant, cg_cluster_rows=cluster)
+    assert shrank    # the nested sets really drop dofs here
+
+
+@pytest.mark.parametrize("kind", ["two_cells", "grid"])
+def test_emi_step_parity_plain_sdc(torch_dev, kind):
+    torch, dev = torch_dev
+    wl = emi_tiny(kind)
+    _run(wl, torch, dev, 2, 0.0)
+
+
+@pytest.mark.parametrize("M", [1, 2, 4])
+def test_emi_parity_other_node_counts(torch_dev, M):
+    torch, dev = torch_dev
+    wl = emi_tiny("two_cells")
+    wl.M = M
+    _run(wl, torch, dev, 2, wl.tol, sweeps=M + 1)
+
+
+def test_emi_parity_frozen_gating(torch_dev):
+    torch, dev = torch_dev
+    wl = emi_tiny("grid")
+    wl.w0 = np.full(wl.n_pairs, 0.05)
+    _run(wl, torch, dev, 2, wl.tol, w_frozen=True)
+
+
+def test_emi_host_entry_and_nodes(torch_dev):
+    torch, dev = torch_dev
+    wl = emi_tiny("two_cells")
+    ctx = _ctx(wl, torch, dev)
+    du = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
+    dw = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    ctx.step(du, dw, 0.0, wl.dt, wl.sweeps, wl.tol)
+    U = torch.empty((wl.M, wl.n), dtype=torch.float64, device=dev)
+    Wn = torch.empty((wl.M, wl.n_pairs), dtype=torch.float64, device=dev)
+    ctx.nodes(U, Wn)
+    assert torch.equal(U[-1], du) and torch.equal(Wn[-1], dw)
+    hu, hw = wl.u0.copy(), wl.w0.copy()
+    ctx.step_host(hu, hw, 0.0, wl.dt, wl.sweeps, wl.tol)
+    assert np.array_equal(hu, du.cpu().numpy()) and np.array_equal(hw, dw.cpu().numpy())
+    ctx.close()
+
+
+def test_emi_context_rejects_monodomain_only_calls(torch_dev):
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import SdcError
+    wl = emi_tiny("two_cells")
+    ctx = _ctx(wl, torch, dev)
+    with pytest.raises(SdcError):
+        ctx.set_stimulus([0], 1.0, 0.0, 1.0)
+    with pytest.raises(SdcError):
+        ctx.set_dof_scale(np.ones(wl.n))
+    du = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
+    dw = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    tp = ctx.new_tape(wl.sweeps, dev)
+    with pytest.raises(SdcError):
+        ctx.step_taped(du, dw, 0.0, wl.dt, wl.sweeps, wl.tol, tp)
+    ctx.close()
