@@ -53,18 +53,27 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 1000 for w1, 50 = 1 ms for w2, 300 for "
+                         "w1l/w5, 100 for w0/w3, 200 for w4)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w3", "w4"], default="w1",
-                    help="w3: 96-instance batch, batched launches vs per-instance launches; "
-                         "w4: gradient by the discrete adjoint vs finite differences")
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4"],
+                    default="w1",
+                    help="w2: cell-by-cell (EMI) bricks; w3: 96-instance batch, batched launches "
+                         "vs per-instance launches; w4: gradient by the discrete adjoint vs "
+                         "finite differences")
     ap.add_argument("--fd-directions", type=int, default=16)
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/reference/e2e runs")
-    return ap.parse_args()
+    ap.add_argument("--emi-w-frozen", action="store_true", help="w2: hold the gating at w = 0")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
+                      "w4": 200}[args.workload]
+    return args
 
 
 def make_workload(name):
@@ -412,6 +421,188 @@ def run_gb300(args):
     return 0
 
 
+def run_emi(args):
+    """Cell-by-cell (EMI) bricks: 8x4x4 myocytes of 100x20x20 um on 2 um voxels
+    (1,471,260 dofs, 277,264 membrane pairs), M = 3, dt = 0.02 ms, 4 sweeps,
+    TOL = 1e-5, Aliev-Panfilov gating on the cell-bath pairs (--emi-w-frozen
+    holds w = 0 as in the paper's own EMI runs); the first cell starts
+    excited.  Adaptive vs plain SDC, as for the slab."""
+    import torch
+    from workloads.emi import emi_bricks
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Context, default_options
+
+    frozen = bool(args.emi_w_frozen)
+    wl = emi_bricks(w_frozen=frozen)
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream(dev)
+    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, w_frozen=int(frozen),
+                           cg_maxit=100000)
+    ctx = Context.from_emi(wl, options=opts, stream=stream.cuda_stream)
+    u0 = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
+    w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def trajectory(tol, sweeps, steps, timed):
+        u, w = u0.clone(), w0.clone()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)] if timed else None
+        agg = {"active_dof_sweeps": 0, "pcg_ms": 0.0, "pcg_launches": 0, "pcg_bytes": 0.0,
+               "pcg_ops": 0.0, "launches": 0, "phase_ms": np.zeros(5), "row_iters": 0.0,
+               "iters_max": 0}
+        for n in range(steps):
+            if timed:
+                flush.fill_(n)
+                ev[n][0].record(stream)
+            st = ctx.step(u, w, n * wl.dt, wl.dt, sweeps, tol)
+            if timed:
+                ev[n][1].record(stream)
+            agg["active_dof_sweeps"] += sum(st.n_active[:st.sweeps_run])
+            agg["pcg_ms"] += st.phase_ms[1]
+            agg["pcg_launches"] += st.phase_launches[1]
+            agg["pcg_bytes"] += pcg_bytes(st, wl.M, sweeps)
+            agg["pcg_ops"] += pcg_ops(st, wl.M, sweeps)
+            agg["launches"] += st.kernel_launches
+            agg["phase_ms"] += np.array(st.phase_ms[:5])
+            for k in range(st.sweeps_run):
+                for m in range(wl.M):
+                    agg["row_iters"] += st.n_active[k] * st.cg_iters[k][m]
+                    agg["iters_max"] = max(agg["iters_max"], st.cg_iters[k][m])
+        torch.cuda.synchronize(dev)
+        total_ms = sum(a.elapsed_time(b) for a, b in ev) if timed else None
+        return u, w, total_ms, agg
+
+    trajectory(wl.tol, wl.sweeps, Wm, timed=False)
+    props = torch.cuda.get_device_properties(dev)
+    dev_id = str(getattr(props, "uuid", "")) or str(local)
+    if dev_id and not dev_id.startswith("GPU-") and len(dev_id) > 8:
+        dev_id = "GPU-" + dev_id
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(dev_id)
+    ua, _, ms_adapt, agg_a = trajectory(wl.tol, wl.sweeps, K, timed=True)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms_adapt = max_over_ranks(ms_adapt, world)
+    value = world * K / (ms_adapt / 1e3)
+
+    extras = {}
+    if not args.no_extras:
+        up, _, ms_plain, agg_p = trajectory(0.0, wl.sweeps, K, timed=True)
+        ur, _, _, _ = trajectory(0.0, args.ref_sweeps, K, timed=False)
+        ref = ur.cpu().numpy()
+        extras = {"plain": {"value": K / (ms_plain / 1e3), "unit": "steps/s",
+                            "ms_per_step": ms_plain / K,
+                            "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_plain / 1e3)},
+                  "speedup_vs_plain": ms_plain / ms_adapt,
+                  "err_vs_ref": {"adaptive": float(np.abs(ua.cpu().numpy() - ref).max()),
+                                 "plain": float(np.abs(up.cpu().numpy() - ref).max()),
+                                 "reference": "plain SDC, %d sweeps, same dt" % args.ref_sweeps,
+                                 "norm": "max |u(t_K) - u_ref(t_K)|"}}
+
+    # end to end through the host-buffer entry point (pinned host u, w)
+    hu_t = torch.tensor(wl.u0, dtype=torch.float64).pin_memory()
+    hw_t = torch.tensor(wl.w0, dtype=torch.float64).pin_memory()
+    hu, hw = hu_t.numpy(), hw_t.numpy()
+    barrier(world)
+    e2e_s = 0.0
+    for n in range(K):
+        t0 = time.perf_counter()
+        ctx.step_host(hu, hw, n * wl.dt, wl.dt, wl.sweeps, wl.tol)
+        e2e_s += time.perf_counter() - t0
+    e2e = {"value": world * K / max_over_ranks(e2e_s, world), "unit": "steps/s",
+           "h2d_bytes_per_step": 8 * (wl.n + wl.n_pairs),
+           "d2h_bytes_per_step": 8 * (wl.n + wl.n_pairs),
+           "api": "sdc_step_host (pinned host u, w)"}
+
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = FP64_LANES_PER_CYCLE * sm_max * 1e6 / 1e9
+    pcg_s = agg_a["pcg_ms"] / 1e3
+    launches = max(1, agg_a["pcg_launches"])
+    ach_ops = agg_a["pcg_ops"] / pcg_s / 1e9 if pcg_s > 0 else None
+    ach_gbs = agg_a["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
+    roofline = {"kernel": "k_pcg* on the EMI node operator (K + membrane pair slots)",
+                "bound": "alu", "achieved": ach_ops, "peak": alu_peak,
+                "unit": "G FP64 lane-op/s", "frac": ach_ops / alu_peak if ach_ops else None,
+                "peak_source": "304 FP64 lanes/cycle (ncu dfma peak_sustained) x %.0f MHz max SM clock"
+                               % sm_max,
+                "traffic": None,
+                "algorithmic_ops_per_launch": agg_a["pcg_ops"] / launches,
+                "algorithmic_bytes_per_launch": agg_a["pcg_bytes"] / launches,
+                "avg_launch_ms": agg_a["pcg_ms"] / launches, "launches": agg_a["pcg_launches"],
+                "share_of_step": agg_a["pcg_ms"] / ms_adapt,
+                "hbm_view": {"achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach_gbs / hbm_peak if ach_gbs else None,
+                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
+                             if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = emi_cpu_baseline(args.cpu_budget, agg_a["row_iters"] / K, frozen)
+
+    phase = dict(zip(("residual", "pcg", "update", "select", "extract"),
+                     (agg_a["phase_ms"] / K).round(4).tolist()))
+    cfg = {"workload": wl.name, "n_dofs": wl.n, "n_pairs": wl.n_pairs, "M": wl.M,
+           "dt_ms": wl.dt, "sweeps": wl.sweeps, "TOL": wl.tol, "alpha": wl.alpha,
+           "cg_rtol": wl.cg_rtol,
+           "gating": "held at w = 0" if frozen else "Aliev-Panfilov on cell-bath pairs", "simulated_ms": round(K * wl.dt, 6),
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+    line = {"metric": "SDC steps/s & active-dof sweeps/s (cell-by-cell bricks), adaptive "
+                      "TOL=%g vs plain; HBM GB/s" % wl.tol,
+            "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": Wm,
+            "ms_per_step": ms_adapt / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_adapt / 1e3),
+            "cg_iters_max": agg_a["iters_max"], **extras, "phase_ms_per_step": phase,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": agg_a["launches"]}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def emi_cpu_baseline(budget_s, gpu_row_iters_per_step, frozen):
+    """The oracle's EMI step on a two-cell instance of the same construction
+    (100x20x20 um bricks, 2 um voxels), single thread, within the budget; its
+    rate in CG row-iterations/s converted to steps/s of the full workload with
+    the full workload's row-iterations per step measured on the GPU."""
+    import oracle
+    from workloads.emi import emi_bricks
+    wl = emi_bricks(cells=(2, 1, 1), w_frozen=frozen)
+    S = oracle.System.from_mesh(wl.mesh)
+    u, w = wl.u0.copy(), wl.w0.copy()
+    done, secs, row_iters = 0, 0.0, 0.0
+    while secs < budget_s and done < 10:
+        t0 = time.perf_counter()
+        r = S.step_emi(wl, u, w, w_frozen=frozen)
+        secs += time.perf_counter() - t0
+        if r["status"] != 0:
+            raise RuntimeError("oracle EMI step failed with status %d" % r["status"])
+        st = r["stats"]
+        row_iters += sum(st.n_active[k] * st.cg_iters[k * 8 + m]
+                         for k in range(st.sweeps_run) for m in range(wl.M))
+        u, w = r["u"], r["w"]
+        done += 1
+    rate = row_iters / secs
+    return {"value": rate / gpu_row_iters_per_step, "unit": "steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": "%d oracle steps of the 2-cell instance (%d dofs) in %.1f s: %.3g CG "
+                      "row-iterations/s, divided by the full workload's %.3g row-iterations per "
+                      "step" % (done, wl.n, secs, rate, gpu_row_iters_per_step),
+            "sample_steps_per_s": done / secs}
+
+
+
 def run_batch(args):
     """96 2D instances (sides log-uniform in [64, 512], D ~ U[0.5, 2]): one
     batched step of all instances vs the same steps as per-instance launches."""
@@ -588,9 +779,9 @@ SEED_FD = 2311_07206 + 40
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload in ("w3", "w4"):
+    if args.impl == "reference" and args.workload in ("w2", "w3", "w4"):
         print(json.dumps({"impl": "reference", "unavailable":
-                          "the reference arm times the oracle on the slab workload only"}))
+                          "the reference arm times the oracle on the monodomain workloads only"}))
         return 0
     if args.impl == "reference":
         return run_reference(args)
@@ -598,6 +789,8 @@ def main():
         return run_batch(args)
     if args.workload == "w4":
         return run_grad(args)
+    if args.workload == "w2":
+        return run_emi(args)
     return run_gb300(args)
 
 

@@ -344,9 +344,12 @@ typedef struct {
  * context sdc_step and sdc_step_host take d_v = the n_nodes potentials u and
  * d_w = the n_pairs gating values (entries of kind-1 pairs are left as
  * given); sdc_get_nodes writes M * n_nodes potentials and M * n_pairs gating
- * values, both [m][index].  Not available on such a context: tapes, the
- * adjoint, stimuli, sdc_set_dof_scale (SDC_E_INVALID).  The profile option
- * counts launches per phase but records no device times. */
+ * values, both [m][index].  In sdc_stats, nnz_active[k] counts the stored
+ * off-diagonal entries of the node-solve operator: those of K[I_k, I_k] plus
+ * one per pair end whose other end is also active; the operator is built per
+ * node (phase EXTRACT), the coupling into the later nodes' right-hand sides
+ * runs after each solve (phase UPDATE).  Not available on such a context:
+ * tapes, the adjoint, stimuli, sdc_set_dof_scale (SDC_E_INVALID). */
 sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* emi,
                           const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream);
 

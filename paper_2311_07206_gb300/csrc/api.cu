@@ -504,7 +504,7 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     if (c->is_emi) {
         if (tape) return fail(c, SDC_E_INVALID, "tapes are not available for EMI contexts");
         EmiStepArgs ea{N, M, s, &c->K, &B, &c->emi, &c->act, &c->n_act, &c->pcg, &c->opt, &c->co,
-                       &c->ion, c->h_pin, &c->err};
+                       &c->ion, c->h_pin, &c->err, &c->events};
         const int st = emi_step(ea, d_v, d_w, dt, sweeps, TOL, stats);
         c->last_sweeps = sweeps;
         c->stepped = true;

@@ -137,9 +137,10 @@ __global__ void k_emi_build(int n, const int* __restrict__ act, const double* __
                             const double* __restrict__ Jpm, const int* __restrict__ pos,
                             double Cm, double c, double* __restrict__ eval,
                             int* __restrict__ ecol, int* __restrict__ elen,
-                            double* __restrict__ mc) {
+                            double* __restrict__ mc, unsigned long long* __restrict__ slots) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
+    int added = 0;
+    if (q < n) {
     const int g = act ? act[q] : q;
     int cnt = alen[q];
     for (int t = 0; t < cnt; ++t) {
@@ -156,10 +157,17 @@ __global__ void k_emi_build(int n, const int* __restrict__ act, const double* __
             eval[(size_t)cnt * ld + q] = -coef / c;
             ecol[(size_t)cnt * ld + q] = jq;
             ++cnt;
+            ++added;
         }
     }
     elen[q] = cnt;
     mc[q] = pd;
+    }
+    // pair slots stored (statistics): one atomic per warp
+    if (slots) {
+        const int tot = __reduce_add_sync(0xffffffffu, added);
+        if ((threadIdx.x & 31) == 0 && tot) atomicAdd(slots, (unsigned long long)tot);
+    }
 }
 
 // b_m' -= dt Qhat_m'm ((K + D_m) dv_m) for the later nodes m' > m
@@ -295,7 +303,7 @@ int emi_setup(const sdc_emi& e, int N, int M, int k_width, int ld, cudaStream_t 
               dalloc(&E.Wp, (size_t)NP * M) && dalloc(&E.Ip, (size_t)NP * M) &&
               dalloc(&E.Jp, (size_t)NP * M) && dalloc(&E.A.val, width * ld) &&
               dalloc(&E.A.col, width * ld) && dalloc(&E.A.len, ld) && dalloc(&E.pos, N) &&
-              dalloc(&E.wstage, NP);
+              dalloc(&E.wstage, NP) && dalloc(&E.slots, 1);
     if (ok && e.robin) ok = upload(&E.robin, e.robin, N, s);
     if (!ok) {
         why = "EMI buffer allocation failed";
@@ -318,6 +326,7 @@ void emi_free(EmiDev& E) {
     for (int* p : ip) cudaFree(p);
     double* dp[] = {E.parea, E.robin, E.Wp, E.Ip, E.Jp, E.A.val, E.wstage};
     for (double* p : dp) cudaFree(p);
+    cudaFree(E.slots);
     E = EmiDev();
 }
 
@@ -341,20 +350,49 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
     const Coll& co = *a.co;
     cudaStream_t s = a.s;
     const double tol_drop = a.opt->alpha * TOL;
-    int launches[SDC_N_PHASES] = {0, 0, 0, 0, 0};
     auto fail = [&](int st, const std::string& msg) {
         *a.err = msg;
         return st;
     };
+    // kernel phases: launch counts always, device time with the profile option
+    const bool prof = a.opt->profile != 0 && a.events;
+    struct Mark { int phase, ea, eb, k, m; };
+    std::vector<Mark> marks;
+    int ev_used = 0, launches[SDC_N_PHASES] = {0, 0, 0, 0, 0};
+    int cur_k = -1, cur_m = -1;
+    auto next_event = [&]() -> int {
+        if (ev_used == (int)a.events->size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            a.events->push_back(e);
+        }
+        return ev_used++;
+    };
+    auto run = [&](int phase, int nk, auto&& fn) {
+        int ea = -1;
+        if (prof) {
+            ea = next_event();
+            cudaEventRecord((*a.events)[ea], s);
+        }
+        fn();
+        if (prof) {
+            const int eb = next_event();
+            cudaEventRecord((*a.events)[eb], s);
+            marks.push_back({phase, ea, eb, cur_k, cur_m});
+        }
+        launches[phase] += nk;
+    };
+
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), s);
     const double big = 1.7976931348623157e308;
     cudaMemcpyAsync(&B.sc->margin, &big, sizeof(double), cudaMemcpyHostToDevice, s);
-    dispatch_M(M, [&](auto mc) {
-        constexpr int MM = decltype(mc)::value;
-        k_emi_spread<MM><<<nbk(N, 256), 256, 0, s>>>(N, d_u, B.V);
-        k_emi_spread<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, d_w, E.Wp);
+    run(SDC_PHASE_RESIDUAL, 2, [&] {
+        dispatch_M(M, [&](auto mc) {
+            constexpr int MM = decltype(mc)::value;
+            k_emi_spread<MM><<<nbk(N, 256), 256, 0, s>>>(N, d_u, B.V);
+            k_emi_spread<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, d_w, E.Wp);
+        });
     });
-    launches[SDC_PHASE_RESIDUAL] += 2;
 
     int n = N;
     const int* act = nullptr;
@@ -369,27 +407,36 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             stats->sweeps_run = k + 1;
         }
         if (n == 0) continue;
+        cur_k = k;
+        cur_m = -1;
         // compact positions of the current list (partners outside it read -1)
-        if (act) launch_pos_set(n, act, E.pos, 0, s);
-        else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 0);
-        dispatch_M(M, [&](auto mc) {
-            constexpr int MM = decltype(mc)::value;
-            k_emi_pair_eval<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, E.pk, E.pl, E.pkind, B.V, E.Wp,
-                                                            *a.ion, E.g_gap,
-                                                            a.opt->reaction_implicit, E.Ip, E.Jp);
-            k_emi_residual<MM><<<nbk(n, 128), 128, 0, s>>>(
-                n, act, a.K->K.val, a.K->K.col, a.K->K.len, a.K->K.ld, a.K->kdiag, E.robin,
-                E.np_ptr, E.np_pid, E.np_part, E.np_sign, E.parea, E.Ip, NP, B.V, d_u, E.Cm, dt,
-                co, B.ld, B.R, B.J, B.kdc);
+        run(SDC_PHASE_SELECT, 1, [&] {
+            if (act) launch_pos_set(n, act, E.pos, 0, s);
+            else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 0);
         });
-        launches[SDC_PHASE_RESIDUAL] += 3;
-        for (int m = 0; m < M; ++m) {
+        run(SDC_PHASE_RESIDUAL, 2, [&] {
+            dispatch_M(M, [&](auto mc) {
+                constexpr int MM = decltype(mc)::value;
+                k_emi_pair_eval<MM><<<nbk(NP, 256), 256, 0, s>>>(
+                    NP, E.pk, E.pl, E.pkind, B.V, E.Wp, *a.ion, E.g_gap, a.opt->reaction_implicit,
+                    E.Ip, E.Jp);
+                k_emi_residual<MM><<<nbk(n, 128), 128, 0, s>>>(
+                    n, act, a.K->K.val, a.K->K.col, a.K->K.len, a.K->K.ld, a.K->kdiag, E.robin,
+                    E.np_ptr, E.np_pid, E.np_part, E.np_sign, E.parea, E.Ip, NP, B.V, d_u, E.Cm,
+                    dt, co, B.ld, B.R, B.J, B.kdc);
+            });
+        });
+        cudaMemsetAsync(E.slots, 0, sizeof(unsigned long long), s);
+        for (int m = 0; m < M && status == SDC_OK; ++m) {
+            cur_m = m;
             const double c = dt * co.Qh[m * kMaxM + m];
             const double* Jm = E.Jp + (size_t)m * NP;
-            k_emi_build<<<nbk(n, 128), 128, 0, s>>>(n, act, A->val, A->col, A->len, A->ld, B.ld,
-                                                    E.np_ptr, E.np_pid, E.np_part, E.parea, Jm,
-                                                    E.pos, E.Cm, c, E.A.val, E.A.col, E.A.len,
-                                                    B.mc);
+            run(SDC_PHASE_EXTRACT, 1, [&] {
+                k_emi_build<<<nbk(n, 128), 128, 0, s>>>(
+                    n, act, A->val, A->col, A->len, A->ld, B.ld, E.np_ptr, E.np_pid, E.np_part,
+                    E.parea, Jm, E.pos, E.Cm, c, E.A.val, E.A.col, E.A.len, B.mc,
+                    m == 0 ? E.slots : nullptr);
+            });
             PcgRole role{};
             role.b = B.R + (size_t)m * B.ld;
             role.x = B.D + (size_t)m * B.ld;
@@ -401,47 +448,51 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             role.c = c;
             role.iters_out = &B.sc->cg_iters[k * kMaxM + m];
             role.relres_out = &B.sc->cg_relres[k * kMaxM + m];
-            if (launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol, a.opt->cg_maxit, *a.pcg, B,
-                                s) != SDC_OK) {
-                status = fail(SDC_E_CUDA, std::string("cooperative CG launch: ") +
-                                              cudaGetErrorString(cudaGetLastError()));
-                break;
-            }
-            launches[SDC_PHASE_PCG] += 1;
-            launches[SDC_PHASE_EXTRACT] += 1;
-            if (m + 1 < M) {
-                k_emi_couple<<<nbk(n, 128), 128, 0, s>>>(
-                    n, act, m, M, A->val, A->col, A->len, A->ld, B.ld, B.kdc, E.np_ptr, E.np_pid,
-                    E.np_part, E.parea, Jm, E.pos, B.D + (size_t)m * B.ld, dt, co, B.R);
-                launches[SDC_PHASE_PCG] += 1;
+            run(SDC_PHASE_PCG, 1, [&] {
+                if (launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol, a.opt->cg_maxit, *a.pcg,
+                                    B, s) != SDC_OK)
+                    status = fail(SDC_E_CUDA, std::string("cooperative CG launch: ") +
+                                                  cudaGetErrorString(cudaGetLastError()));
+            });
+            if (status == SDC_OK && m + 1 < M) {
+                cur_m = -1;
+                run(SDC_PHASE_UPDATE, 1, [&] {
+                    k_emi_couple<<<nbk(n, 128), 128, 0, s>>>(
+                        n, act, m, M, A->val, A->col, A->len, A->ld, B.ld, B.kdc, E.np_ptr,
+                        E.np_pid, E.np_part, E.parea, Jm, E.pos, B.D + (size_t)m * B.ld, dt, co,
+                        B.R);
+                });
             }
         }
         if (status != SDC_OK) break;
-        // u update and selection flags (the node gating is not used: w_frozen)
-        launch_update(M, n, act, nullptr, dt, *a.ion, co, tol_drop, 1, B, s);
-        launches[SDC_PHASE_UPDATE] += 1;
-        if (!a.opt->w_frozen) {
-            dispatch_M(M, [&](auto mc) {
-                constexpr int MM = decltype(mc)::value;
-                k_emi_wsweep<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, E.pk, E.pl, E.pkind, E.pos, B.V,
-                                                             E.Wp, d_w, dt, *a.ion, co,
-                                                             &B.sc->err);
-            });
-            launches[SDC_PHASE_UPDATE] += 1;
-        }
-        if (act) launch_pos_set(n, act, E.pos, 1, s);
-        else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 1);
-        launches[SDC_PHASE_SELECT] += 2;
+        cur_m = -1;
+        run(SDC_PHASE_UPDATE, a.opt->w_frozen ? 1 : 2, [&] {
+            // u update and selection flags (no node gating: w_frozen), then the pair gating
+            launch_update(M, n, act, nullptr, dt, *a.ion, co, tol_drop, 1, B, s);
+            if (!a.opt->w_frozen)
+                dispatch_M(M, [&](auto mc) {
+                    constexpr int MM = decltype(mc)::value;
+                    k_emi_wsweep<MM><<<nbk(NP, 256), 256, 0, s>>>(
+                        NP, E.pk, E.pl, E.pkind, E.pos, B.V, E.Wp, d_w, dt, *a.ion, co,
+                        &B.sc->err);
+                });
+        });
         int* next = (k + 1 < sweeps) ? (*a.act)[k + 1] : (*a.act)[0];
-        launch_select(n, act, next, B, s);
-        launches[SDC_PHASE_SELECT] += 2;
+        run(SDC_PHASE_SELECT, 3, [&] {
+            if (act) launch_pos_set(n, act, E.pos, 1, s);
+            else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 1);
+            launch_select(n, act, next, B, s);
+        });
+        unsigned long long slots = 0;
         cudaMemcpyAsync(&a.h_pin[0], &B.sc->count, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&a.h_pin[1], &B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&slots, E.slots, sizeof(slots), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             status = fail(SDC_E_CUDA, std::string("sweep: ") +
                                           cudaGetErrorString(cudaGetLastError()));
             break;
         }
+        if (stats) stats->nnz_active[k] = nnz + (long long)slots;
         const int n_next = a.h_pin[0];
         if (a.h_pin[1] != SDC_OK) {
             status = fail(a.h_pin[1], "sweep " + std::to_string(k) + ": " +
@@ -450,8 +501,7 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         }
         if (k + 1 < sweeps && n_next > 0) {
             Ell& An = B.A[cur];
-            launch_extract(n, *A, B.map, An, B, s);
-            launches[SDC_PHASE_EXTRACT] += 1;
+            run(SDC_PHASE_EXTRACT, 1, [&] { launch_extract(n, *A, B.map, An, B, s); });
             unsigned long long hn = 0;
             cudaMemcpyAsync(&hn, &B.sc->nnz, sizeof(hn), cudaMemcpyDeviceToHost, s);
             if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -466,12 +516,14 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         n = n_next;
     }
     if (status == SDC_OK) {
-        dispatch_M(M, [&](auto mc) {
-            constexpr int MM = decltype(mc)::value;
-            k_emi_final<MM><<<nbk(N, 256), 256, 0, s>>>(N, B.V, d_u);
-            k_emi_final<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, E.Wp, d_w);
+        cur_k = cur_m = -1;
+        run(SDC_PHASE_RESIDUAL, 2, [&] {
+            dispatch_M(M, [&](auto mc) {
+                constexpr int MM = decltype(mc)::value;
+                k_emi_final<MM><<<nbk(N, 256), 256, 0, s>>>(N, B.V, d_u);
+                k_emi_final<MM><<<nbk(NP, 256), 256, 0, s>>>(NP, E.Wp, d_w);
+            });
         });
-        launches[SDC_PHASE_RESIDUAL] += 2;
         if (cudaStreamSynchronize(s) != cudaSuccess)
             status = fail(SDC_E_CUDA, std::string("EMI step: ") +
                                           cudaGetErrorString(cudaGetLastError()));
@@ -495,6 +547,14 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         for (int ph = 0; ph < SDC_N_PHASES; ++ph) {
             stats->phase_launches[ph] = launches[ph];
             stats->kernel_launches += launches[ph];
+            stats->phase_ms[ph] = 0.0;
+        }
+        for (const Mark& mk : marks) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, (*a.events)[mk.ea], (*a.events)[mk.eb]) == cudaSuccess) {
+                stats->phase_ms[mk.phase] += ms;
+                if (mk.phase == SDC_PHASE_PCG) stats->cg_ms[mk.k][mk.m] = ms;
+            }
         }
     }
     return status;

@@ -259,6 +259,7 @@ struct EmiDev {
     Ell A;                      // node-solve operator B + c (K + D_m) restricted (ld = B.ld)
     int* pos = nullptr;         // [N] compact row of a dof in the current list, -1 outside
     double* wstage = nullptr;   // [np] host-call staging
+    unsigned long long* slots = nullptr;   // pair slots stored by the last build (statistics)
 };
 // Copies the pair data (host arrays validated by the caller) and allocates
 // the EMI buffers.
@@ -279,6 +280,7 @@ struct EmiStepArgs {
     const Ionic* ion;
     int* h_pin;                 // pinned: [0] count, [1] err
     std::string* err;
+    std::vector<cudaEvent_t>* events;   // profiling event pool (profile option)
 };
 int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int sweeps, double TOL,
              sdc_stats* stats);

@@ -72,115 +72,98 @@ class EmiWorkload:
 
 
 def emi_from_labels(lab: np.ndarray, h: float, sigma_i: float, sigma_e: float):
-    """Dofs, tetrahedra, membrane pairs and Robin areas of a labelled voxel grid."""
+    """Dofs, tetrahedra, membrane pairs and Robin areas of a labelled voxel grid.
+
+    Numbering: vertices in x-fastest order, at each vertex one dof per label of
+    its voxels in ascending label order.  Elements: voxels in x-fastest order,
+    six Kuhn tetrahedra per voxel in the order of the axis permutations.  Pairs
+    sorted by (first dof, second dof, kind); each membrane face adds a quarter
+    of its area to the pair of every one of its four vertices."""
+    lab = np.asarray(lab, dtype=np.int64)
     nx, ny, nz = lab.shape
     vx, vy, vz = nx + 1, ny + 1, nz + 1
+    L = int(lab.max()) + 1
+    I, J, Kz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    # voxels in x-fastest order
+    order = lambda a: np.ascontiguousarray(a.transpose(2, 1, 0)).reshape(-1)
+    vi, vj, vk, vl = order(I), order(J), order(Kz), order(lab)
 
     def vid(i, j, k):
         return i + vx * (j + vy * k)
 
-    nvert = vx * vy * vz
-    # labels around each vertex
-    vlabels = [set() for _ in range(nvert)]
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                c = int(lab[i, j, k])
-                for dk in (0, 1):
-                    for dj in (0, 1):
-                        for di in (0, 1):
-                            vlabels[vid(i + di, j + dj, k + dk)].add(c)
-    dof = {}
-    xyz, dlab = [], []
-    for k in range(vz):
-        for j in range(vy):
-            for i in range(vx):
-                v = vid(i, j, k)
-                for c in sorted(vlabels[v]):
-                    dof[(v, c)] = len(xyz)
-                    xyz.append((i * h, j * h, k * h))
-                    dlab.append(c)
-    xyz = np.array(xyz, dtype=np.float64)
-    dlab = np.array(dlab, dtype=np.int32)
-    elems, esig = [], []
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                c = int(lab[i, j, k])
-                s = sigma_e if c == 0 else sigma_i
-                for perm in _PERMS:
-                    off = [0, 0, 0]
-                    vs = []
-                    for step in range(4):
-                        if step > 0:
-                            off[perm[step - 1]] += 1
-                        vs.append(dof[(vid(i + off[0], j + off[1], k + off[2]), c)])
-                    elems.append(vs)
-                    esig.append(s * np.eye(3))
-    elems = np.array(elems, dtype=np.int32)
-    esig = np.array(esig, dtype=np.float64)
-    # membrane faces between voxels of different labels
+    # (vertex, label) keys of every voxel corner -> dof numbers
+    corners = [vid(vi + di, vj + dj, vk + dk) * L + vl
+               for dk in (0, 1) for dj in (0, 1) for di in (0, 1)]
+    keys = np.unique(np.concatenate(corners))
+    vert = keys // L
+    dlab = (keys % L).astype(np.int32)
+    xyz = np.stack([vert % vx, (vert // vx) % vy, vert // (vx * vy)], axis=1).astype(np.float64) * h
+
+    def dof(v, c):
+        return np.searchsorted(keys, v * L + c).astype(np.int32)
+
+    # six Kuhn tetrahedra per voxel
+    tets = []
+    for perm in _PERMS:
+        off = np.zeros(3, np.int64)
+        vs = []
+        for step in range(4):
+            if step > 0:
+                off[perm[step - 1]] += 1
+            vs.append(dof(vid(vi + off[0], vj + off[1], vk + off[2]), vl))
+        tets.append(np.stack(vs, axis=1))
+    elems = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    sig = np.where(np.repeat(vl, 6) == 0, sigma_e, sigma_i)
+    esig = sig[:, None, None] * np.eye(3)[None]
+    # membrane faces: voxel pairs of different labels across each axis
     quarter = h * h / 4.0
-    acc = {}
-
-    def add_face(verts, ca, cb):
-        if ca == cb:
-            return
-        if ca == 0 or cb == 0:
-            cell, ecs = (ca, cb) if cb == 0 else (cb, ca)
-            kind = 0
-            first, second = cell, ecs
-        else:
-            kind = 1
-            first, second = min(ca, cb), max(ca, cb)
-        for v in verts:
-            key = (dof[(v, first)], dof[(v, second)], kind)
-            acc[key] = acc.get(key, 0.0) + quarter
-
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                c = int(lab[i, j, k])
-                if i + 1 < nx:
-                    add_face([vid(i + 1, j, k), vid(i + 1, j + 1, k), vid(i + 1, j, k + 1),
-                              vid(i + 1, j + 1, k + 1)], c, int(lab[i + 1, j, k]))
-                if j + 1 < ny:
-                    add_face([vid(i, j + 1, k), vid(i + 1, j + 1, k), vid(i, j + 1, k + 1),
-                              vid(i + 1, j + 1, k + 1)], c, int(lab[i, j + 1, k]))
-                if k + 1 < nz:
-                    add_face([vid(i, j, k + 1), vid(i + 1, j, k + 1), vid(i, j + 1, k + 1),
-                              vid(i + 1, j + 1, k + 1)], c, int(lab[i, j, k + 1]))
-    keys = sorted(acc)
-    pk = np.array([key[0] for key in keys], dtype=np.int32)
-    pl = np.array([key[1] for key in keys], dtype=np.int32)
-    pkind = np.array([key[2] for key in keys], dtype=np.int32)
-    parea = np.array([acc[key] for key in keys], dtype=np.float64)
+    f_first, f_second, f_kind = [], [], []
+    face_verts = {0: ((1, 0, 0), (1, 1, 0), (1, 0, 1), (1, 1, 1)),
+                  1: ((0, 1, 0), (1, 1, 0), (0, 1, 1), (1, 1, 1)),
+                  2: ((0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1))}
+    for ax in range(3):
+        nb = [0, 0, 0]
+        nb[ax] = 1
+        a = lab[:lab.shape[0] - nb[0], :lab.shape[1] - nb[1], :lab.shape[2] - nb[2]]
+        b = lab[nb[0]:, nb[1]:, nb[2]:]
+        ii, jj, kk = np.nonzero(a != b)
+        ca, cb = a[ii, jj, kk], b[ii, jj, kk]
+        ecs = (ca == 0) | (cb == 0)
+        first = np.where(ecs, np.maximum(ca, cb), np.minimum(ca, cb))
+        second = np.where(ecs, 0, np.maximum(ca, cb))
+        for d in face_verts[ax]:
+            v = vid(ii + d[0], jj + d[1], kk + d[2])
+            f_first.append(dof(v, first))
+            f_second.append(dof(v, second))
+            f_kind.append(np.where(ecs, 0, 1))
+    f_first = np.concatenate(f_first).astype(np.int64)
+    f_second = np.concatenate(f_second).astype(np.int64)
+    f_kind = np.concatenate(f_kind).astype(np.int64)
+    n = keys.size
+    pkey, counts = np.unique((f_first * n + f_second) * 2 + f_kind, return_counts=True)
+    pk = (pkey // 2 // n).astype(np.int32)
+    pl = (pkey // 2 % n).astype(np.int32)
+    pkind = (pkey % 2).astype(np.int32)
+    parea = counts * quarter
     # outer box faces: Robin measure on the dofs of the boundary voxels' labels
-    robin = np.zeros(len(xyz))
-
-    def add_bface(verts, c):
-        for v in verts:
-            robin[dof[(v, c)]] += quarter
-
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                c = int(lab[i, j, k])
-                if i == 0:
-                    add_bface([vid(0, j, k), vid(0, j + 1, k), vid(0, j, k + 1), vid(0, j + 1, k + 1)], c)
-                if i == nx - 1:
-                    add_bface([vid(nx, j, k), vid(nx, j + 1, k), vid(nx, j, k + 1),
-                               vid(nx, j + 1, k + 1)], c)
-                if j == 0:
-                    add_bface([vid(i, 0, k), vid(i + 1, 0, k), vid(i, 0, k + 1), vid(i + 1, 0, k + 1)], c)
-                if j == ny - 1:
-                    add_bface([vid(i, ny, k), vid(i + 1, ny, k), vid(i, ny, k + 1),
-                               vid(i + 1, ny, k + 1)], c)
-                if k == 0:
-                    add_bface([vid(i, j, 0), vid(i + 1, j, 0), vid(i, j + 1, 0), vid(i + 1, j + 1, 0)], c)
-                if k == nz - 1:
-                    add_bface([vid(i, j, nz), vid(i + 1, j, nz), vid(i, j + 1, nz),
-                               vid(i + 1, j + 1, nz)], c)
+    b_dofs = []
+    for ax in range(3):
+        for side in (0, 1):
+            sl = [slice(None)] * 3
+            sl[ax] = 0 if side == 0 else lab.shape[ax] - 1
+            sub = lab[tuple(sl)]
+            g = np.meshgrid(*[np.arange(m) for m in sub.shape], indexing="ij")
+            c = sub.reshape(-1)
+            other = [g[0].reshape(-1), g[1].reshape(-1)]
+            for d0 in (0, 1):
+                for d1 in (0, 1):
+                    idx = [None, None, None]
+                    rest = [q for q in range(3) if q != ax]
+                    idx[ax] = np.full(c.size, 0 if side == 0 else lab.shape[ax])
+                    idx[rest[0]] = other[0] + d0
+                    idx[rest[1]] = other[1] + d1
+                    b_dofs.append(dof(vid(idx[0], idx[1], idx[2]), c))
+    robin = np.bincount(np.concatenate(b_dofs), minlength=n) * quarter
     mesh = Mesh(3, xyz, elems, elem_sigma=esig, meta={"h": h, "voxels": lab.shape})
     return mesh, pk, pl, parea, pkind, robin, dlab
 
