@@ -359,7 +359,7 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
 /* sdc_pcg_solve for callers that cannot allocate device memory (the paper has
  * no counterpart; this is a service of the library).  Same arguments, results
  * and errors as sdc_pcg_solve, but no device memory is allocated or freed:
- * the workspace is a static array of the library, reserved (about 3.2 MB) on
+ * the workspace is a static array of the library, reserved (about 3.3 MB) on
  * every GPU that loads the library until the process exits.
  *   - n <= SDC_PCG_NOALLOC_MAX_ROWS, else SDC_E_INVALID with a message from
  *     sdc_last_error(NULL), and nothing is launched.

@@ -109,8 +109,8 @@ int alloc_buffers(sdc_ctx* c) {
     B.max_blocks = std::max(P.max_blocks_general, P.sms);
     bool ok = dalloc(&B.V, (size_t)N * M) && dalloc(&B.W, (size_t)N * M) &&
               dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
-              dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.z, ld) &&
-              dalloc(&B.p, ld) && dalloc(&B.q, ld) && dalloc(&B.dA, ld) && dalloc(&B.idA, ld) &&
+              dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.u, ld) &&
+              dalloc(&B.p, ld) && dalloc(&B.s, ld) && dalloc(&B.w, ld) && dalloc(&B.idA, ld) &&
               dalloc(&B.flag, ld) &&
               dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
               dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
@@ -138,7 +138,7 @@ int alloc_buffers(sdc_ctx* c) {
             cudaMemcpyAsync(B.inst_off, c->inst_off.data(), (nseg + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, c->stream);
     }
-    if (ok) ok = dalloc(&B.part, 2 * (size_t)B.max_blocks);
+    if (ok) ok = dalloc(&B.part, 4 * (size_t)B.max_blocks);
     if (!ok) return SDC_E_NOMEM;
     if (cudaMallocHost(&c->h_pin, 4 * sizeof(int)) != cudaSuccess) return SDC_E_NOMEM;
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), c->stream);
@@ -149,7 +149,7 @@ void free_adjoint(AdjointBuffers& W);
 
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
-    double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.z, B.p, B.q, B.dA, B.idA, B.part,
+    double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.u, B.p, B.s, B.w, B.idA, B.part,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
     int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff, B.inst_off, B.bounds, B.segtab,
@@ -835,17 +835,17 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     cudaStream_t s = (cudaStream_t)stream;
     const int block = 256;
     const int maxb = pcg_max_blocks(block);
-    // workspace: 6 vectors, 2 * maxb partial sums, then the scalars
-    const size_t nd = (size_t)6 * n + 2 * (size_t)maxb + 2;
+    // workspace: 6 vectors, 4 * maxb partial sums, then the scalars
+    const size_t nd = (size_t)6 * n + 4 * (size_t)maxb + 2;
     char* ws = nullptr;
     if (cudaMalloc(&ws, nd * sizeof(double) + 64) != cudaSuccess)
         return fail(nullptr, SDC_E_NOMEM, "sdc_pcg_solve: workspace allocation failed");
     double* v = (double*)ws;
     PcgScratch w;
-    w.r = v; w.z = v + n; w.p = v + 2 * (size_t)n; w.q = v + 3 * (size_t)n;
-    w.dA = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.part = v + 6 * (size_t)n;
+    w.r = v; w.u = v + n; w.p = v + 2 * (size_t)n; w.s = v + 3 * (size_t)n;
+    w.w = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.part = v + 6 * (size_t)n;
     w.max_blocks = maxb;
-    w.relres = v + 6 * (size_t)n + 2 * (size_t)maxb;
+    w.relres = v + 6 * (size_t)n + 4 * (size_t)maxb;
     unsigned* sc = (unsigned*)(w.relres + 1);
     w.bar = sc;
     w.err = (int*)(sc + 1);

@@ -10,7 +10,7 @@
 // array below instead of a per-call allocation.
 //
 // Costs and limits of that choice:
-//   * every GPU that loads the library reserves the array (about 3.2 MB) until
+//   * every GPU that loads the library reserves the array (about 3.3 MB) until
 //     the process exits;
 //   * n is limited to SDC_PCG_NOALLOC_MAX_ROWS rows;
 //   * all calls on a device share the one array and it keeps the last call's
@@ -29,10 +29,10 @@
 namespace {
 
 constexpr int kMaxRows = SDC_PCG_NOALLOC_MAX_ROWS;
-constexpr int kMaxBlocks = 4096;   // partial-sum slots per buffer
+constexpr int kMaxBlocks = 4096;   // blocks with partial-sum slots (two sums, two buffers)
 constexpr size_t kVecDoubles = 6 * (size_t)kMaxRows;
 constexpr size_t kScalarDoubles = 4;   // relres, then barrier counter, error, iterations
-constexpr size_t kScratchDoubles = kVecDoubles + 2 * (size_t)kMaxBlocks + kScalarDoubles;
+constexpr size_t kScratchDoubles = kVecDoubles + 4 * (size_t)kMaxBlocks + kScalarDoubles;
 
 static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
 
@@ -89,14 +89,14 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
     cudaStream_t s = (cudaStream_t)stream;
     sdc::PcgScratch w;
     w.r = base;
-    w.z = base + (size_t)n;
+    w.u = base + (size_t)n;
     w.p = base + 2 * (size_t)n;
-    w.q = base + 3 * (size_t)n;
-    w.dA = base + 4 * (size_t)n;
+    w.s = base + 3 * (size_t)n;
+    w.w = base + 4 * (size_t)n;
     w.idA = base + 5 * (size_t)n;
     w.part = base + kVecDoubles;
     w.max_blocks = kMaxBlocks;
-    w.relres = base + kVecDoubles + 2 * (size_t)kMaxBlocks;
+    w.relres = base + kVecDoubles + 4 * (size_t)kMaxBlocks;
     unsigned* sc = (unsigned*)(w.relres + 1);
     w.bar = sc;
     w.err = (int*)(sc + 1);

@@ -91,13 +91,13 @@ struct StepBuffers {
     double* D = nullptr;      // [M][ld] corrections dv
     double* mc = nullptr;     // [ld] lumped mass of the active rows
     double* kdc = nullptr;    // [ld] K_ii of the active rows
-    double* r = nullptr;      // CG vectors [ld]
-    double* z = nullptr;
+    double* r = nullptr;      // CG vectors [ld]: residual, u = D^-1 r, direction p,
+    double* u = nullptr;      // s = A p, w = A u, reciprocal diagonal
     double* p = nullptr;
-    double* q = nullptr;
-    double* dA = nullptr;
+    double* s = nullptr;
+    double* w = nullptr;
     double* idA = nullptr;
-    double* part = nullptr;   // 2 * max_blocks partial sums
+    double* part = nullptr;   // 4 * max_blocks: two partial sums per block, two buffers
     int max_blocks = 0;
     int* flag = nullptr;      // [ld]
     int* map = nullptr;       // [ld] old compact row -> new compact row or -1
@@ -129,7 +129,7 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const double* W, const double* v0, double dt, const Ionic& ion,
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
 // Launch configuration of the restricted PCG solves.
-constexpr int kSmemRows = 3968;     // rows per block of the shared-memory variant
+constexpr int kSmemRows = 4448;     // rows per block of the shared-memory variants
 struct PcgConfig {
     int block = 256;                // block size of the general variant
     int max_blocks_general = 0;     // cooperative grid limit of the general variant
@@ -221,10 +221,10 @@ void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, 
 void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
-// r, z, p, q, dA, idA: n doubles each; part: 2 * max_blocks doubles;
+// r, u, p, s, w, idA: n doubles each; part: 4 * max_blocks doubles;
 // bar, err, iters, relres: one value each, bar and err zero before the launch.
 struct PcgScratch {
-    double *r, *z, *p, *q, *dA, *idA, *part;
+    double *r, *u, *p, *s, *w, *idA, *part;
     int max_blocks;
     unsigned* bar;
     int* err;

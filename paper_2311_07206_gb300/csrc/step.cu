@@ -117,13 +117,15 @@ struct CgParams {
     double c;            // dt * Qhat_mm
     const double* b;     // right-hand side of this node
     double* x;           // correction of this node (output)
-    double* r;
-    double* z;
-    double* p;
-    double* q;
-    double* dA;          // diagonal of the node system
-    double* idA;         // its reciprocal (Jacobi preconditioner)
-    double* part;
+    // CG vectors (global-vector variant; the shared-memory variants keep their
+    // own rows on chip and publish u only)
+    double* r;           // residual
+    double* u;           // D^-1 r (published for the neighbours' gathers)
+    double* p;           // search direction
+    double* s;           // A p
+    double* w;           // A u
+    double* idA;         // reciprocal of the diagonal (Jacobi preconditioner)
+    double* part;        // per-block partial sums, two per block, two buffers
     unsigned* bar;
     int* err;
     double rtol;
@@ -142,7 +144,7 @@ struct CgParams {
     int epi_lo, epi_hi, epi_target_J;
     const double* Jall;
     int inject_fault;    // testing hook: the last block skips the first barrier
-    int L;               // rows per block (shared-memory variant)
+    int L;               // rows per block (shared-memory variants)
 };
 
 // LU-trick coupling of one solved row into the right-hand sides of other nodes.
@@ -154,18 +156,18 @@ __device__ __forceinline__ void cg_couple_row(const CgParams& P, int i, double x
     }
 }
 
-
-// Shared per-block scalars of a CG solve.  Lane 0 of warp 0 derives them from
-// each grid-wide sum (one FP64 division / square root per block, not per
-// thread: the FP64 pipe is the scarce unit on this part).
+// Shared per-block state of a CG solve.  The scalars are derived by lane 0 of
+// warp 0 from each pair of grid-wide sums (one FP64 division chain per block,
+// not per thread: the FP64 pipe is the scarce unit on this part).
 struct CgShared {
-    double red[1024];   // per-thread partial sums
-    double alpha, beta, rho, rho0, thresh, rzmax, rn;
-    int ok, state;      // state: 0 iterating, 1 converged, 2 non-finite
+    double red[2 * 1024];   // per-thread partial sums of the two dot products
+    double wsum[8];         // per-warp totals of the block sum
+    double alpha, beta, inv_gamma, inv_alpha, gamma0, thresh, rzmax, rn;
+    int ok, state;          // state: 0 iterating, 1 converged, 2 non-finite
 };
 
-// The stopping test sqrt(r.z) <= rtol sqrt(r0.z0) is evaluated as
-// r.z <= rzmax with rzmax the largest double whose correctly rounded square
+// The stopping test sqrt(r.u) <= rtol sqrt(r0.u0) is evaluated as
+// r.u <= rzmax with rzmax the largest double whose correctly rounded square
 // root does not exceed the threshold (sqrt is monotone), found once per solve:
 // the same decision without a square root per iteration.
 __device__ __forceinline__ double largest_with_sqrt_at_most(double thresh) {
@@ -179,49 +181,167 @@ __device__ __forceinline__ double largest_with_sqrt_at_most(double thresh) {
     return r;
 }
 
-__device__ __forceinline__ void cg_after_rho0(CgShared& S, double tot, double rtol) {
-    S.rho0 = tot;
-    S.rho = tot;
-    S.rn = tot;
-    S.thresh = rtol * sqrt(tot);
+// Scalars of the Chronopoulos-Gear iteration from gamma = r.u and
+// delta = w.u (u = D^-1 r, w = A u):
+//   first:  alpha = gamma / delta, beta = 0
+//   later:  beta = gamma / gamma_old,
+//           alpha = gamma / (delta - beta gamma / alpha_old)
+// 1/gamma and 1/alpha are kept so that a step needs one division chain.
+__device__ __forceinline__ void cg_first(CgShared& S, double g, double d, double rtol) {
+    S.gamma0 = g;
+    S.rn = g;
+    S.beta = 0.0;
+    S.thresh = rtol * sqrt(g);
     S.rzmax = largest_with_sqrt_at_most(S.thresh);
-    S.state = !isfinite(tot) ? 2 : (tot == 0.0 ? 1 : 0);
-}
-__device__ __forceinline__ void cg_after_pq(CgShared& S, double pq) { S.alpha = S.rho / pq; }
-__device__ __forceinline__ void cg_after_rz(CgShared& S, double rn) {
-    S.rn = rn;
-    if (!isfinite(rn)) {
+    if (!isfinite(g) || !isfinite(d)) {
         S.state = 2;
-    } else if (rn >= 0.0 && rn <= S.rzmax) {
+    } else if (g == 0.0) {
         S.state = 1;
     } else {
-        S.beta = rn / S.rho;
-        S.rho = rn;
+        S.state = 0;
+        S.alpha = g / d;
+        S.inv_gamma = 1.0 / g;
+        S.inv_alpha = d * S.inv_gamma;
     }
 }
-// final relative preconditioned residual sqrt(r.z / r0.z0)
+__device__ __forceinline__ void cg_next(CgShared& S, double g, double d) {
+    S.rn = g;
+    if (!isfinite(g) || !isfinite(d)) {
+        S.state = 2;
+    } else if (g >= 0.0 && g <= S.rzmax) {
+        S.state = 1;
+    } else {
+        const double beta = g * S.inv_gamma;
+        const double den = d - beta * g * S.inv_alpha;
+        S.alpha = g / den;
+        S.inv_gamma = 1.0 / g;
+        S.inv_alpha = den * S.inv_gamma;
+        S.beta = beta;
+    }
+}
+// final relative preconditioned residual sqrt(r.u / r0.u0)
 __device__ __forceinline__ double cg_relres(const CgShared& S) {
-    return S.rho0 > 0.0 ? sqrt(fabs(S.rn) / S.rho0) : 0.0;
+    return S.gamma0 > 0.0 ? sqrt(fabs(S.rn) / S.gamma0) : 0.0;
 }
 
-// Jacobi-PCG on the restricted node system (diagonal preconditioner), whole
-// solve in one cooperative launch, vectors in global memory (any size).
+// Block sum of two values per thread in a fixed order, result in thread 0.
+// Thread t stores (a, b) at red[t], red[1024 + t]; warp w < W = min(4, B/32)
+// adds the warp-rows w, w + W, w + 2W, ... of the block (a balanced tree over
+// at most 8 values per lane, then a shuffle tree), and thread 0 adds the W
+// warp totals in order.  Four summing warps keep every SM sub-partition's
+// FP64 unit busy with a short dependency chain.
+__device__ __forceinline__ void block_sum2(double a, double b, CgShared& S, double& sa,
+                                           double& sb) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int nw = blockDim.x >> 5;
+    const int W = min(4, nw);
+    S.red[t] = a;
+    S.red[1024 + t] = b;
+    __syncthreads();
+    if (wid < W) {
+        const int cnt = (nw - wid + W - 1) / W;   // warp-rows of this warp (<= 8)
+        double x[8], y[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int at = (wid + k * W) * 32 + lane;
+            x[k] = k < cnt ? S.red[at] : 0.0;
+            y[k] = k < cnt ? S.red[1024 + at] : 0.0;
+        }
+        if (cnt > 4) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) { x[k] += x[k + 4]; y[k] += y[k + 4]; }
+        }
+        if (cnt > 2) {
+            x[0] += x[2]; y[0] += y[2];
+            x[1] += x[3]; y[1] += y[3];
+        }
+        if (cnt > 1) { x[0] += x[1]; y[0] += y[1]; }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+            y[0] += __shfl_xor_sync(0xffffffffu, y[0], o);
+        }
+        if (lane == 0) {
+            S.wsum[wid] = x[0];
+            S.wsum[4 + wid] = y[0];
+        }
+    }
+    __syncthreads();
+    sa = sb = 0.0;
+    if (t == 0) {
+        if (W == 4) {
+            sa = (S.wsum[0] + S.wsum[1]) + (S.wsum[2] + S.wsum[3]);
+            sb = (S.wsum[4] + S.wsum[5]) + (S.wsum[6] + S.wsum[7]);
+        } else {
+            for (int k = 0; k < W; ++k) { sa += S.wsum[k]; sb += S.wsum[4 + k]; }
+        }
+    }
+}
+
+// Sum of two values per thread over a group of `nblk` blocks (the whole grid,
+// or one instance's share of a batched launch), fused with the group barrier.
+// Thread 0 publishes the block's pair to part[2 bidx], arrives and waits;
+// warp 0 then adds the nblk pairs in index order (bitwise identical in every
+// block) and lane 0 runs on_total(a, b), which stores the iteration's scalars
+// in shared memory.  A closing CTA barrier makes them visible to the block.
+// Returns false after a barrier timeout.
+template <class F>
+__device__ __forceinline__ bool group_reduce2(double a, double b, CgShared& S, double* part,
+                                              unsigned* bar, int nblk, int bidx, unsigned& epoch,
+                                              long long budget, int* err, F&& on_total) {
+    double sa, sb;
+    block_sum2(a, b, S, sa, sb);
+    epoch += nblk;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int ok = 1;
+        if (lane == 0) {
+            part[2 * bidx] = sa;
+            part[2 * bidx + 1] = sb;
+            ok = barrier_arrive_wait(bar, epoch, budget, err);
+        }
+        __syncwarp();
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+            double ta = 0.0, tb = 0.0;
+            const double2* p2 = reinterpret_cast<const double2*>(part);
+            for (int i = lane; i < nblk; i += 32) {
+                const double2 v = __ldcg(p2 + i);
+                ta += v.x;
+                tb += v.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                tb += __shfl_xor_sync(0xffffffffu, tb, o);
+            }
+            if (lane == 0) on_total(ta, tb);
+        }
+        if (lane == 0) S.ok = ok;
+    }
+    __syncthreads();
+    return S.ok != 0;
+}
+
+// Jacobi-PCG on the restricted node system, whole solve in one cooperative
+// launch, vectors in global memory (any size).
 //
-// The iteration is the standard preconditioned CG, arranged with two grid-wide
-// synchronisation points per iteration: the matrix is applied to z = D^-1 r,
-// and p and q = A p follow from p = z + beta p, q = A z + beta q (the same
-// iterates in exact arithmetic as q = A p; rounding differs only in the order
-// of the additions).  Per iteration:
-//   phase A: s = A z (gathers z of neighbouring rows), p, q updates, p.q
-//            -> grid sum, alpha = rho / p.q
-//   phase B: x += alpha p, r -= alpha q, z = D^-1 r (published), r.z
-//            -> grid sum, convergence test, beta
+// The iteration is preconditioned CG in the arrangement of Chronopoulos and
+// Gear (1989): with u = D^-1 r and w = A u, both dot products of an iteration,
+// gamma = r.u and delta = w.u, are summed in one grid-wide reduction, and
+// s = A p follows from the recurrence s = w + beta s.  Per iteration:
+//   phase 1: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+//            u = D^-1 r (published) -> grid barrier
+//   phase 2: w = A u (gathers u of neighbouring rows; the diagonal part of
+//            A u is D u = r), r.u and w.u -> one grid sum of two values,
+//            convergence test on r.u, then beta and alpha
+// The iterates are those of standard preconditioned CG in exact arithmetic.
 // Rows are processed grid-stride; each thread owns the same rows in every
 // phase.  Block totals are added in a fixed order by every block, so all
 // blocks take identical decisions.
 // One group of `nblk` blocks solves rows [row0, row1): the whole launch, or
 // one instance of a batched launch.  `part` points at the group's first
-// partial-sum slot of buffer 0; buffer 1 is `pstride` doubles further.
+// partial-sum pair of buffer 0; buffer 1 is `pstride` doubles further.
 __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int row0, int row1,
                                           int nblk, int bidx, unsigned* bar, double* part,
                                           int pstride, int* iters_out, double* relres_out) {
@@ -233,75 +353,69 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
     unsigned epoch = 0;
     int buf = 0;
 
-    double acc_part = 0.0;
     for (int i = i0; i < row1; i += stride) {
         const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
         if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
         else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
         const double id = 1.0 / d;
-        P.dA[i] = d;
         P.idA[i] = id;
         const double r = P.b[i];
-        const double z = r * id;
         P.r[i] = r;
-        P.z[i] = z;
+        P.u[i] = r * id;
         P.p[i] = 0.0;
-        P.q[i] = 0.0;
+        P.s[i] = 0.0;
         P.x[i] = 0.0;
-        acc_part += r * z;
     }
     if (P.inject_fault && bidx == nblk - 1) {
         // leave without arriving: every other block's bounded wait runs out
         if (nblk == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
         return;
     }
-    if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
-                      P.err, &S.ok, [&](double t) { cg_after_rho0(S, t, P.rtol); }))
-        return;
-    buf ^= 1;
+    if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
     int it = 0;
-    double beta = 0.0;
-    while (S.state == 0) {
+    bool first = true;
+    while (true) {
+        // phase 2: w = A u, r.u, w.u
+        double ga = 0.0, de = 0.0;
+        for (int i = i0; i < row1; i += stride) {
+            const int len = P.alen[i];
+            double acc = 0.0;
+            for (int t = 0; t < len; ++t)
+                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.u + P.acol[(size_t)t * ld + i]);
+            const double ri = P.r[i];
+            const double ui = P.u[i];
+            const double wi = ri + c * acc;
+            P.w[i] = wi;
+            ga += ri * ui;
+            de += wi * ui;
+        }
+        if (!group_reduce2(ga, de, S, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
+                           P.err, [&](double g, double d) {
+                               if (first) cg_first(S, g, d, P.rtol);
+                               else cg_next(S, g, d);
+                           }))
+            return;
+        buf ^= 1;
+        first = false;
+        if (S.state != 0) break;
         if (it >= P.maxit) {
             if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
             break;
         }
         ++it;
-        // s = A z; p = z + beta p; q = s + beta q; p.q
-        acc_part = 0.0;
+        // phase 1: p, s, x, r, u
+        const double alpha = S.alpha, beta = S.beta;
         for (int i = i0; i < row1; i += stride) {
-            const int len = P.alen[i];
-            double acc = 0.0;
-            for (int t = 0; t < len; ++t)
-                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.z + P.acol[(size_t)t * ld + i]);
-            const double zi = __ldcg(P.z + i);
-            const double si = P.dA[i] * zi + c * acc;
-            const double pi = zi + beta * P.p[i];
-            const double qi = si + beta * P.q[i];
+            const double pi = P.u[i] + beta * P.p[i];
+            const double si = P.w[i] + beta * P.s[i];
             P.p[i] = pi;
-            P.q[i] = qi;
-            acc_part += pi * qi;
-        }
-        if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
-                          P.err, &S.ok, [&](double t) { cg_after_pq(S, t); }))
-            return;
-        buf ^= 1;
-        const double alpha = S.alpha;
-        // x += alpha p, r -= alpha q, z = D^-1 r, r.z
-        acc_part = 0.0;
-        for (int i = i0; i < row1; i += stride) {
-            P.x[i] += alpha * P.p[i];
-            const double r = P.r[i] - alpha * P.q[i];
+            P.s[i] = si;
+            P.x[i] += alpha * pi;
+            const double r = P.r[i] - alpha * si;
             P.r[i] = r;
-            const double z = r * P.idA[i];
-            P.z[i] = z;
-            acc_part += r * z;
+            P.u[i] = r * P.idA[i];
         }
-        if (!group_reduce(acc_part, S.red, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
-                          P.err, &S.ok, [&](double t) { cg_after_rz(S, t); }))
-            return;
-        buf ^= 1;
-        beta = S.beta;
+        if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
     }
     if (S.state == 2) {
         if (lead) raise_error(P.err, SDC_E_NONFINITE);
@@ -326,7 +440,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
 
 __global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
     __shared__ CgShared S;
-    pcg_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar, P.part, (int)gridDim.x,
+    pcg_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar, P.part, 2 * (int)gridDim.x,
               P.iters_out, P.relres_out);
 }
 
@@ -342,7 +456,7 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_batch(CgParams P, const SegBloc
     __shared__ CgShared S;
     const SegBlock g = tab[blockIdx.x];
     pcg_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
-              P.part + g.blk0, (int)gridDim.x, seg_iters + g.seg, seg_relres + g.seg);
+              P.part + 2 * g.blk0, 2 * (int)gridDim.x, seg_iters + g.seg, seg_relres + g.seg);
 }
 
 // Compact boundaries of the batch instances in a sorted active list:
@@ -362,10 +476,11 @@ __global__ void k_seg_bounds(const int* __restrict__ count, const int* __restric
 }
 
 // Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
-// block b owns the contiguous rows [b L, b L + L); their x, r, z, p, q,
-// diagonal and reciprocal diagonal stay in shared memory for the whole solve.
-// Only z is published to global memory (coalesced) for the neighbours'
-// gathers; the matrix is read through the read-only path.
+// block b owns the contiguous rows [b L, b L + L); their r, u, p, s, w and
+// reciprocal diagonal stay in shared memory for the whole solve.  u is
+// published to global memory (coalesced) for the neighbours' gathers and x is
+// accumulated in place in global memory; the matrix is read through the
+// read-only path.
 __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
     extern __shared__ double sm[];
     __shared__ CgShared S;
@@ -373,14 +488,14 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
     const int L = P.L, ld = P.ld;
     const int r0 = blockIdx.x * L;
     const int nl = max(0, min(P.n - r0, L));
-    double* __restrict__ sx = sm;
-    double* __restrict__ sr = sm + L;
-    double* __restrict__ sz = sm + 2 * L;
-    double* __restrict__ sp = sm + 3 * L;
-    double* __restrict__ sq = sm + 4 * L;
-    double* __restrict__ sd = sm + 5 * L;
-    double* __restrict__ si = sm + 6 * L;
-    double* __restrict__ zg = P.z;
+    double* __restrict__ sr = sm;
+    double* __restrict__ su = sm + L;
+    double* __restrict__ sp = sm + 2 * L;
+    double* __restrict__ ss = sm + 3 * L;
+    double* __restrict__ sw = sm + 4 * L;
+    double* __restrict__ si = sm + 5 * L;
+    double* __restrict__ ug = P.u;
+    double* __restrict__ xg = P.x;
     const double* __restrict__ aval = P.aval;
     const int* __restrict__ acol = P.acol;
     const int* __restrict__ alen = P.alen;
@@ -388,76 +503,71 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
     unsigned epoch = 0;
     int buf = 0;
 
-    double part = 0.0;
     for (int l = t; l < nl; l += B) {
         const int i = r0 + l;
         const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
         if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
         else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
         const double id = 1.0 / d;
-        sd[l] = d;
         si[l] = id;
         const double r = P.b[i];
-        const double z = r * id;
+        const double u = r * id;
         sr[l] = r;
-        sz[l] = z;
-        zg[i] = z;
+        su[l] = u;
+        ug[i] = u;
         sp[l] = 0.0;
-        sq[l] = 0.0;
-        sx[l] = 0.0;
-        part += r * z;
+        ss[l] = 0.0;
+        xg[i] = 0.0;
     }
     if (P.inject_fault && blockIdx.x == G - 1) {
         if (G == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
         return;
     }
-    if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                     [&](double tot) { cg_after_rho0(S, tot, P.rtol); }))
-        return;
-    buf ^= 1;
+    if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
     int it = 0;
-    double beta = 0.0;
-    while (S.state == 0) {
-        if (it >= P.maxit) {
-            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
-            break;
-        }
-        ++it;
-        part = 0.0;
+    bool first = true;
+    while (true) {
+        double ga = 0.0, de = 0.0;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
             const int len = __ldg(alen + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(zg + __ldg(acol + (size_t)k * ld + i));
-            const double zi = sz[l];
-            const double s_i = sd[l] * zi + c * acc;
-            const double pi = zi + beta * sp[l];
-            const double qi = s_i + beta * sq[l];
-            sp[l] = pi;
-            sq[l] = qi;
-            part += pi * qi;
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + __ldg(acol + (size_t)k * ld + i));
+            const double ri = sr[l], ui = su[l];
+            const double wi = ri + c * acc;
+            sw[l] = wi;
+            ga += ri * ui;
+            de += wi * ui;
         }
-        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                         [&](double tot) { cg_after_pq(S, tot); }))
+        if (!group_reduce2(ga, de, S, P.part + buf * 2 * G, P.bar, G, (int)blockIdx.x, epoch,
+                           P.budget, P.err, [&](double g, double d) {
+                               if (first) cg_first(S, g, d, P.rtol);
+                               else cg_next(S, g, d);
+                           }))
             return;
         buf ^= 1;
-        const double alpha = S.alpha;
-        part = 0.0;
+        first = false;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
         for (int l = t; l < nl; l += B) {
-            sx[l] += alpha * sp[l];
-            const double r = sr[l] - alpha * sq[l];
+            const double pi = su[l] + beta * sp[l];
+            const double s_i = sw[l] + beta * ss[l];
+            sp[l] = pi;
+            ss[l] = s_i;
+            xg[r0 + l] += alpha * pi;
+            const double r = sr[l] - alpha * s_i;
             sr[l] = r;
-            const double z = r * si[l];
-            sz[l] = z;
-            zg[r0 + l] = z;
-            part += r * z;
+            const double u = r * si[l];
+            su[l] = u;
+            ug[r0 + l] = u;
         }
-        if (!grid_reduce(part, S.red, P.part + buf * G, P.bar, epoch, P.budget, P.err, &S.ok,
-                         [&](double tot) { cg_after_rz(S, tot); }))
-            return;
-        buf ^= 1;
-        beta = S.beta;
+        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
     }
     if (S.state == 2) {
         if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
@@ -467,27 +577,26 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
         *P.iters_out = it;
         *P.relres_out = cg_relres(S);
     }
-    for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
+    // x is complete and visible: the last grid sum followed its last update
     if (P.epi_lo < P.epi_hi) {
-        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
             const int len = __ldg(alen + i);
-            const double xi = sx[l];
+            const double xi = __ldcg(xg + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(P.x + __ldg(acol + (size_t)k * ld + i));
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
             cg_couple_row(P, i, xi, acc);
         }
     }
 }
 
 // Thread-block-cluster variant for small active sets (n <= C * L rows, one
-// cluster of C CTAs).  The same iteration as k_pcg_smem; z and x of other CTAs
-// are read from their shared memory (distributed shared memory), block totals
-// are exchanged through shared memory, and the hardware cluster barrier
-// replaces the global arrival counter, so the iteration loop touches no global
-// memory besides the (read-only) matrix.  Every CTA takes the same decisions
+// cluster of C CTAs).  The same iteration as k_pcg_smem; u of other CTAs is
+// read from their shared memory (distributed shared memory), block totals are
+// exchanged through shared memory, and the hardware cluster barrier replaces
+// the global arrival counter, so the iteration loop touches no global memory
+// besides the (read-only) matrix and x.  Every CTA takes the same decisions
 // (same totals, same order) and leaves only after a final cluster barrier, so
 // no CTA reads the shared memory of one that has exited.
 __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
@@ -495,9 +604,8 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
     cgx::cluster_group cl = cgx::this_cluster();
     extern __shared__ double sm[];
     __shared__ CgShared S;
-    __shared__ double cpart[2];
-    __shared__ double* zr[16];
-    __shared__ double* xr[16];
+    __shared__ double cpart[4];
+    __shared__ double* ur[16];
     __shared__ double* pr[16];
     const int B = blockDim.x, t = threadIdx.x;
     const int C = (int)cl.num_blocks();
@@ -505,72 +613,64 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
     const int L = P.L, ld = P.ld;
     const int r0 = rank * L;
     const int nl = max(0, min(P.n - r0, L));
-    const int nact = min(B, nl);
-    double* __restrict__ sx = sm;
-    double* __restrict__ sr = sm + L;
-    double* __restrict__ sz = sm + 2 * L;
-    double* __restrict__ sp = sm + 3 * L;
-    double* __restrict__ sq = sm + 4 * L;
-    double* __restrict__ sd = sm + 5 * L;
-    double* __restrict__ si = sm + 6 * L;
+    double* __restrict__ sr = sm;
+    double* __restrict__ su = sm + L;
+    double* __restrict__ sp = sm + 2 * L;
+    double* __restrict__ ss = sm + 3 * L;
+    double* __restrict__ sw = sm + 4 * L;
+    double* __restrict__ si = sm + 5 * L;
+    double* __restrict__ xg = P.x;
     const double* __restrict__ aval = P.aval;
     const int* __restrict__ acol = P.acol;
     const int* __restrict__ alen = P.alen;
     const double c = P.c;
     if (t < C) {
-        zr[t] = cl.map_shared_rank(sz, t);
-        xr[t] = cl.map_shared_rank(sx, t);
+        ur[t] = cl.map_shared_rank(su, t);
         pr[t] = cl.map_shared_rank(cpart, t);
     }
     int buf = 0;
-    // cluster-wide sum; lane 0 of warp 0 derives the scalars from the total
-    auto reduce = [&](double v, auto&& on_total) {
-        S.red[t] = v;
-        __syncthreads();
-        if (t < 32) {
-            double s = 0.0;
-            for (int i = t; i < nact; i += 32) s += S.red[i];
-            s = warp_sum(s);
-            if (t == 0) cpart[buf] = s;
+    // cluster-wide sum of two values; lane 0 of warp 0 derives the scalars
+    auto reduce2 = [&](double a, double b, auto&& on_total) {
+        double sa, sb;
+        block_sum2(a, b, S, sa, sb);
+        if (t == 0) {
+            cpart[2 * buf] = sa;
+            cpart[2 * buf + 1] = sb;
         }
         cl.sync();
         if (t < 32) {
-            double tot = t < C ? pr[t][buf] : 0.0;
-            tot = warp_sum(tot);
-            if (t == 0) on_total(tot);
+            double ta = t < C ? pr[t][2 * buf] : 0.0;
+            double tb = t < C ? pr[t][2 * buf + 1] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ta += __shfl_xor_sync(0xffffffffu, ta, o);
+                tb += __shfl_xor_sync(0xffffffffu, tb, o);
+            }
+            if (t == 0) on_total(ta, tb);
         }
         buf ^= 1;
         __syncthreads();
     };
 
-    double part = 0.0;
     for (int l = t; l < nl; l += B) {
         const int i = r0 + l;
         const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
         if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
         else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
         const double id = 1.0 / d;
-        sd[l] = d;
         si[l] = id;
         const double r = P.b[i];
-        const double z = r * id;
         sr[l] = r;
-        sz[l] = z;
+        su[l] = r * id;
         sp[l] = 0.0;
-        sq[l] = 0.0;
-        sx[l] = 0.0;
-        part += r * z;
+        ss[l] = 0.0;
+        xg[i] = 0.0;
     }
-    reduce(part, [&](double tot) { cg_after_rho0(S, tot, P.rtol); });
+    cl.sync();
     int it = 0;
-    double beta = 0.0;
-    while (S.state == 0) {
-        if (it >= P.maxit) {
-            if (rank == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
-            break;
-        }
-        ++it;
-        part = 0.0;
+    bool first = true;
+    while (true) {
+        double ga = 0.0, de = 0.0;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
             const int len = __ldg(alen + i);
@@ -578,29 +678,37 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
             for (int k = 0; k < len; ++k) {
                 const int j = __ldg(acol + (size_t)k * ld + i);
                 const int owner = j / L;
-                acc += __ldg(aval + (size_t)k * ld + i) * zr[owner][j - owner * L];
+                acc += __ldg(aval + (size_t)k * ld + i) * ur[owner][j - owner * L];
             }
-            const double zi = sz[l];
-            const double s_i = sd[l] * zi + c * acc;
-            const double pi = zi + beta * sp[l];
-            const double qi = s_i + beta * sq[l];
-            sp[l] = pi;
-            sq[l] = qi;
-            part += pi * qi;
+            const double ri = sr[l], ui = su[l];
+            const double wi = ri + c * acc;
+            sw[l] = wi;
+            ga += ri * ui;
+            de += wi * ui;
         }
-        reduce(part, [&](double tot) { cg_after_pq(S, tot); });
-        const double alpha = S.alpha;
-        part = 0.0;
+        reduce2(ga, de, [&](double g, double d) {
+            if (first) cg_first(S, g, d, P.rtol);
+            else cg_next(S, g, d);
+        });
+        first = false;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (rank == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
         for (int l = t; l < nl; l += B) {
-            sx[l] += alpha * sp[l];
-            const double r = sr[l] - alpha * sq[l];
+            const double pi = su[l] + beta * sp[l];
+            const double s_i = sw[l] + beta * ss[l];
+            sp[l] = pi;
+            ss[l] = s_i;
+            xg[r0 + l] += alpha * pi;
+            const double r = sr[l] - alpha * s_i;
             sr[l] = r;
-            const double z = r * si[l];
-            sz[l] = z;
-            part += r * z;
+            su[l] = r * si[l];
         }
-        reduce(part, [&](double tot) { cg_after_rz(S, tot); });
-        beta = S.beta;
+        cl.sync();   // u of every CTA is final before the gathers
     }
     if (S.state == 2) {
         if (rank == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
@@ -609,19 +717,15 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
             *P.iters_out = it;
             *P.relres_out = cg_relres(S);
         }
-        for (int l = t; l < nl; l += B) P.x[r0 + l] = sx[l];
         if (P.epi_lo < P.epi_hi) {
-            cl.sync();   // every CTA's x is final
+            cl.sync();   // every CTA's x is final (cluster-scope ordering covers global memory)
             for (int l = t; l < nl; l += B) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
-                const double xi = sx[l];
+                const double xi = __ldcg(xg + i);
                 double acc = 0.0;
-                for (int k = 0; k < len; ++k) {
-                    const int j = __ldg(acol + (size_t)k * ld + i);
-                    const int owner = j / L;
-                    acc += __ldg(aval + (size_t)k * ld + i) * xr[owner][j - owner * L];
-                }
+                for (int k = 0; k < len; ++k)
+                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
                 cg_couple_row(P, i, xi, acc);
             }
         }
@@ -855,13 +959,13 @@ int pcg_max_blocks(int block) {
 
 int pcg_cluster_size(int block) {
     cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(7 * kSmemRows * sizeof(double)));
+                         (int)(6 * kSmemRows * sizeof(double)));
     cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     for (int C = 16; C >= 2; C /= 2) {
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(C);
         lc.blockDim = dim3(block);
-        lc.dynamicSmemBytes = (size_t)7 * kSmemRows * sizeof(double);
+        lc.dynamicSmemBytes = (size_t)6 * kSmemRows * sizeof(double);
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = C;
@@ -900,10 +1004,10 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
     P.r = B.r;
-    P.z = B.z;
+    P.u = B.u;
     P.p = B.p;
-    P.q = B.q;
-    P.dA = B.dA;
+    P.s = B.s;
+    P.w = B.w;
     P.idA = B.idA;
     P.part = B.part;
     P.bar = &B.sc->bar;
@@ -942,10 +1046,10 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
     P.b = role.b;
     P.x = role.x;
     P.r = B.r;
-    P.z = B.z;
+    P.u = B.u;
     P.p = B.p;
-    P.q = B.q;
-    P.dA = B.dA;
+    P.s = B.s;
+    P.w = B.w;
     P.idA = B.idA;
     P.part = B.part;
     P.bar = &B.sc->bar;
@@ -981,7 +1085,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         static bool cattr_set = false;
         if (!cattr_set) {
             cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(7 * kSmemRows * sizeof(double)));
+                                 (int)(6 * kSmemRows * sizeof(double)));
             cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cattr_set = true;
         }
@@ -992,7 +1096,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(C);
         lc.blockDim = dim3(cfg.smem_block);
-        lc.dynamicSmemBytes = (size_t)7 * P.L * sizeof(double);
+        lc.dynamicSmemBytes = (size_t)6 * P.L * sizeof(double);
         lc.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1014,14 +1118,14 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         grid = std::max(grid, nblk(n, kSmemRows));
         grid = std::max(grid, 1);
         P.L = nblk(n, grid);
-        const size_t smem = (size_t)7 * P.L * sizeof(double);
+        const size_t smem = (size_t)6 * P.L * sizeof(double);
         // the largest systems keep every SM's FP64 pipe busy with 32 warps;
         // smaller ones favour shorter block-level reductions
         const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
         static bool attr_set = false;
         if (!attr_set) {
             cudaFuncSetAttribute(k_pcg_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(7 * kSmemRows * sizeof(double)));
+                                 (int)(6 * kSmemRows * sizeof(double)));
             attr_set = true;
         }
         cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_smem, dim3(grid),
@@ -1078,10 +1182,10 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
     P.r = B.r;
-    P.z = B.z;
+    P.u = B.u;
     P.p = B.p;
-    P.q = B.q;
-    P.dA = B.dA;
+    P.s = B.s;
+    P.w = B.w;
     P.idA = B.idA;
     P.part = B.part;
     P.bar = nullptr;
@@ -1148,10 +1252,10 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.b = b;
     P.x = x;
     P.r = w.r;
-    P.z = w.z;
+    P.u = w.u;
     P.p = w.p;
-    P.q = w.q;
-    P.dA = w.dA;
+    P.s = w.s;
+    P.w = w.w;
     P.idA = w.idA;
     P.part = w.part;
     P.bar = w.bar;

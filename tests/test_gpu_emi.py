@@ -131,3 +131,42 @@ def test_emi_context_rejects_monodomain_only_calls(torch_dev):
     with pytest.raises(SdcError):
         ctx.step_taped(du, dw, 0.0, wl.dt, wl.sweeps, wl.tol, tp)
     ctx.close()
+
+
+def test_emi_parity_full_size_cells(torch_dev):
+    """Two 100x20x20 um cells on 2 um voxels (53,274 dofs): the node solves
+    run on the shared-memory PCG variant over many blocks; one adaptive step
+    against the oracle."""
+    torch, dev = torch_dev
+    from workloads.emi import emi_bricks
+    wl = emi_bricks(cells=(2, 1, 1))
+    assert wl.n > 50000
+    assert _run(wl, torch, dev, 1, wl.tol)
+
+
+@pytest.mark.slow
+def test_emi_bricks_full_size_properties(torch_dev):
+    """The 8x4x4-cell workload at full size (1,471,260 dofs) in the launch
+    configuration the benchmark times: a step is bitwise reproducible, every
+    node solve met the CG tolerance, the sets are nested, and adaptive and
+    plain SDC agree to the order of TOL."""
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import default_options, Context
+    from workloads.emi import emi_bricks
+    wl = emi_bricks()
+    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, cg_maxit=100000)
+    ctx = Context.from_emi(wl, options=opts, stream=torch.cuda.current_stream(dev).cuda_stream)
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    outs = []
+    for tol in (wl.tol, wl.tol, 0.0):
+        u, w = t64(wl.u0), t64(wl.w0)
+        st = ctx.step(u, w, 0.0, wl.dt, wl.sweeps, tol)
+        assert st.cg_relres_max <= wl.cg_rtol
+        acts = [ctx.active(k) for k in range(1, wl.sweeps)]
+        for a, b in zip(acts[1:], acts[:-1]):
+            assert np.all(np.isin(a, b))
+        outs.append((u.cpu().numpy(), w.cpu().numpy(), list(st.n_active[:wl.sweeps])))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2] and outs[0][2][-1] < wl.n
+    assert np.abs(outs[0][0] - outs[2][0]).max() <= 10 * wl.tol
+    ctx.close()
