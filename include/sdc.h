@@ -108,12 +108,18 @@ typedef struct {
                               in shared memory whenever |I_k| <= 4096 * SM count             */
     int cg_rows_per_block; /* shared-memory variant: target rows per block (0 = 512)          */
     int cg_cluster_rows;   /* solves with |I_k| <= this run on one thread-block cluster
-                              (16 CTAs, distributed shared memory); default 20000, 0 = never */
+                              (16 CTAs, distributed shared memory); default 10000, 0 = never */
     int profile;           /* 1: bracket every kernel launch with CUDA events on the context's
                               stream and report device time per phase in sdc_stats; default 0 */
     int inject_fault;      /* testing hook, default 0.  1: in every CG launch the last block
                               leaves without arriving at the first grid barrier, so the other
                               blocks' bounded waits run out and the step returns SDC_E_TIMEOUT */
+    int cg_pipelined;      /* arrangement of the CG iteration (the same iterates in exact
+                              arithmetic): 1 pipelined (one grid synchronisation per iteration,
+                              the sums overlapped with the product); 0 classical (two); -1
+                              automatic: pipelined for monodomain contexts, classical for
+                              cell-by-cell contexts, whose long ill-conditioned solves need its
+                              smaller rounding error; default -1.  Batches are pipelined.      */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */
@@ -202,7 +208,7 @@ sdc_status sdc_get_matrix(const sdc_ctx* ctx, int* row_ptr, int* col, double* va
  * d_len[i] <= width entries, entry t at d_val[t * ld + i], column
  * d_col[t * ld + i] in [0, n); ld >= n.  Every array is caller-owned device
  * memory of the current device; d_x receives the solution.  The workspace
- * (6 n doubles plus a few per SM) is allocated and freed inside the call, which
+ * (11 n doubles plus a few per SM) is allocated and freed inside the call, which
  * synchronises `stream` (a cudaStream_t, NULL = legacy default).  iters and
  * relres (host, may be NULL) receive the iteration count and the final
  * sqrt(r'z / r0'z0).  Errors: SDC_E_INVALID (nothing launched),
@@ -359,7 +365,7 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
 /* sdc_pcg_solve for callers that cannot allocate device memory (the paper has
  * no counterpart; this is a service of the library).  Same arguments, results
  * and errors as sdc_pcg_solve, but no device memory is allocated or freed:
- * the workspace is a static array of the library, reserved (about 3.3 MB) on
+ * the workspace is a static array of the library, reserved (about 6.2 MB) on
  * every GPU that loads the library until the process exits.
  *   - n <= SDC_PCG_NOALLOC_MAX_ROWS, else SDC_E_INVALID with a message from
  *     sdc_last_error(NULL), and nothing is launched.

@@ -42,7 +42,7 @@ class sdc_options(C.Structure):
                 ("cg_smem_block_size", C.c_int), ("cg_cluster_max", C.c_int),
                 ("cg_max_blocks", C.c_int), ("cg_variant", C.c_int),
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
-                ("profile", C.c_int), ("inject_fault", C.c_int)]
+                ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int)]
 
 
 class sdc_stats(C.Structure):

@@ -104,6 +104,7 @@ int alloc_buffers(sdc_ctx* c) {
     P.cluster = std::min(pcg_cluster_size(P.smem_block), c->opt.cg_cluster_max);
     P.cluster_rows = c->opt.cg_cluster_rows;
     P.inject_fault = c->opt.inject_fault;
+    P.pipelined = c->opt.cg_pipelined != 0;
     P.budget = c->opt.spin_budget;
     if (P.max_blocks_general < 1 || P.sms < 1) return SDC_E_CUDA;
     B.max_blocks = std::max(P.max_blocks_general, P.sms);
@@ -111,6 +112,7 @@ int alloc_buffers(sdc_ctx* c) {
               dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
               dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.u, ld) &&
               dalloc(&B.p, ld) && dalloc(&B.s, ld) && dalloc(&B.w, ld) && dalloc(&B.idA, ld) &&
+              dalloc(&B.q, ld) && dalloc(&B.z, ld) && dalloc(&B.nv, ld) && dalloc(&B.m, 2 * ld) &&
               dalloc(&B.flag, ld) &&
               dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
               dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
@@ -138,7 +140,7 @@ int alloc_buffers(sdc_ctx* c) {
             cudaMemcpyAsync(B.inst_off, c->inst_off.data(), (nseg + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, c->stream);
     }
-    if (ok) ok = dalloc(&B.part, 4 * (size_t)B.max_blocks);
+    if (ok) ok = dalloc(&B.part, 12 * (size_t)B.max_blocks);
     if (!ok) return SDC_E_NOMEM;
     if (cudaMallocHost(&c->h_pin, 4 * sizeof(int)) != cudaSuccess) return SDC_E_NOMEM;
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), c->stream);
@@ -150,6 +152,7 @@ void free_adjoint(AdjointBuffers& W);
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
     double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.u, B.p, B.s, B.w, B.idA, B.part,
+                    B.q, B.z, B.nv, B.m,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
     int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff, B.inst_off, B.bounds, B.segtab,
@@ -237,9 +240,10 @@ void sdc_default_options(sdc_options* o) {
     o->cg_max_blocks = 0;
     o->cg_variant = 0;
     o->cg_rows_per_block = 0;
-    o->cg_cluster_rows = 20000;
+    o->cg_cluster_rows = 10000;
     o->profile = 0;
     o->inject_fault = 0;
+    o->cg_pipelined = -1;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -319,7 +323,7 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.cg_smem_block_size > 1024 || o.cg_smem_block_size % 32 != 0 || o.cg_cluster_max < 1 ||
         o.cg_cluster_max > 16 || o.inject_fault < 0 ||
         o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
-        o.cg_cluster_rows < 0)
+        o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
@@ -835,17 +839,21 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     cudaStream_t s = (cudaStream_t)stream;
     const int block = 256;
     const int maxb = pcg_max_blocks(block);
-    // workspace: 6 vectors, 4 * maxb partial sums, then the scalars
-    const size_t nd = (size_t)6 * n + 4 * (size_t)maxb + 2;
+    // workspace: 11 vectors, 12 * maxb for the partial-sum records (16-byte aligned:
+    // they are read with 16-byte loads), then the scalars
+    const size_t po = ((size_t)11 * n + 1) & ~(size_t)1;
+    const size_t nd = po + 12 * (size_t)maxb + 2;
     char* ws = nullptr;
     if (cudaMalloc(&ws, nd * sizeof(double) + 64) != cudaSuccess)
         return fail(nullptr, SDC_E_NOMEM, "sdc_pcg_solve: workspace allocation failed");
     double* v = (double*)ws;
     PcgScratch w;
     w.r = v; w.u = v + n; w.p = v + 2 * (size_t)n; w.s = v + 3 * (size_t)n;
-    w.w = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.part = v + 6 * (size_t)n;
+    w.w = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.q = v + 6 * (size_t)n;
+    w.z = v + 7 * (size_t)n; w.nv = v + 8 * (size_t)n; w.m = v + 9 * (size_t)n;
+    w.part = v + po;
     w.max_blocks = maxb;
-    w.relres = v + 6 * (size_t)n + 4 * (size_t)maxb;
+    w.relres = v + po + 12 * (size_t)maxb;
     unsigned* sc = (unsigned*)(w.relres + 1);
     w.bar = sc;
     w.err = (int*)(sc + 1);

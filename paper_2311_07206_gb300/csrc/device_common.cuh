@@ -194,4 +194,163 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& epoch, lon
     return group_barrier(bar, (int)gridDim.x, epoch, budget, err, ok_flag);
 }
 
+// ---- exact sums on the integer pipes -----------------------------------------
+// FP64 is the scarce unit on this part (a warp FP64 instruction occupies a
+// sub-partition's FP64 unit for ~76 cycles whatever the number of active
+// lanes), so the dot-product reductions of the CG run in exact fixed point on
+// the integer units instead.  A set of doubles is summed at a common binary
+// scale: with F the largest biased exponent field of the set, value
+// v = +-M 2^(f - 1075) (M the 53-bit significand, f >= 1) becomes the integer
+// q = +-trunc(M 2^(f - F + 48)), i.e. v = q 2^(F - 1123) up to a truncation
+// below 2^(F - 1123), 2^-101 of the largest term.  |q| < 2^101, so sums of up
+// to 2^26 terms fit a signed 128-bit integer.  Integer addition is exact and
+// associative: a sum does not depend on its order or grouping.  A field of
+// 2047 (Inf or NaN) makes the sum NaN.
+
+// biased exponent field (denormals and zero count as 1)
+__device__ __forceinline__ int xs_field(double v) {
+    const int f = (int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ff;
+    return f < 1 ? 1 : f;
+}
+
+// v as a signed fixed-point integer at the scale of field F (F >= field of v)
+__device__ __forceinline__ __int128 xs_fixed(double v, int F) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const int f = (int)(bits >> 52) & 0x7ff;
+    const unsigned long long mant = (bits & 0xfffffffffffffull) | (f > 0 ? (1ull << 52) : 0ull);
+    const int sh = 48 - (F - (f < 1 ? 1 : f));
+    unsigned __int128 q;
+    if (sh >= 0) q = (unsigned __int128)mant << sh;
+    else q = -sh >= 53 ? 0 : (unsigned __int128)(mant >> -sh);
+    const __int128 sq = (__int128)q;
+    return (bits >> 63) ? -sq : sq;
+}
+
+// exact warp sum of a signed 128-bit value (full warp): seven limbs summed
+// with the integer warp reduction, the top limb signed
+__device__ __forceinline__ __int128 xs_warp_sum(__int128 q) {
+    const unsigned __int128 u = (unsigned __int128)q;
+    unsigned __int128 tot = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const unsigned limb = (unsigned)(u >> (20 * k)) & 0xfffffu;
+        tot += (unsigned __int128)__reduce_add_sync(0xffffffffu, limb) << (20 * k);
+    }
+    const int top = (int)(q >> 120);
+    tot += (unsigned __int128)(__int128)__reduce_add_sync(0xffffffffu, top) << 120;
+    return (__int128)tot;
+}
+
+// q 2^(F - 1123) rounded to the nearest double (ties to even)
+__device__ __forceinline__ double xs_to_double(__int128 q, int F) {
+    if (F >= 2047) return __longlong_as_double(0x7ff8000000000000ll);
+    if (q == 0) return 0.0;
+    const bool neg = q < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-q) : (unsigned __int128)q;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int L = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    unsigned long long mant;
+    int e = F - 1123;
+    if (L <= 52) {
+        mant = lo;
+    } else {
+        const int sh = L - 52;
+        mant = (unsigned long long)(a >> sh);
+        const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+        e += sh;
+    }
+    const double d = ldexp((double)mant, e);
+    return neg ? -d : d;
+}
+
+// Exact sum of two values per thread over the block.  Every thread gets the
+// block's exponent fields Fa, Fb; warp 0 gets the block sums qa, qb (at those
+// scales) in all its lanes.  scratch: >= 2 * 32 ints and 2 * 32 int128.
+struct XsScratch {
+    int fmax[64];
+    __int128 q[64];
+};
+__device__ __forceinline__ void xs_block_sum2(double a, double b, XsScratch& X, int& Fa, int& Fb,
+                                              __int128& qa, __int128& qb) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int fa = __reduce_max_sync(0xffffffffu, xs_field(a));
+    int fb = __reduce_max_sync(0xffffffffu, xs_field(b));
+    if (lane == 0) {
+        X.fmax[wid] = fa;
+        X.fmax[32 + wid] = fb;
+    }
+    __syncthreads();
+    fa = __reduce_max_sync(0xffffffffu, lane < nw ? X.fmax[lane] : 1);
+    fb = __reduce_max_sync(0xffffffffu, lane < nw ? X.fmax[32 + lane] : 1);
+    const __int128 sa = xs_warp_sum(xs_fixed(a, fa));
+    const __int128 sb = xs_warp_sum(xs_fixed(b, fb));
+    if (lane == 0) {
+        X.q[wid] = sa;
+        X.q[32 + wid] = sb;
+    }
+    __syncthreads();
+    Fa = fa;
+    Fb = fb;
+    qa = qb = 0;
+    if (wid == 0) {
+        qa = xs_warp_sum(lane < nw ? X.q[lane] : (__int128)0);
+        qb = xs_warp_sum(lane < nw ? X.q[32 + lane] : (__int128)0);
+    }
+}
+
+// Record of one block's exact partial sums, as published for a group sum
+// (48 bytes, 16-byte aligned).
+struct __align__(16) XsRecord {
+    unsigned long long alo, ahi, blo, bhi;
+    int fa, fb, pad0, pad1;
+};
+__device__ __forceinline__ XsRecord xs_load_cg(const XsRecord* p) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(p);
+    const ulonglong2 a = __ldcg(q), b = __ldcg(q + 1);
+    const int4 c = __ldcg(reinterpret_cast<const int4*>(q + 2));
+    XsRecord r;
+    r.alo = a.x; r.ahi = a.y; r.blo = b.x; r.bhi = b.y;
+    r.fa = c.x; r.fb = c.y; r.pad0 = 0; r.pad1 = 0;
+    return r;
+}
+__device__ __forceinline__ void xs_store(XsRecord* r, int fa, int fb, __int128 qa, __int128 qb) {
+    r->alo = (unsigned long long)qa;
+    r->ahi = (unsigned long long)((unsigned __int128)qa >> 64);
+    r->blo = (unsigned long long)qb;
+    r->bhi = (unsigned long long)((unsigned __int128)qb >> 64);
+    r->fa = fa;
+    r->fb = fb;
+}
+
+// Exact totals of n records (one warp, all lanes get the result): the common
+// field is the largest block field; block sums are aligned by an arithmetic
+// right shift (truncation below 2^-101 of the largest term) and added.
+template <class Load>
+__device__ __forceinline__ void xs_group_total(int n, Load&& load, double& ta, double& tb) {
+    const int lane = threadIdx.x & 31;
+    int fa = 1, fb = 1;
+    for (int i = lane; i < n; i += 32) {
+        const XsRecord r = load(i);
+        fa = max(fa, r.fa);
+        fb = max(fb, r.fb);
+    }
+    fa = __reduce_max_sync(0xffffffffu, fa);
+    fb = __reduce_max_sync(0xffffffffu, fb);
+    __int128 sa = 0, sb = 0;
+    for (int i = lane; i < n; i += 32) {
+        const XsRecord r = load(i);
+        const __int128 qa = (__int128)(((unsigned __int128)r.ahi << 64) | r.alo);
+        const __int128 qb = (__int128)(((unsigned __int128)r.bhi << 64) | r.blo);
+        const int da = fa - r.fa, db = fb - r.fb;
+        sa += da >= 127 ? (qa < 0 ? (__int128)-1 : (__int128)0) : (qa >> da);
+        sb += db >= 127 ? (qb < 0 ? (__int128)-1 : (__int128)0) : (qb >> db);
+    }
+    sa = xs_warp_sum(sa);
+    sb = xs_warp_sum(sb);
+    ta = xs_to_double(sa, fa);
+    tb = xs_to_double(sb, fb);
+}
+
 }  // namespace sdc

@@ -350,6 +350,9 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
     const Coll& co = *a.co;
     cudaStream_t s = a.s;
     const double tol_drop = a.opt->alpha * TOL;
+    // the classical CG arrangement unless the pipelined one is asked for explicitly
+    PcgConfig pcg = *a.pcg;
+    pcg.pipelined = a.opt->cg_pipelined == 1;
     auto fail = [&](int st, const std::string& msg) {
         *a.err = msg;
         return st;
@@ -449,8 +452,8 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             role.iters_out = &B.sc->cg_iters[k * kMaxM + m];
             role.relres_out = &B.sc->cg_relres[k * kMaxM + m];
             run(SDC_PHASE_PCG, 1, [&] {
-                if (launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol, a.opt->cg_maxit, *a.pcg,
-                                    B, s) != SDC_OK)
+                if (launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol, a.opt->cg_maxit, pcg, B,
+                                    s) != SDC_OK)
                     status = fail(SDC_E_CUDA, std::string("cooperative CG launch: ") +
                                                   cudaGetErrorString(cudaGetLastError()));
             });

@@ -91,13 +91,17 @@ struct StepBuffers {
     double* D = nullptr;      // [M][ld] corrections dv
     double* mc = nullptr;     // [ld] lumped mass of the active rows
     double* kdc = nullptr;    // [ld] K_ii of the active rows
-    double* r = nullptr;      // CG vectors [ld]: residual, u = D^-1 r, direction p,
-    double* u = nullptr;      // s = A p, w = A u, reciprocal diagonal
-    double* p = nullptr;
+    double* r = nullptr;      // CG vectors [ld]: residual, u = D^-1 r, w = A u, direction p,
+    double* u = nullptr;      // s = A p, q = D^-1 s, z = A q, nv = A m, reciprocal diagonal;
+    double* p = nullptr;      // m = D^-1 w [2 ld] (two buffers)
     double* s = nullptr;
     double* w = nullptr;
+    double* q = nullptr;
+    double* z = nullptr;
+    double* nv = nullptr;
+    double* m = nullptr;
     double* idA = nullptr;
-    double* part = nullptr;   // 4 * max_blocks: two partial sums per block, two buffers
+    double* part = nullptr;   // 12 * max_blocks: one 48-byte exact-sum record per block, two buffers
     int max_blocks = 0;
     int* flag = nullptr;      // [ld]
     int* map = nullptr;       // [ld] old compact row -> new compact row or -1
@@ -129,7 +133,12 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const double* W, const double* v0, double dt, const Ionic& ion,
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
 // Launch configuration of the restricted PCG solves.
-constexpr int kSmemRows = 4448;     // rows per block of the shared-memory variants
+constexpr int kSmemVectors = 9;     // per-row doubles in shared memory, shared-memory variant
+constexpr int kSmemRows = 3200;     // rows per block of the shared-memory variant
+constexpr int kClusterVectors = 11; // per-row doubles in shared memory, cluster variant
+constexpr int kClusterRows = 2592;  // rows per CTA of the cluster variant
+constexpr int kSmemVectorsC = 6;    // classical arrangement, shared-memory form
+constexpr int kSmemRowsC = 4768;
 struct PcgConfig {
     int block = 256;                // block size of the general variant
     int max_blocks_general = 0;     // cooperative grid limit of the general variant
@@ -145,6 +154,7 @@ struct PcgConfig {
     int max_blocks_batch = 0;       // cooperative grid limit of the batched variant
     int batch_rows_per_block = 1024;
     int inject_fault = 0;
+    int pipelined = 1;              // 1: pipelined CG; 0: classical arrangement
     long long budget = 0;
 };
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
@@ -221,10 +231,11 @@ void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, 
 void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
-// r, u, p, s, w, idA: n doubles each; part: 4 * max_blocks doubles;
+// r, u, w, p, s, q, z, nv, idA: n doubles each; m: 2 n doubles;
+// part: 12 * max_blocks doubles (16-byte aligned);
 // bar, err, iters, relres: one value each, bar and err zero before the launch.
 struct PcgScratch {
-    double *r, *u, *p, *s, *w, *idA, *part;
+    double *r, *u, *w, *p, *s, *q, *z, *nv, *m, *idA, *part;
     int max_blocks;
     unsigned* bar;
     int* err;

@@ -13,6 +13,7 @@
 //   extract  : K[I_{k+1}, I_{k+1}] from K[I_k, I_k] through the old->new row map
 
 #include <cfloat>
+#include <cstdint>
 
 #include <cooperative_groups.h>
 
@@ -117,15 +118,20 @@ struct CgParams {
     double c;            // dt * Qhat_mm
     const double* b;     // right-hand side of this node
     double* x;           // correction of this node (output)
-    // CG vectors (global-vector variant; the shared-memory variants keep their
-    // own rows on chip and publish u only)
-    double* r;           // residual
-    double* u;           // D^-1 r (published for the neighbours' gathers)
-    double* p;           // search direction
-    double* s;           // A p
-    double* w;           // A u
+    // CG vectors of the global-vector variant (the shared-memory variants keep
+    // their rows on chip): residual r, u = D^-1 r, w = A u, the recurrences
+    // p, s = A p, q = D^-1 s, z = A q, and nv = A m
+    double* r;
+    double* u;           // also: u published for the initial product A u
+    double* w;
+    double* p;
+    double* s;
+    double* q;
+    double* z;
+    double* nv;
+    double* m;           // m = D^-1 w, published for the neighbours' gathers, two buffers of ld
     double* idA;         // reciprocal of the diagonal (Jacobi preconditioner)
-    double* part;        // per-block partial sums, two per block, two buffers
+    double* part;        // per-block exact-sum records, two buffers
     unsigned* bar;
     int* err;
     double rtol;
@@ -134,7 +140,7 @@ struct CgParams {
     int* iters_out;
     double* relres_out;
     // epilogue: LU-trick coupling into the later nodes' right-hand sides
-    int m, M;
+    int m_node, M;
     double dt;
     double* R;
     double qh[kMaxM];    // coupling coefficient per target node
@@ -156,13 +162,13 @@ __device__ __forceinline__ void cg_couple_row(const CgParams& P, int i, double x
     }
 }
 
-// Shared per-block state of a CG solve.  The scalars are derived by lane 0 of
-// warp 0 from each pair of grid-wide sums (one FP64 division chain per block,
-// not per thread: the FP64 pipe is the scarce unit on this part).
+// Shared per-block state of a CG solve.  The scalars are derived by lane 0
+// of warps 0 and 1 from each pair of grid-wide sums (a few FP64 operations
+// per block, not per thread: the FP64 pipe is the scarce unit on this part).
 struct CgShared {
-    double red[2 * 1024];   // per-thread partial sums of the two dot products
-    double wsum[8];         // per-warp totals of the block sum
-    double alpha, beta, inv_gamma, inv_alpha, gamma0, thresh, rzmax, rn;
+    XsScratch xs;           // exact block sums
+    double alpha, beta, den, gamma0, rzmax, rn;
+    double inv_g[2];        // 1 / gamma of the last two sums (warp 1)
     int ok, state;          // state: 0 iterating, 1 converged, 2 non-finite
 };
 
@@ -181,42 +187,34 @@ __device__ __forceinline__ double largest_with_sqrt_at_most(double thresh) {
     return r;
 }
 
-// Scalars of the Chronopoulos-Gear iteration from gamma = r.u and
-// delta = w.u (u = D^-1 r, w = A u):
-//   first:  alpha = gamma / delta, beta = 0
-//   later:  beta = gamma / gamma_old,
-//           alpha = gamma / (delta - beta gamma / alpha_old)
-// 1/gamma and 1/alpha are kept so that a step needs one division chain.
-__device__ __forceinline__ void cg_first(CgShared& S, double g, double d, double rtol) {
-    S.gamma0 = g;
-    S.rn = g;
-    S.beta = 0.0;
-    S.thresh = rtol * sqrt(g);
-    S.rzmax = largest_with_sqrt_at_most(S.thresh);
-    if (!isfinite(g) || !isfinite(d)) {
-        S.state = 2;
-    } else if (g == 0.0) {
-        S.state = 1;
+// Scalars of sum number t from gamma = r.u and delta = w.u:
+//   t = 0:  alpha = gamma / delta, beta = 0, den = delta
+//   t > 0:  beta = gamma / gamma_old, den = delta - beta^2 den_old,
+//           alpha = gamma / den
+// (den_t = delta_t - beta_t gamma_t / alpha_{t-1}, since
+// alpha_{t-1} = gamma_{t-1} / den_{t-1}).  Warp 0 lane 0 runs this chain;
+// warp 1 lane 0 meanwhile forms 1/gamma for the next beta and, on the first
+// sum, the stopping bound, so the chain holds one division.
+__device__ __forceinline__ void cg_scalars(CgShared& S, int wid, int t, double g, double d,
+                                           double rtol) {
+    if (wid == 0) {
+        S.rn = g;
+        if (t == 0) S.gamma0 = g;
+        if (!isfinite(g) || !isfinite(d)) {
+            S.state = 2;
+        } else if (t == 0 ? g == 0.0 : (g >= 0.0 && g <= S.rzmax)) {
+            S.state = 1;
+        } else {
+            const double beta = t == 0 ? 0.0 : g * S.inv_g[(t - 1) & 1];
+            const double den = t == 0 ? d : fma(-beta, beta * S.den, d);
+            S.alpha = g / den;
+            S.beta = beta;
+            S.den = den;
+            S.state = 0;
+        }
     } else {
-        S.state = 0;
-        S.alpha = g / d;
-        S.inv_gamma = 1.0 / g;
-        S.inv_alpha = d * S.inv_gamma;
-    }
-}
-__device__ __forceinline__ void cg_next(CgShared& S, double g, double d) {
-    S.rn = g;
-    if (!isfinite(g) || !isfinite(d)) {
-        S.state = 2;
-    } else if (g >= 0.0 && g <= S.rzmax) {
-        S.state = 1;
-    } else {
-        const double beta = g * S.inv_gamma;
-        const double den = d - beta * g * S.inv_alpha;
-        S.alpha = g / den;
-        S.inv_gamma = 1.0 / g;
-        S.inv_alpha = den * S.inv_gamma;
-        S.beta = beta;
+        S.inv_g[t & 1] = 1.0 / g;
+        if (t == 0) S.rzmax = largest_with_sqrt_at_most(rtol * sqrt(g));
     }
 }
 // final relative preconditioned residual sqrt(r.u / r0.u0)
@@ -224,130 +222,566 @@ __device__ __forceinline__ double cg_relres(const CgShared& S) {
     return S.gamma0 > 0.0 ? sqrt(fabs(S.rn) / S.gamma0) : 0.0;
 }
 
-// Block sum of two values per thread in a fixed order, result in thread 0.
-// Thread t stores (a, b) at red[t], red[1024 + t]; warp w < W = min(4, B/32)
-// adds the warp-rows w, w + W, w + 2W, ... of the block (a balanced tree over
-// at most 8 values per lane, then a shuffle tree), and thread 0 adds the W
-// warp totals in order.  Four summing warps keep every SM sub-partition's
-// FP64 unit busy with a short dependency chain.
-__device__ __forceinline__ void block_sum2(double a, double b, CgShared& S, double& sa,
-                                           double& sb) {
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int nw = blockDim.x >> 5;
-    const int W = min(4, nw);
-    S.red[t] = a;
-    S.red[1024 + t] = b;
-    __syncthreads();
-    if (wid < W) {
-        const int cnt = (nw - wid + W - 1) / W;   // warp-rows of this warp (<= 8)
-        double x[8], y[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int at = (wid + k * W) * 32 + lane;
-            x[k] = k < cnt ? S.red[at] : 0.0;
-            y[k] = k < cnt ? S.red[1024 + at] : 0.0;
-        }
-        if (cnt > 4) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) { x[k] += x[k + 4]; y[k] += y[k + 4]; }
-        }
-        if (cnt > 2) {
-            x[0] += x[2]; y[0] += y[2];
-            x[1] += x[3]; y[1] += y[3];
-        }
-        if (cnt > 1) { x[0] += x[1]; y[0] += y[1]; }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
-            y[0] += __shfl_xor_sync(0xffffffffu, y[0], o);
-        }
-        if (lane == 0) {
-            S.wsum[wid] = x[0];
-            S.wsum[4 + wid] = y[0];
-        }
-    }
-    __syncthreads();
-    sa = sb = 0.0;
-    if (t == 0) {
-        if (W == 4) {
-            sa = (S.wsum[0] + S.wsum[1]) + (S.wsum[2] + S.wsum[3]);
-            sb = (S.wsum[4] + S.wsum[5]) + (S.wsum[6] + S.wsum[7]);
-        } else {
-            for (int k = 0; k < W; ++k) { sa += S.wsum[k]; sb += S.wsum[4 + k]; }
-        }
-    }
-}
-
-// Sum of two values per thread over a group of `nblk` blocks (the whole grid,
-// or one instance's share of a batched launch), fused with the group barrier.
-// Thread 0 publishes the block's pair to part[2 bidx], arrives and waits;
-// warp 0 then adds the nblk pairs in index order (bitwise identical in every
-// block) and lane 0 runs on_total(a, b), which stores the iteration's scalars
-// in shared memory.  A closing CTA barrier makes them visible to the block.
-// Returns false after a barrier timeout.
-template <class F>
-__device__ __forceinline__ bool group_reduce2(double a, double b, CgShared& S, double* part,
-                                              unsigned* bar, int nblk, int bidx, unsigned& epoch,
-                                              long long budget, int* err, F&& on_total) {
-    double sa, sb;
-    block_sum2(a, b, S, sa, sb);
+// Block part of a group sum: exact block sums of (a, b); thread 0 publishes
+// them to part[bidx] and arrives at the group barrier, which also publishes
+// every global write the block made before it.  Returns false (in every
+// thread) after a barrier timeout.
+__device__ __forceinline__ bool cg_publish_arrive(double a, double b, CgShared& S, XsRecord* part,
+                                                  unsigned* bar, int nblk, int bidx,
+                                                  unsigned& epoch, long long budget, int* err) {
+    int fa, fb;
+    __int128 qa, qb;
+    xs_block_sum2(a, b, S.xs, fa, fb, qa, qb);
     epoch += nblk;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        int ok = 1;
-        if (lane == 0) {
-            part[2 * bidx] = sa;
-            part[2 * bidx + 1] = sb;
-            ok = barrier_arrive_wait(bar, epoch, budget, err);
-        }
-        __syncwarp();
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok) {
-            double ta = 0.0, tb = 0.0;
-            const double2* p2 = reinterpret_cast<const double2*>(part);
-            for (int i = lane; i < nblk; i += 32) {
-                const double2 v = __ldcg(p2 + i);
-                ta += v.x;
-                tb += v.y;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ta += __shfl_xor_sync(0xffffffffu, ta, o);
-                tb += __shfl_xor_sync(0xffffffffu, tb, o);
-            }
-            if (lane == 0) on_total(ta, tb);
-        }
-        if (lane == 0) S.ok = ok;
+    if (threadIdx.x == 0) {
+        xs_store(part + bidx, fa, fb, qa, qb);
+        S.ok = barrier_arrive_wait(bar, epoch, budget, err);
     }
     __syncthreads();
     return S.ok != 0;
 }
 
-// Jacobi-PCG on the restricted node system, whole solve in one cooperative
-// launch, vectors in global memory (any size).
+// Jacobi-PCG on the restricted node system in the pipelined arrangement of
+// Ghysels and Vanroose (2014), whole solve in one cooperative launch.
 //
-// The iteration is preconditioned CG in the arrangement of Chronopoulos and
-// Gear (1989): with u = D^-1 r and w = A u, both dot products of an iteration,
-// gamma = r.u and delta = w.u, are summed in one grid-wide reduction, and
-// s = A p follows from the recurrence s = w + beta s.  Per iteration:
-//   phase 1: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
-//            u = D^-1 r (published) -> grid barrier
-//   phase 2: w = A u (gathers u of neighbouring rows; the diagonal part of
-//            A u is D u = r), r.u and w.u -> one grid sum of two values,
-//            convergence test on r.u, then beta and alpha
+// With u = D^-1 r, w = A u and m = D^-1 w, an iteration needs the two dot
+// products gamma = r.u and delta = w.u and one product n = A m, and the
+// product does not depend on the iteration's scalars.  So one grid-wide
+// synchronisation per iteration both publishes m for the neighbours' gathers
+// and completes the sums: after it, warps 0 and 1 add the blocks' exact
+// partial sums and derive alpha and beta while the other warps form n = A m.
+// Per iteration:
+//   U+L (local): z = n + beta z, q = m + beta q, s = w + beta s,
+//                p = u + beta p, x += alpha p, r -= alpha s, u -= alpha q,
+//                w -= alpha z; then r.u, w.u and m = D^-1 w (published)
+//   sync:        exact block sums, group barrier
+//   S (overlap): n = A m (the diagonal part of A m is D m = w)  ||  totals,
+//                convergence test on r.u, beta and alpha
 // The iterates are those of standard preconditioned CG in exact arithmetic.
-// Rows are processed grid-stride; each thread owns the same rows in every
-// phase.  Block totals are added in a fixed order by every block, so all
-// blocks take identical decisions.
-// One group of `nblk` blocks solves rows [row0, row1): the whole launch, or
-// one instance of a batched launch.  `part` points at the group's first
-// partial-sum pair of buffer 0; buffer 1 is `pstride` doubles further.
+// m is published to two alternating buffers: a block may write the next m
+// while a slower neighbour still gathers the current one.
+//
+// One group of `nblk` blocks solves rows [row0, row1) in contiguous chunks of
+// Lg rows per block: the whole launch, or one instance of a batched launch.
+// `part` points at the group's first record of buffer 0; buffer 1 is
+// `pstride` records further.  Threads [sp0, B) form the products while warps
+// 0 and 1 sum; blocks under 256 threads do both in turn.
 __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int row0, int row1,
-                                          int nblk, int bidx, unsigned* bar, double* part,
+                                          int nblk, int bidx, unsigned* bar, XsRecord* part,
                                           int pstride, int* iters_out, double* relres_out) {
+    const int B = blockDim.x, t = threadIdx.x;
+    const int Lg = (row1 - row0 + nblk - 1) / nblk;
+    const int c0 = row0 + bidx * Lg;
+    const int c1 = min(row1, c0 + Lg);
+    const bool lead = (bidx == 0 && t == 0);
+    const int sp0 = B >= 256 ? 64 : 0;
+    const int ld = P.ld;
+    const double c = P.c;
+    double* const mbuf[2] = {P.m, P.m + ld};
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int i = c0 + t; i < c1; i += B) {
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
+        P.idA[i] = id;
+        const double r = P.b[i];
+        P.r[i] = r;
+        P.u[i] = r * id;
+        P.p[i] = 0.0;
+        P.s[i] = 0.0;
+        P.q[i] = 0.0;
+        P.z[i] = 0.0;
+        P.x[i] = 0.0;
+    }
+    if (P.inject_fault && bidx == nblk - 1) {
+        // leave without arriving: every other block's bounded wait runs out
+        if (nblk == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+    // w = A u; first r.u, w.u and m
+    double ga = 0.0, de = 0.0;
+    for (int i = c0 + t; i < c1; i += B) {
+        const int len = P.alen[i];
+        double acc = 0.0;
+        for (int k = 0; k < len; ++k)
+            acc += P.aval[(size_t)k * ld + i] * __ldcg(P.u + P.acol[(size_t)k * ld + i]);
+        const double ri = P.r[i], ui = P.u[i];
+        const double wi = ri + c * acc;
+        P.w[i] = wi;
+        ga += ri * ui;
+        de += wi * ui;
+        mbuf[0][i] = P.idA[i] * wi;
+    }
+    int it = 0, nsum = 0;
+    while (true) {
+        if (!cg_publish_arrive(ga, de, S, part + buf * pstride, bar, nblk, bidx, epoch,
+                               P.budget, P.err))
+            return;
+        const double* mc = mbuf[nsum & 1];
+        auto totals = [&]() {
+            double g, d;
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        };
+        if (sp0 > 0 && t < 64) totals();
+        if (t >= sp0) {
+            for (int i = c0 + t - sp0; i < c1; i += B - sp0) {
+                const int len = P.alen[i];
+                double acc = 0.0;
+                for (int k = 0; k < len; ++k)
+                    acc += P.aval[(size_t)k * ld + i] * __ldcg(mc + P.acol[(size_t)k * ld + i]);
+                P.nv[i] = P.w[i] + c * acc;
+            }
+        }
+        if (sp0 == 0 && t < 64) totals();
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        double* mn = mbuf[nsum & 1];
+        ga = de = 0.0;
+        for (int i = c0 + t; i < c1; i += B) {
+            const double mi = __ldcg(mc + i);
+            const double wi = P.w[i], ui = P.u[i];
+            const double zi = P.nv[i] + beta * P.z[i];
+            const double qi = mi + beta * P.q[i];
+            const double si = wi + beta * P.s[i];
+            const double pi = ui + beta * P.p[i];
+            P.z[i] = zi;
+            P.q[i] = qi;
+            P.s[i] = si;
+            P.p[i] = pi;
+            P.x[i] += alpha * pi;
+            const double r2 = P.r[i] - alpha * si;
+            const double u2 = ui - alpha * qi;
+            const double w2 = wi - alpha * zi;
+            P.r[i] = r2;
+            P.u[i] = u2;
+            P.w[i] = w2;
+            ga += r2 * u2;
+            de += w2 * u2;
+            mn[i] = P.idA[i] * w2;
+        }
+    }
+    if (S.state == 2) {
+        if (lead) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (lead) {
+        *iters_out = it;
+        *relres_out = cg_relres(S);
+    }
+    // x is complete and visible in every block: the last group barrier followed its update.
+    if (P.epi_lo < P.epi_hi) {
+        for (int i = c0 + t; i < c1; i += B) {
+            const int len = P.alen[i];
+            const double xi = __ldcg(P.x + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcg(CgParams P) {
+    __shared__ CgShared S;
+    pcg_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar,
+              reinterpret_cast<XsRecord*>(P.part), (int)gridDim.x, P.iters_out, P.relres_out);
+}
+
+// Batched variant: independent solves of the instances of a batch (disjoint
+// diagonal blocks of the system) in one cooperative launch.  Block b works on
+// the group tab[b] describes: that instance's compact rows, its own barrier
+// counter and partial-sum records, its own iteration count.  Groups never
+// wait for each other, so a converged instance's blocks leave early.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcg_batch(CgParams P, const SegBlock* __restrict__ tab,
+                                                        unsigned* __restrict__ bars,
+                                                        int* __restrict__ seg_iters,
+                                                        double* __restrict__ seg_relres) {
+    __shared__ CgShared S;
+    const SegBlock g = tab[blockIdx.x];
+    pcg_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
+              reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x, seg_iters + g.seg,
+              seg_relres + g.seg);
+}
+
+// Compact boundaries of the batch instances in a sorted active list:
+// bounds[s] = first position p with act[p] >= inst_off[s] (lower bound).
+__global__ void k_seg_bounds(const int* __restrict__ count, const int* __restrict__ act, int nseg,
+                             const int* __restrict__ inst_off, int* __restrict__ bounds) {
+    const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sidx > nseg) return;
+    const int n = *count;
+    const int key = inst_off[sidx];
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (act[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    bounds[sidx] = lo;
+}
+
+// Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
+// block b owns the contiguous rows [b L, b L + L); their r, u, w, p, s, q, z,
+// n and reciprocal diagonal stay in shared memory for the whole solve.  m is
+// published to global memory (coalesced, two buffers) for the neighbours'
+// gathers and x is accumulated in place in global memory; the matrix is read
+// through the read-only path.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    const int G = gridDim.x, B = blockDim.x, t = threadIdx.x;
+    const int L = P.L, ld = P.ld;
+    const int r0 = blockIdx.x * L;
+    const int nl = max(0, min(P.n - r0, L));
+    const int sp0 = B >= 256 ? 64 : 0;
+    // per-row vectors in shared memory (addressed from one base: fewer live registers)
+#define SR(l) sm[(l)]
+#define SU(l) sm[L + (l)]
+#define SW(l) sm[2 * L + (l)]
+#define SP(l) sm[3 * L + (l)]
+#define SS(l) sm[4 * L + (l)]
+#define SQ(l) sm[5 * L + (l)]
+#define SZ(l) sm[6 * L + (l)]
+#define SN(l) sm[7 * L + (l)]
+#define SI(l) sm[8 * L + (l)]
+    double* __restrict__ ug = P.u;
+    double* __restrict__ xg = P.x;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
+        SI(l) = id;
+        const double r = P.b[i];
+        const double u = r * id;
+        SR(l) = r;
+        SU(l) = u;
+        ug[i] = u;
+        SP(l) = 0.0;
+        SS(l) = 0.0;
+        SQ(l) = 0.0;
+        SZ(l) = 0.0;
+        xg[i] = 0.0;
+    }
+    if (P.inject_fault && blockIdx.x == G - 1) {
+        if (G == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+    double ga = 0.0, de = 0.0;
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const int len = __ldg(alen + i);
+        double acc = 0.0;
+        for (int k = 0; k < len; ++k)
+            acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + __ldg(acol + (size_t)k * ld + i));
+        const double ri = SR(l), ui = SU(l);
+        const double wi = ri + c * acc;
+        SW(l) = wi;
+        ga += ri * ui;
+        de += wi * ui;
+        P.m[i] = SI(l) * wi;
+    }
+    int it = 0, nsum = 0;
+    while (true) {
+        if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, (int)blockIdx.x, epoch,
+                               P.budget, P.err))
+            return;
+        const double* mc = P.m + (nsum & 1) * (size_t)ld;
+        auto totals = [&]() {
+            double g, d;
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        };
+        if (sp0 > 0 && t < 64) totals();
+        if (t >= sp0) {
+            for (int l = t - sp0; l < nl; l += B - sp0) {
+                const int i = r0 + l;
+                const int len = __ldg(alen + i);
+                double acc = 0.0;
+                for (int k = 0; k < len; ++k)
+                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(mc + __ldg(acol + (size_t)k * ld + i));
+                SN(l) = SW(l) + c * acc;
+            }
+        }
+        if (sp0 == 0 && t < 64) totals();
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        double* mn = P.m + (nsum & 1) * (size_t)ld;
+        ga = de = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const double mi = __ldcg(mc + i);
+            const double wi = SW(l), ui = SU(l);
+            const double zi = SN(l) + beta * SZ(l);
+            const double qi = mi + beta * SQ(l);
+            const double s_i = wi + beta * SS(l);
+            const double pi = ui + beta * SP(l);
+            SZ(l) = zi;
+            SQ(l) = qi;
+            SS(l) = s_i;
+            SP(l) = pi;
+            xg[i] += alpha * pi;
+            const double r2 = SR(l) - alpha * s_i;
+            const double u2 = ui - alpha * qi;
+            const double w2 = wi - alpha * zi;
+            SR(l) = r2;
+            SU(l) = u2;
+            SW(l) = w2;
+            ga += r2 * u2;
+            de += w2 * u2;
+            mn[i] = SI(l) * w2;
+        }
+    }
+    if (S.state == 2) {
+        if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+    }
+    // x is complete and visible: the last grid barrier followed its last update
+    if (P.epi_lo < P.epi_hi) {
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            const double xi = __ldcg(xg + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+#undef SR
+#undef SU
+#undef SW
+#undef SP
+#undef SS
+#undef SQ
+#undef SZ
+#undef SN
+#undef SI
+
+// Thread-block-cluster variant for small active sets (n <= C * L rows, one
+// cluster of C CTAs).  The same iteration as k_pcg_smem; m of other CTAs is
+// read from their shared memory (distributed shared memory, two buffers),
+// the blocks' exact partial sums are exchanged through shared memory, and the
+// hardware cluster barrier replaces the global arrival counter, so the
+// iteration loop touches no global memory besides the read-only matrix and x.
+// Every CTA takes the same decisions (same totals) and leaves only after a
+// final cluster barrier, so no CTA reads the shared memory of one that has
+// exited.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    __shared__ XsRecord crec[2];
+    __shared__ double* mr[2][16];
+    __shared__ XsRecord* pr[16];
+    const int B = blockDim.x, t = threadIdx.x;
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int L = P.L, ld = P.ld;
+    const int r0 = rank * L;
+    const int nl = max(0, min(P.n - r0, L));
+    const int sp0 = B >= 256 ? 64 : 0;
+    double* __restrict__ sr = sm;
+    double* __restrict__ su = sm + L;
+    double* __restrict__ sw = sm + 2 * L;
+    double* __restrict__ sp = sm + 3 * L;
+    double* __restrict__ ss = sm + 4 * L;
+    double* __restrict__ sq = sm + 5 * L;
+    double* __restrict__ sz = sm + 6 * L;
+    double* __restrict__ sn = sm + 7 * L;
+    double* __restrict__ si = sm + 8 * L;
+    double* const smb[2] = {sm + 9 * L, sm + 10 * L};
+    double* __restrict__ xg = P.x;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    if (t < C) {
+        mr[0][t] = cl.map_shared_rank(smb[0], t);
+        mr[1][t] = cl.map_shared_rank(smb[1], t);
+        pr[t] = cl.map_shared_rank(crec, t);
+    }
+    // the initial product A u gathers u through the second buffer
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        const double id = 1.0 / d;
+        si[l] = id;
+        const double r = P.b[i];
+        const double u = r * id;
+        sr[l] = r;
+        su[l] = u;
+        smb[1][l] = u;
+        sp[l] = 0.0;
+        ss[l] = 0.0;
+        sq[l] = 0.0;
+        sz[l] = 0.0;
+        xg[i] = 0.0;
+    }
+    cl.sync();
+    double ga = 0.0, de = 0.0;
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const int len = __ldg(alen + i);
+        double acc = 0.0;
+        for (int k = 0; k < len; ++k) {
+            const int j = __ldg(acol + (size_t)k * ld + i);
+            const int owner = j / L;
+            acc += __ldg(aval + (size_t)k * ld + i) * mr[1][owner][j - owner * L];
+        }
+        const double ri = sr[l], ui = su[l];
+        const double wi = ri + c * acc;
+        sw[l] = wi;
+        ga += ri * ui;
+        de += wi * ui;
+        smb[0][l] = si[l] * wi;
+    }
+    int it = 0, nsum = 0, buf = 0;
+    while (true) {
+        {
+            int fa, fb;
+            __int128 qa, qb;
+            xs_block_sum2(ga, de, S.xs, fa, fb, qa, qb);
+            if (t == 0) xs_store(&crec[buf], fa, fb, qa, qb);
+        }
+        cl.sync();   // m and the partial sums of every CTA are visible
+        const int cb = nsum & 1;
+        auto totals = [&]() {
+            double g, d;
+            xs_group_total(C, [&](int k) { return pr[k][buf]; }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        };
+        if (sp0 > 0 && t < 64) totals();
+        if (t >= sp0) {
+            for (int l = t - sp0; l < nl; l += B - sp0) {
+                const int i = r0 + l;
+                const int len = __ldg(alen + i);
+                double acc = 0.0;
+                for (int k = 0; k < len; ++k) {
+                    const int j = __ldg(acol + (size_t)k * ld + i);
+                    const int owner = j / L;
+                    acc += __ldg(aval + (size_t)k * ld + i) * mr[cb][owner][j - owner * L];
+                }
+                sn[l] = sw[l] + c * acc;
+            }
+        }
+        if (sp0 == 0 && t < 64) totals();
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (rank == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        const double* mcur = smb[cb];
+        double* mn = smb[cb ^ 1];
+        ga = de = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const double mi = mcur[l];
+            const double wi = sw[l], ui = su[l];
+            const double zi = sn[l] + beta * sz[l];
+            const double qi = mi + beta * sq[l];
+            const double s_i = wi + beta * ss[l];
+            const double pi = ui + beta * sp[l];
+            sz[l] = zi;
+            sq[l] = qi;
+            ss[l] = s_i;
+            sp[l] = pi;
+            xg[i] += alpha * pi;
+            const double r2 = sr[l] - alpha * s_i;
+            const double u2 = ui - alpha * qi;
+            const double w2 = wi - alpha * zi;
+            sr[l] = r2;
+            su[l] = u2;
+            sw[l] = w2;
+            ga += r2 * u2;
+            de += w2 * u2;
+            mn[l] = si[l] * w2;
+        }
+    }
+    if (S.state == 2) {
+        if (rank == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+    } else {
+        if (rank == 0 && t == 0) {
+            *P.iters_out = it;
+            *P.relres_out = cg_relres(S);
+        }
+        if (P.epi_lo < P.epi_hi) {
+            // every CTA's x is final: its last update preceded the last cluster barrier
+            for (int l = t; l < nl; l += B) {
+                const int i = r0 + l;
+                const int len = __ldg(alen + i);
+                const double xi = __ldcg(xg + i);
+                double acc = 0.0;
+                for (int k = 0; k < len; ++k)
+                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+                cg_couple_row(P, i, xi, acc);
+            }
+        }
+    }
+    cl.sync();   // nobody leaves while another CTA may still read its shared memory
+}
+
+// ---- classical arrangement (Chronopoulos and Gear, 1989) ----------------------
+// The same Jacobi-PCG with two synchronisation points per iteration and no
+// pipelining: u = D^-1 r is published, a grid barrier, then w = A u and the
+// two dot products r.u, w.u summed in one grid reduction, after which
+// s = w + beta s and p = u + beta p give the update.  Its recurrences carry
+// fewer vectors than the pipelined form, so its rounding stays close to that
+// of textbook CG over long, ill-conditioned solves (cell-by-cell systems).
+__device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int row0, int row1,
+                                           int nblk, int bidx, unsigned* bar, XsRecord* part,
+                                           int pstride, int* iters_out, double* relres_out) {
+    const int t = threadIdx.x;
     const int stride = nblk * blockDim.x;
-    const int i0 = row0 + bidx * blockDim.x + threadIdx.x;
-    const bool lead = (bidx == 0 && threadIdx.x == 0);
+    const int i0 = row0 + bidx * blockDim.x + t;
+    const bool lead = (bidx == 0 && t == 0);
     const int ld = P.ld;
     const double c = P.c;
     unsigned epoch = 0;
@@ -372,8 +806,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         return;
     }
     if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
-    int it = 0;
-    bool first = true;
+    int it = 0, nsum = 0;
     while (true) {
         // phase 2: w = A u, r.u, w.u
         double ga = 0.0, de = 0.0;
@@ -389,14 +822,17 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
             ga += ri * ui;
             de += wi * ui;
         }
-        if (!group_reduce2(ga, de, S, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
-                           P.err, [&](double g, double d) {
-                               if (first) cg_first(S, g, d, P.rtol);
-                               else cg_next(S, g, d);
-                           }))
+        if (!cg_publish_arrive(ga, de, S, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
+                               P.err))
             return;
+        if (t < 64) {
+            double g, d;
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        }
+        __syncthreads();
+        ++nsum;
         buf ^= 1;
-        first = false;
         if (S.state != 0) break;
         if (it >= P.maxit) {
             if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
@@ -438,50 +874,17 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
     }
 }
 
-__global__ void __launch_bounds__(1024, 1) k_pcg(CgParams P) {
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgc(CgParams P) {
     __shared__ CgShared S;
-    pcg_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar, P.part, 2 * (int)gridDim.x,
-              P.iters_out, P.relres_out);
+    pcgc_group(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar,
+               reinterpret_cast<XsRecord*>(P.part), (int)gridDim.x, P.iters_out, P.relres_out);
 }
 
-// Batched variant: independent solves of the instances of a batch (disjoint
-// diagonal blocks of the system) in one cooperative launch.  Block b works on
-// the group tab[b] describes: that instance's compact rows, its own barrier
-// counter and partial-sum slots, its own iteration count.  Groups never wait
-// for each other, so a converged instance's blocks leave early.
-__global__ void __launch_bounds__(1024, 1) k_pcg_batch(CgParams P, const SegBlock* __restrict__ tab,
-                                                        unsigned* __restrict__ bars,
-                                                        int* __restrict__ seg_iters,
-                                                        double* __restrict__ seg_relres) {
-    __shared__ CgShared S;
-    const SegBlock g = tab[blockIdx.x];
-    pcg_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
-              P.part + 2 * g.blk0, 2 * (int)gridDim.x, seg_iters + g.seg, seg_relres + g.seg);
-}
-
-// Compact boundaries of the batch instances in a sorted active list:
-// bounds[s] = first position p with act[p] >= inst_off[s] (lower bound).
-__global__ void k_seg_bounds(const int* __restrict__ count, const int* __restrict__ act, int nseg,
-                             const int* __restrict__ inst_off, int* __restrict__ bounds) {
-    const int sidx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (sidx > nseg) return;
-    const int n = *count;
-    const int key = inst_off[sidx];
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (act[mid] < key) lo = mid + 1; else hi = mid;
-    }
-    bounds[sidx] = lo;
-}
-
-// Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
-// block b owns the contiguous rows [b L, b L + L); their r, u, p, s, w and
-// reciprocal diagonal stay in shared memory for the whole solve.  u is
-// published to global memory (coalesced) for the neighbours' gathers and x is
-// accumulated in place in global memory; the matrix is read through the
-// read-only path.
-__global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
+// Shared-memory form of the classical arrangement (rows as in k_pcg_smem;
+// r, u, p, s, w and the reciprocal diagonal on chip, u published).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
     extern __shared__ double sm[];
     __shared__ CgShared S;
     const int G = gridDim.x, B = blockDim.x, t = threadIdx.x;
@@ -524,8 +927,8 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
         return;
     }
     if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
-    int it = 0;
-    bool first = true;
+    XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
+    int it = 0, nsum = 0;
     while (true) {
         double ga = 0.0, de = 0.0;
         for (int l = t; l < nl; l += B) {
@@ -540,14 +943,17 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
             ga += ri * ui;
             de += wi * ui;
         }
-        if (!group_reduce2(ga, de, S, P.part + buf * 2 * G, P.bar, G, (int)blockIdx.x, epoch,
-                           P.budget, P.err, [&](double g, double d) {
-                               if (first) cg_first(S, g, d, P.rtol);
-                               else cg_next(S, g, d);
-                           }))
+        if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, (int)blockIdx.x, epoch,
+                               P.budget, P.err))
             return;
+        if (t < 64) {
+            double g, d;
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        }
+        __syncthreads();
+        ++nsum;
         buf ^= 1;
-        first = false;
         if (S.state != 0) break;
         if (it >= P.maxit) {
             if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
@@ -589,148 +995,6 @@ __global__ void __launch_bounds__(1024, 1) k_pcg_smem(CgParams P) {
             cg_couple_row(P, i, xi, acc);
         }
     }
-}
-
-// Thread-block-cluster variant for small active sets (n <= C * L rows, one
-// cluster of C CTAs).  The same iteration as k_pcg_smem; u of other CTAs is
-// read from their shared memory (distributed shared memory), block totals are
-// exchanged through shared memory, and the hardware cluster barrier replaces
-// the global arrival counter, so the iteration loop touches no global memory
-// besides the (read-only) matrix and x.  Every CTA takes the same decisions
-// (same totals, same order) and leaves only after a final cluster barrier, so
-// no CTA reads the shared memory of one that has exited.
-__global__ void __launch_bounds__(1024, 1) k_pcg_cluster(CgParams P) {
-    namespace cgx = cooperative_groups;
-    cgx::cluster_group cl = cgx::this_cluster();
-    extern __shared__ double sm[];
-    __shared__ CgShared S;
-    __shared__ double cpart[4];
-    __shared__ double* ur[16];
-    __shared__ double* pr[16];
-    const int B = blockDim.x, t = threadIdx.x;
-    const int C = (int)cl.num_blocks();
-    const int rank = (int)cl.block_rank();
-    const int L = P.L, ld = P.ld;
-    const int r0 = rank * L;
-    const int nl = max(0, min(P.n - r0, L));
-    double* __restrict__ sr = sm;
-    double* __restrict__ su = sm + L;
-    double* __restrict__ sp = sm + 2 * L;
-    double* __restrict__ ss = sm + 3 * L;
-    double* __restrict__ sw = sm + 4 * L;
-    double* __restrict__ si = sm + 5 * L;
-    double* __restrict__ xg = P.x;
-    const double* __restrict__ aval = P.aval;
-    const int* __restrict__ acol = P.acol;
-    const int* __restrict__ alen = P.alen;
-    const double c = P.c;
-    if (t < C) {
-        ur[t] = cl.map_shared_rank(su, t);
-        pr[t] = cl.map_shared_rank(cpart, t);
-    }
-    int buf = 0;
-    // cluster-wide sum of two values; lane 0 of warp 0 derives the scalars
-    auto reduce2 = [&](double a, double b, auto&& on_total) {
-        double sa, sb;
-        block_sum2(a, b, S, sa, sb);
-        if (t == 0) {
-            cpart[2 * buf] = sa;
-            cpart[2 * buf + 1] = sb;
-        }
-        cl.sync();
-        if (t < 32) {
-            double ta = t < C ? pr[t][2 * buf] : 0.0;
-            double tb = t < C ? pr[t][2 * buf + 1] : 0.0;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ta += __shfl_xor_sync(0xffffffffu, ta, o);
-                tb += __shfl_xor_sync(0xffffffffu, tb, o);
-            }
-            if (t == 0) on_total(ta, tb);
-        }
-        buf ^= 1;
-        __syncthreads();
-    };
-
-    for (int l = t; l < nl; l += B) {
-        const int i = r0 + l;
-        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
-        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
-        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
-        const double id = 1.0 / d;
-        si[l] = id;
-        const double r = P.b[i];
-        sr[l] = r;
-        su[l] = r * id;
-        sp[l] = 0.0;
-        ss[l] = 0.0;
-        xg[i] = 0.0;
-    }
-    cl.sync();
-    int it = 0;
-    bool first = true;
-    while (true) {
-        double ga = 0.0, de = 0.0;
-        for (int l = t; l < nl; l += B) {
-            const int i = r0 + l;
-            const int len = __ldg(alen + i);
-            double acc = 0.0;
-            for (int k = 0; k < len; ++k) {
-                const int j = __ldg(acol + (size_t)k * ld + i);
-                const int owner = j / L;
-                acc += __ldg(aval + (size_t)k * ld + i) * ur[owner][j - owner * L];
-            }
-            const double ri = sr[l], ui = su[l];
-            const double wi = ri + c * acc;
-            sw[l] = wi;
-            ga += ri * ui;
-            de += wi * ui;
-        }
-        reduce2(ga, de, [&](double g, double d) {
-            if (first) cg_first(S, g, d, P.rtol);
-            else cg_next(S, g, d);
-        });
-        first = false;
-        if (S.state != 0) break;
-        if (it >= P.maxit) {
-            if (rank == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
-            break;
-        }
-        ++it;
-        const double alpha = S.alpha, beta = S.beta;
-        for (int l = t; l < nl; l += B) {
-            const double pi = su[l] + beta * sp[l];
-            const double s_i = sw[l] + beta * ss[l];
-            sp[l] = pi;
-            ss[l] = s_i;
-            xg[r0 + l] += alpha * pi;
-            const double r = sr[l] - alpha * s_i;
-            sr[l] = r;
-            su[l] = r * si[l];
-        }
-        cl.sync();   // u of every CTA is final before the gathers
-    }
-    if (S.state == 2) {
-        if (rank == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
-    } else {
-        if (rank == 0 && t == 0) {
-            *P.iters_out = it;
-            *P.relres_out = cg_relres(S);
-        }
-        if (P.epi_lo < P.epi_hi) {
-            cl.sync();   // every CTA's x is final (cluster-scope ordering covers global memory)
-            for (int l = t; l < nl; l += B) {
-                const int i = r0 + l;
-                const int len = __ldg(alen + i);
-                const double xi = __ldcg(xg + i);
-                double acc = 0.0;
-                for (int k = 0; k < len; ++k)
-                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
-                cg_couple_row(P, i, xi, acc);
-            }
-        }
-    }
-    cl.sync();   // nobody leaves while another CTA may still read its shared memory
 }
 
 template <int M>
@@ -949,23 +1213,58 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
 
 int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
 
+using PcgKernel = void (*)(CgParams);
+using PcgBatchKernel = void (*)(CgParams, const SegBlock*, unsigned*, int*, double*);
+
+// instantiation for a block size: the register budget follows the largest block
+PcgKernel pcg_general_kernel(int block) {
+    return block > 512 ? k_pcg<1024> : block > 256 ? k_pcg<512> : k_pcg<256>;
+}
+PcgKernel pcg_smem_kernel(int block) { return block > 512 ? k_pcg_smem<1024> : k_pcg_smem<512>; }
+PcgKernel pcg_cluster_kernel(int block) {
+    return block > 512 ? k_pcg_cluster<1024> : k_pcg_cluster<512>;
+}
+PcgKernel pcgc_general_kernel(int block) {
+    return block > 512 ? k_pcgc<1024> : block > 256 ? k_pcgc<512> : k_pcgc<256>;
+}
+PcgKernel pcgc_smem_kernel(int block) { return block > 512 ? k_pcgc_smem<1024> : k_pcgc_smem<512>; }
+PcgBatchKernel pcg_batch_kernel(int block) {
+    return block > 512 ? k_pcg_batch<1024> : block > 256 ? k_pcg_batch<512> : k_pcg_batch<256>;
+}
+
+// opt-in dynamic shared memory of the on-chip variants (set once per instantiation)
+void pcg_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    for (PcgKernel k : {k_pcg_smem<512>, k_pcg_smem<1024>})
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemVectors * kSmemRows * sizeof(double)));
+    for (PcgKernel k : {k_pcgc_smem<512>, k_pcgc_smem<1024>})
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemVectorsC * kSmemRowsC * sizeof(double)));
+    for (PcgKernel k : {k_pcg_cluster<512>, k_pcg_cluster<1024>}) {
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kClusterVectors * kClusterRows * sizeof(double)));
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    done = true;
+}
+
 int pcg_max_blocks(int block) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_general_kernel(block), block, 0);
     return sms * per;
 }
 
 int pcg_cluster_size(int block) {
-    cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(6 * kSmemRows * sizeof(double)));
-    cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    pcg_smem_attrs();
     for (int C = 16; C >= 2; C /= 2) {
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(C);
         lc.blockDim = dim3(block);
-        lc.dynamicSmemBytes = (size_t)6 * kSmemRows * sizeof(double);
+        lc.dynamicSmemBytes = (size_t)kClusterVectors * kClusterRows * sizeof(double);
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
         at[0].val.clusterDim.x = C;
@@ -974,7 +1273,8 @@ int pcg_cluster_size(int block) {
         lc.attrs = at;
         lc.numAttrs = 1;
         int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_pcg_cluster, &lc) == cudaSuccess &&
+        if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)pcg_cluster_kernel(block), &lc) ==
+                cudaSuccess &&
             nclusters >= 1)
             return C;
         cudaGetLastError();
@@ -987,6 +1287,21 @@ int pcg_sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms;
+}
+
+// CG vectors of a context's step buffers
+void set_cg_vectors(CgParams& P, StepBuffers& B) {
+    P.r = B.r;
+    P.u = B.u;
+    P.w = B.w;
+    P.p = B.p;
+    P.s = B.s;
+    P.q = B.q;
+    P.z = B.z;
+    P.nv = B.nv;
+    P.m = B.m;
+    P.idA = B.idA;
+    P.part = B.part;
 }
 
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
@@ -1003,13 +1318,7 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.c = dt * co.Qh[m * kMaxM + m];
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
-    P.r = B.r;
-    P.u = B.u;
-    P.p = B.p;
-    P.s = B.s;
-    P.w = B.w;
-    P.idA = B.idA;
-    P.part = B.part;
+    set_cg_vectors(P, B);
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -1017,7 +1326,7 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.budget = cfg.budget;
     P.iters_out = &B.sc->cg_iters[sweep * kMaxM + m];
     P.relres_out = &B.sc->cg_relres[sweep * kMaxM + m];
-    P.m = m;
+    P.m_node = m;
     P.M = co.M;
     P.epi_lo = m + 1;
     P.epi_hi = co.M;
@@ -1045,13 +1354,7 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
     P.c = role.c;
     P.b = role.b;
     P.x = role.x;
-    P.r = B.r;
-    P.u = B.u;
-    P.p = B.p;
-    P.s = B.s;
-    P.w = B.w;
-    P.idA = B.idA;
-    P.part = B.part;
+    set_cg_vectors(P, B);
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -1059,7 +1362,7 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
     P.budget = cfg.budget;
     P.iters_out = role.iters_out;
     P.relres_out = role.relres_out;
-    P.m = 0;
+    P.m_node = 0;
     P.M = M;
     P.epi_lo = role.epi_lo;
     P.epi_hi = role.epi_hi;
@@ -1077,26 +1380,45 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
 
 int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
     const int n = P.n;
+    // the exact-sum records are read with 16-byte loads
+    if (reinterpret_cast<uintptr_t>(P.part) % 16 != 0) return SDC_E_INVALID;
     cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
     void* args[] = {&P};
+    if (!cfg.pipelined) {
+        // classical arrangement: shared-memory form when it fits, else global vectors
+        if (cfg.variant != 1 && n <= cfg.sms * kSmemRowsC) {
+            const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+            int grid = std::max(nblk(n, kSmemRowsC), nblk(n, rpb));
+            grid = std::min(grid, cfg.sms);
+            if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
+            grid = std::max(std::max(grid, nblk(n, kSmemRowsC)), 1);
+            P.L = nblk(n, grid);
+            const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
+            pcg_smem_attrs();
+            cudaError_t e = cudaLaunchCooperativeKernel(
+                (const void*)pcgc_smem_kernel(blk), dim3(grid), dim3(blk), args,
+                (size_t)kSmemVectorsC * P.L * sizeof(double), s);
+            return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+        }
+        int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));
+        if (grid < 1) grid = 1;
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcgc_general_kernel(cfg.block),
+                                                    dim3(grid), dim3(cfg.block), args, 0, s);
+        return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+    }
     // cluster variant: one cluster of cfg.cluster CTAs for small active sets
     if (cfg.variant != 1 && cfg.cluster > 0 && !cfg.inject_fault && n <= cfg.cluster_rows &&
-        n <= cfg.cluster * kSmemRows) {
-        static bool cattr_set = false;
-        if (!cattr_set) {
-            cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(6 * kSmemRows * sizeof(double)));
-            cudaFuncSetAttribute(k_pcg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            cattr_set = true;
-        }
+        n <= cfg.cluster * kClusterRows) {
+        pcg_smem_attrs();
         // enough CTAs for the FP64 work, never more rows per CTA than fit
-        int C = std::min(cfg.cluster, std::max(nblk(n, cfg.cluster_rows_per_cta), nblk(n, kSmemRows)));
+        int C = std::min(cfg.cluster,
+                         std::max(nblk(n, cfg.cluster_rows_per_cta), nblk(n, kClusterRows)));
         C = std::max(C, 1);
         P.L = nblk(n, C);
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(C);
         lc.blockDim = dim3(cfg.smem_block);
-        lc.dynamicSmemBytes = (size_t)6 * P.L * sizeof(double);
+        lc.dynamicSmemBytes = (size_t)kClusterVectors * P.L * sizeof(double);
         lc.stream = s;
         cudaLaunchAttribute at[1];
         at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1105,7 +1427,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         at[0].val.clusterDim.z = 1;
         lc.attrs = at;
         lc.numAttrs = 1;
-        cudaError_t e = cudaLaunchKernelEx(&lc, k_pcg_cluster, P);
+        cudaError_t e = cudaLaunchKernelEx(&lc, pcg_cluster_kernel(cfg.smem_block), P);
         return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
     }
     // shared-memory variant: one block per SM at most, each owning <= kSmemRows rows
@@ -1118,23 +1440,19 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         grid = std::max(grid, nblk(n, kSmemRows));
         grid = std::max(grid, 1);
         P.L = nblk(n, grid);
-        const size_t smem = (size_t)6 * P.L * sizeof(double);
+        const size_t smem = (size_t)kSmemVectors * P.L * sizeof(double);
         // the largest systems keep every SM's FP64 pipe busy with 32 warps;
         // smaller ones favour shorter block-level reductions
         const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_pcg_smem, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(6 * kSmemRows * sizeof(double)));
-            attr_set = true;
-        }
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_smem, dim3(grid),
+        pcg_smem_attrs();
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_smem_kernel(blk), dim3(grid),
                                                     dim3(blk), args, smem, s);
         return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
     }
     int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));
     if (grid < 1) grid = 1;
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(cfg.block),
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_general_kernel(cfg.block), dim3(grid),
+                                                dim3(cfg.block),
                                                 args, 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
@@ -1143,7 +1461,7 @@ int pcg_batch_max_blocks(int block) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_batch, block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_batch_kernel(block), block, 0);
     return sms * per;
 }
 
@@ -1181,13 +1499,7 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.c = dt * co.Qh[m * kMaxM + m];
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
-    P.r = B.r;
-    P.u = B.u;
-    P.p = B.p;
-    P.s = B.s;
-    P.w = B.w;
-    P.idA = B.idA;
-    P.part = B.part;
+    set_cg_vectors(P, B);
     P.bar = nullptr;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -1195,7 +1507,7 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.budget = cfg.budget;
     P.iters_out = nullptr;
     P.relres_out = nullptr;
-    P.m = m;
+    P.m_node = m;
     P.M = co.M;
     P.epi_lo = m + 1;
     P.epi_hi = co.M;
@@ -1228,7 +1540,8 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
             return SDC_E_CUDA;
         const SegBlock* dtab = reinterpret_cast<const SegBlock*>(B.segtab);
         void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3((int)tab.size()),
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_batch_kernel(cfg.block),
+                                                    dim3((int)tab.size()),
                                                     dim3(cfg.block), args, 0, s);
         if (e != cudaSuccess) return SDC_E_CUDA;
     }
@@ -1253,9 +1566,13 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.x = x;
     P.r = w.r;
     P.u = w.u;
+    P.w = w.w;
     P.p = w.p;
     P.s = w.s;
-    P.w = w.w;
+    P.q = w.q;
+    P.z = w.z;
+    P.nv = w.nv;
+    P.m = w.m;
     P.idA = w.idA;
     P.part = w.part;
     P.bar = w.bar;
@@ -1265,7 +1582,7 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.budget = budget;
     P.iters_out = w.iters;
     P.relres_out = w.relres;
-    P.m = 0;
+    P.m_node = 0;
     P.M = 1;            // no coupling into other nodes
     P.epi_lo = 0;
     P.epi_hi = 0;
@@ -1276,10 +1593,12 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = 0.0;
     P.inject_fault = 0;
     P.L = 0;
+    if (reinterpret_cast<uintptr_t>(w.part) % 16 != 0) return SDC_E_INVALID;
     int grid = std::min(std::min(w.max_blocks, pcg_max_blocks(block)), nblk(n, block));
     if (grid < 1) grid = 1;
     void* args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_pcg, dim3(grid), dim3(block), args,
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_general_kernel(block), dim3(grid),
+                                                dim3(block), args,
                                                 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }

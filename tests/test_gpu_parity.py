@@ -60,10 +60,14 @@ def _compare_step(ctx, S, wl, v, w, t, sweeps, tol, torch, dev, cg_rtol=None, no
         ctx.nodes(Vg, Wg)
         assert _relmax(Vg.cpu().numpy(), r["V"]) <= RTOL
         assert _relmax(Wg.cpu().numpy(), r["W"]) <= RTOL
-    # CG iteration counts agree (a tie at the stopping test may shift one by 1)
+    # CG iteration counts agree (a tie at the stopping test may shift one by 1).
+    # On systems with fewer rows than a few iterations CG terminates at the
+    # rounding floor, where the pipelined recurrences may take an extra step
+    # or two before their residual estimate passes the test.
     for k in range(sweeps):
         for m in range(wl.M):
-            assert abs(st.cg_iters[k][m] - r["stats"].cg_iters[k * 8 + m]) <= 1
+            a, b = st.cg_iters[k][m], r["stats"].cg_iters[k * 8 + m]
+            assert abs(a - b) <= 1 or wl.n <= 2 * max(a, b), (k, m, a, b)
     return r, st
 
 
@@ -108,12 +112,15 @@ def test_assembly_matches_oracle(torch_dev, case):
 
 
 # ------------------------------------------------------------------ step parity
-@pytest.mark.parametrize("variant,cluster", [(1, 0), (2, 0), (0, 1 << 30)])
+@pytest.mark.parametrize("variant,cluster,pipe", [(1, 0, 1), (2, 0, 1), (0, 1 << 30, 1),
+                                                   (1, 0, 0), (2, 0, 0)])
 @pytest.mark.parametrize("tol", [0.0, 1e-4])
-def test_step_parity_2d_square(torch_dev, tol, variant, cluster):
+def test_step_parity_2d_square(torch_dev, tol, variant, cluster, pipe):
+    """Pipelined (pipe = 1) and classical (pipe = 0) arrangements of the CG in
+    every variant it has."""
     torch, dev = torch_dev
     wl = W.w0_square()
-    ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_cluster_rows=cluster)
+    ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_cluster_rows=cluster, cg_pipelined=pipe)
     S = oracle.System.from_mesh(wl.mesh, wl.sigma)
     v, w = wl.v0.copy(), wl.w0.copy()
     for n in range(12):
@@ -124,16 +131,18 @@ def test_step_parity_2d_square(torch_dev, tol, variant, cluster):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant,rows,cluster", [(1, 0, 0), (2, 0, 0), (2, 64, 0), (2, 4096, 0),
-                                                   (2, 0, 1 << 30)])
-def test_step_parity_3d_slab_with_stimulus(torch_dev, variant, rows, cluster):
+@pytest.mark.parametrize("variant,rows,cluster,pipe", [(1, 0, 0, 1), (2, 0, 0, 1), (2, 64, 0, 1),
+                                                        (2, 4096, 0, 1), (2, 0, 1 << 30, 1),
+                                                        (1, 0, 0, 0), (2, 64, 0, 0)])
+def test_step_parity_3d_slab_with_stimulus(torch_dev, variant, rows, cluster, pipe):
     """Every CG variant: global vectors; per-block shared memory with 64 rows
     per block (many blocks, tiny chunks) and with 4096 rows per block (fewest
-    blocks); and one thread-block cluster for every solve."""
+    blocks); one thread-block cluster for every solve; pipelined (pipe = 1)
+    and classical (pipe = 0) arrangements."""
     torch, dev = torch_dev
     wl = _small_slab()
     ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_rows_per_block=rows,
-               cg_cluster_rows=cluster)
+               cg_cluster_rows=cluster, cg_pipelined=pipe)
     S = oracle.System.from_mesh(wl.mesh, wl.sigma)
     v, w = wl.v0.copy(), wl.w0.copy()
     for n in range(24):   # stimulus on for the first 20 steps, then off
