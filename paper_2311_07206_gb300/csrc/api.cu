@@ -112,7 +112,7 @@ int alloc_buffers(sdc_ctx* c) {
               dalloc(&B.R, ld * M) && dalloc(&B.J, ld * M) && dalloc(&B.D, ld * M) &&
               dalloc(&B.mc, ld) && dalloc(&B.kdc, ld) && dalloc(&B.r, ld) && dalloc(&B.u, ld) &&
               dalloc(&B.p, ld) && dalloc(&B.s, ld) && dalloc(&B.w, ld) && dalloc(&B.idA, ld) &&
-              dalloc(&B.q, ld) && dalloc(&B.z, ld) && dalloc(&B.nv, ld) && dalloc(&B.m, 2 * ld) &&
+              dalloc(&B.z, ld) && dalloc(&B.nv, ld) && dalloc(&B.m, 2 * ld) &&
               dalloc(&B.flag, ld) &&
               dalloc(&B.map, ld) && dalloc(&B.blockcnt, nbu) && dalloc(&B.blockoff, nbu) &&
               dalloc(&B.blockmarg, nbu) && dalloc(&B.sc, 1) && dalloc(&B.vtmp, N) &&
@@ -152,7 +152,7 @@ void free_adjoint(AdjointBuffers& W);
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
     double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.u, B.p, B.s, B.w, B.idA, B.part,
-                    B.q, B.z, B.nv, B.m,
+                    B.z, B.nv, B.m,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
     int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff, B.inst_off, B.bounds, B.segtab,
@@ -839,9 +839,9 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     cudaStream_t s = (cudaStream_t)stream;
     const int block = 256;
     const int maxb = pcg_max_blocks(block);
-    // workspace: 11 vectors, 12 * maxb for the partial-sum records (16-byte aligned:
+    // workspace: 10 vectors, 12 * maxb for the partial-sum records (16-byte aligned:
     // they are read with 16-byte loads), then the scalars
-    const size_t po = ((size_t)11 * n + 1) & ~(size_t)1;
+    const size_t po = ((size_t)10 * n + 1) & ~(size_t)1;
     const size_t nd = po + 12 * (size_t)maxb + 2;
     char* ws = nullptr;
     if (cudaMalloc(&ws, nd * sizeof(double) + 64) != cudaSuccess)
@@ -849,8 +849,8 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     double* v = (double*)ws;
     PcgScratch w;
     w.r = v; w.u = v + n; w.p = v + 2 * (size_t)n; w.s = v + 3 * (size_t)n;
-    w.w = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n; w.q = v + 6 * (size_t)n;
-    w.z = v + 7 * (size_t)n; w.nv = v + 8 * (size_t)n; w.m = v + 9 * (size_t)n;
+    w.w = v + 4 * (size_t)n; w.idA = v + 5 * (size_t)n;
+    w.z = v + 6 * (size_t)n; w.nv = v + 7 * (size_t)n; w.m = v + 8 * (size_t)n;
     w.part = v + po;
     w.max_blocks = maxb;
     w.relres = v + po + 12 * (size_t)maxb;

@@ -5,12 +5,12 @@
 // every byte of device memory through its own pool and forbids raw cudaMalloc
 // (it would bypass the pool's budget or fragment it), and time-critical loops
 // in which cudaMalloc/cudaFree may block or synchronise the device.  They pass
-// inputs and outputs as usual; the solver's workspace (eleven vectors, per-block
+// inputs and outputs as usual; the solver's workspace (ten vectors, per-block
 // partial sums, the barrier counter and status words) lives in the file-scope
 // array below instead of a per-call allocation.
 //
 // Costs and limits of that choice:
-//   * every GPU that loads the library reserves the array (about 6.2 MB) until
+//   * every GPU that loads the library reserves the array (about 5.6 MB) until
 //     the process exits;
 //   * n is limited to SDC_PCG_NOALLOC_MAX_ROWS rows;
 //   * all calls on a device share the one array and it keeps the last call's
@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kMaxRows = SDC_PCG_NOALLOC_MAX_ROWS;
 constexpr int kMaxBlocks = 4096;   // blocks with partial-sum records (48 bytes, two buffers)
-constexpr size_t kVecDoubles = 11 * (size_t)kMaxRows;
+constexpr size_t kVecDoubles = 10 * (size_t)kMaxRows;
 constexpr size_t kScalarDoubles = 4;   // relres, then barrier counter, error, iterations
 constexpr size_t kScratchDoubles = kVecDoubles + 12 * (size_t)kMaxBlocks + kScalarDoubles;
 
@@ -94,10 +94,9 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
     w.s = base + 3 * (size_t)n;
     w.w = base + 4 * (size_t)n;
     w.idA = base + 5 * (size_t)n;
-    w.q = base + 6 * (size_t)n;
-    w.z = base + 7 * (size_t)n;
-    w.nv = base + 8 * (size_t)n;
-    w.m = base + 9 * (size_t)n;
+    w.z = base + 6 * (size_t)n;
+    w.nv = base + 7 * (size_t)n;
+    w.m = base + 8 * (size_t)n;
     w.part = base + kVecDoubles;
     w.max_blocks = kMaxBlocks;
     w.relres = base + kVecDoubles + 12 * (size_t)kMaxBlocks;

@@ -92,11 +92,10 @@ struct StepBuffers {
     double* mc = nullptr;     // [ld] lumped mass of the active rows
     double* kdc = nullptr;    // [ld] K_ii of the active rows
     double* r = nullptr;      // CG vectors [ld]: residual, u = D^-1 r, w = A u, direction p,
-    double* u = nullptr;      // s = A p, q = D^-1 s, z = A q, nv = A m, reciprocal diagonal;
+    double* u = nullptr;      // s = A p, z = A D^-1 s, nv = A m, reciprocal diagonal;
     double* p = nullptr;      // m = D^-1 w [2 ld] (two buffers)
     double* s = nullptr;
     double* w = nullptr;
-    double* q = nullptr;
     double* z = nullptr;
     double* nv = nullptr;
     double* m = nullptr;
@@ -133,10 +132,10 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const double* W, const double* v0, double dt, const Ionic& ion,
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
 // Launch configuration of the restricted PCG solves.
-constexpr int kSmemVectors = 9;     // per-row doubles in shared memory, shared-memory variant
-constexpr int kSmemRows = 3200;     // rows per block of the shared-memory variant
-constexpr int kClusterVectors = 11; // per-row doubles in shared memory, cluster variant
-constexpr int kClusterRows = 2592;  // rows per CTA of the cluster variant
+constexpr int kSmemVectors = 8;     // per-row doubles in shared memory, shared-memory variant
+constexpr int kSmemRows = 3584;     // rows per block of the shared-memory variant
+constexpr int kClusterVectors = 10; // per-row doubles in shared memory, cluster variant
+constexpr int kClusterRows = 2848;  // rows per CTA of the cluster variant
 constexpr int kSmemVectorsC = 6;    // classical arrangement, shared-memory form
 constexpr int kSmemRowsC = 4768;
 struct PcgConfig {
@@ -231,11 +230,11 @@ void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, 
 void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
-// r, u, w, p, s, q, z, nv, idA: n doubles each; m: 2 n doubles;
+// r, u, w, p, s, z, nv, idA: n doubles each; m: 2 n doubles;
 // part: 12 * max_blocks doubles (16-byte aligned);
 // bar, err, iters, relres: one value each, bar and err zero before the launch.
 struct PcgScratch {
-    double *r, *u, *w, *p, *s, *q, *z, *nv, *m, *idA, *part;
+    double *r, *u, *w, *p, *s, *z, *nv, *m, *idA, *part;
     int max_blocks;
     unsigned* bar;
     int* err;

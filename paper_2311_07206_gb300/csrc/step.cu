@@ -120,13 +120,12 @@ struct CgParams {
     double* x;           // correction of this node (output)
     // CG vectors of the global-vector variant (the shared-memory variants keep
     // their rows on chip): residual r, u = D^-1 r, w = A u, the recurrences
-    // p, s = A p, q = D^-1 s, z = A q, and nv = A m
+    // p, s = A p, z = A D^-1 s, and nv = A m
     double* r;
     double* u;           // also: u published for the initial product A u
     double* w;
     double* p;
     double* s;
-    double* q;
     double* z;
     double* nv;
     double* m;           // m = D^-1 w, published for the neighbours' gathers, two buffers of ld
@@ -251,9 +250,10 @@ __device__ __forceinline__ bool cg_publish_arrive(double a, double b, CgShared& 
 // and completes the sums: after it, warps 0 and 1 add the blocks' exact
 // partial sums and derive alpha and beta while the other warps form n = A m.
 // Per iteration:
-//   U+L (local): z = n + beta z, q = m + beta q, s = w + beta s,
-//                p = u + beta p, x += alpha p, r -= alpha s, u -= alpha q,
-//                w -= alpha z; then r.u, w.u and m = D^-1 w (published)
+//   U+L (local): z = n + beta z, s = w + beta s, p = u + beta p,
+//                x += alpha p, r -= alpha s, w -= alpha z, then u = D^-1 r
+//                and m = D^-1 w directly (not by recurrence: exact relations
+//                that keep u consistent with r), r.u, w.u; m is published
 //   sync:        exact block sums, group barrier
 //   S (overlap): n = A m (the diagonal part of A m is D m = w)  ||  totals,
 //                convergence test on r.u, beta and alpha
@@ -292,7 +292,6 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         P.u[i] = r * id;
         P.p[i] = 0.0;
         P.s[i] = 0.0;
-        P.q[i] = 0.0;
         P.z[i] = 0.0;
         P.x[i] = 0.0;
     }
@@ -351,26 +350,24 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         double* mn = mbuf[nsum & 1];
         ga = de = 0.0;
         for (int i = c0 + t; i < c1; i += B) {
-            const double mi = __ldcg(mc + i);
+            const double id = P.idA[i];
             const double wi = P.w[i], ui = P.u[i];
             const double zi = P.nv[i] + beta * P.z[i];
-            const double qi = mi + beta * P.q[i];
             const double si = wi + beta * P.s[i];
             const double pi = ui + beta * P.p[i];
             P.z[i] = zi;
-            P.q[i] = qi;
             P.s[i] = si;
             P.p[i] = pi;
             P.x[i] += alpha * pi;
             const double r2 = P.r[i] - alpha * si;
-            const double u2 = ui - alpha * qi;
             const double w2 = wi - alpha * zi;
+            const double u2 = id * r2;
             P.r[i] = r2;
             P.u[i] = u2;
             P.w[i] = w2;
             ga += r2 * u2;
             de += w2 * u2;
-            mn[i] = P.idA[i] * w2;
+            mn[i] = id * w2;
         }
     }
     if (S.state == 2) {
@@ -435,8 +432,8 @@ __global__ void k_seg_bounds(const int* __restrict__ count, const int* __restric
 }
 
 // Shared-memory variant of the same iteration for n <= gridDim.x * L rows:
-// block b owns the contiguous rows [b L, b L + L); their r, u, w, p, s, q, z,
-// n and reciprocal diagonal stay in shared memory for the whole solve.  m is
+// block b owns the contiguous rows [b L, b L + L); their r, u, w, p, s, z, n
+// and reciprocal diagonal stay in shared memory for the whole solve.  m is
 // published to global memory (coalesced, two buffers) for the neighbours'
 // gathers and x is accumulated in place in global memory; the matrix is read
 // through the read-only path.
@@ -455,10 +452,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
 #define SW(l) sm[2 * L + (l)]
 #define SP(l) sm[3 * L + (l)]
 #define SS(l) sm[4 * L + (l)]
-#define SQ(l) sm[5 * L + (l)]
-#define SZ(l) sm[6 * L + (l)]
-#define SN(l) sm[7 * L + (l)]
-#define SI(l) sm[8 * L + (l)]
+#define SZ(l) sm[5 * L + (l)]
+#define SN(l) sm[6 * L + (l)]
+#define SI(l) sm[7 * L + (l)]
     double* __restrict__ ug = P.u;
     double* __restrict__ xg = P.x;
     const double* __restrict__ aval = P.aval;
@@ -483,7 +479,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
         ug[i] = u;
         SP(l) = 0.0;
         SS(l) = 0.0;
-        SQ(l) = 0.0;
         SZ(l) = 0.0;
         xg[i] = 0.0;
     }
@@ -543,26 +538,24 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
         ga = de = 0.0;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
-            const double mi = __ldcg(mc + i);
+            const double id = SI(l);
             const double wi = SW(l), ui = SU(l);
             const double zi = SN(l) + beta * SZ(l);
-            const double qi = mi + beta * SQ(l);
             const double s_i = wi + beta * SS(l);
             const double pi = ui + beta * SP(l);
             SZ(l) = zi;
-            SQ(l) = qi;
             SS(l) = s_i;
             SP(l) = pi;
             xg[i] += alpha * pi;
             const double r2 = SR(l) - alpha * s_i;
-            const double u2 = ui - alpha * qi;
             const double w2 = wi - alpha * zi;
+            const double u2 = id * r2;
             SR(l) = r2;
             SU(l) = u2;
             SW(l) = w2;
             ga += r2 * u2;
             de += w2 * u2;
-            mn[i] = SI(l) * w2;
+            mn[i] = id * w2;
         }
     }
     if (S.state == 2) {
@@ -591,7 +584,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
 #undef SW
 #undef SP
 #undef SS
-#undef SQ
 #undef SZ
 #undef SN
 #undef SI
@@ -626,11 +618,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
     double* __restrict__ sw = sm + 2 * L;
     double* __restrict__ sp = sm + 3 * L;
     double* __restrict__ ss = sm + 4 * L;
-    double* __restrict__ sq = sm + 5 * L;
-    double* __restrict__ sz = sm + 6 * L;
-    double* __restrict__ sn = sm + 7 * L;
-    double* __restrict__ si = sm + 8 * L;
-    double* const smb[2] = {sm + 9 * L, sm + 10 * L};
+    double* __restrict__ sz = sm + 5 * L;
+    double* __restrict__ sn = sm + 6 * L;
+    double* __restrict__ si = sm + 7 * L;
+    double* const smb[2] = {sm + 8 * L, sm + 9 * L};
     double* __restrict__ xg = P.x;
     const double* __restrict__ aval = P.aval;
     const int* __restrict__ acol = P.acol;
@@ -656,7 +647,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
         smb[1][l] = u;
         sp[l] = 0.0;
         ss[l] = 0.0;
-        sq[l] = 0.0;
         sz[l] = 0.0;
         xg[i] = 0.0;
     }
@@ -718,31 +708,28 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
         }
         ++it;
         const double alpha = S.alpha, beta = S.beta;
-        const double* mcur = smb[cb];
         double* mn = smb[cb ^ 1];
         ga = de = 0.0;
         for (int l = t; l < nl; l += B) {
             const int i = r0 + l;
-            const double mi = mcur[l];
+            const double id = si[l];
             const double wi = sw[l], ui = su[l];
             const double zi = sn[l] + beta * sz[l];
-            const double qi = mi + beta * sq[l];
             const double s_i = wi + beta * ss[l];
             const double pi = ui + beta * sp[l];
             sz[l] = zi;
-            sq[l] = qi;
             ss[l] = s_i;
             sp[l] = pi;
             xg[i] += alpha * pi;
             const double r2 = sr[l] - alpha * s_i;
-            const double u2 = ui - alpha * qi;
             const double w2 = wi - alpha * zi;
+            const double u2 = id * r2;
             sr[l] = r2;
             su[l] = u2;
             sw[l] = w2;
             ga += r2 * u2;
             de += w2 * u2;
-            mn[l] = si[l] * w2;
+            mn[l] = id * w2;
         }
     }
     if (S.state == 2) {
@@ -1296,7 +1283,6 @@ void set_cg_vectors(CgParams& P, StepBuffers& B) {
     P.w = B.w;
     P.p = B.p;
     P.s = B.s;
-    P.q = B.q;
     P.z = B.z;
     P.nv = B.nv;
     P.m = B.m;
@@ -1569,7 +1555,6 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.w = w.w;
     P.p = w.p;
     P.s = w.s;
-    P.q = w.q;
     P.z = w.z;
     P.nv = w.nv;
     P.m = w.m;
