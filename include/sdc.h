@@ -100,7 +100,7 @@ typedef struct {
                               stored; default 1e-12, 0 keeps every structural entry           */
     long long spin_budget; /* SM clock cycles a device-side barrier may wait; default 4e9     */
     int cg_block_size;     /* threads per block of the global-vector CG (64..1024, multiple
-                              of 32); default 256                                             */
+                              of 32); default 1024.  Batches use min(this, 256)               */
     int cg_smem_block_size;/* threads per block of the shared-memory and cluster CG; default 512 */
     int cg_cluster_max;    /* largest cluster (CTAs) for the cluster CG, 1..16; default 16      */
     int cg_max_blocks;     /* 0: no limit on the cooperative CG grid                          */

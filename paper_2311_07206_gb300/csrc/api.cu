@@ -127,7 +127,8 @@ int alloc_buffers(sdc_ctx* c) {
     if (ok && !c->inst_off.empty()) {
         const int nseg = (int)c->inst_off.size() - 1;
         B.nseg = nseg;
-        P.max_blocks_batch = pcg_batch_max_blocks(P.block);
+        P.batch_block = std::min(P.block, 256);
+        P.max_blocks_batch = pcg_batch_max_blocks(P.batch_block);
         if (c->opt.cg_max_blocks > 0)
             P.max_blocks_batch = std::min(P.max_blocks_batch, c->opt.cg_max_blocks);
         B.max_blocks = std::max(B.max_blocks, P.max_blocks_batch);
@@ -234,7 +235,7 @@ void sdc_default_options(sdc_options* o) {
     o->w_frozen = 0;
     o->drop_rel = 1e-12;
     o->spin_budget = 4000000000LL;
-    o->cg_block_size = 256;
+    o->cg_block_size = 1024;
     o->cg_smem_block_size = 512;
     o->cg_cluster_max = 16;
     o->cg_max_blocks = 0;

@@ -1526,9 +1526,9 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
             return SDC_E_CUDA;
         const SegBlock* dtab = reinterpret_cast<const SegBlock*>(B.segtab);
         void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_batch_kernel(cfg.block),
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_batch_kernel(cfg.batch_block),
                                                     dim3((int)tab.size()),
-                                                    dim3(cfg.block), args, 0, s);
+                                                    dim3(cfg.batch_block), args, 0, s);
         if (e != cudaSuccess) return SDC_E_CUDA;
     }
     return SDC_OK;

@@ -44,7 +44,7 @@ def test_default_options(lib):
     from paper_2311_07206_gb300 import default_options
     o = default_options()
     assert o.alpha == 0.1 and o.cg_rtol == 1e-10 and o.reaction_implicit == 1
-    assert o.w_frozen == 0 and o.inject_fault == 0 and o.cg_block_size == 256
+    assert o.w_frozen == 0 and o.inject_fault == 0 and o.cg_block_size == 1024
     assert o.cg_pipelined == -1
 
 
