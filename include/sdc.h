@@ -120,6 +120,14 @@ typedef struct {
                               automatic: pipelined for monodomain contexts, classical for
                               cell-by-cell contexts, whose long ill-conditioned solves need its
                               smaller rounding error; default -1.  Batches are pipelined.      */
+    int energy_stop;       /* 1: end the sweeps of a step once the energy norm of the sweep's
+                              corrections, E_k = sum_m dv_m' A~_m dv_m with A~_m the node system
+                              matrix, is at most ((1 - rho) / rho * TOL)^2 (Sec. 3.2); `sweeps`
+                              is then the largest number of sweeps.  Monodomain contexts, not
+                              with a tape or in a batch; default 0                            */
+    double sdc_rho;        /* SDC contraction rho for energy_stop, in [0, 1); 0: estimated after
+                              each sweep as sqrt(E_k / E_{k-1}) (so no stop after the first
+                              sweep); default 0                                               */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */
@@ -135,6 +143,8 @@ typedef struct {
     int phase_launches[SDC_N_PHASES];
     double phase_ms[SDC_N_PHASES];
     double cg_ms[SDC_MAX_SWEEPS][SDC_MAX_M];  /* device ms per node solve (profile option) */
+    double energy[SDC_MAX_SWEEPS];         /* E_k = sum_m dv_m' A~_m dv_m of sweep k, from the CG
+                                              scalars (sum of alpha gamma over each solve)    */
 } sdc_stats;
 
 /* Fill defaults (values above). */

@@ -419,7 +419,14 @@ double krow(const Csr& K, int i, const double* x) {
 extern "C" {
 
 typedef struct { double ga, gs, a, eps, mu1, mu2, cw; } ora_ionic;
-typedef struct { double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen; } ora_opts;
+// energy_stop: end the sweeps once the energy norm of the sweep's corrections,
+// sum over the nodes of dv_m' A~_m dv_m (A~_m the node system matrix), is at most
+// ((1 - rho) / rho * TOL)^2 (Sec. 3.2); rho > 0 is the SDC contraction, rho = 0
+// estimates it after each sweep as sqrt(E_k / E_{k-1}) (no stop after the first).
+typedef struct {
+    double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen;
+    int energy_stop; double rho;
+} ora_opts;
 #define ORA_MAX_SWEEPS 64
 #define ORA_MAX_M 8
 typedef struct {
@@ -428,6 +435,7 @@ typedef struct {
     int cg_iters[ORA_MAX_SWEEPS * ORA_MAX_M];
     double cg_relres_max;
     double min_margin;
+    double energy[ORA_MAX_SWEEPS];   // sum over the nodes of dv_m' A~_m dv_m
 } ora_stats;
 
 int ora_collocation(int M, double* tau, double* Q, double* Qhat) {
@@ -540,6 +548,7 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
     size_t log_pos = 0;
     int status = ORA_OK;
 
+    double energy_prev = 0.0;
     for (int k = 0; k < sweeps; ++k) {
         if (st) {
             st->n_active[k] = (int)act.size();
@@ -550,6 +559,7 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
             log_pos += act.size();
         }
         if (act.empty()) continue;
+        double energy = 0.0;
         // residual of the collocation system at the current iterate (active rows only)
         for (int m = 0; m < M; ++m)
             for (int i : act) {
@@ -591,7 +601,15 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
             }
             if (rc != ORA_OK) return rc;
             for (int i : act) delta[(size_t)m * N + i] = x[i];
+            // energy norm of this node's correction in its own system matrix
+            for (int i : act) {
+                double s = 0.0;
+                for (int q = K.ptr[i]; q < K.ptr[i + 1]; ++q)
+                    if (K.col[q] != i) s += K.val[q] * x[K.col[q]];
+                energy += x[i] * (dA[i] * x[i] + c * s);
+            }
         }
+        if (st) st->energy[k] = energy;
         // v update on the active rows; inactive rows are held fixed
         for (int m = 0; m < M; ++m)
             for (int i : act) V[(size_t)m * N + i] += delta[(size_t)m * N + i];
@@ -628,6 +646,16 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
             if (!std::isfinite(amax)) return ORA_NONFINITE;
             if (st && tol_drop > 0.0) st->min_margin = std::min(st->min_margin, std::fabs(amax - tol_drop));
             if (amax >= tol_drop) next.push_back(i);
+        }
+        if (o->energy_stop) {
+            // Sec. 3.2: geometric-series estimate of the remaining energy-norm error
+            double rho = o->rho;
+            if (!(rho > 0.0)) rho = k > 0 && energy_prev > 0.0 ? std::sqrt(energy / energy_prev) : 0.0;
+            energy_prev = energy;
+            if (rho > 0.0 && rho < 1.0) {
+                const double lim = (1.0 - rho) / rho * tol;
+                if (energy <= lim * lim) break;
+            }
         }
         if (forced_counts) {
             // replace the selection by the given set of the next sweep

@@ -42,7 +42,8 @@ class sdc_options(C.Structure):
                 ("cg_smem_block_size", C.c_int), ("cg_cluster_max", C.c_int),
                 ("cg_max_blocks", C.c_int), ("cg_variant", C.c_int),
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
-                ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int)]
+                ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
+                ("energy_stop", C.c_int), ("sdc_rho", C.c_double)]
 
 
 class sdc_stats(C.Structure):
@@ -52,7 +53,8 @@ class sdc_stats(C.Structure):
                 ("cg_relres_max", C.c_double), ("min_margin", C.c_double),
                 ("kernel_launches", C.c_int), ("phase_launches", C.c_int * SDC_N_PHASES),
                 ("phase_ms", C.c_double * SDC_N_PHASES),
-                ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS)]
+                ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS),
+                ("energy", C.c_double * SDC_MAX_SWEEPS)]
 
 
 class sdc_tape(C.Structure):

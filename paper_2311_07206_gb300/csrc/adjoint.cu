@@ -480,7 +480,7 @@ int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaSt
         cudaMemsetAsync(W.vkfull, 0, (size_t)M * N * sizeof(double), s);
         cudaMemsetAsync(W.ffull, 0, (size_t)M * N * sizeof(double), s);
         for (int m = M - 1; m >= 0 && status == SDC_OK; --m) {
-            PcgRole role;
+            PcgRole role{};
             role.b = B.R + (size_t)m * ld;            // dvbar_m (coupled)
             role.x = W.X + (size_t)m * ld;            // bbar_m
             role.J = B.J + (size_t)m * ld;

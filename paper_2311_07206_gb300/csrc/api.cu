@@ -143,7 +143,8 @@ int alloc_buffers(sdc_ctx* c) {
     }
     if (ok) ok = dalloc(&B.part, 12 * (size_t)B.max_blocks);
     if (!ok) return SDC_E_NOMEM;
-    if (cudaMallocHost(&c->h_pin, 4 * sizeof(int)) != cudaSuccess) return SDC_E_NOMEM;
+    // pinned: [0] count, [1] err, then kMaxM node energies at byte 16
+    if (cudaMallocHost(&c->h_pin, 16 + kMaxM * sizeof(double)) != cudaSuccess) return SDC_E_NOMEM;
     cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), c->stream);
     return SDC_OK;
 }
@@ -213,10 +214,15 @@ bool finite_all(const double* a, int n) {
     return true;
 }
 
-// Read the error flag and the next active count; resets the flag.
-int sync_sweep(sdc_ctx* c, int& count) {
+// Read the error flag and the next active count (and, for the energy-norm
+// stop, the node energies of sweep k into the pinned buffer at byte 16).
+int sync_sweep(sdc_ctx* c, int& count, int energy_sweep = -1) {
     cudaMemcpyAsync(&c->h_pin[0], &c->B.sc->count, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     cudaMemcpyAsync(&c->h_pin[1], &c->B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (energy_sweep >= 0)
+        cudaMemcpyAsync(reinterpret_cast<char*>(c->h_pin) + 16,
+                        &c->B.sc->cg_energy[energy_sweep * kMaxM], c->M * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SDC_E_CUDA;
     count = c->h_pin[0];
     return c->h_pin[1];
@@ -245,6 +251,8 @@ void sdc_default_options(sdc_options* o) {
     o->profile = 0;
     o->inject_fault = 0;
     o->cg_pipelined = -1;
+    o->energy_stop = 0;
+    o->sdc_rho = 0.0;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -324,10 +332,13 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.cg_smem_block_size > 1024 || o.cg_smem_block_size % 32 != 0 || o.cg_cluster_max < 1 ||
         o.cg_cluster_max > 16 || o.inject_fault < 0 ||
         o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
-        o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1)
+        o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
+        o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0))
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
+    if ((emi || inst_off) && o.energy_stop)
+        return fail(nullptr, SDC_E_INVALID, "energy_stop: monodomain contexts only (not EMI, not batches)");
     if (emi) {
         if (emi->n_pairs < 1 || !emi->pair_k || !emi->pair_l || !emi->pair_area || !emi->pair_kind)
             return fail(nullptr, SDC_E_INVALID, "EMI: no pairs or NULL pair arrays");
@@ -506,6 +517,8 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     c->n_act.assign(sweeps, 0);
     if (B.nseg > 0) c->inst_active.assign((size_t)sweeps * B.nseg, 0);
     if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (tape && c->opt.energy_stop)
+        return fail(c, SDC_E_INVALID, "energy_stop: not available with a tape");
     if (c->is_emi) {
         if (tape) return fail(c, SDC_E_INVALID, "tapes are not available for EMI contexts");
         EmiStepArgs ea{N, M, s, &c->K, &B, &c->emi, &c->act, &c->n_act, &c->pcg, &c->opt, &c->co,
@@ -563,6 +576,7 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     long long nnz = c->K.nnz - N;
     int cur = 0;                   // ping-pong index of the restricted matrix
     int status = SDC_OK;
+    double energy_prev = 0.0;
     int k = 0;
     for (k = 0; k < sweeps; ++k) {
         c->n_act[k] = n;
@@ -641,7 +655,21 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
                             cudaMemcpyDeviceToHost, s);
         }
         int n_next = 0;
-        int e = sync_sweep(c, n_next);
+        int e = sync_sweep(c, n_next, c->opt.energy_stop ? k : -1);
+        bool stop_now = false;
+        if (c->opt.energy_stop && e == SDC_OK) {
+            // Sec. 3.2: the geometric series bounds the remaining energy-norm error
+            const double* he = reinterpret_cast<const double*>(reinterpret_cast<char*>(c->h_pin) + 16);
+            double E = 0.0;
+            for (int m = 0; m < M; ++m) E += he[m];
+            double rho = c->opt.sdc_rho;
+            if (!(rho > 0.0)) rho = k > 0 && energy_prev > 0.0 ? std::sqrt(E / energy_prev) : 0.0;
+            energy_prev = E;
+            if (rho > 0.0 && rho < 1.0) {
+                const double lim = (1.0 - rho) / rho * TOL;
+                stop_now = E <= lim * lim;
+            }
+        }
         if (batched) c->seg_bounds.assign(c->h_bounds, c->h_bounds + B.nseg + 1);
         if (tape && tape->mode == SDC_TAPE_RECORD && e == SDC_OK) {
             tape->n_active[k] = n;
@@ -652,6 +680,10 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         if (e != SDC_OK) {
             status = e == SDC_E_CUDA ? cuda_fail(c, "sweep") : fail(c, (sdc_status)e,
                      "sweep %d: %s", k, sdc_status_string(e));
+            break;
+        }
+        if (stop_now) {
+            ++k;
             break;
         }
         if (k + 1 < sweeps && n_next > 0) {
@@ -674,7 +706,8 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         run(SDC_PHASE_RESIDUAL, 1, [&] { launch_final(N, M, B.V, B.W, d_v, d_w, s); });
         if (cudaStreamSynchronize(s) != cudaSuccess) status = cuda_fail(c, "sdc_step");
     }
-    c->last_sweeps = sweeps;
+    const int sweeps_done = std::min(k, sweeps);   // fewer after an energy-norm stop
+    c->last_sweeps = status == SDC_OK ? sweeps_done : sweeps;
     c->stepped = true;
     if (tape && tape->mode == SDC_TAPE_RECORD) {
         tape->sweeps = sweeps;
@@ -682,12 +715,18 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     }
     if (stats) {
         std::vector<int> it(SDC_MAX_SWEEPS * kMaxM);
-        std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM);
+        std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM), en(SDC_MAX_SWEEPS * kMaxM);
         double mg = 0.0;
         cudaMemcpyAsync(it.data(), B.sc->cg_iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(rr.data(), B.sc->cg_relres, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(en.data(), B.sc->cg_energy, en.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        for (int kk = 0; kk < stats->sweeps_run; ++kk) {
+            double E = 0.0;
+            for (int m = 0; m < M; ++m) E += en[kk * kMaxM + m];
+            stats->energy[kk] = E;
+        }
         if (B.nseg > 0) {
             const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * B.nseg;
             std::vector<int> si(cnt);
@@ -708,7 +747,7 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
                     rr[kk * kMaxM + m] = mr;
                 }
         }
-        for (int kk = 0; kk < sweeps; ++kk)
+        for (int kk = 0; kk < stats->sweeps_run; ++kk)
             for (int m = 0; m < M; ++m) {
                 stats->cg_iters[kk][m] = it[kk * kMaxM + m];
                 stats->cg_relres_max = std::max(stats->cg_relres_max, rr[kk * kMaxM + m]);

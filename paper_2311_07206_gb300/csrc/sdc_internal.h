@@ -35,6 +35,7 @@ struct DevScalars {
     double margin;             // min |max_m |dv| - TOL_drop| of the newest selection
     int cg_iters[SDC_MAX_SWEEPS * kMaxM];
     double cg_relres[SDC_MAX_SWEEPS * kMaxM];
+    double cg_energy[SDC_MAX_SWEEPS * kMaxM];   // dv_m' A~_m dv_m per node solve
 };
 
 // ELL-R matrix in column-major slots: entry t of row i at [t * ld + i],
@@ -176,6 +177,7 @@ struct PcgRole {
     double c;               // dt * Qhat_mm of the solved node
     int* iters_out;
     double* relres_out;
+    double* energy_out;     // may be null
 };
 int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,
                     int maxit, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);

@@ -138,6 +138,7 @@ struct CgParams {
     long long budget;
     int* iters_out;
     double* relres_out;
+    double* energy_out;  // x' A x of the solution (may be null)
     // epilogue: LU-trick coupling into the later nodes' right-hand sides
     int m_node, M;
     double dt;
@@ -167,6 +168,7 @@ __device__ __forceinline__ void cg_couple_row(const CgParams& P, int i, double x
 struct CgShared {
     XsScratch xs;           // exact block sums
     double alpha, beta, den, gamma0, rzmax, rn;
+    double energy;          // x' A x of the iterate: sum of alpha_t gamma_t over the steps taken
     double inv_g[2];        // 1 / gamma of the last two sums (warp 1)
     int ok, state;          // state: 0 iterating, 1 converged, 2 non-finite
 };
@@ -198,7 +200,10 @@ __device__ __forceinline__ void cg_scalars(CgShared& S, int wid, int t, double g
                                            double rtol) {
     if (wid == 0) {
         S.rn = g;
-        if (t == 0) S.gamma0 = g;
+        if (t == 0) {
+            S.gamma0 = g;
+            S.energy = 0.0;
+        }
         if (!isfinite(g) || !isfinite(d)) {
             S.state = 2;
         } else if (t == 0 ? g == 0.0 : (g >= 0.0 && g <= S.rzmax)) {
@@ -210,12 +215,17 @@ __device__ __forceinline__ void cg_scalars(CgShared& S, int wid, int t, double g
             S.beta = beta;
             S.den = den;
             S.state = 0;
+            // the iterate is x = sum_t alpha_t p_t with A-conjugate p_t, so
+            // x' A x = sum_t alpha_t^2 p_t' A p_t = sum_t alpha_t gamma_t
+            S.energy = fma(S.alpha, g, S.energy);
         }
     } else {
         S.inv_g[t & 1] = 1.0 / g;
         if (t == 0) S.rzmax = largest_with_sqrt_at_most(rtol * sqrt(g));
     }
 }
+// Sec. 3.2 energy-norm termination: in exact arithmetic the CG iterate from
+// x0 = 0 has x' A x = sum_t alpha_t gamma_t, so the norm needs no product.
 // final relative preconditioned residual sqrt(r.u / r0.u0)
 __device__ __forceinline__ double cg_relres(const CgShared& S) {
     return S.gamma0 > 0.0 ? sqrt(fabs(S.rn) / S.gamma0) : 0.0;
@@ -377,6 +387,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
     if (lead) {
         *iters_out = it;
         *relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
     }
     // x is complete and visible in every block: the last group barrier followed its update.
     if (P.epi_lo < P.epi_hi) {
@@ -565,6 +576,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
     if (blockIdx.x == 0 && t == 0) {
         *P.iters_out = it;
         *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
     }
     // x is complete and visible: the last grid barrier followed its last update
     if (P.epi_lo < P.epi_hi) {
@@ -738,6 +750,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
         if (rank == 0 && t == 0) {
             *P.iters_out = it;
             *P.relres_out = cg_relres(S);
+            if (P.energy_out) *P.energy_out = S.energy;
         }
         if (P.epi_lo < P.epi_hi) {
             // every CTA's x is final: its last update preceded the last cluster barrier
@@ -847,6 +860,7 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
     if (lead) {
         *iters_out = it;
         *relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
     }
     // x is complete in every block of the group: the last group sum followed its update.
     if (P.epi_lo < P.epi_hi) {
@@ -969,6 +983,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
     if (blockIdx.x == 0 && t == 0) {
         *P.iters_out = it;
         *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
     }
     // x is complete and visible: the last grid sum followed its last update
     if (P.epi_lo < P.epi_hi) {
@@ -1312,6 +1327,7 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.budget = cfg.budget;
     P.iters_out = &B.sc->cg_iters[sweep * kMaxM + m];
     P.relres_out = &B.sc->cg_relres[sweep * kMaxM + m];
+    P.energy_out = &B.sc->cg_energy[sweep * kMaxM + m];
     P.m_node = m;
     P.M = co.M;
     P.epi_lo = m + 1;
@@ -1348,6 +1364,7 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
     P.budget = cfg.budget;
     P.iters_out = role.iters_out;
     P.relres_out = role.relres_out;
+    P.energy_out = role.energy_out;
     P.m_node = 0;
     P.M = M;
     P.epi_lo = role.epi_lo;
@@ -1493,6 +1510,7 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.budget = cfg.budget;
     P.iters_out = nullptr;
     P.relres_out = nullptr;
+    P.energy_out = nullptr;
     P.m_node = m;
     P.M = co.M;
     P.epi_lo = m + 1;
@@ -1567,6 +1585,7 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
     P.budget = budget;
     P.iters_out = w.iters;
     P.relres_out = w.relres;
+    P.energy_out = nullptr;
     P.m_node = 0;
     P.M = 1;            // no coupling into other nodes
     P.epi_lo = 0;

@@ -98,3 +98,17 @@ def test_emi_create_rejects_bad_pairs_before_device_work(lib, bad):
         Context(3, wl.mesh.xyz, wl.mesh.elems, sigma=np.eye(3), elem_sigma=wl.mesh.elem_sigma,
                 ionic=wl.ionic, M=wl.M, emi=emi)
     assert e.value.status == -1 and "EMI" in str(e.value)
+
+
+def test_energy_stop_rejected_for_emi_and_bad_rho_before_device_work(lib):
+    from paper_2311_07206_gb300 import Context, SdcError, default_options
+    from workloads.emi import emi_tiny
+    wl = emi_tiny("two_cells")
+    with pytest.raises(SdcError) as e:
+        Context.from_emi(wl, options=default_options(energy_stop=1))
+    assert e.value.status == -1
+    import workloads as W
+    sq = W.w0_square(n=9, length=2.5)
+    with pytest.raises(SdcError) as e:
+        Context.from_workload(sq, options=default_options(energy_stop=1, sdc_rho=1.0))
+    assert e.value.status == -1

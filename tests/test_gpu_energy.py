@@ -1,0 +1,83 @@
+"""GPU parity of the energy-norm termination of the sweeps (Sec. 3.2): the
+library forms each node solve's energy from its CG scalars (sum of alpha
+gamma), the oracle from the definition dv' A~ dv; both end the step after the
+same sweep, with the same states (1e-10) and energies within the CG
+tolerance's effect (1e-8 relative)."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_07206_gb300 import build as b
+    b.build()
+    return torch, torch.device("cuda:0")
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(1.0, np.abs(b).max())
+
+
+@pytest.mark.parametrize("case,rho,tol", [("square", 0.0, 1e-4), ("square", 0.3, 1e-5),
+                                          ("slab", 0.0, 1e-5), ("slab", 0.2, 1e-6)])
+def test_energy_stop_parity(torch_dev, case, rho, tol):
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import Context, default_options
+    if case == "square":
+        wl = W.w0_square()
+    else:
+        mesh = W.kuhn3d(31, 11, 6, 0.1)
+        stim = np.nonzero((mesh.xyz <= 0.5 + 1e-12).all(axis=1))[0].astype(np.int32)
+        wl = W.Workload("slab_31x11x6", mesh, np.diag([1.0, 0.25, 0.25]), dict(W.AP_BENCH), M=4,
+                        dt=0.05, sweeps=12, tol=tol, steps=10, v0=np.zeros(mesh.n_nodes),
+                        w0=np.zeros(mesh.n_nodes), stim_nodes=stim, stim_amp=2.0,
+                        stim_t_on=0.0, stim_t_off=1.0)
+    sweeps = 12
+    ctx = Context.from_workload(wl, options=default_options(energy_stop=1, sdc_rho=rho),
+                                stream=torch.cuda.current_stream(dev).cuda_stream)
+    S = oracle.System.from_mesh(wl.mesh, wl.sigma)
+    v, w = wl.v0.copy(), wl.w0.copy()
+    early = False
+    for n in range(8):
+        t = n * wl.dt
+        dv = torch.tensor(v, dtype=torch.float64, device=dev)
+        dw = torch.tensor(w, dtype=torch.float64, device=dev)
+        st = ctx.step(dv, dw, t, wl.dt, sweeps, tol)
+        r = S.step(wl.ionic, wl.M, v, w, wl.dt, sweeps, tol, alpha=wl.alpha, cg_rtol=wl.cg_rtol,
+                   istim=wl.stim_vector(t), want_log=True, energy_stop=True, rho=rho)
+        assert r["status"] == 0
+        assert st.sweeps_run == r["stats"].sweeps_run, n
+        early |= st.sweeps_run < sweeps
+        for k in range(st.sweeps_run):
+            e_ora = r["stats"].energy[k]
+            assert abs(st.energy[k] - e_ora) <= 1e-8 * max(e_ora, 1e-300), (n, k)
+            if r["stats"].n_active[k]:
+                assert np.array_equal(ctx.active(k), r["active"][k])
+        assert _relmax(dv.cpu().numpy(), r["v"]) <= 1e-10
+        assert _relmax(dw.cpu().numpy(), r["w"]) <= 1e-10
+        v, w = r["v"], r["w"]
+    assert early    # the stop really ended steps before the sweep limit
+    ctx.close()
+
+
+def test_energy_stop_rejects_tapes(torch_dev):
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import Context, SdcError, default_options
+    wl = W.w0_square(n=17, length=5.0)
+    ctx = Context.from_workload(wl, options=default_options(energy_stop=1),
+                                stream=torch.cuda.current_stream(dev).cuda_stream)
+    v = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
+    w = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    tp = ctx.new_tape(wl.sweeps, dev)
+    with pytest.raises(SdcError):
+        ctx.step_taped(v, w, 0.0, wl.dt, wl.sweeps, wl.tol, tp)
+    ctx.close()
