@@ -119,7 +119,8 @@ typedef struct {
                               the sums overlapped with the product); 0 classical (two); -1
                               automatic: pipelined for monodomain contexts, classical for
                               cell-by-cell contexts, whose long ill-conditioned solves need its
-                              smaller rounding error; default -1.  Batches are pipelined.      */
+                              smaller rounding error, and for batches, whose many small groups
+                              favour its lighter rows; default -1                              */
     int energy_stop;       /* 1: end the sweeps of a step once the energy norm of the sweep's
                               corrections, E_k = sum_m dv_m' A~_m dv_m with A~_m the node system
                               matrix, is at most ((1 - rho) / rho * TOL)^2 (Sec. 3.2); `sweeps`

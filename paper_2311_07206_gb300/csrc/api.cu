@@ -128,6 +128,7 @@ int alloc_buffers(sdc_ctx* c) {
         const int nseg = (int)c->inst_off.size() - 1;
         B.nseg = nseg;
         P.batch_block = std::min(P.block, 256);
+        P.batch_pipelined = c->opt.cg_pipelined == 1;
         P.max_blocks_batch = pcg_batch_max_blocks(P.batch_block);
         if (c->opt.cg_max_blocks > 0)
             P.max_blocks_batch = std::min(P.max_blocks_batch, c->opt.cg_max_blocks);

@@ -153,6 +153,7 @@ struct PcgConfig {
     int big_rows = 300000;          // shared-memory variant uses 1024 threads from here on
     int max_blocks_batch = 0;       // cooperative grid limit of the batched variant
     int batch_block = 256;          // block size of the batched variant
+    int batch_pipelined = 0;        // arrangement of the batched variant
     int batch_rows_per_block = 1024;
     int inject_fault = 0;
     int pipelined = 1;              // 1: pipelined CG; 0: classical arrangement

@@ -882,6 +882,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc(CgParams P) {
                reinterpret_cast<XsRecord*>(P.part), (int)gridDim.x, P.iters_out, P.relres_out);
 }
 
+// Batched form of the classical arrangement (one group of blocks per instance).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgc_batch(CgParams P, const SegBlock* __restrict__ tab,
+                                                         unsigned* __restrict__ bars,
+                                                         int* __restrict__ seg_iters,
+                                                         double* __restrict__ seg_relres) {
+    __shared__ CgShared S;
+    const SegBlock g = tab[blockIdx.x];
+    pcgc_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
+               reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x, seg_iters + g.seg,
+               seg_relres + g.seg);
+}
+
 // Shared-memory form of the classical arrangement (rows as in k_pcg_smem;
 // r, u, p, s, w and the reciprocal diagonal on chip, u published).
 template <int MAXT>
@@ -1230,8 +1243,10 @@ PcgKernel pcgc_general_kernel(int block) {
     return block > 512 ? k_pcgc<1024> : block > 256 ? k_pcgc<512> : k_pcgc<256>;
 }
 PcgKernel pcgc_smem_kernel(int block) { return block > 512 ? k_pcgc_smem<1024> : k_pcgc_smem<512>; }
-PcgBatchKernel pcg_batch_kernel(int block) {
-    return block > 512 ? k_pcg_batch<1024> : block > 256 ? k_pcg_batch<512> : k_pcg_batch<256>;
+// Batches: the 64-register instantiation whatever the block size, so that
+// several blocks share an SM and one cooperative wave holds more instances.
+PcgBatchKernel pcg_batch_kernel(int, bool pipelined) {
+    return pipelined ? k_pcg_batch<1024> : k_pcgc_batch<1024>;
 }
 
 // opt-in dynamic shared memory of the on-chip variants (set once per instantiation)
@@ -1464,7 +1479,10 @@ int pcg_batch_max_blocks(int block) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_batch_kernel(block), block, 0);
+    int per2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_batch_kernel(block, true), block, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, pcg_batch_kernel(block, false), block, 0);
+    per = std::min(per, per2);
     return sms * per;
 }
 
@@ -1544,7 +1562,8 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
             return SDC_E_CUDA;
         const SegBlock* dtab = reinterpret_cast<const SegBlock*>(B.segtab);
         void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_batch_kernel(cfg.batch_block),
+        cudaError_t e = cudaLaunchCooperativeKernel(
+            (const void*)pcg_batch_kernel(cfg.batch_block, cfg.batch_pipelined),
                                                     dim3((int)tab.size()),
                                                     dim3(cfg.batch_block), args, 0, s);
         if (e != cudaSuccess) return SDC_E_CUDA;
