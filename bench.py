@@ -58,11 +58,12 @@ def parse():
                          "w1l/w5, 100 for w0/w3, 200 for w4)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4"],
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4", "sweet"],
                     default="w1",
                     help="w2: cell-by-cell (EMI) bricks; w3: 96-instance batch, batched launches "
                          "vs per-instance launches; w4: gradient by the discrete adjoint vs "
-                         "finite differences")
+                         "finite differences; sweet: final error vs drop tolerance for several "
+                         "SDC tolerances on the 2D square (energy-norm stop)")
     ap.add_argument("--fd-directions", type=int, default=16)
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
@@ -72,7 +73,7 @@ def parse():
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
-                      "w4": 200}[args.workload]
+                      "w4": 200, "sweet": 100}[args.workload]
     return args
 
 
@@ -603,6 +604,68 @@ def emi_cpu_baseline(budget_s, gpu_row_iters_per_step, frozen):
 
 
 
+def run_sweet(args):
+    """Sweet-line study (Sec. 5.2): final error on the 2D square (65x65 nodes,
+    M = 3, dt = 0.1, t = 10) against the drop tolerance TOL_drop = alpha TOL
+    for several SDC tolerances TOL.  The sweeps end by the energy-norm test of
+    Sec. 3.2 with the paper's rho = 0.05 (at most 12); the reference is plain
+    SDC with 12 sweeps.  The paper finds TOL_drop = TOL / 10 close to the
+    largest drop tolerance that leaves the accuracy unchanged."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Context, default_options
+
+    wl = W.w0_square()
+    K, Wm = args.steps, args.warmup
+    stream = torch.cuda.current_stream(dev)
+
+    def run(tol, alpha, energy_stop, sweeps, timed=False):
+        opts = default_options(alpha=alpha, energy_stop=int(energy_stop), sdc_rho=0.05,
+                               cg_rtol=wl.cg_rtol)
+        ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
+        v = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
+        w = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ads, swp = 0, 0
+        e0.record(stream)
+        for n in range(K):
+            st = ctx.step(v, w, n * wl.dt, wl.dt, sweeps, tol)
+            ads += sum(st.n_active[:st.sweeps_run])
+            swp += st.sweeps_run
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.close()
+        return v.cpu().numpy(), e0.elapsed_time(e1), ads, swp
+
+    for _ in range(max(1, Wm)):
+        run(1e-4, 0.1, True, 12)
+    ref, _, _, _ = run(0.0, 0.1, False, 12)
+    rows = []
+    for tol in (1e-3, 1e-4, 1e-5, 1e-6):
+        for alpha in (0.001, 0.01, 0.1, 1.0, 10.0):
+            v, ms, ads, swp = run(tol, alpha, True, 12)
+            rows.append({"TOL": tol, "TOL_drop": alpha * tol, "alpha": alpha,
+                         "err": float(np.abs(v - ref).max()), "ms_per_step": ms / K,
+                         "mean_sweeps": swp / K, "active_dof_sweeps_per_step": ads / K})
+    at = [r for r in rows if r["TOL"] == 1e-4 and r["alpha"] == 0.1][0]
+    line = {"metric": "sweet-line study: max error at t = 10 vs TOL_drop (2D square, energy-norm "
+                      "stop, rho = 0.05)",
+            "value": 1e3 / at["ms_per_step"], "unit": "steps/s at TOL = 1e-4, TOL_drop = 1e-5",
+            "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": at["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "n_dofs": wl.n, "M": wl.M, "dt_ms": wl.dt,
+                       "max_sweeps": 12, "rho": 0.05, "reference": "plain SDC, 12 sweeps"},
+            "table": rows}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+
 def run_batch(args):
     """96 2D instances (sides log-uniform in [64, 512], D ~ U[0.5, 2]): one
     batched step of all instances vs the same steps as per-instance launches."""
@@ -779,7 +842,7 @@ SEED_FD = 2311_07206 + 40
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload in ("w2", "w3", "w4"):
+    if args.impl == "reference" and args.workload in ("w2", "w3", "w4", "sweet"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the reference arm times the oracle on the monodomain workloads only"}))
         return 0
@@ -789,6 +852,8 @@ def main():
         return run_batch(args)
     if args.workload == "w4":
         return run_grad(args)
+    if args.workload == "sweet":
+        return run_sweet(args)
     if args.workload == "w2":
         return run_emi(args)
     return run_gb300(args)

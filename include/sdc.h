@@ -129,6 +129,10 @@ typedef struct {
     double sdc_rho;        /* SDC contraction rho for energy_stop, in [0, 1); 0: estimated after
                               each sweep as sqrt(E_k / E_{k-1}) (so no stop after the first
                               sweep); default 0                                               */
+    int sdc_qhat;          /* lower-triangular preconditioner of the sweeps (Sec. 3.1):
+                              0 LU trick, Qhat = U^T with Q^T = L U (default); 1 implicit Euler,
+                              the right-looking rectangle rule, Qhat_mj = tau_j - tau_{j-1} for
+                              j <= m (tau_0 = 0)                                              */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */

@@ -40,7 +40,7 @@ class _Ionic(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("reaction_implicit", C.c_int), ("w_frozen", C.c_int),
-                ("energy_stop", C.c_int), ("rho", C.c_double)]
+                ("energy_stop", C.c_int), ("rho", C.c_double), ("qhat", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -169,17 +169,18 @@ class System:
              alpha: float = 0.1, cg_rtol: float = 1e-10, cg_maxit: int = 10000,
              istim=None, reaction_implicit: bool = True, w_frozen: bool = False,
              want_log: bool = False, want_nodes: bool = False, energy_stop: bool = False,
-             rho: float = 0.0):
+             rho: float = 0.0, qhat: str = "lu"):
         """One SDC step.  Returns dict(v, w, status, stats, active[, V, W]).
         energy_stop ends the sweeps by the energy-norm test of Sec. 3.2 with SDC
         contraction rho (0: estimated from successive sweeps); `sweeps` is then
-        the largest number of sweeps."""
+        the largest number of sweeps.  qhat: "lu" (LU trick) or "ie" (implicit
+        Euler) preconditioner of the sweep."""
         n = self.n
         v = np.array(v, dtype=np.float64, copy=True)
         w = np.array(w, dtype=np.float64, copy=True)
         st = Stats()
         opts = _Opts(alpha, cg_rtol, cg_maxit, int(reaction_implicit), int(w_frozen),
-                     int(energy_stop), float(rho))
+                     int(energy_stop), float(rho), {"lu": 0, "ie": 1}[qhat])
         log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
         Vn = np.zeros((M, n)) if want_nodes else None
         Wn = np.zeros((M, n)) if want_nodes else None

@@ -148,12 +148,21 @@ struct Collocation {
     std::vector<double> tau, Q, Qhat;  // row-major M x M
 };
 
-bool make_collocation(int M, Collocation& c) {
-    if (M < 1 || M > 8) return false;
+// qhat = 0: LU trick (Qhat = U^T with Q^T = L U); qhat = 1: implicit Euler, the
+// right-looking rectangle rule of Sec. 3.1 in cumulative form,
+// Qhat_mj = tau_j - tau_{j-1} for j <= m (tau_0 = 0), i.e. z_m = z_0 + sum_{j<=m} dtau_j f(z_j).
+bool make_collocation(int M, Collocation& c, int qhat = 0) {
+    if (M < 1 || M > 8 || qhat < 0 || qhat > 1) return false;
     std::vector<long double> tau, Q, Qh;
     if (!radau_nodes(M, tau)) return false;
     quadrature_matrix(tau, Q);
-    if (!lu_trick(M, Q, Qh)) return false;
+    if (qhat == 0) {
+        if (!lu_trick(M, Q, Qh)) return false;
+    } else {
+        Qh.assign((size_t)M * M, 0.0L);
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j <= m; ++j) Qh[(size_t)m * M + j] = tau[j] - (j > 0 ? tau[j - 1] : 0.0L);
+    }
     c.M = M;
     c.tau.assign(tau.begin(), tau.end());
     c.Q.assign(Q.begin(), Q.end());
@@ -423,9 +432,10 @@ typedef struct { double ga, gs, a, eps, mu1, mu2, cw; } ora_ionic;
 // sum over the nodes of dv_m' A~_m dv_m (A~_m the node system matrix), is at most
 // ((1 - rho) / rho * TOL)^2 (Sec. 3.2); rho > 0 is the SDC contraction, rho = 0
 // estimates it after each sweep as sqrt(E_k / E_{k-1}) (no stop after the first).
+// qhat: 0 LU trick, 1 implicit Euler (make_collocation)
 typedef struct {
     double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen;
-    int energy_stop; double rho;
+    int energy_stop; double rho; int qhat;
 } ora_opts;
 #define ORA_MAX_SWEEPS 64
 #define ORA_MAX_M 8
@@ -521,7 +531,8 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
     const Csr& K = S.K;
     const int N = K.n;
     Collocation col;
-    if (!make_collocation(M, col) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 || dt <= 0)
+    if (!make_collocation(M, col, o->qhat) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 ||
+        dt <= 0)
         return ORA_INVALID;
     const std::vector<double>& Q = col.Q;
     const std::vector<double>& Qh = col.Qhat;
@@ -696,7 +707,8 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
     const Csr& K = S.K;
     const int N = K.n, NP = n_pairs;
     Collocation col;
-    if (!make_collocation(M, col) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 || dt <= 0)
+    if (!make_collocation(M, col, o->qhat) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || tol < 0 ||
+        dt <= 0)
         return ORA_INVALID;
     const std::vector<double>& Q = col.Q;
     const std::vector<double>& Qh = col.Qhat;

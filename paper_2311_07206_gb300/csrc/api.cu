@@ -254,6 +254,7 @@ void sdc_default_options(sdc_options* o) {
     o->cg_pipelined = -1;
     o->energy_stop = 0;
     o->sdc_rho = 0.0;
+    o->sdc_qhat = 0;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -334,7 +335,8 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.cg_cluster_max > 16 || o.inject_fault < 0 ||
         o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
         o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
-        o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0))
+        o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
+        o.sdc_qhat < 0 || o.sdc_qhat > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
@@ -375,6 +377,12 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
     if (!radau_collocation(M, c->tau, Q, Qh)) {
         delete c;
         return fail(nullptr, SDC_E_INVALID, "collocation setup failed for M = %d", M);
+    }
+    if (o.sdc_qhat == 1) {
+        // implicit Euler: Qhat_mj = tau_j - tau_{j-1} for j <= m (tau_0 = 0)
+        for (int m = 0; m < M; ++m)
+            for (int j = 0; j < M; ++j)
+                Qh[m * M + j] = j <= m ? c->tau[j] - (j > 0 ? c->tau[j - 1] : 0.0) : 0.0;
     }
     c->co.M = M;
     for (int m = 0; m < kMaxM; ++m)

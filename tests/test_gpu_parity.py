@@ -209,6 +209,31 @@ def test_empty_active_sets_and_single_sweep(torch_dev):
     ctx.close()
 
 
+@pytest.mark.parametrize("tol", [0.0, 1e-4])
+def test_step_parity_implicit_euler_qhat(torch_dev, tol):
+    """The implicit-Euler preconditioner of the sweeps (option sdc_qhat = 1)
+    against the oracle's (qhat="ie")."""
+    torch, dev = torch_dev
+    wl = W.w0_square()
+    ctx = _ctx(wl, torch, dev, sdc_qhat=1)
+    S = oracle.System.from_mesh(wl.mesh, wl.sigma)
+    v, w = wl.v0.copy(), wl.w0.copy()
+    for n in range(6):
+        dv = torch.tensor(v, dtype=torch.float64, device=dev)
+        dw = torch.tensor(w, dtype=torch.float64, device=dev)
+        st = ctx.step(dv, dw, n * wl.dt, wl.dt, wl.sweeps, tol)
+        r = S.step(wl.ionic, wl.M, v, w, wl.dt, wl.sweeps, tol, alpha=wl.alpha,
+                   cg_rtol=wl.cg_rtol, istim=wl.stim_vector(n * wl.dt), want_log=True, qhat="ie")
+        assert r["status"] == 0
+        assert _relmax(dv.cpu().numpy(), r["v"]) <= RTOL
+        assert _relmax(dw.cpu().numpy(), r["w"]) <= RTOL
+        for k in range(wl.sweeps):
+            if r["stats"].n_active[k]:
+                assert np.array_equal(ctx.active(k), r["active"][k])
+        v, w = r["v"], r["w"]
+    ctx.close()
+
+
 def test_tol_zero_is_plain_and_deterministic(torch_dev):
     torch, dev = torch_dev
     wl = W.w0_square()
