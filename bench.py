@@ -70,7 +70,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/reference/e2e runs")
     ap.add_argument("--emi-w-frozen", action="store_true", help="w2: hold the gating at w = 0")
+    ap.add_argument("--reorder", type=int, choices=[0, 1], default=None,
+                    help="library-internal Morton numbering of the dofs (default: on for the "
+                         "randomly numbered tissue mesh w5, off otherwise)")
     args = ap.parse_args()
+    if args.reorder is None:
+        args.reorder = 1 if args.workload == "w5" else 0
     if args.steps is None:
         args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
                       "w4": 200, "sweet": 100}[args.workload]
@@ -81,9 +86,10 @@ def make_workload(name):
     return {"w1": W.w1_slab, "w1l": W.w1l_slab, "w0": W.w0_square, "w5": W.w5_tissue}[name]()
 
 
-def config_of(wl, K):
+def config_of(wl, K, reorder=0):
     return {"workload": wl.name, "n_dofs": wl.n, "M": wl.M, "dt_ms": wl.dt, "sweeps": wl.sweeps,
             "TOL": wl.tol, "alpha": wl.alpha, "cg_rtol": wl.cg_rtol,
+            "dof_numbering": "library Morton order" if reorder else "as generated",
             "simulated_ms": round(K * wl.dt, 6),
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
 
@@ -278,7 +284,7 @@ def run_gb300(args):
     wl = make_workload(args.workload)
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream(dev)
-    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha)
+    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, reorder=args.reorder)
     ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
     v0 = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
@@ -410,7 +416,7 @@ def run_gb300(args):
     line = {"metric": metric_of(wl), "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms_adapt / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, K),
+            "config": config_of(wl, K, args.reorder),
             "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_adapt / 1e3),
             **extras,
             "phase_ms_per_step": phase,

@@ -133,6 +133,12 @@ typedef struct {
                               0 LU trick, Qhat = U^T with Q^T = L U (default); 1 implicit Euler,
                               the right-looking rectangle rule, Qhat_mj = tau_j - tau_{j-1} for
                               j <= m (tau_0 = 0)                                              */
+    int reorder;           /* 1: number the dofs internally in Morton (Z-curve) order of their
+                              coordinates, so that the rows a block owns and the neighbours it
+                              gathers lie close in memory (randomly numbered unstructured
+                              meshes); states, stimuli, scales, active lists, node values and
+                              the matrix stay in the caller's numbering.  Not with tapes or the
+                              adjoint, in batches or EMI contexts; default 0                  */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */

@@ -43,7 +43,8 @@ class sdc_options(C.Structure):
                 ("cg_max_blocks", C.c_int), ("cg_variant", C.c_int),
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
                 ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
-                ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int)]
+                ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int),
+                ("reorder", C.c_int)]
 
 
 class sdc_stats(C.Structure):

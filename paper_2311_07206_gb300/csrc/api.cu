@@ -40,6 +40,11 @@ struct sdc_ctx {
     AdjointBuffers AW;            // adjoint workspace, allocated on first use
     bool is_emi = false;          // cell-by-cell model (sdc_create_emi)
     EmiDev emi;
+    // internal dof numbering (reorder option): perm[new] = old, inv[old] = new
+    std::vector<int> h_perm, h_inv;
+    int* d_perm = nullptr;
+    double* vp = nullptr;         // states in the internal numbering during a step
+    double* wp = nullptr;
     bool stepped = false;
     std::string err;
 };
@@ -172,6 +177,11 @@ void free_all(sdc_ctx* c) {
     free_mesh_dev(c->K.mesh);
     free_adjoint(c->AW);
     emi_free(c->emi);
+    cudaFree(c->d_perm);
+    cudaFree(c->vp);
+    cudaFree(c->wp);
+    c->d_perm = nullptr;
+    c->vp = c->wp = nullptr;
     for (int* p : c->act) cudaFree(p);
     c->act.clear();
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -255,6 +265,7 @@ void sdc_default_options(sdc_options* o) {
     o->energy_stop = 0;
     o->sdc_rho = 0.0;
     o->sdc_qhat = 0;
+    o->reorder = 0;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -294,6 +305,44 @@ sdc_status sdc_radau(int M, double* tau, double* Q, double* Qhat) {
 }  // extern "C"
 
 namespace {
+
+// Morton (Z-curve) order of points: 21 bits per coordinate after scaling to
+// the bounding box, bits interleaved, ties kept in input order.
+std::vector<int> morton_order(int dim, int n, const double* xyz) {
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) {
+        lo[d] = hi[d] = xyz[d];
+        for (int i = 1; i < n; ++i) {
+            lo[d] = std::min(lo[d], xyz[(size_t)i * dim + d]);
+            hi[d] = std::max(hi[d], xyz[(size_t)i * dim + d]);
+        }
+    }
+    double ext = 0.0;
+    for (int d = 0; d < dim; ++d) ext = std::max(ext, hi[d] - lo[d]);
+    const double sc = ext > 0.0 ? 2097151.0 / ext : 0.0;
+    auto spread = [](unsigned long long v) {   // 21 bits -> every third bit
+        v &= 0x1fffffull;
+        v = (v | v << 32) & 0x1f00000000ffffull;
+        v = (v | v << 16) & 0x1f0000ff0000ffull;
+        v = (v | v << 8) & 0x100f00f00f00f00full;
+        v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+        v = (v | v << 2) & 0x1249249249249249ull;
+        return v;
+    };
+    std::vector<unsigned long long> key(n);
+    for (int i = 0; i < n; ++i) {
+        unsigned long long k = 0;
+        for (int d = 0; d < dim; ++d) {
+            const unsigned long long q = (unsigned long long)((xyz[(size_t)i * dim + d] - lo[d]) * sc);
+            k |= spread(q) << d;
+        }
+        key[i] = k;
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+    return order;
+}
 
 sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
                        const sdc_options* opt, void* stream, const std::vector<int>* inst_off,
@@ -336,12 +385,14 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
         o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
         o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
-        o.sdc_qhat < 0 || o.sdc_qhat > 1)
+        o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
     if ((emi || inst_off) && o.energy_stop)
         return fail(nullptr, SDC_E_INVALID, "energy_stop: monodomain contexts only (not EMI, not batches)");
+    if ((emi || inst_off) && o.reorder)
+        return fail(nullptr, SDC_E_INVALID, "reorder: monodomain contexts only (not EMI, not batches)");
     if (emi) {
         if (emi->n_pairs < 1 || !emi->pair_k || !emi->pair_l || !emi->pair_area || !emi->pair_kind)
             return fail(nullptr, SDC_E_INVALID, "EMI: no pairs or NULL pair arrays");
@@ -391,7 +442,29 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
             c->co.Qh[m * kMaxM + j] = (m < M && j < M) ? Qh[m * M + j] : 0.0;
         }
     std::string why;
-    int rc = assemble_device(*mesh, o.drop_rel, c->stream, c->K, why);
+    sdc_mesh pm = *mesh;   // the mesh in the internal numbering
+    std::vector<double> pxyz, pscale;
+    std::vector<int> pelem;
+    if (o.reorder) {
+        const int N = mesh->n_nodes, dim = mesh->dim;
+        c->h_perm = morton_order(dim, N, mesh->xyz);
+        c->h_inv.assign(N, 0);
+        for (int i = 0; i < N; ++i) c->h_inv[c->h_perm[i]] = i;
+        pxyz.resize((size_t)N * dim);
+        for (int i = 0; i < N; ++i)
+            for (int d = 0; d < dim; ++d) pxyz[(size_t)i * dim + d] = mesh->xyz[(size_t)c->h_perm[i] * dim + d];
+        const int ne = mesh->elem_ptr[mesh->n_elems];
+        pelem.resize(ne);
+        for (int k = 0; k < ne; ++k) pelem[k] = c->h_inv[mesh->elem_node[k]];
+        pm.xyz = pxyz.data();
+        pm.elem_node = pelem.data();
+        if (mesh->dof_scale) {
+            pscale.resize(N);
+            for (int i = 0; i < N; ++i) pscale[i] = mesh->dof_scale[c->h_perm[i]];
+            pm.dof_scale = pscale.data();
+        }
+    }
+    int rc = assemble_device(pm, o.drop_rel, c->stream, c->K, why);
     if (rc != SDC_OK) {
         free_all(c);
         delete c;
@@ -402,6 +475,15 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         free_all(c);
         delete c;
         return fail(nullptr, (sdc_status)rc, "device buffer allocation failed");
+    }
+    if (o.reorder) {
+        if (!dalloc(&c->d_perm, c->N) || !dalloc(&c->vp, c->N) || !dalloc(&c->wp, c->N) ||
+            cudaMemcpyAsync(c->d_perm, c->h_perm.data(), c->N * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return fail(nullptr, SDC_E_NOMEM, "reorder: buffer allocation failed");
+        }
     }
     if (emi) {
         c->is_emi = true;
@@ -454,7 +536,7 @@ sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, dou
     c->stim = nullptr;
     if (n == 0) return SDC_OK;
     std::vector<double> h(c->N, 0.0);
-    for (int i = 0; i < n; ++i) h[nodes[i]] = amp;
+    for (int i = 0; i < n; ++i) h[c->h_inv.empty() ? nodes[i] : c->h_inv[nodes[i]]] = amp;
     if (!dalloc(&c->stim, c->N)) return fail(c, SDC_E_NOMEM, "stimulus allocation failed");
     if (cudaMemcpyAsync(c->stim, h.data(), c->N * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
@@ -505,7 +587,36 @@ sdc_status sdc_step_taped(sdc_ctx* c, double* d_v, double* d_w, double t, double
 }  // extern "C"
 
 namespace {
+sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                     double TOL, sdc_stats* stats, sdc_tape* tape);
+
+// The step in the caller's numbering: with the reorder option the states are
+// gathered into the internal numbering, stepped and scattered back.
 sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                     double TOL, sdc_stats* stats, sdc_tape* tape) {
+    if (!c) return SDC_E_INVALID;
+    if (!c->d_perm || c->is_emi) return step_core(c, d_v, d_w, t, dt, sweeps, TOL, stats, tape);
+    if (!d_v || !d_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SDC_E_INVALID, "dt must be positive");
+    if (sweeps < 1 || sweeps > SDC_MAX_SWEEPS)
+        return fail(c, SDC_E_INVALID, "sweeps = %d outside [1, %d]", sweeps, SDC_MAX_SWEEPS);
+    if (!(TOL >= 0.0)) return fail(c, SDC_E_INVALID, "TOL must be >= 0");
+    if (tape) return fail(c, SDC_E_INVALID, "reorder: tapes are not available");
+    launch_perm_gather(c->N, c->d_perm, d_v, c->vp, c->stream);
+    launch_perm_gather(c->N, c->d_perm, d_w, c->wp, c->stream);
+    sdc_status st = step_core(c, c->vp, c->wp, t, dt, sweeps, TOL, stats, nullptr);
+    launch_perm_scatter(c->N, c->d_perm, c->vp, d_v, c->stream);
+    launch_perm_scatter(c->N, c->d_perm, c->wp, d_w, c->stream);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess && st == SDC_OK)
+        st = cuda_fail(c, "sdc_step (permutation)");
+    if (stats) {
+        stats->phase_launches[SDC_PHASE_RESIDUAL] += 4;
+        stats->kernel_launches += 4;
+    }
+    return st;
+}
+
+sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
                      double TOL, sdc_stats* stats, sdc_tape* tape) {
     if (!c) return SDC_E_INVALID;
     if (!d_v || !d_w) return fail(c, SDC_E_INVALID, "NULL state pointer");
@@ -805,8 +916,14 @@ sdc_status sdc_get_nodes(const sdc_ctx* cc, double* d_V, double* d_W) {
     sdc_ctx* c = const_cast<sdc_ctx*>(cc);
     if (!c) return SDC_E_INVALID;
     if (!d_V || !d_W) return fail(c, SDC_E_INVALID, "NULL output");
-    if (c->is_emi) emi_nodes_out(c->emi, c->N, c->M, c->B.V, d_V, d_W, c->stream);
-    else launch_nodes_out(c->N, c->M, c->B.V, c->B.W, d_V, d_W, c->stream);
+    if (c->is_emi) {
+        emi_nodes_out(c->emi, c->N, c->M, c->B.V, d_V, d_W, c->stream);
+    } else if (c->d_perm) {
+        launch_nodes_out_perm(c->N, c->M, c->d_perm, c->B.V, d_V, c->stream);
+        launch_nodes_out_perm(c->N, c->M, c->d_perm, c->B.W, d_W, c->stream);
+    } else {
+        launch_nodes_out(c->N, c->M, c->B.V, c->B.W, d_V, d_W, c->stream);
+    }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return cuda_fail(c, "sdc_get_nodes");
     return SDC_OK;
 }
@@ -827,6 +944,11 @@ sdc_status sdc_get_active(const sdc_ctx* cc, int sweep, int* h_idx, int* n) {
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)
         return cuda_fail(c, "sdc_get_active");
+    if (!c->h_perm.empty()) {
+        // internal rows -> the caller's dofs, ascending
+        for (int i = 0; i < cnt; ++i) h_idx[i] = c->h_perm[h_idx[i]];
+        std::sort(h_idx, h_idx + cnt);
+    }
     return SDC_OK;
 }
 
@@ -853,6 +975,34 @@ sdc_status sdc_get_matrix(const sdc_ctx* cc, int* row_ptr, int* col, double* val
     cudaMemcpyAsync(kd.data(), c->K.kdiag, N * sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(mass, c->K.mass, N * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, "sdc_get_matrix");
+    if (!c->h_perm.empty()) {
+        // the caller's numbering: row r is internal row inv[r], columns mapped back and sorted
+        const std::vector<int>& P = c->h_perm;
+        const std::vector<int>& I = c->h_inv;
+        std::vector<double> ms(N);
+        for (int r = 0; r < N; ++r) ms[r] = mass[I[r]];
+        std::copy(ms.begin(), ms.end(), mass);
+        long long pos = 0;
+        row_ptr[0] = 0;
+        std::vector<std::pair<int, double>> row;
+        for (int r = 0; r < N; ++r) {
+            const int i = I[r];
+            row.clear();
+            row.push_back({r, kd[i]});
+            for (int t = 0; t < el[i]; ++t)
+                row.push_back({P[ec[(size_t)t * E.ld + i]], ev[(size_t)t * E.ld + i]});
+            std::sort(row.begin(), row.end(),
+                      [](const std::pair<int, double>& x, const std::pair<int, double>& y) {
+                          return x.first < y.first;
+                      });
+            for (const auto& e : row) {
+                col[pos] = e.first;
+                val[pos++] = e.second;
+            }
+            row_ptr[r + 1] = (int)pos;
+        }
+        return SDC_OK;
+    }
     long long pos = 0;
     row_ptr[0] = 0;
     for (int i = 0; i < N; ++i) {
@@ -1107,6 +1257,7 @@ sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0
     if (!(dt > 0.0)) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: dt must be positive");
     if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available for batches");
     if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available for EMI contexts");
+    if (c->d_perm) return fail(c, SDC_E_INVALID, "sdc_step_adjoint: not available with reorder");
     if (tape->n_active[0] != c->N)
         return fail(c, SDC_E_INVALID, "sdc_step_adjoint: the first sweep must cover every dof");
     if (!ensure_adjoint(c)) return fail(c, SDC_E_NOMEM, "adjoint workspace allocation failed");
@@ -1160,6 +1311,12 @@ sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
             if (!std::isfinite(h_scale[i]) || !(h_scale[i] > 0.0))
                 return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: scale %d not positive", i);
     std::string why;
+    std::vector<double> ps;
+    if (h_scale && !c->h_perm.empty()) {
+        ps.resize(c->N);
+        for (int i = 0; i < c->N; ++i) ps[i] = h_scale[c->h_perm[i]];
+        h_scale = ps.data();
+    }
     const int rc = reassemble_device(c->K, h_scale, c->opt.drop_rel, c->stream, why);
     if (rc != SDC_OK) return fail(c, (sdc_status)rc, "%s", why.c_str());
     return SDC_OK;

@@ -162,6 +162,12 @@ struct PcgConfig {
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
                int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
 int pcg_sm_count();
+// dof permutation (perm[new] = old): dst[i] = src[perm[i]] / dst[perm[i]] = src[i]
+void launch_perm_gather(int N, const int* perm, const double* src, double* dst, cudaStream_t s);
+void launch_perm_scatter(int N, const int* perm, const double* src, double* dst, cudaStream_t s);
+// node values [new][M] -> [m][old]
+void launch_nodes_out_perm(int N, int M, const int* perm, const double* X, double* out,
+                           cudaStream_t s);
 // Message returned by sdc_last_error(NULL) on the calling thread.
 void set_thread_error(const char* msg);
 

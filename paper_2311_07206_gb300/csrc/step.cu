@@ -52,6 +52,24 @@ __global__ void k_nodes_out(int N, int M, const double* __restrict__ V, const do
     }
 }
 
+__global__ void k_perm_gather(int N, const int* __restrict__ perm, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) dst[i] = src[perm[i]];
+}
+__global__ void k_perm_scatter(int N, const int* __restrict__ perm, const double* __restrict__ src,
+                               double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) dst[perm[i]] = src[i];
+}
+__global__ void k_nodes_out_perm(int N, int M, const int* __restrict__ perm,
+                                 const double* __restrict__ X, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int o = perm[i];
+    for (int m = 0; m < M; ++m) out[(size_t)m * N + o] = X[(size_t)i * M + m];
+}
+
 template <int M>
 __global__ void k_residual(int n, const int* __restrict__ act, const double* __restrict__ kval,
                            const int* __restrict__ kcol, const int* __restrict__ klen, int ldk,
@@ -1207,6 +1225,17 @@ void launch_spread(int N, int M, const double* v0, const double* w0, double* V, 
 void launch_final(int N, int M, const double* V, const double* W, double* v, double* w,
                   cudaStream_t s) {
     k_final<<<nblk(N, 256), 256, 0, s>>>(N, M, V, W, v, w);
+}
+
+void launch_perm_gather(int N, const int* perm, const double* src, double* dst, cudaStream_t s) {
+    if (N > 0) k_perm_gather<<<nblk(N, 256), 256, 0, s>>>(N, perm, src, dst);
+}
+void launch_perm_scatter(int N, const int* perm, const double* src, double* dst, cudaStream_t s) {
+    if (N > 0) k_perm_scatter<<<nblk(N, 256), 256, 0, s>>>(N, perm, src, dst);
+}
+void launch_nodes_out_perm(int N, int M, const int* perm, const double* X, double* out,
+                           cudaStream_t s) {
+    if (N > 0) k_nodes_out_perm<<<nblk(N, 256), 256, 0, s>>>(N, M, perm, X, out);
 }
 
 void launch_nodes_out(int N, int M, const double* V, const double* W, double* Vo, double* Wo,
