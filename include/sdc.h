@@ -124,8 +124,9 @@ typedef struct {
     int energy_stop;       /* 1: end the sweeps of a step once the energy norm of the sweep's
                               corrections, E_k = sum_m dv_m' A~_m dv_m with A~_m the node system
                               matrix, is at most ((1 - rho) / rho * TOL)^2 (Sec. 3.2); `sweeps`
-                              is then the largest number of sweeps.  Monodomain contexts, not
-                              with a tape or in a batch; default 0                            */
+                              is then the largest number of sweeps.  Monodomain and
+                              cell-by-cell contexts (there A~_m = B + c_m (A + sum over pairs of
+                              the pair Jacobian)); not with a tape or in a batch; default 0   */
     double sdc_rho;        /* SDC contraction rho for energy_stop, in [0, 1); 0: estimated after
                               each sweep as sqrt(E_k / E_{k-1}) (so no stop after the first
                               sweep); default 0                                               */
@@ -139,6 +140,14 @@ typedef struct {
                               meshes); states, stimuli, scales, active lists, node values and
                               the matrix stay in the caller's numbering.  Not with tapes or the
                               adjoint, in batches or EMI contexts; default 0                  */
+    int drop_rule;         /* drop tolerance of the selections: 0 TOL_drop = alpha TOL (default);
+                              1 the a priori tolerance of Sec. 4.1 (Eq. drop-tolerance):
+                              TOL_drop = exp(-eta dt) (1 - rho) / (r + 1) TOL with rho = sdc_rho
+                              (required in (0, 1)), c = max |dv| of the step's first sweep, r
+                              the least integer >= 0 with c rho^r <= (1 - rho) TOL, and eta =
+                              max(0, -min dI/dv) / C_m over the first sweep's linearisation
+                              (zero with reaction_implicit = 0); computed on the device once
+                              per step, reported in sdc_stats.tol_drop.  Not in batches      */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */
@@ -156,6 +165,7 @@ typedef struct {
     double cg_ms[SDC_MAX_SWEEPS][SDC_MAX_M];  /* device ms per node solve (profile option) */
     double energy[SDC_MAX_SWEEPS];         /* E_k = sum_m dv_m' A~_m dv_m of sweep k, from the CG
                                               scalars (sum of alpha gamma over each solve)    */
+    double tol_drop;                       /* the drop tolerance the step's selections used   */
 } sdc_stats;
 
 /* Fill defaults (values above). */

@@ -40,13 +40,15 @@ class _Ionic(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("reaction_implicit", C.c_int), ("w_frozen", C.c_int),
-                ("energy_stop", C.c_int), ("rho", C.c_double), ("qhat", C.c_int)]
+                ("energy_stop", C.c_int), ("rho", C.c_double), ("qhat", C.c_int),
+                ("drop_rule", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("sweeps_run", C.c_int), ("n_active", C.c_int * MAX_SWEEPS),
                 ("cg_iters", C.c_int * (MAX_SWEEPS * MAX_M)), ("cg_relres_max", C.c_double),
-                ("min_margin", C.c_double), ("energy", C.c_double * MAX_SWEEPS)]
+                ("min_margin", C.c_double), ("energy", C.c_double * MAX_SWEEPS),
+                ("tol_drop", C.c_double)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -169,18 +171,20 @@ class System:
              alpha: float = 0.1, cg_rtol: float = 1e-10, cg_maxit: int = 10000,
              istim=None, reaction_implicit: bool = True, w_frozen: bool = False,
              want_log: bool = False, want_nodes: bool = False, energy_stop: bool = False,
-             rho: float = 0.0, qhat: str = "lu"):
+             rho: float = 0.0, qhat: str = "lu", drop_rule: int = 0):
         """One SDC step.  Returns dict(v, w, status, stats, active[, V, W]).
         energy_stop ends the sweeps by the energy-norm test of Sec. 3.2 with SDC
         contraction rho (0: estimated from successive sweeps); `sweeps` is then
         the largest number of sweeps.  qhat: "lu" (LU trick) or "ie" (implicit
-        Euler) preconditioner of the sweep."""
+        Euler) preconditioner of the sweep.  drop_rule 1 selects with the a
+        priori drop tolerance of Sec. 4.1 (rho > 0 given, c from the first sweep)
+        instead of alpha TOL; stats.tol_drop is the value used."""
         n = self.n
         v = np.array(v, dtype=np.float64, copy=True)
         w = np.array(w, dtype=np.float64, copy=True)
         st = Stats()
         opts = _Opts(alpha, cg_rtol, cg_maxit, int(reaction_implicit), int(w_frozen),
-                     int(energy_stop), float(rho), {"lu": 0, "ie": 1}[qhat])
+                     int(energy_stop), float(rho), {"lu": 0, "ie": 1}[qhat], int(drop_rule))
         log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
         Vn = np.zeros((M, n)) if want_nodes else None
         Wn = np.zeros((M, n)) if want_nodes else None
@@ -223,9 +227,11 @@ class System:
         return dict(v=v, w=w, status=rc, stats=st)
 
     def step_emi(self, wl, u, w, sweeps=None, tol=None, cg_rtol=None, w_frozen=False,
-                 want_log=False):
+                 want_log=False, energy_stop=False, rho=0.0, alpha=None, drop_rule=0):
         """One SDC step of a cell-by-cell workload (K of this system = the
-        subdomain stiffness; pairs, Robin and membrane data from `wl`)."""
+        subdomain stiffness; pairs, Robin and membrane data from `wl`).
+        `energy_stop` ends the sweeps by the energy-norm test of Sec. 3.2
+        (`rho` given, or estimated from successive sweep energies when 0)."""
         n = self.n
         sweeps = wl.sweeps if sweeps is None else sweeps
         tol = wl.tol if tol is None else tol
@@ -233,7 +239,8 @@ class System:
         u = np.array(u, dtype=np.float64, copy=True)
         w = np.array(w, dtype=np.float64, copy=True)
         st = Stats()
-        opts = _Opts(wl.alpha, cg_rtol, 100000, 1, int(w_frozen))
+        opts = _Opts(wl.alpha if alpha is None else alpha, cg_rtol, 100000, 1, int(w_frozen),
+                     int(energy_stop), rho, 0, int(drop_rule))
         log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
         rob = _f64(wl.robin)
         pk, pl, pa, pkd = _i32(wl.pair_k), _i32(wl.pair_l), _f64(wl.pair_area), _i32(wl.pair_kind)

@@ -433,9 +433,11 @@ typedef struct { double ga, gs, a, eps, mu1, mu2, cw; } ora_ionic;
 // ((1 - rho) / rho * TOL)^2 (Sec. 3.2); rho > 0 is the SDC contraction, rho = 0
 // estimates it after each sweep as sqrt(E_k / E_{k-1}) (no stop after the first).
 // qhat: 0 LU trick, 1 implicit Euler (make_collocation)
+// drop_rule: 0 TOL_drop = alpha TOL; 1 the a priori drop tolerance of Sec. 4.1
+// (drop_tolerance below) with the given rho > 0 and c from the first sweep
 typedef struct {
     double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen;
-    int energy_stop; double rho; int qhat;
+    int energy_stop; double rho; int qhat; int drop_rule;
 } ora_opts;
 #define ORA_MAX_SWEEPS 64
 #define ORA_MAX_M 8
@@ -446,7 +448,23 @@ typedef struct {
     double cg_relres_max;
     double min_margin;
     double energy[ORA_MAX_SWEEPS];   // sum over the nodes of dv_m' A~_m dv_m
+    double tol_drop;                 // the drop tolerance the selections used
 } ora_stats;
+
+// A priori drop tolerance of Sec. 4.1 (Eq. drop-tolerance with Theorems 1 and 2):
+//   TOL_drop = exp(-eta T) (1 - rho) / (r + 1) TOL,
+// r the least integer >= 0 with r >= log((1 - rho) TOL / c) / log(rho) (Eq. r-condition),
+// c = ||dv^0||_inf the first correction (the linear-convergence constant at k = 0, Sec. 4.2),
+// eta = max(0, -min dI/dv) / Cm over the linearisation of the correction equation,
+// T = dt, the interval the correction equation of one step is posed on.
+static double drop_tolerance(double c, double neg_jmin, double Cm, double rho, double tol,
+                             double dt) {
+    if (!(tol > 0.0)) return 0.0;
+    double r = 0.0;
+    if (c > 0.0) r = std::max(0.0, std::ceil(std::log((1.0 - rho) * tol / c) / std::log(rho)));
+    const double eta = std::max(0.0, neg_jmin) / Cm;
+    return std::exp(-eta * dt) * (1.0 - rho) / (r + 1.0) * tol;
+}
 
 int ora_collocation(int M, double* tau, double* Q, double* Qhat) {
     Collocation c;
@@ -537,7 +555,8 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
     const std::vector<double>& Q = col.Q;
     const std::vector<double>& Qh = col.Qhat;
     Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
-    const double tol_drop = o->alpha * tol;
+    double tol_drop = o->alpha * tol;
+    if (o->drop_rule && !(o->rho > 0.0 && o->rho < 1.0)) return ORA_INVALID;
 
     std::vector<double> v0(v, v + N), w0(w, w + N);
     // collocation iterates V[m][i], W[m][i], spread predictor
@@ -621,6 +640,16 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
             }
         }
         if (st) st->energy[k] = energy;
+        if (o->drop_rule && k == 0) {
+            // c and eta from the first sweep (all dofs active)
+            double cmax = 0.0, neg_jmin = 0.0;
+            for (int m = 0; m < M; ++m)
+                for (int i : act) {
+                    cmax = std::max(cmax, std::fabs(delta[(size_t)m * N + i]));
+                    neg_jmin = std::max(neg_jmin, -J[(size_t)m * N + i]);
+                }
+            tol_drop = drop_tolerance(cmax, neg_jmin, 1.0, o->rho, tol, dt);
+        }
         // v update on the active rows; inactive rows are held fixed
         for (int m = 0; m < M; ++m)
             for (int i : act) V[(size_t)m * N + i] += delta[(size_t)m * N + i];
@@ -685,6 +714,7 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
     }
     if (Vn) std::copy(V.begin(), V.end(), Vn);
     if (Wn) std::copy(W.begin(), W.end(), Wn);
+    if (st) st->tol_drop = tol_drop;
     return status;
 }
 
@@ -713,7 +743,8 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
     const std::vector<double>& Q = col.Q;
     const std::vector<double>& Qh = col.Qhat;
     Ionic p{ip->ga, ip->gs, ip->a, ip->eps, ip->mu1, ip->mu2, ip->cw};
-    const double tol_drop = o->alpha * tol;
+    double tol_drop = o->alpha * tol;
+    if (o->drop_rule && !(o->rho > 0.0 && o->rho < 1.0)) return ORA_INVALID;
     // pairs incident to each node, with the sign of the node in v = u_k - u_l
     std::vector<std::vector<std::pair<int, int>>> inc(N);
     for (int q = 0; q < NP; ++q) {
@@ -742,6 +773,7 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
     auto arow = [&](int i, const double* x) {
         return krow(K, i, x) + (robin ? robin[i] : 0.0) * x[i];
     };
+    double energy_prev = 0.0;
     for (int k = 0; k < sweeps; ++k) {
         if (st) {
             st->n_active[k] = (int)act.size();
@@ -752,6 +784,7 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
             log_pos += act.size();
         }
         if (act.empty()) continue;
+        double energy = 0.0;
         for (int m = 0; m < M; ++m)
             for (int q = 0; q < NP; ++q) {
                 const double v = U[(size_t)m * N + pk[q]] - U[(size_t)m * N + pl[q]];
@@ -823,6 +856,21 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
             }
             if (rc != ORA_OK) return rc;
             for (int i : act) delta[(size_t)m * N + i] = x[i];
+            // energy norm of this node's correction in its own system matrix
+            std::vector<double> ax(N, 0.0);
+            apply(x, ax);
+            for (int i : act) energy += x[i] * ax[i];
+        }
+        if (st) st->energy[k] = energy;
+        if (o->drop_rule && k == 0) {
+            // c from the first sweep; eta from the pair Jacobians (membrane currents
+            // and gap junctions) over C_m
+            double cmax = 0.0, neg_jmin = 0.0;
+            for (int m = 0; m < M; ++m) {
+                for (int i : act) cmax = std::max(cmax, std::fabs(delta[(size_t)m * N + i]));
+                for (int q = 0; q < NP; ++q) neg_jmin = std::max(neg_jmin, -Jp[(size_t)m * NP + q]);
+            }
+            tol_drop = drop_tolerance(cmax, neg_jmin, Cm, o->rho, tol, dt);
         }
         for (int m = 0; m < M; ++m)
             for (int i : act) U[(size_t)m * N + i] += delta[(size_t)m * N + i];
@@ -860,12 +908,23 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
             if (st && tol_drop > 0.0) st->min_margin = std::min(st->min_margin, std::fabs(amax - tol_drop));
             if (amax >= tol_drop) next.push_back(i);
         }
+        if (o->energy_stop) {
+            // Sec. 3.2: geometric-series estimate of the remaining energy-norm error
+            double rho = o->rho;
+            if (!(rho > 0.0)) rho = k > 0 && energy_prev > 0.0 ? std::sqrt(energy / energy_prev) : 0.0;
+            energy_prev = energy;
+            if (rho > 0.0 && rho < 1.0) {
+                const double lim = (1.0 - rho) / rho * tol;
+                if (energy <= lim * lim) break;
+            }
+        }
         for (int i : act) on[i] = 0;
         for (int i : next) on[i] = 1;
         act.swap(next);
     }
     for (int i = 0; i < N; ++i) u[i] = U[(size_t)(M - 1) * N + i];
     for (int q = 0; q < NP; ++q) w[q] = Wp[(size_t)(M - 1) * NP + q];
+    if (st) st->tol_drop = tol_drop;
     return ORA_OK;
 }
 

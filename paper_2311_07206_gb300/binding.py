@@ -44,7 +44,7 @@ class sdc_options(C.Structure):
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
                 ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
                 ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int),
-                ("reorder", C.c_int)]
+                ("reorder", C.c_int), ("drop_rule", C.c_int)]
 
 
 class sdc_stats(C.Structure):
@@ -55,7 +55,7 @@ class sdc_stats(C.Structure):
                 ("kernel_launches", C.c_int), ("phase_launches", C.c_int * SDC_N_PHASES),
                 ("phase_ms", C.c_double * SDC_N_PHASES),
                 ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS),
-                ("energy", C.c_double * SDC_MAX_SWEEPS)]
+                ("energy", C.c_double * SDC_MAX_SWEEPS), ("tol_drop", C.c_double)]
 
 
 class sdc_tape(C.Structure):
@@ -436,15 +436,6 @@ class Batch:
                 _check(L.sdc_batch_set_stimulus(self._h, b, nodes.ctypes.data_as(_ip), nodes.size,
                                                 wl.stim_amp, wl.stim_t_on, wl.stim_t_off),
                        L.sdc_batch_context(self._h))
-
-    @classmethod
-    def from_emi(cls, wl, options=None, stream=0):
-        """Cell-by-cell context of an EMI workload (state: n potentials, n_pairs gating)."""
-        emi = dict(pair_k=wl.pair_k, pair_l=wl.pair_l, pair_area=wl.pair_area,
-                   pair_kind=wl.pair_kind, robin=wl.robin, Cm=wl.Cm, g_gap=wl.g_gap)
-        return cls(wl.mesh.dim, wl.mesh.xyz, wl.mesh.elems, sigma=np.eye(3),
-                   elem_sigma=wl.mesh.elem_sigma, ionic=wl.ionic, M=wl.M, options=options,
-                   stream=stream, emi=emi)
 
     def close(self):
         if getattr(self, "_h", None) and _lib is not None:

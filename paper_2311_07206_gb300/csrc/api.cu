@@ -266,6 +266,7 @@ void sdc_default_options(sdc_options* o) {
     o->sdc_rho = 0.0;
     o->sdc_qhat = 0;
     o->reorder = 0;
+    o->drop_rule = 0;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -385,12 +386,17 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.inject_fault > 1 || o.cg_variant < 0 || o.cg_variant > 2 || o.cg_rows_per_block < 0 ||
         o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
         o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
-        o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1)
+        o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1 ||
+        o.drop_rule < 0 || o.drop_rule > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
+    if (o.drop_rule == 1 && !(o.sdc_rho > 0.0))
+        return fail(nullptr, SDC_E_INVALID, "drop_rule = 1 needs a given sdc_rho in (0, 1)");
+    if (inst_off && o.drop_rule)
+        return fail(nullptr, SDC_E_INVALID, "drop_rule: not available for batches");
     if (!(ionic->mu2 > 0.0) && !o.w_frozen)
         return fail(nullptr, SDC_E_INVALID, "mu2 must be positive");
-    if ((emi || inst_off) && o.energy_stop)
-        return fail(nullptr, SDC_E_INVALID, "energy_stop: monodomain contexts only (not EMI, not batches)");
+    if (inst_off && o.energy_stop)
+        return fail(nullptr, SDC_E_INVALID, "energy_stop: not available for batches");
     if ((emi || inst_off) && o.reorder)
         return fail(nullptr, SDC_E_INVALID, "reorder: monodomain contexts only (not EMI, not batches)");
     if (emi) {
@@ -628,6 +634,8 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     const int N = c->N, M = c->M;
     cudaStream_t s = c->stream;
     const double tol_drop = c->opt.alpha * TOL;
+    // the a priori drop tolerance (drop rule 1) lives on the device from the first sweep on
+    const double* drop_dev = c->opt.drop_rule && TOL > 0.0 ? &c->B.sc->tol_drop : nullptr;
     const double stim_on = (c->stim && c->stim_t_on <= t && t < c->stim_t_off) ? 1.0 : 0.0;
     while ((int)c->act.size() < sweeps) {
         int* p = nullptr;
@@ -641,10 +649,11 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         return fail(c, SDC_E_INVALID, "energy_stop: not available with a tape");
     if (c->is_emi) {
         if (tape) return fail(c, SDC_E_INVALID, "tapes are not available for EMI contexts");
+        int done = sweeps;
         EmiStepArgs ea{N, M, s, &c->K, &B, &c->emi, &c->act, &c->n_act, &c->pcg, &c->opt, &c->co,
-                       &c->ion, c->h_pin, &c->err, &c->events};
+                       &c->ion, c->h_pin, &c->err, &c->events, &done};
         const int st = emi_step(ea, d_v, d_w, dt, sweeps, TOL, stats);
-        c->last_sweeps = sweeps;
+        c->last_sweeps = done;
         c->stepped = true;
         return (sdc_status)st;
     }
@@ -738,8 +747,13 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
             });
         }
         if (status != SDC_OK) break;
+        if (k == 0 && drop_dev)
+            run(SDC_PHASE_SELECT, 2, [&] {
+                launch_drop_rule(n, M, B.D, B.ld, n, B.J, B.ld, 1.0, c->opt.sdc_rho, TOL, dt, B, s);
+            });
         run(SDC_PHASE_UPDATE, 1, [&] {
-            launch_update(M, n, act, d_w, dt, c->ion, c->co, tol_drop, c->opt.w_frozen, B, s);
+            launch_update(M, n, act, d_w, dt, c->ion, c->co, tol_drop, c->opt.w_frozen, B, s,
+                          drop_dev);
         });
         int* next = (k + 1 < sweeps) ? c->act[k + 1] : c->act[0];
         const bool replay = tape && tape->mode == SDC_TAPE_REPLAY;
@@ -846,6 +860,11 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
             double E = 0.0;
             for (int m = 0; m < M; ++m) E += en[kk * kMaxM + m];
             stats->energy[kk] = E;
+        }
+        stats->tol_drop = tol_drop;
+        if (drop_dev) {
+            cudaMemcpyAsync(&stats->tol_drop, drop_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
         }
         if (B.nseg > 0) {
             const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * B.nseg;

@@ -350,6 +350,8 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
     const Coll& co = *a.co;
     cudaStream_t s = a.s;
     const double tol_drop = a.opt->alpha * TOL;
+    // the a priori drop tolerance (drop rule 1) lives on the device from the first sweep on
+    const double* drop_dev = a.opt->drop_rule && TOL > 0.0 ? &B.sc->tol_drop : nullptr;
     // the classical CG arrangement unless the pipelined one is asked for explicitly
     PcgConfig pcg = *a.pcg;
     pcg.pipelined = a.opt->cg_pipelined == 1;
@@ -402,7 +404,10 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
     const Ell* A = &a.K->K;
     long long nnz = a.K->nnz - N;
     int cur = 0, status = SDC_OK;
-    for (int k = 0; k < sweeps; ++k) {
+    const bool estop = a.opt->energy_stop != 0;
+    double energy_prev = 0.0;
+    int k = 0;
+    for (k = 0; k < sweeps; ++k) {
         (*a.n_act)[k] = n;
         if (stats) {
             stats->n_active[k] = n;
@@ -451,6 +456,7 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             role.c = c;
             role.iters_out = &B.sc->cg_iters[k * kMaxM + m];
             role.relres_out = &B.sc->cg_relres[k * kMaxM + m];
+            role.energy_out = &B.sc->cg_energy[k * kMaxM + m];
             run(SDC_PHASE_PCG, 1, [&] {
                 if (launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol, a.opt->cg_maxit, pcg, B,
                                     s) != SDC_OK)
@@ -469,9 +475,15 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         }
         if (status != SDC_OK) break;
         cur_m = -1;
+        if (k == 0 && drop_dev)
+            run(SDC_PHASE_SELECT, 2, [&] {
+                // eta from the pair Jacobians (membrane and gap junction) over C_m
+                launch_drop_rule(n, M, B.D, B.ld, NP, E.Jp, NP, E.Cm, a.opt->sdc_rho, TOL, dt, B,
+                                 s);
+            });
         run(SDC_PHASE_UPDATE, a.opt->w_frozen ? 1 : 2, [&] {
             // u update and selection flags (no node gating: w_frozen), then the pair gating
-            launch_update(M, n, act, nullptr, dt, *a.ion, co, tol_drop, 1, B, s);
+            launch_update(M, n, act, nullptr, dt, *a.ion, co, tol_drop, 1, B, s, drop_dev);
             if (!a.opt->w_frozen)
                 dispatch_M(M, [&](auto mc) {
                     constexpr int MM = decltype(mc)::value;
@@ -490,6 +502,9 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         cudaMemcpyAsync(&a.h_pin[0], &B.sc->count, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&a.h_pin[1], &B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&slots, E.slots, sizeof(slots), cudaMemcpyDeviceToHost, s);
+        if (estop)
+            cudaMemcpyAsync(reinterpret_cast<char*>(a.h_pin) + 16, &B.sc->cg_energy[k * kMaxM],
+                            M * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) {
             status = fail(SDC_E_CUDA, std::string("sweep: ") +
                                           cudaGetErrorString(cudaGetLastError()));
@@ -501,6 +516,22 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             status = fail(a.h_pin[1], "sweep " + std::to_string(k) + ": " +
                                           sdc_status_string(a.h_pin[1]));
             break;
+        }
+        if (estop) {
+            // Sec. 3.2: the geometric series bounds the remaining energy-norm error
+            const double* he = reinterpret_cast<const double*>(reinterpret_cast<char*>(a.h_pin) + 16);
+            double En = 0.0;
+            for (int m = 0; m < M; ++m) En += he[m];
+            double rho = a.opt->sdc_rho;
+            if (!(rho > 0.0)) rho = k > 0 && energy_prev > 0.0 ? std::sqrt(En / energy_prev) : 0.0;
+            energy_prev = En;
+            if (rho > 0.0 && rho < 1.0) {
+                const double lim = (1.0 - rho) / rho * TOL;
+                if (En <= lim * lim) {
+                    ++k;
+                    break;
+                }
+            }
         }
         if (k + 1 < sweeps && n_next > 0) {
             Ell& An = B.A[cur];
@@ -531,15 +562,28 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             status = fail(SDC_E_CUDA, std::string("EMI step: ") +
                                           cudaGetErrorString(cudaGetLastError()));
     }
+    if (a.sweeps_done) *a.sweeps_done = status == SDC_OK ? std::min(k, sweeps) : sweeps;
     if (stats) {
         std::vector<int> it(SDC_MAX_SWEEPS * kMaxM);
-        std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM);
+        std::vector<double> rr(SDC_MAX_SWEEPS * kMaxM), en(SDC_MAX_SWEEPS * kMaxM);
         double mg = 0.0;
         cudaMemcpyAsync(it.data(), B.sc->cg_iters, it.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(rr.data(), B.sc->cg_relres, rr.size() * sizeof(double),
                         cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(en.data(), B.sc->cg_energy, en.size() * sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        for (int kk = 0; kk < stats->sweeps_run; ++kk) {
+            double En = 0.0;
+            for (int m = 0; m < M; ++m) En += en[kk * kMaxM + m];
+            stats->energy[kk] = En;
+        }
+        stats->tol_drop = tol_drop;
+        if (drop_dev) {
+            cudaMemcpyAsync(&stats->tol_drop, drop_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+        }
         for (int kk = 0; kk < sweeps; ++kk)
             for (int m = 0; m < M; ++m) {
                 stats->cg_iters[kk][m] = it[kk * kMaxM + m];

@@ -36,6 +36,9 @@ struct DevScalars {
     int cg_iters[SDC_MAX_SWEEPS * kMaxM];
     double cg_relres[SDC_MAX_SWEEPS * kMaxM];
     double cg_energy[SDC_MAX_SWEEPS * kMaxM];   // dv_m' A~_m dv_m per node solve
+    unsigned long long drop_c;     // bits of max |dv| of the first sweep (drop rule 1)
+    unsigned long long drop_eta;   // bits of max(0, -dI/dv) of the first sweep
+    double tol_drop;               // the a priori drop tolerance of the step (drop rule 1)
 };
 
 // ELL-R matrix in column-major slots: entry t of row i at [t * ld + i],
@@ -258,8 +261,15 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
                           int maxit, long long budget, int block, const PcgScratch& w,
                           cudaStream_t s);
 int pcg_cluster_size(int block);
+// tol_drop_dev: when set, the selection reads TOL_drop there instead of tol_drop
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
-                   const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s);
+                   const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s,
+                   const double* tol_drop_dev = nullptr);
+// A priori drop tolerance of Sec. 4.1 into B.sc->tol_drop, from the first sweep's
+// corrections (n rows of D, M nodes) and Jacobians (nj entries per node at stride ldj).
+void launch_drop_rule(int n, int M, const double* D, int ld, int nj, const double* J, int ldj,
+                      double Cm, double rho, double TOL, double dt, StepBuffers& B,
+                      cudaStream_t s);
 void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s);
 void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepBuffers& B,
                     cudaStream_t s);
@@ -298,9 +308,10 @@ struct EmiStepArgs {
     const sdc_options* opt;
     const Coll* co;
     const Ionic* ion;
-    int* h_pin;                 // pinned: [0] count, [1] err
+    int* h_pin;                 // pinned: [0] count, [1] err, node energies from byte 16
     std::string* err;
     std::vector<cudaEvent_t>* events;   // profiling event pool (profile option)
+    int* sweeps_done;           // out: sweeps run (fewer after an energy-norm stop)
 };
 int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int sweeps, double TOL,
              sdc_stats* stats);

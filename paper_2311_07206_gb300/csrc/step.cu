@@ -1036,8 +1036,9 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
                          const double* __restrict__ w0, double dt, Ionic ion, Coll co,
                          double tol_drop, int w_frozen, int* __restrict__ flag,
                          int* __restrict__ blockcnt, double* __restrict__ blockmarg,
-                         int* __restrict__ err) {
+                         int* __restrict__ err, const double* __restrict__ tol_drop_dev) {
     __shared__ int wc[32];
+    if (tol_drop_dev) tol_drop = *tol_drop_dev;
     __shared__ double wmg[32];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
@@ -1656,13 +1657,62 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
 }
 
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
-                   const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s) {
+                   const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s,
+                   const double* tol_drop_dev) {
     dispatch_M(M, [&](auto mc) {
         constexpr int MM = decltype(mc)::value;
         k_update<MM><<<nblk(n, kUpdateBlock), kUpdateBlock, 0, s>>>(
             n, act, B.D, B.ld, B.V, B.W, w0, dt, ion, co, tol_drop, w_frozen, B.flag, B.blockcnt,
-            B.blockmarg, &B.sc->err);
+            B.blockmarg, &B.sc->err, tol_drop_dev);
     });
+}
+
+// Inputs of the a priori drop tolerance (Sec. 4.1): c = max over nodes and rows of |dv|
+// of the first sweep, and max(0, -dI/dv) over its linearisation.  Both are >= 0, so
+// their IEEE bit patterns order like the values and atomicMax on the bits takes the max.
+__global__ void k_drop_inputs(int n, int M, const double* __restrict__ D, int ld, int nj,
+                              const double* __restrict__ J, int ldj,
+                              unsigned long long* cbits, unsigned long long* ebits) {
+    double cm = 0.0, em = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride)
+        for (int m = 0; m < M; ++m) cm = fmax(cm, fabs(D[(size_t)m * ld + p]));
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nj; p += stride)
+        for (int m = 0; m < M; ++m) em = fmax(em, -J[(size_t)m * ldj + p]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+        em = fmax(em, __shfl_xor_sync(0xffffffffu, em, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(cbits, (unsigned long long)__double_as_longlong(cm));
+        atomicMax(ebits, (unsigned long long)__double_as_longlong(em));
+    }
+}
+
+// TOL_drop = exp(-eta dt) (1 - rho) / (r + 1) TOL (Eq. drop-tolerance), r the least
+// integer >= 0 with r >= log((1 - rho) TOL / c) / log(rho) (Eq. r-condition), eta =
+// max(0, -dI/dv) / Cm.
+__global__ void k_drop_final(const unsigned long long* cbits, const unsigned long long* ebits,
+                             double Cm, double rho, double TOL, double dt, double* out) {
+    if (threadIdx.x != 0) return;
+    const double c = __longlong_as_double((long long)*cbits);
+    const double eta = __longlong_as_double((long long)*ebits) / Cm;
+    double r = 0.0;
+    if (c > 0.0) r = fmax(0.0, ceil(log((1.0 - rho) * TOL / c) / log(rho)));
+    *out = TOL > 0.0 ? exp(-eta * dt) * (1.0 - rho) / (r + 1.0) * TOL : 0.0;
+}
+
+void launch_drop_rule(int n, int M, const double* D, int ld, int nj, const double* J, int ldj,
+                      double Cm, double rho, double TOL, double dt, StepBuffers& B,
+                      cudaStream_t s) {
+    const int rows = n > nj ? n : nj;
+    int nb = nblk(rows, 256);
+    if (nb > 1216) nb = 1216;                 // 8 blocks per SM, grid-stride beyond
+    if (nb < 1) nb = 1;
+    k_drop_inputs<<<nb, 256, 0, s>>>(n, M, D, ld, nj, J, ldj, &B.sc->drop_c, &B.sc->drop_eta);
+    k_drop_final<<<1, 32, 0, s>>>(&B.sc->drop_c, &B.sc->drop_eta, Cm, rho, TOL, dt,
+                                  &B.sc->tol_drop);
 }
 
 void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s) {

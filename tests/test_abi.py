@@ -100,15 +100,34 @@ def test_emi_create_rejects_bad_pairs_before_device_work(lib, bad):
     assert e.value.status == -1 and "EMI" in str(e.value)
 
 
-def test_energy_stop_rejected_for_emi_and_bad_rho_before_device_work(lib):
-    from paper_2311_07206_gb300 import Context, SdcError, default_options
+def test_energy_stop_rejected_for_batches_and_bad_rho_before_device_work(lib):
+    from paper_2311_07206_gb300 import Batch, Context, SdcError, default_options
     from workloads.emi import emi_tiny
+    import workloads as W
     wl = emi_tiny("two_cells")
     with pytest.raises(SdcError) as e:
-        Context.from_emi(wl, options=default_options(energy_stop=1))
+        Context.from_emi(wl, options=default_options(energy_stop=1, sdc_rho=-0.5))
     assert e.value.status == -1
-    import workloads as W
     sq = W.w0_square(n=9, length=2.5)
     with pytest.raises(SdcError) as e:
         Context.from_workload(sq, options=default_options(energy_stop=1, sdc_rho=1.0))
     assert e.value.status == -1
+    with pytest.raises(SdcError) as e:
+        Batch([sq, sq], options=default_options(energy_stop=1))
+    assert e.value.status == -1 and "batch" in str(e.value)
+
+
+def test_drop_rule_validation_before_device_work(lib):
+    """drop_rule 1 (the a priori drop tolerance of Sec. 4.1) needs a given
+    contraction rho and is per context, not per batch."""
+    from paper_2311_07206_gb300 import Batch, Context, SdcError, default_options
+    import workloads as W
+    sq = W.w0_square(n=9, length=2.5)
+    assert default_options().drop_rule == 0
+    for opts in (dict(drop_rule=1), dict(drop_rule=2, sdc_rho=0.05), dict(drop_rule=-1)):
+        with pytest.raises(SdcError) as e:
+            Context.from_workload(sq, options=default_options(**opts))
+        assert e.value.status == -1
+    with pytest.raises(SdcError) as e:
+        Batch([sq, sq], options=default_options(drop_rule=1, sdc_rho=0.05))
+    assert e.value.status == -1 and "batch" in str(e.value)
