@@ -58,12 +58,14 @@ def parse():
                          "w1l/w5, 100 for w0/w3, 200 for w4)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4", "sweet"],
+    ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4", "sweet",
+                                           "sweet_emi"],
                     default="w1",
                     help="w2: cell-by-cell (EMI) bricks; w3: 96-instance batch, batched launches "
                          "vs per-instance launches; w4: gradient by the discrete adjoint vs "
-                         "finite differences; sweet: final error vs drop tolerance for several "
-                         "SDC tolerances on the 2D square (energy-norm stop)")
+                         "finite differences; sweet / sweet_emi: final error vs drop tolerance "
+                         "for several SDC tolerances on the 2D square / the 2D branched "
+                         "cell-by-cell myocytes (energy-norm stop)")
     ap.add_argument("--fd-directions", type=int, default=16)
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
@@ -78,7 +80,7 @@ def parse():
         args.reorder = 1 if args.workload == "w5" else 0
     if args.steps is None:
         args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
-                      "w4": 200, "sweet": 100}[args.workload]
+                      "w4": 200, "sweet": 100, "sweet_emi": 125}[args.workload]
     return args
 
 
@@ -611,12 +613,20 @@ def emi_cpu_baseline(budget_s, gpu_row_iters_per_step, frozen):
 
 
 def run_sweet(args):
-    """Sweet-line study (Sec. 5.2): final error on the 2D square (65x65 nodes,
-    M = 3, dt = 0.1, t = 10) against the drop tolerance TOL_drop = alpha TOL
-    for several SDC tolerances TOL.  The sweeps end by the energy-norm test of
-    Sec. 3.2 with the paper's rho = 0.05 (at most 12); the reference is plain
-    SDC with 12 sweeps.  The paper finds TOL_drop = TOL / 10 close to the
-    largest drop tolerance that leaves the accuracy unchanged."""
+    """Sweet-line study (Sec. 5.2): final error against the drop tolerance
+    TOL_drop = alpha TOL for several SDC tolerances TOL, the sweeps ended by the
+    energy-norm test of Sec. 3.2 with the paper's rho = 0.05 (at most 12); the
+    reference is plain SDC with 12 sweeps.  Per TOL also the non-adaptive run
+    (alpha = 0: same stop, no dropping), whose time over the adaptive one at
+    alpha = 0.1 is the speedup of the adaptivity, and the a priori drop
+    tolerance of Sec. 4.1 (drop_rule 1, same rho).
+
+    sweet: the 2D monodomain square (65x65 nodes, M = 3, dt = 0.1, 100 steps to
+    t = 10).  sweet_emi: the 2D cell-by-cell branched myocytes of
+    emi_branched_2d on 2.5 um pixels (28,809 dofs), gating held at w = 0 as in
+    the paper's EMI runs, M = 3, dt = 0.02 ms, 125 steps to t = 2.5 ms (the time
+    of the paper's EMI sweet-line figure).  The paper finds TOL_drop = TOL / 10
+    close to the largest drop tolerance that leaves the accuracy unchanged."""
     import torch
 
     world, rank, local = dist_setup(args)
@@ -624,52 +634,80 @@ def run_sweet(args):
     dev = torch.device("cuda", local)
     from paper_2311_07206_gb300 import Context, default_options
 
-    wl = W.w0_square()
+    emi = args.workload == "sweet_emi"
+    if emi:
+        from workloads.emi import emi_branched_2d
+        wl = emi_branched_2d(h=2.5)
+        x0, y0 = wl.u0, wl.w0
+    else:
+        wl = W.w0_square()
+        x0, y0 = wl.v0, wl.w0
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream(dev)
 
-    def run(tol, alpha, energy_stop, sweeps, timed=False):
+    def run(tol, alpha, energy_stop, sweeps, drop_rule=0, keep_active=False):
         opts = default_options(alpha=alpha, energy_stop=int(energy_stop), sdc_rho=0.05,
-                               cg_rtol=wl.cg_rtol)
-        ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
-        v = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
-        w = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+                               cg_rtol=wl.cg_rtol, drop_rule=drop_rule,
+                               w_frozen=int(emi), cg_maxit=100000)
+        ctx = (Context.from_emi(wl, options=opts, stream=stream.cuda_stream) if emi else
+               Context.from_workload(wl, options=opts, stream=stream.cuda_stream))
+        v = torch.tensor(x0, dtype=torch.float64, device=dev)
+        w = torch.tensor(y0, dtype=torch.float64, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ads, swp = 0, 0
+        ads, swp, tds, act = 0, 0, [], []
         e0.record(stream)
         for n in range(K):
             st = ctx.step(v, w, n * wl.dt, wl.dt, sweeps, tol)
             ads += sum(st.n_active[:st.sweeps_run])
             swp += st.sweeps_run
+            tds.append(st.tol_drop)
+            if keep_active:
+                act.append(list(st.n_active[:st.sweeps_run]))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ctx.close()
-        return v.cpu().numpy(), e0.elapsed_time(e1), ads, swp
+        return v.cpu().numpy(), e0.elapsed_time(e1), ads, swp, float(np.mean(tds)), act
 
     for _ in range(max(1, Wm)):
         run(1e-4, 0.1, True, 12)
-    ref, _, _, _ = run(0.0, 0.1, False, 12)
-    rows = []
+    ref = run(0.0, 0.1, False, 12)[0]
+    rows, active_profile = [], None
     for tol in (1e-3, 1e-4, 1e-5, 1e-6):
-        for alpha in (0.001, 0.01, 0.1, 1.0, 10.0):
-            v, ms, ads, swp = run(tol, alpha, True, 12)
-            rows.append({"TOL": tol, "TOL_drop": alpha * tol, "alpha": alpha,
+        for alpha, rule in ((0.0, 0), (0.001, 0), (0.01, 0), (0.1, 0), (1.0, 0), (10.0, 0),
+                            (None, 1)):
+            keep = tol == 1e-4 and alpha == 0.1
+            v, ms, ads, swp, td, act = run(tol, alpha if alpha is not None else 0.1, True, 12,
+                                           drop_rule=rule, keep_active=keep)
+            if keep:
+                active_profile = act
+            rows.append({"TOL": tol, "TOL_drop": td, "alpha": alpha,
+                         "drop_rule": "a priori (Sec. 4.1)" if rule else "alpha TOL",
                          "err": float(np.abs(v - ref).max()), "ms_per_step": ms / K,
                          "mean_sweeps": swp / K, "active_dof_sweeps_per_step": ads / K})
+    for r in rows:
+        base = [q for q in rows if q["TOL"] == r["TOL"] and q["alpha"] == 0.0][0]
+        r["speedup_vs_alpha0"] = base["ms_per_step"] / r["ms_per_step"]
     at = [r for r in rows if r["TOL"] == 1e-4 and r["alpha"] == 0.1][0]
-    line = {"metric": "sweet-line study: max error at t = 10 vs TOL_drop (2D square, energy-norm "
-                      "stop, rho = 0.05)",
+    # mean active dofs per sweep index over the steps (the paper's active-dof figure)
+    mean_active = []
+    if active_profile:
+        for k in range(max(len(a) for a in active_profile)):
+            mean_active.append(float(np.mean([a[k] if k < len(a) else 0 for a in active_profile])))
+    what = ("2D cell-by-cell branched myocytes, w = 0" if emi else "2D monodomain square")
+    line = {"metric": "sweet-line study: max error at t = %g ms vs TOL_drop (%s, energy-norm "
+                      "stop, rho = 0.05)" % (K * wl.dt, what),
             "value": 1e3 / at["ms_per_step"], "unit": "steps/s at TOL = 1e-4, TOL_drop = 1e-5",
             "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": at["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "n_dofs": wl.n, "M": wl.M, "dt_ms": wl.dt,
-                       "max_sweeps": 12, "rho": 0.05, "reference": "plain SDC, 12 sweeps"},
+                       "max_sweeps": 12, "rho": 0.05, "reference": "plain SDC, 12 sweeps",
+                       "speedup_alpha_0.1_vs_non_adaptive": at["speedup_vs_alpha0"]},
+            "mean_active_dofs_per_sweep_at_TOL_1e-4_alpha_0.1": mean_active,
             "table": rows}
     if rank == 0:
         print(json.dumps(line))
     return 0
-
 
 
 def run_batch(args):
@@ -848,7 +886,7 @@ SEED_FD = 2311_07206 + 40
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload in ("w2", "w3", "w4", "sweet"):
+    if args.impl == "reference" and args.workload in ("w2", "w3", "w4", "sweet", "sweet_emi"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the reference arm times the oracle on the monodomain workloads only"}))
         return 0
@@ -858,7 +896,7 @@ def main():
         return run_batch(args)
     if args.workload == "w4":
         return run_grad(args)
-    if args.workload == "sweet":
+    if args.workload in ("sweet", "sweet_emi"):
         return run_sweet(args)
     if args.workload == "w2":
         return run_emi(args)

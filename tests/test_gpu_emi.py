@@ -38,7 +38,7 @@ def _ctx(wl, torch, dev, **opts):
                             stream=torch.cuda.current_stream(dev).cuda_stream)
 
 
-def _run(wl, torch, dev, steps, tol, sweeps=None, w_frozen=False, **opts):
+def _run(wl, torch, dev, steps, tol, sweeps=None, w_frozen=False, iters_rel=0.0, **opts):
     sweeps = wl.sweeps if sweeps is None else sweeps
     ctx = _ctx(wl, torch, dev, w_frozen=int(w_frozen), **opts)
     S = oracle.System.from_mesh(wl.mesh)
@@ -58,7 +58,9 @@ def _run(wl, torch, dev, steps, tol, sweeps=None, w_frozen=False, **opts):
             if r["stats"].n_active[k]:
                 assert np.array_equal(ctx.active(k), r["active"][k]), "sweep %d" % k
             for m in range(wl.M):
-                assert abs(st.cg_iters[k][m] - r["stats"].cg_iters[k * 8 + m]) <= 1
+                ref = r["stats"].cg_iters[k * 8 + m]
+                assert abs(st.cg_iters[k][m] - ref) <= max(1, iters_rel * ref)
+        assert st.cg_relres_max <= wl.cg_rtol
         shrank |= st.n_active[sweeps - 1] < wl.n
         # kind-1 (gap junction) pairs carry no gating: left as given
         gap = wl.pair_kind == 1
@@ -170,3 +172,20 @@ def test_emi_bricks_full_size_properties(torch_dev):
     assert outs[0][2] == outs[1][2] and outs[0][2][-1] < wl.n
     assert np.abs(outs[0][0] - outs[2][0]).max() <= 10 * wl.tol
     ctx.close()
+
+
+@pytest.mark.parametrize("variant,cluster", [(0, 20000), (1, 0)])
+def test_emi_parity_2d_branched_cells(torch_dev, variant, cluster):
+    """The 2D cell-by-cell mesh (triangles, edge membranes) of the branched
+    myocytes at 10 um pixels, gating held at w = 0 as in the paper's EMI runs.
+    Its node solves take 300-400 CG iterations; at that length the iteration
+    where the recursively updated residual of a finite-precision CG crosses
+    rtol depends on the rounding of its sums (the oracle sums in index order,
+    the kernels exactly), so counts agree to 10 % here while the states agree
+    to 1e-10 and the active sets exactly."""
+    torch, dev = torch_dev
+    from workloads.emi import emi_tiny
+    wl = emi_tiny("branched_2d")
+    assert wl.mesh.dim == 2
+    assert _run(wl, torch, dev, 3, wl.tol, w_frozen=True, iters_rel=0.1, cg_variant=variant,
+                cg_cluster_rows=cluster)

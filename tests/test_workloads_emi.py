@@ -158,3 +158,115 @@ def test_tiny_workloads_have_both_pair_kinds():
     # kind 0 is oriented cell -> bath
     assert np.all(wl.labels[wl.pair_k[wl.pair_kind == 0]] > 0)
     assert np.all(wl.labels[wl.pair_l[wl.pair_kind == 0]] == 0)
+
+
+def _loops_2d(lab: np.ndarray, h: float, sigma_i: float, sigma_e: float):
+    """The 2D generator's definitions, one pixel, edge and vertex at a time."""
+    nx, ny = lab.shape
+    vx, vy = nx + 1, ny + 1
+
+    def vid(i, j):
+        return i + vx * j
+
+    vlabels = [set() for _ in range(vx * vy)]
+    for j in range(ny):
+        for i in range(nx):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    vlabels[vid(i + di, j + dj)].add(int(lab[i, j]))
+    dof, xyz, dlab = {}, [], []
+    for j in range(vy):
+        for i in range(vx):
+            for c in sorted(vlabels[vid(i, j)]):
+                dof[(vid(i, j), c)] = len(xyz)
+                xyz.append((i * h, j * h))
+                dlab.append(c)
+    elems, esig = [], []
+    for j in range(ny):
+        for i in range(nx):
+            c = int(lab[i, j])
+            a, b = dof[(vid(i, j), c)], dof[(vid(i + 1, j), c)]
+            cc, d = dof[(vid(i + 1, j + 1), c)], dof[(vid(i, j + 1), c)]
+            for tri in ((a, b, cc), (a, cc, d)):
+                elems.append(tri)
+                esig.append((sigma_e if c == 0 else sigma_i) * np.eye(3))
+    acc = {}
+
+    def add_edge(verts, ca, cb):
+        if ca == cb:
+            return
+        if ca == 0 or cb == 0:
+            first, second, kind = max(ca, cb), 0, 0
+        else:
+            first, second, kind = min(ca, cb), max(ca, cb), 1
+        for v in verts:
+            key = (dof[(v, first)], dof[(v, second)], kind)
+            acc[key] = acc.get(key, 0.0) + h / 2
+
+    robin = np.zeros(len(xyz))
+    for j in range(ny):
+        for i in range(nx):
+            c = int(lab[i, j])
+            if i + 1 < nx:
+                add_edge([vid(i + 1, j), vid(i + 1, j + 1)], c, int(lab[i + 1, j]))
+            if j + 1 < ny:
+                add_edge([vid(i, j + 1), vid(i + 1, j + 1)], c, int(lab[i, j + 1]))
+            for on, verts in ((i == 0, [vid(0, j), vid(0, j + 1)]),
+                              (i == nx - 1, [vid(nx, j), vid(nx, j + 1)]),
+                              (j == 0, [vid(i, 0), vid(i + 1, 0)]),
+                              (j == ny - 1, [vid(i, ny), vid(i + 1, ny)])):
+                if on:
+                    for v in verts:
+                        robin[dof[(v, c)]] += h / 2
+    keys = sorted(acc)
+    mesh = Mesh(2, np.array(xyz), np.array(elems, np.int32), elem_sigma=np.array(esig))
+    return (mesh, np.array([k[0] for k in keys], np.int32), np.array([k[1] for k in keys], np.int32),
+            np.array([acc[k] for k in keys]), np.array([k[2] for k in keys], np.int32), robin,
+            np.array(dlab, np.int32))
+
+
+@pytest.mark.parametrize("case", ["cells", "mixed"])
+def test_vectorised_2d_generator_matches_loops(case):
+    from workloads.emi import emi_from_labels_2d
+    if case == "cells":
+        lab = np.zeros((9, 6), np.int32)
+        lab[1:4, 1:3], lab[4:8, 1:3], lab[2:5, 4:5] = 1, 2, 3
+        h = 2.0
+    else:
+        lab, h = np.random.default_rng(3).integers(0, 3, size=(6, 5)).astype(np.int32), 1.25
+    a = emi_from_labels_2d(lab, h, 3.0, 20.0)
+    b = _loops_2d(lab, h, 3.0, 20.0)
+    assert np.array_equal(a[0].xyz, b[0].xyz) and np.array_equal(a[0].elems, b[0].elems)
+    assert np.array_equal(a[0].elem_sigma, b[0].elem_sigma)
+    for x, y in zip(a[1:], b[1:]):
+        assert x.shape == y.shape
+        np.testing.assert_allclose(x, y, rtol=1e-15, atol=0)
+
+
+def test_branched_2d_layout_measures():
+    """Membrane measure = the cells' perimeters less twice the shared (gap
+    junction) edges; Robin measure = the box perimeter; every cell reachable
+    from the first through gap junctions."""
+    from workloads.emi import branched_labels_2d, emi_from_labels_2d
+    h = 2.5
+    lab = branched_labels_2d(h)
+    mesh, pk, pl, pa, kind, robin, dlab = emi_from_labels_2d(lab, h, 3.0, 20.0)
+    per = 0.0
+    for c in range(1, lab.max() + 1):
+        m = lab == c
+        per += h * (np.abs(np.diff(np.pad(m, 1).astype(int), axis=0)).sum()
+                    + np.abs(np.diff(np.pad(m, 1).astype(int), axis=1)).sum())
+    gap = pa[kind == 1].sum()
+    assert pa[kind == 0].sum() + 2 * gap == pytest.approx(per, rel=1e-14)
+    assert robin.sum() == pytest.approx(2 * h * (lab.shape[0] + lab.shape[1]), rel=1e-14)
+    adj = {}
+    for k, l in zip(pk[kind == 1], pl[kind == 1]):
+        adj.setdefault(dlab[k], set()).add(dlab[l])
+        adj.setdefault(dlab[l], set()).add(dlab[k])
+    seen, todo = {1}, [1]
+    while todo:
+        for nb in adj.get(todo.pop(), ()):
+            if nb not in seen:
+                seen.add(nb)
+                todo.append(nb)
+    assert seen == set(range(1, lab.max() + 1))

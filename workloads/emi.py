@@ -212,6 +212,137 @@ def emi_bricks(cells=(8, 4, 4), cell_um=(100.0, 20.0, 20.0), h=2.0, gap_vox=1, m
     return wl
 
 
+def emi_from_labels_2d(lab: np.ndarray, h: float, sigma_i: float, sigma_e: float):
+    """The 2D analogue of emi_from_labels on a labelled pixel grid.
+
+    Numbering: vertices in x-fastest order, at each vertex one dof per label of
+    its pixels in ascending label order.  Elements: pixels in x-fastest order,
+    two right triangles per pixel split along the (i, j)-(i+1, j+1) diagonal.
+    Membranes are the pixel edges between different labels: an edge of length
+    h gives each of its two vertices half its length, accumulated per pair of
+    dofs; outer box edges give their vertices' dofs half their length of Robin
+    measure."""
+    lab = np.asarray(lab, dtype=np.int64)
+    nx, ny = lab.shape
+    vx, vy = nx + 1, ny + 1
+    L = int(lab.max()) + 1
+    I, J = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    order = lambda a: np.ascontiguousarray(a.T).reshape(-1)     # pixels in x-fastest order
+    pi, pj, pl = order(I), order(J), order(lab)
+
+    def vid(i, j):
+        return i + vx * j
+
+    corners = [vid(pi + di, pj + dj) * L + pl for dj in (0, 1) for di in (0, 1)]
+    keys = np.unique(np.concatenate(corners))
+    vert = keys // L
+    dlab = (keys % L).astype(np.int32)
+    xyz = np.stack([vert % vx, vert // vx], axis=1).astype(np.float64) * h
+
+    def dof(v, c):
+        return np.searchsorted(keys, v * L + c).astype(np.int32)
+
+    a = dof(vid(pi, pj), pl)
+    b = dof(vid(pi + 1, pj), pl)
+    c = dof(vid(pi + 1, pj + 1), pl)
+    d = dof(vid(pi, pj + 1), pl)
+    elems = np.stack([np.stack([a, b, c], axis=1), np.stack([a, c, d], axis=1)],
+                     axis=1).reshape(-1, 3).astype(np.int32)
+    sig = np.where(np.repeat(pl, 2) == 0, sigma_e, sigma_i)
+    esig = sig[:, None, None] * np.eye(3)[None]
+    half = h / 2.0
+    f_first, f_second, f_kind = [], [], []
+    # the shared edge of pixels (i, j) and (i, j) + e_ax, as two vertex offsets
+    edge_verts = {0: ((1, 0), (1, 1)), 1: ((0, 1), (1, 1))}
+    for ax in range(2):
+        nb = [0, 0]
+        nb[ax] = 1
+        p = lab[:nx - nb[0], :ny - nb[1]]
+        q = lab[nb[0]:, nb[1]:]
+        ii, jj = np.nonzero(p != q)
+        ca, cb = p[ii, jj], q[ii, jj]
+        ecs = (ca == 0) | (cb == 0)
+        first = np.where(ecs, np.maximum(ca, cb), np.minimum(ca, cb))
+        second = np.where(ecs, 0, np.maximum(ca, cb))
+        for dv in edge_verts[ax]:
+            v = vid(ii + dv[0], jj + dv[1])
+            f_first.append(dof(v, first))
+            f_second.append(dof(v, second))
+            f_kind.append(np.where(ecs, 0, 1))
+    f_first = np.concatenate(f_first).astype(np.int64)
+    f_second = np.concatenate(f_second).astype(np.int64)
+    f_kind = np.concatenate(f_kind).astype(np.int64)
+    n = keys.size
+    pkey, counts = np.unique((f_first * n + f_second) * 2 + f_kind, return_counts=True)
+    pk = (pkey // 2 // n).astype(np.int32)
+    plr = (pkey // 2 % n).astype(np.int32)
+    pkind = (pkey % 2).astype(np.int32)
+    parea = counts * half
+    b_dofs = []
+    for ax in range(2):
+        for side in (0, 1):
+            if ax == 0:
+                i0 = 0 if side == 0 else nx - 1
+                cl, jj = lab[i0, :], np.arange(ny)
+                iv = np.full(ny, 0 if side == 0 else nx)
+                b_dofs += [dof(vid(iv, jj), cl), dof(vid(iv, jj + 1), cl)]
+            else:
+                j0 = 0 if side == 0 else ny - 1
+                cl, ii = lab[:, j0], np.arange(nx)
+                jv = np.full(nx, 0 if side == 0 else ny)
+                b_dofs += [dof(vid(ii, jv), cl), dof(vid(ii + 1, jv), cl)]
+    robin = np.bincount(np.concatenate(b_dofs), minlength=n) * half
+    mesh = Mesh(2, xyz, elems, elem_sigma=esig, meta={"h": h, "pixels": lab.shape})
+    return mesh, pk, plr, parea, pkind, robin, dlab
+
+
+def branched_labels_2d(h=1.25):
+    """A branching arrangement of myocytes in a 700 x 240 um bath: a trunk of two
+    cells splits through a connector cell into two rows of two cells, each of
+    which splits again into two rows (17 cells, all 15 um thick); cells touch end
+    to end (gap-junction edges).  Lengths in um on an h-um pixel grid."""
+    px = lambda um: int(round(um / h))
+    lab = np.zeros((px(700.0), px(240.0)), dtype=np.int32)
+    cells = []
+    t = 15.0
+
+    def row(x0, x1, yc, parts=2):
+        xs = np.linspace(x0, x1, parts + 1)
+        for a, b in zip(xs[:-1], xs[1:]):
+            cells.append((a, b, yc - t / 2, yc + t / 2))
+
+    row(10.0, 230.0, 120.0)                          # trunk
+    cells.append((230.0, 245.0, 52.5, 187.5))        # connector to level 1
+    row(245.0, 465.0, 60.0)
+    row(245.0, 465.0, 180.0)
+    cells.append((465.0, 480.0, 22.5, 97.5))         # connectors to level 2
+    cells.append((465.0, 480.0, 142.5, 217.5))
+    for yc in (30.0, 90.0, 150.0, 210.0):
+        row(480.0, 690.0, yc)
+    for cid, (x0, x1, y0, y1) in enumerate(cells, start=1):
+        lab[px(x0):px(x1), px(y0):px(y1)] = cid
+    return lab
+
+
+def emi_branched_2d(h=1.25, dt=0.02, sweeps=12, tol=1e-4, steps=125, name=None) -> EmiWorkload:
+    """2D cell-by-cell workload in the shape of the paper's 2D EMI example
+    (Sec. 5.1: branched myocytes in 700 x 240 um, leftmost cell excited, gating
+    fixed at w = 0): branched_labels_2d on h-um pixels, same units and
+    coefficients as emi_bricks (C_m = 1, sigma_i = 3e4, sigma_e = 2e5 um/ms,
+    gap junctions 5 % of 1/(R_g C_m) per length, Robin 1e-4 sigma_e / box)."""
+    lab = branched_labels_2d(h)
+    sigma_i, sigma_e = 3.0e4, 2.0e5
+    mesh, pk, pl, parea, pkind, robin_area, dlab = emi_from_labels_2d(lab, h, sigma_i, sigma_e)
+    n = mesh.n_nodes
+    u0 = np.where(dlab == 1, 1.0, 0.0)
+    box = max(lab.shape) * h
+    return EmiWorkload(name or "emi_branched_2d_%d_dofs" % n, mesh, pk, pl, parea, pkind,
+                       robin_area, dlab, dict(AP_BENCH), M=3, dt=dt, sweeps=sweeps, tol=tol,
+                       steps=steps, u0=u0, w0=np.zeros(pk.size), robin_eps=1e-4 * sigma_e / box,
+                       Cm=1.0, g_gap=0.05 * 222.0, sigma_i=sigma_i, sigma_e=sigma_e,
+                       meta={"seed": SEED_BASE + 2, "w_frozen": True, "labels": lab.shape})
+
+
 def emi_tiny(kind="pair"):
     """Small EMI problems for exact checks."""
     if kind == "two_cells":
@@ -220,4 +351,6 @@ def emi_tiny(kind="pair"):
     if kind == "grid":
         return emi_bricks(cells=(2, 2, 1), cell_um=(10.0, 4.0, 4.0), h=2.0, gap_vox=1, margin=2,
                           name="emi_2x2_cells", dt=0.02, sweeps=4, tol=1e-4, steps=3)
+    if kind == "branched_2d":
+        return emi_branched_2d(h=10.0, sweeps=4, tol=1e-4, steps=3, name="emi_branched_2d_tiny")
     raise ValueError(kind)
