@@ -59,13 +59,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", choices=["w1", "w1l", "w0", "w5", "w2", "w3", "w4", "sweet",
-                                           "sweet_emi"],
+                                           "sweet_emi", "order"],
                     default="w1",
                     help="w2: cell-by-cell (EMI) bricks; w3: 96-instance batch, batched launches "
                          "vs per-instance launches; w4: gradient by the discrete adjoint vs "
                          "finite differences; sweet / sweet_emi: final error vs drop tolerance "
                          "for several SDC tolerances on the 2D square / the 2D branched "
-                         "cell-by-cell myocytes (energy-norm stop)")
+                         "cell-by-cell myocytes (energy-norm stop); order: error vs device "
+                         "time for M = 2..6 and dt = 0.025..0.2 ms on the slab")
     ap.add_argument("--fd-directions", type=int, default=16)
     ap.add_argument("--ref-sweeps", type=int, default=12)
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work")
@@ -80,7 +81,7 @@ def parse():
         args.reorder = 1 if args.workload == "w5" else 0
     if args.steps is None:
         args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
-                      "w4": 200, "sweet": 100, "sweet_emi": 125}[args.workload]
+                      "w4": 200, "sweet": 100, "sweet_emi": 125, "order": 80}[args.workload]
     return args
 
 
@@ -710,6 +711,79 @@ def run_sweet(args):
     return 0
 
 
+def run_order(args):
+    """Collocation order against step size (the speedup lever of Sec. 6: higher
+    M with larger dt trades sweeps against order).  The slab of the headline
+    workload (201x71x31 nodes, 1 ms corner stimulus) is integrated to t = 4 ms
+    with M = 2, 3, 4, 6 nodes and dt = 0.025 .. 0.2 ms, adaptive (alpha = 0.1)
+    with the energy-norm stop (rho = 0.05, at most 12 sweeps) at TOL = 1e-5;
+    the error is max |v(4) - v_ref(4)| against plain SDC with M = 4, dt =
+    0.0125 ms and 12 sweeps (order 7 once converged).  Each row gives the
+    device time per simulated ms; rows that no other row beats in both error and
+    time are marked pareto."""
+    import dataclasses
+
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2311_07206_gb300 import Context, default_options
+
+    base = W.w1_slab()
+    T, tol = 4.0, 1e-5
+    stream = torch.cuda.current_stream(dev)
+
+    def run(M, dt, tol, sweeps, energy_stop):
+        wl = dataclasses.replace(base, M=M, dt=dt)
+        opts = default_options(alpha=0.1, energy_stop=int(energy_stop), sdc_rho=0.05,
+                               cg_rtol=1e-12)
+        ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
+        v = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
+        w = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+        steps = int(round(T / dt))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        swp, ads = 0, 0
+        e0.record(stream)
+        for n in range(steps):
+            st = ctx.step(v, w, n * dt, dt, sweeps, tol)
+            swp += st.sweeps_run
+            ads += sum(st.n_active[:st.sweeps_run])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.close()
+        return v.cpu().numpy(), e0.elapsed_time(e1), swp / steps, ads / steps
+
+    for _ in range(max(1, args.warmup)):
+        run(3, 0.2, tol, 12, True)
+    ref = run(4, 0.0125, 0.0, 12, False)[0]
+    rows = []
+    for M in (2, 3, 4, 6):
+        for dt in (0.025, 0.05, 0.1, 0.2):
+            v, ms, sw, ads = run(M, dt, tol, 12, True)
+            rows.append({"M": M, "dt_ms": dt, "err": float(np.abs(v - ref).max()),
+                         "ms_per_simulated_ms": ms / T, "mean_sweeps": sw,
+                         "active_dof_sweeps_per_step": ads})
+    for r in rows:
+        r["pareto"] = not any(q["err"] <= r["err"] and q["ms_per_simulated_ms"] <
+                              r["ms_per_simulated_ms"] for q in rows if q is not r)
+    head = [r for r in rows if r["M"] == 4 and r["dt_ms"] == 0.05][0]
+    line = {"metric": "collocation order vs step size: max error at t = 4 ms vs device time "
+                      "(slab 201x71x31, adaptive, energy-norm stop)",
+            "value": 1e3 / head["ms_per_simulated_ms"],
+            "unit": "simulated ms per s at M = 4, dt = 0.05 ms",
+            "n_gpus": world, "steps": int(round(T / 0.05)), "warmup": args.warmup,
+            "ms_per_step": head["ms_per_simulated_ms"] * 0.05, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": base.name, "n_dofs": base.n, "TOL": tol, "alpha": 0.1,
+                       "rho": 0.05, "max_sweeps": 12, "t_end_ms": T, "cg_rtol": 1e-12,
+                       "reference": "plain SDC, M = 4, dt = 0.0125 ms, 12 sweeps"},
+            "table": rows}
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def run_batch(args):
     """96 2D instances (sides log-uniform in [64, 512], D ~ U[0.5, 2]): one
     batched step of all instances vs the same steps as per-instance launches."""
@@ -886,7 +960,8 @@ SEED_FD = 2311_07206 + 40
 
 def main():
     args = parse()
-    if args.impl == "reference" and args.workload in ("w2", "w3", "w4", "sweet", "sweet_emi"):
+    if args.impl == "reference" and args.workload in ("w2", "w3", "w4", "sweet", "sweet_emi",
+                                                      "order"):
         print(json.dumps({"impl": "reference", "unavailable":
                           "the reference arm times the oracle on the monodomain workloads only"}))
         return 0
@@ -898,6 +973,8 @@ def main():
         return run_grad(args)
     if args.workload in ("sweet", "sweet_emi"):
         return run_sweet(args)
+    if args.workload == "order":
+        return run_order(args)
     if args.workload == "w2":
         return run_emi(args)
     return run_gb300(args)
