@@ -148,6 +148,10 @@ typedef struct {
                               max(0, -min dI/dv) / C_m over the first sweep's linearisation
                               (zero with reaction_implicit = 0); computed on the device once
                               per step, reported in sdc_stats.tol_drop.  Not in batches      */
+    int cg_scaled;         /* 1: pipelined shared-memory solves run in the symmetrically scaled
+                              form, CG on diag^-1/2 A diag^-1/2 (the same iterates as
+                              Jacobi-PCG with fewer FP64 operations per row and six vectors on
+                              chip); 0: the Jacobi form; default 1                          */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */

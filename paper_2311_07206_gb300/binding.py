@@ -44,7 +44,7 @@ class sdc_options(C.Structure):
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
                 ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
                 ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int),
-                ("reorder", C.c_int), ("drop_rule", C.c_int)]
+                ("reorder", C.c_int), ("drop_rule", C.c_int), ("cg_scaled", C.c_int)]
 
 
 class sdc_stats(C.Structure):

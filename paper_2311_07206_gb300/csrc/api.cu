@@ -110,6 +110,7 @@ int alloc_buffers(sdc_ctx* c) {
     P.cluster_rows = c->opt.cg_cluster_rows;
     P.inject_fault = c->opt.inject_fault;
     P.pipelined = c->opt.cg_pipelined != 0;
+    P.scaled = c->opt.cg_scaled;
     P.budget = c->opt.spin_budget;
     if (P.max_blocks_general < 1 || P.sms < 1) return SDC_E_CUDA;
     B.max_blocks = std::max(P.max_blocks_general, P.sms);
@@ -148,6 +149,10 @@ int alloc_buffers(sdc_ctx* c) {
                             cudaMemcpyHostToDevice, c->stream);
     }
     if (ok) ok = dalloc(&B.part, 12 * (size_t)B.max_blocks);
+    if (ok && c->opt.cg_scaled) {
+        B.sval_width = c->K.K.width;
+        ok = dalloc(&B.sv, ld) && dalloc(&B.sval, (size_t)std::max(B.sval_width, 1) * ld);
+    }
     if (!ok) return SDC_E_NOMEM;
     // pinned: [0] count, [1] err, then kMaxM node energies at byte 16
     if (cudaMallocHost(&c->h_pin, 16 + kMaxM * sizeof(double)) != cudaSuccess) return SDC_E_NOMEM;
@@ -160,7 +165,7 @@ void free_adjoint(AdjointBuffers& W);
 void free_all(sdc_ctx* c) {
     StepBuffers& B = c->B;
     double* dp[] = {B.V, B.W, B.R, B.J, B.D, B.mc, B.kdc, B.r, B.u, B.p, B.s, B.w, B.idA, B.part,
-                    B.z, B.nv, B.m,
+                    B.z, B.nv, B.m, B.sv, B.sval,
                     B.blockmarg, B.vtmp, B.wtmp, c->K.kdiag, c->K.mass, c->stim};
     for (double* p : dp) cudaFree(p);
     int* ip[] = {B.flag, B.map, B.blockcnt, B.blockoff, B.inst_off, B.bounds, B.segtab,
@@ -267,6 +272,7 @@ void sdc_default_options(sdc_options* o) {
     o->sdc_qhat = 0;
     o->reorder = 0;
     o->drop_rule = 0;
+    o->cg_scaled = 1;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -387,7 +393,7 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
         o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
         o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1 ||
-        o.drop_rule < 0 || o.drop_rule > 1)
+        o.drop_rule < 0 || o.drop_rule > 1 || o.cg_scaled < 0 || o.cg_scaled > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (o.drop_rule == 1 && !(o.sdc_rho > 0.0))
         return fail(nullptr, SDC_E_INVALID, "drop_rule = 1 needs a given sdc_rho in (0, 1)");
@@ -494,6 +500,13 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
     if (emi) {
         c->is_emi = true;
         rc = emi_setup(*emi, c->N, M, c->K.K.width, c->B.ld, c->stream, c->emi, why);
+        if (rc == SDC_OK && c->B.sval && c->emi.A.width > c->B.sval_width) {
+            // the node operator carries pair slots besides K's: widen the scaled values
+            cudaFree(c->B.sval);
+            c->B.sval = nullptr;
+            c->B.sval_width = c->emi.A.width;
+            if (!dalloc(&c->B.sval, (size_t)c->B.sval_width * c->B.ld)) rc = SDC_E_NOMEM;
+        }
         if (rc != SDC_OK) {
             free_all(c);
             delete c;

@@ -105,6 +105,9 @@ struct StepBuffers {
     double* m = nullptr;
     double* idA = nullptr;
     double* part = nullptr;   // 12 * max_blocks: one 48-byte exact-sum record per block, two buffers
+    double* sv = nullptr;     // [ld] diag^-1/2 of the scaled solve
+    double* sval = nullptr;   // [sval_width][ld] scaled off-diagonal values of the scaled solve
+    int sval_width = 0;
     int max_blocks = 0;
     int* flag = nullptr;      // [ld]
     int* map = nullptr;       // [ld] old compact row -> new compact row or -1
@@ -136,6 +139,8 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const double* W, const double* v0, double dt, const Ionic& ion,
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
 // Launch configuration of the restricted PCG solves.
+constexpr int kSmemVectorsS = 6;    // the same for the symmetrically scaled variant
+constexpr int kSmemRowsS = 4800;    // rows per block of the symmetrically scaled variant
 constexpr int kSmemVectors = 8;     // per-row doubles in shared memory, shared-memory variant
 constexpr int kSmemRows = 3584;     // rows per block of the shared-memory variant
 constexpr int kClusterVectors = 10; // per-row doubles in shared memory, cluster variant
@@ -160,6 +165,7 @@ struct PcgConfig {
     int batch_rows_per_block = 1024;
     int inject_fault = 0;
     int pipelined = 1;              // 1: pipelined CG; 0: classical arrangement
+    int scaled = 1;                 // pipelined shared-memory solves in the scaled form
     long long budget = 0;
 };
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,

@@ -169,6 +169,10 @@ struct CgParams {
     const double* Jall;
     int inject_fault;    // testing hook: the last block skips the first barrier
     int L;               // rows per block (shared-memory variants)
+    // symmetrically scaled form (k_pcg_scaled): s = diag^-1/2 per row and the
+    // scaled off-diagonal values c s_i a_ij s_j, rebuilt per solve (null: not used)
+    double* sv;
+    double* sval;
 };
 
 // LU-trick coupling of one solved row into the right-hand sides of other nodes.
@@ -420,6 +424,148 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
     }
 }
 
+// The symmetrically scaled form of pcg_group (see k_pcg_scaled): CG on
+// I + c S K_off S with S = diag^-1/2, vectors in global memory, any size.
+__device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S, int nblk,
+                                                 int bidx) {
+    const int B = blockDim.x, t = threadIdx.x;
+    const int n = P.n;
+    const int Lg = (n + nblk - 1) / nblk;
+    const int c0 = bidx * Lg;
+    const int c1 = min(n, c0 + Lg);
+    const bool lead = (bidx == 0 && t == 0);
+    const int sp0 = B >= 256 ? 64 : 0;
+    const int ld = P.ld;
+    const double c = P.c;
+    double* const mbuf[2] = {P.m, P.m + ld};
+    double* __restrict__ sg = P.sv;
+    double* __restrict__ sval = P.sval;
+    XsRecord* const part = reinterpret_cast<XsRecord*>(P.part);
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int i = c0 + t; i < c1; i += B) {
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        double si = 0.0;
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        else si = rsqrt(d);
+        sg[i] = si;
+        const double r = si * P.b[i];
+        P.r[i] = r;
+        P.u[i] = r;
+        P.p[i] = 0.0;
+        P.s[i] = 0.0;
+        P.z[i] = 0.0;
+        P.x[i] = 0.0;
+    }
+    if (P.inject_fault && bidx == nblk - 1) {
+        if (nblk == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+    double ga = 0.0, de = 0.0;
+    for (int i = c0 + t; i < c1; i += B) {
+        const int len = P.alen[i];
+        const double csi = c * __ldcg(sg + i);
+        const double ri = __ldcg(P.r + i);
+        double acc = ri;
+        for (int k = 0; k < len; ++k) {
+            const size_t q = (size_t)k * ld + i;
+            const int j = P.acol[q];
+            const double a = csi * P.aval[q] * __ldcg(sg + j);
+            sval[q] = a;
+            acc += a * __ldcg(P.u + j);
+        }
+        P.w[i] = acc;
+        ga += ri * ri;
+        de += acc * ri;
+        mbuf[0][i] = acc;
+    }
+    int it = 0, nsum = 0;
+    while (true) {
+        if (!cg_publish_arrive(ga, de, S, part + buf * nblk, P.bar, nblk, bidx, epoch,
+                               P.budget, P.err))
+            return;
+        const double* mc = mbuf[nsum & 1];
+        auto totals = [&]() {
+            double g, d;
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * nblk + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        };
+        if (sp0 > 0 && t < 64) totals();
+        if (t >= sp0) {
+            for (int i = c0 + t - sp0; i < c1; i += B - sp0) {
+                const int len = P.alen[i];
+                double acc = P.w[i];
+                for (int k = 0; k < len; ++k) {
+                    const size_t q = (size_t)k * ld + i;
+                    acc += __ldcg(sval + q) * __ldcg(mc + P.acol[q]);
+                }
+                P.nv[i] = acc;
+            }
+        }
+        if (sp0 == 0 && t < 64) totals();
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        double* mn = mbuf[nsum & 1];
+        ga = de = 0.0;
+        for (int i = c0 + t; i < c1; i += B) {
+            const double wi = P.w[i], ri = P.r[i];
+            const double zi = P.nv[i] + beta * P.z[i];
+            const double si = wi + beta * P.s[i];
+            const double pi = ri + beta * P.p[i];
+            P.z[i] = zi;
+            P.s[i] = si;
+            P.p[i] = pi;
+            P.x[i] += alpha * pi;
+            const double r2 = ri - alpha * si;
+            const double w2 = wi - alpha * zi;
+            P.r[i] = r2;
+            P.w[i] = w2;
+            ga += r2 * r2;
+            de += w2 * r2;
+            mn[i] = w2;
+        }
+    }
+    if (S.state == 2) {
+        if (lead) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (lead) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
+    }
+    // x = S x~ on this block's rows; the epilogue gathers neighbours' x after a barrier
+    for (int i = c0 + t; i < c1; i += B) P.x[i] = __ldcg(sg + i) * __ldcg(P.x + i);
+    if (P.epi_lo < P.epi_hi) {
+        if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+        for (int i = c0 + t; i < c1; i += B) {
+            const int len = P.alen[i];
+            const double xi = __ldcg(P.x + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgs(CgParams P) {
+    __shared__ CgShared S;
+    pcg_group_scaled(P, S, (int)gridDim.x, (int)blockIdx.x);
+}
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcg(CgParams P) {
     __shared__ CgShared S;
@@ -617,6 +763,174 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
 #undef SZ
 #undef SN
 #undef SI
+
+// Symmetrically scaled form of the pipelined shared-memory solve.  Jacobi-PCG
+// on A = diag(d) + c K_off is CG on S A S = I + c S K_off S with S = diag(d)^-1/2,
+// x = S x~, b~ = S b: the same iterates, the same stopping quantity
+// (r~.r~ = r.D^-1 r) and the same energy (x~' S A S x~ = x' A x).  Per
+// row-iteration it saves the two preconditioner products (u = D^-1 r, m = D^-1 w)
+// and the scaling of the product by c, and keeps six vectors on chip instead of
+// eight (4800 rows per block).  The scaled off-diagonals c s_i a_ij s_j are
+// written once per solve to P.sval (each block its own rows, after a grid barrier
+// that publishes s).  Per row-iteration: len FMAs of the product (started from
+// w_i, the unit diagonal), six recurrence FMAs, two dot FMAs.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    const int G = gridDim.x, B = blockDim.x, t = threadIdx.x;
+    const int L = P.L, ld = P.ld;
+    const int r0 = blockIdx.x * L;
+    const int nl = max(0, min(P.n - r0, L));
+    const int sp0 = B >= 256 ? 64 : 0;
+#define SR(l) sm[(l)]
+#define SW(l) sm[L + (l)]
+#define SP(l) sm[2 * L + (l)]
+#define SS(l) sm[3 * L + (l)]
+#define SZ(l) sm[4 * L + (l)]
+#define SN(l) sm[5 * L + (l)]
+    double* __restrict__ ug = P.u;
+    double* __restrict__ xg = P.x;
+    double* __restrict__ sg = P.sv;
+    double* __restrict__ sval = P.sval;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        double si = 0.0;
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        else si = rsqrt(d);
+        sg[i] = si;
+        const double r = si * P.b[i];
+        SR(l) = r;
+        ug[i] = r;
+        SP(l) = 0.0;
+        SS(l) = 0.0;
+        SZ(l) = 0.0;
+        xg[i] = 0.0;
+    }
+    if (P.inject_fault && blockIdx.x == G - 1) {
+        if (G == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+    // scaled rows of this block, and w = (I + c S K_off S) r~
+    double ga = 0.0, de = 0.0;
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const int len = __ldg(alen + i);
+        const double csi = c * __ldcg(sg + i);
+        const double ri = SR(l);
+        double acc = ri;
+        for (int k = 0; k < len; ++k) {
+            const size_t q = (size_t)k * ld + i;
+            const int j = __ldg(acol + q);
+            const double a = csi * __ldg(aval + q) * __ldcg(sg + j);
+            sval[q] = a;
+            acc += a * __ldcg(ug + j);
+        }
+        SW(l) = acc;
+        ga += ri * ri;
+        de += acc * ri;
+        P.m[i] = acc;
+    }
+    int it = 0, nsum = 0;
+    while (true) {
+        if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, (int)blockIdx.x, epoch,
+                               P.budget, P.err))
+            return;
+        const double* mc = P.m + (nsum & 1) * (size_t)ld;
+        auto totals = [&]() {
+            double g, d;
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        };
+        if (sp0 > 0 && t < 64) totals();
+        if (t >= sp0) {
+            for (int l = t - sp0; l < nl; l += B - sp0) {
+                const int i = r0 + l;
+                const int len = __ldg(alen + i);
+                double acc = SW(l);
+                for (int k = 0; k < len; ++k) {
+                    const size_t q = (size_t)k * ld + i;
+                    acc += __ldcg(sval + q) * __ldcg(mc + __ldg(acol + q));
+                }
+                SN(l) = acc;
+            }
+        }
+        if (sp0 == 0 && t < 64) totals();
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        double* mn = P.m + (nsum & 1) * (size_t)ld;
+        ga = de = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const double wi = SW(l), ri = SR(l);
+            const double zi = SN(l) + beta * SZ(l);
+            const double s_i = wi + beta * SS(l);
+            const double pi = ri + beta * SP(l);
+            SZ(l) = zi;
+            SS(l) = s_i;
+            SP(l) = pi;
+            xg[i] += alpha * pi;
+            const double r2 = ri - alpha * s_i;
+            const double w2 = wi - alpha * zi;
+            SR(l) = r2;
+            SW(l) = w2;
+            ga += r2 * r2;
+            de += w2 * r2;
+            mn[i] = w2;
+        }
+    }
+    if (S.state == 2) {
+        if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
+    }
+    // x = S x~ on this block's rows; the epilogue gathers neighbours' x after a barrier
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        xg[i] = __ldcg(sg + i) * __ldcg(xg + i);
+    }
+    if (P.epi_lo < P.epi_hi) {
+        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            const double xi = __ldcg(xg + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+#undef SR
+#undef SW
+#undef SP
+#undef SS
+#undef SZ
+#undef SN
 
 // Thread-block-cluster variant for small active sets (n <= C * L rows, one
 // cluster of C CTAs).  The same iteration as k_pcg_smem; m of other CTAs is
@@ -1266,6 +1580,12 @@ PcgKernel pcg_general_kernel(int block) {
     return block > 512 ? k_pcg<1024> : block > 256 ? k_pcg<512> : k_pcg<256>;
 }
 PcgKernel pcg_smem_kernel(int block) { return block > 512 ? k_pcg_smem<1024> : k_pcg_smem<512>; }
+PcgKernel pcgs_general_kernel(int block) {
+    return block > 512 ? k_pcgs<1024> : block > 256 ? k_pcgs<512> : k_pcgs<256>;
+}
+PcgKernel pcg_scaled_kernel(int block) {
+    return block > 512 ? k_pcg_scaled<1024> : k_pcg_scaled<512>;
+}
 PcgKernel pcg_cluster_kernel(int block) {
     return block > 512 ? k_pcg_cluster<1024> : k_pcg_cluster<512>;
 }
@@ -1289,6 +1609,9 @@ void pcg_smem_attrs() {
     for (PcgKernel k : {k_pcgc_smem<512>, k_pcgc_smem<1024>})
         cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemVectorsC * kSmemRowsC * sizeof(double)));
+    for (PcgKernel k : {k_pcg_scaled<512>, k_pcg_scaled<1024>})
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemVectorsS * kSmemRowsS * sizeof(double)));
     for (PcgKernel k : {k_pcg_cluster<512>, k_pcg_cluster<1024>}) {
         cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kClusterVectors * kClusterRows * sizeof(double)));
@@ -1302,7 +1625,9 @@ int pcg_max_blocks(int block) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_general_kernel(block), block, 0);
-    return sms * per;
+    int per_s = 0;   // the scaled form shares the grid limit: take the smaller occupancy
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_s, pcgs_general_kernel(block), block, 0);
+    return sms * std::min(per, per_s);
 }
 
 int pcg_cluster_size(int block) {
@@ -1350,9 +1675,16 @@ void set_cg_vectors(CgParams& P, StepBuffers& B) {
     P.part = B.part;
 }
 
+// buffers of the scaled form, when the context has them and they hold A's width
+void set_scaled_buffers(CgParams& P, const Ell& A, StepBuffers& B) {
+    const bool fits = B.sv && B.sval && A.width <= B.sval_width && A.ld == B.ld;
+    P.sv = fits ? B.sv : nullptr;
+    P.sval = fits ? B.sval : nullptr;
+}
+
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,
                int sweep, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
-    CgParams P;
+    CgParams P{};
     P.n = n;
     P.ld = B.ld;
     P.aval = A.val;
@@ -1365,6 +1697,7 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
     set_cg_vectors(P, B);
+    set_scaled_buffers(P, A, B);
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -1389,7 +1722,7 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
 
 int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,
                     int maxit, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
-    CgParams P;
+    CgParams P{};
     P.n = n;
     P.ld = B.ld;
     P.aval = A.val;
@@ -1402,6 +1735,7 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
     P.b = role.b;
     P.x = role.x;
     set_cg_vectors(P, B);
+    set_scaled_buffers(P, A, B);
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -1478,6 +1812,24 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         cudaError_t e = cudaLaunchKernelEx(&lc, pcg_cluster_kernel(cfg.smem_block), P);
         return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
     }
+    // symmetrically scaled shared-memory form: one block per SM at most.  Up to the Jacobi
+    // form's capacity only: above it (the 686k-row tissue mesh) 4,500 on-chip rows per block
+    // leave too little L1 for the irregular gathers and the global-vector kernel is faster
+    // (16.1 against 18.9 ms of PCG per step)
+    if (cfg.variant != 1 && cfg.scaled && P.sv && P.sval && n <= cfg.sms * kSmemRows) {
+        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+        int grid = std::max(nblk(n, kSmemRowsS), nblk(n, rpb));
+        grid = std::min(grid, cfg.sms);
+        if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
+        grid = std::max(std::max(grid, nblk(n, kSmemRowsS)), 1);
+        P.L = nblk(n, grid);
+        const size_t smem = (size_t)kSmemVectorsS * P.L * sizeof(double);
+        const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
+        pcg_smem_attrs();
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_scaled_kernel(blk),
+                                                    dim3(grid), dim3(blk), args, smem, s);
+        return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
+    }
     // shared-memory variant: one block per SM at most, each owning <= kSmemRows rows
     const bool smem_ok = cfg.variant != 1 && n <= cfg.sms * kSmemRows;
     if (smem_ok && cfg.variant != 1) {
@@ -1499,8 +1851,9 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
     }
     int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));
     if (grid < 1) grid = 1;
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcg_general_kernel(cfg.block), dim3(grid),
-                                                dim3(cfg.block),
+    const PcgKernel kg = cfg.scaled && P.sv && P.sval ? pcgs_general_kernel(cfg.block)
+                                                      : pcg_general_kernel(cfg.block);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)kg, dim3(grid), dim3(cfg.block),
                                                 args, 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
@@ -1538,7 +1891,7 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
         for (int g = 0; g < nseg; ++g)
             if (want[g] > 0) want[g] = std::max(1, (int)(want[g] * f));
     }
-    CgParams P;
+    CgParams P{};
     P.n = n;
     P.ld = B.ld;
     P.aval = A.val;
@@ -1605,7 +1958,7 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
                           const double* J, double c, const double* b, double* x, double rtol,
                           int maxit, long long budget, int block, const PcgScratch& w,
                           cudaStream_t s) {
-    CgParams P;
+    CgParams P{};
     P.n = n;
     P.ld = A.ld;
     P.aval = A.val;

@@ -45,7 +45,7 @@ def test_default_options(lib):
     o = default_options()
     assert o.alpha == 0.1 and o.cg_rtol == 1e-10 and o.reaction_implicit == 1
     assert o.w_frozen == 0 and o.inject_fault == 0 and o.cg_block_size == 1024
-    assert o.cg_pipelined == -1
+    assert o.cg_pipelined == -1 and o.cg_scaled == 1 and o.drop_rule == 0
 
 
 @pytest.mark.parametrize("M", range(1, 9))

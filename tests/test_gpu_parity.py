@@ -112,15 +112,18 @@ def test_assembly_matches_oracle(torch_dev, case):
 
 
 # ------------------------------------------------------------------ step parity
-@pytest.mark.parametrize("variant,cluster,pipe", [(1, 0, 1), (2, 0, 1), (0, 1 << 30, 1),
-                                                   (1, 0, 0), (2, 0, 0)])
+@pytest.mark.parametrize("variant,cluster,pipe,scaled", [(1, 0, 1, 1), (2, 0, 1, 1),
+                                                          (2, 0, 1, 0), (0, 1 << 30, 1, 1),
+                                                          (1, 0, 0, 1), (2, 0, 0, 1)])
 @pytest.mark.parametrize("tol", [0.0, 1e-4])
-def test_step_parity_2d_square(torch_dev, tol, variant, cluster, pipe):
+def test_step_parity_2d_square(torch_dev, tol, variant, cluster, pipe, scaled):
     """Pipelined (pipe = 1) and classical (pipe = 0) arrangements of the CG in
-    every variant it has."""
+    every variant it has; the pipelined shared-memory solve in the
+    symmetrically scaled (scaled = 1) and the Jacobi form."""
     torch, dev = torch_dev
     wl = W.w0_square()
-    ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_cluster_rows=cluster, cg_pipelined=pipe)
+    ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_cluster_rows=cluster, cg_pipelined=pipe,
+               cg_scaled=scaled)
     S = oracle.System.from_mesh(wl.mesh, wl.sigma)
     v, w = wl.v0.copy(), wl.w0.copy()
     for n in range(12):
@@ -131,18 +134,21 @@ def test_step_parity_2d_square(torch_dev, tol, variant, cluster, pipe):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant,rows,cluster,pipe", [(1, 0, 0, 1), (2, 0, 0, 1), (2, 64, 0, 1),
-                                                        (2, 4096, 0, 1), (2, 0, 1 << 30, 1),
-                                                        (1, 0, 0, 0), (2, 64, 0, 0)])
-def test_step_parity_3d_slab_with_stimulus(torch_dev, variant, rows, cluster, pipe):
+@pytest.mark.parametrize("variant,rows,cluster,pipe,scaled",
+                         [(1, 0, 0, 1, 1), (1, 0, 0, 1, 0), (2, 0, 0, 1, 1), (2, 64, 0, 1, 1),
+                          (2, 4096, 0, 1, 1),
+                          (2, 0, 0, 1, 0), (2, 64, 0, 1, 0), (2, 0, 1 << 30, 1, 1),
+                          (1, 0, 0, 0, 1), (2, 64, 0, 0, 1)])
+def test_step_parity_3d_slab_with_stimulus(torch_dev, variant, rows, cluster, pipe, scaled):
     """Every CG variant: global vectors; per-block shared memory with 64 rows
     per block (many blocks, tiny chunks) and with 4096 rows per block (fewest
-    blocks); one thread-block cluster for every solve; pipelined (pipe = 1)
-    and classical (pipe = 0) arrangements."""
+    blocks), in the symmetrically scaled (scaled = 1) and the Jacobi form; one
+    thread-block cluster for every solve; pipelined (pipe = 1) and classical
+    (pipe = 0) arrangements."""
     torch, dev = torch_dev
     wl = _small_slab()
     ctx = _ctx(wl, torch, dev, cg_variant=variant, cg_rows_per_block=rows,
-               cg_cluster_rows=cluster, cg_pipelined=pipe)
+               cg_cluster_rows=cluster, cg_pipelined=pipe, cg_scaled=scaled)
     S = oracle.System.from_mesh(wl.mesh, wl.sigma)
     v, w = wl.v0.copy(), wl.w0.copy()
     for n in range(24):   # stimulus on for the first 20 steps, then off
