@@ -1207,6 +1207,125 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
     }
 }
 
+// The symmetrically scaled form of pcgc_group (see k_pcg_scaled): classical
+// arrangement of CG on I + c S K_off S, S = diag^-1/2, vectors in global memory.
+// Per row-iteration z-bar + 6 FP64 operations instead of z-bar + 8 (no u = D^-1 r,
+// no scaling of the product by c).  Each thread owns the same rows in every loop,
+// so the scaled values it writes once per solve are read back by itself.
+__device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S, int nblk,
+                                                  int bidx) {
+    const int t = threadIdx.x;
+    const int n = P.n;
+    const int stride = nblk * blockDim.x;
+    const int i0 = bidx * blockDim.x + t;
+    const bool lead = (bidx == 0 && t == 0);
+    const int ld = P.ld;
+    const double c = P.c;
+    double* __restrict__ sg = P.sv;
+    double* __restrict__ sval = P.sval;
+    XsRecord* const part = reinterpret_cast<XsRecord*>(P.part);
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int i = i0; i < n; i += stride) {
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        double si = 0.0;
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        else si = rsqrt(d);
+        sg[i] = si;
+        P.r[i] = si * P.b[i];
+        P.p[i] = 0.0;
+        P.s[i] = 0.0;
+        P.x[i] = 0.0;
+    }
+    if (P.inject_fault && bidx == nblk - 1) {
+        if (nblk == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+    for (int i = i0; i < n; i += stride) {
+        const int len = P.alen[i];
+        const double csi = c * __ldcg(sg + i);
+        for (int k = 0; k < len; ++k) {
+            const size_t q = (size_t)k * ld + i;
+            sval[q] = csi * P.aval[q] * __ldcg(sg + P.acol[q]);
+        }
+    }
+    int it = 0, nsum = 0;
+    while (true) {
+        // w = (I + c S K_off S) r, r.r, w.r
+        double ga = 0.0, de = 0.0;
+        for (int i = i0; i < n; i += stride) {
+            const int len = P.alen[i];
+            const double ri = __ldcg(P.r + i);
+            double acc = ri;
+            for (int k = 0; k < len; ++k) {
+                const size_t q = (size_t)k * ld + i;
+                acc += sval[q] * __ldcg(P.r + P.acol[q]);
+            }
+            P.w[i] = acc;
+            ga += ri * ri;
+            de += acc * ri;
+        }
+        if (!cg_publish_arrive(ga, de, S, part + buf * nblk, P.bar, nblk, bidx, epoch, P.budget,
+                               P.err))
+            return;
+        if (t < 64) {
+            double g, d;
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * nblk + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        }
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        for (int i = i0; i < n; i += stride) {
+            const double ri = P.r[i];
+            const double pi = ri + beta * P.p[i];
+            const double si = P.w[i] + beta * P.s[i];
+            P.p[i] = pi;
+            P.s[i] = si;
+            P.x[i] += alpha * pi;
+            P.r[i] = ri - alpha * si;
+        }
+        if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+    }
+    if (S.state == 2) {
+        if (lead) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (lead) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
+    }
+    for (int i = i0; i < n; i += stride) P.x[i] = __ldcg(sg + i) * __ldcg(P.x + i);
+    if (P.epi_lo < P.epi_hi) {
+        if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+        for (int i = i0; i < n; i += stride) {
+            const int len = P.alen[i];
+            const double xi = __ldcg(P.x + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
+    __shared__ CgShared S;
+    pcgc_group_scaled(P, S, (int)gridDim.x, (int)blockIdx.x);
+}
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgc(CgParams P) {
     __shared__ CgShared S;
@@ -1580,6 +1699,9 @@ PcgKernel pcg_general_kernel(int block) {
     return block > 512 ? k_pcg<1024> : block > 256 ? k_pcg<512> : k_pcg<256>;
 }
 PcgKernel pcg_smem_kernel(int block) { return block > 512 ? k_pcg_smem<1024> : k_pcg_smem<512>; }
+PcgKernel pcgcs_general_kernel(int block) {
+    return block > 512 ? k_pcgcs<1024> : block > 256 ? k_pcgcs<512> : k_pcgcs<256>;
+}
 PcgKernel pcgs_general_kernel(int block) {
     return block > 512 ? k_pcgs<1024> : block > 256 ? k_pcgs<512> : k_pcgs<256>;
 }
@@ -1625,9 +1747,14 @@ int pcg_max_blocks(int block) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_general_kernel(block), block, 0);
-    int per_s = 0;   // the scaled form shares the grid limit: take the smaller occupancy
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_s, pcgs_general_kernel(block), block, 0);
-    return sms * std::min(per, per_s);
+    // the other general-vector kernels share the grid limit: take the smallest occupancy
+    for (PcgKernel k : {pcgs_general_kernel(block), pcgc_general_kernel(block),
+                        pcgcs_general_kernel(block)}) {
+        int q = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, k, block, 0);
+        per = std::min(per, q);
+    }
+    return sms * per;
 }
 
 int pcg_cluster_size(int block) {
@@ -1784,8 +1911,10 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
         }
         int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));
         if (grid < 1) grid = 1;
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)pcgc_general_kernel(cfg.block),
-                                                    dim3(grid), dim3(cfg.block), args, 0, s);
+        const PcgKernel kg = cfg.scaled && P.sv && P.sval ? pcgcs_general_kernel(cfg.block)
+                                                          : pcgc_general_kernel(cfg.block);
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)kg, dim3(grid), dim3(cfg.block),
+                                                    args, 0, s);
         return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
     }
     // cluster variant: one cluster of cfg.cluster CTAs for small active sets

@@ -180,12 +180,14 @@ def test_emi_parity_2d_branched_cells(torch_dev, variant, cluster):
     myocytes at 10 um pixels, gating held at w = 0 as in the paper's EMI runs.
     Its node solves take 300-400 CG iterations; at that length the iteration
     where the recursively updated residual of a finite-precision CG crosses
-    rtol depends on the rounding of its sums (the oracle sums in index order,
-    the kernels exactly), so counts agree to 10 % here while the states agree
-    to 1e-10 and the active sets exactly."""
+    rtol depends on the rounding of its sums and recurrences (the oracle runs
+    the textbook recurrences summed in index order; the kernels run the
+    Chronopoulos-Gear recurrences, exact sums, Jacobi or scaled form), so counts
+    agree to 15 % here while the states agree to 1e-10 and the active sets
+    exactly."""
     torch, dev = torch_dev
     from workloads.emi import emi_tiny
     wl = emi_tiny("branched_2d")
     assert wl.mesh.dim == 2
-    assert _run(wl, torch, dev, 3, wl.tol, w_frozen=True, iters_rel=0.1, cg_variant=variant,
+    assert _run(wl, torch, dev, 3, wl.tol, w_frozen=True, iters_rel=0.15, cg_variant=variant,
                 cg_cluster_rows=cluster)
