@@ -140,6 +140,7 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
                      const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
 // Launch configuration of the restricted PCG solves.
 constexpr int kSmemVectorsS = 6;    // the same for the symmetrically scaled variant
+constexpr int kSmemVectorsCS = 4;   // the scaled classical shared-memory variant (kSmemRowsC rows)
 constexpr int kSmemRowsS = 4800;    // rows per block of the symmetrically scaled variant
 constexpr int kSmemVectors = 8;     // per-row doubles in shared memory, shared-memory variant
 constexpr int kSmemRows = 3584;     // rows per block of the shared-memory variant

@@ -1348,6 +1348,136 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_batch(CgParams P, const SegBlo
 
 // Shared-memory form of the classical arrangement (rows as in k_pcg_smem;
 // r, u, p, s, w and the reciprocal diagonal on chip, u published).
+// Shared-memory form of pcgc_group_scaled: rows as in k_pcgc_smem, r, p, s, w on
+// chip (four vectors), r published for the neighbours' products.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgc_scaled(CgParams P) {
+    extern __shared__ double sm[];
+    __shared__ CgShared S;
+    const int G = gridDim.x, B = blockDim.x, t = threadIdx.x;
+    const int L = P.L, ld = P.ld;
+    const int r0 = blockIdx.x * L;
+    const int nl = max(0, min(P.n - r0, L));
+    double* __restrict__ sr = sm;
+    double* __restrict__ sp = sm + L;
+    double* __restrict__ ss = sm + 2 * L;
+    double* __restrict__ sw = sm + 3 * L;
+    double* __restrict__ ug = P.u;
+    double* __restrict__ xg = P.x;
+    double* __restrict__ sg = P.sv;
+    double* __restrict__ sval = P.sval;
+    const double* __restrict__ aval = P.aval;
+    const int* __restrict__ acol = P.acol;
+    const int* __restrict__ alen = P.alen;
+    const double c = P.c;
+    unsigned epoch = 0;
+    int buf = 0;
+
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        double si = 0.0;
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        else si = rsqrt(d);
+        sg[i] = si;
+        const double r = si * P.b[i];
+        sr[l] = r;
+        ug[i] = r;
+        sp[l] = 0.0;
+        ss[l] = 0.0;
+        xg[i] = 0.0;
+    }
+    if (P.inject_fault && blockIdx.x == G - 1) {
+        if (G == 1 && t == 0) raise_error(P.err, SDC_E_TIMEOUT);
+        return;
+    }
+    if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+    // scaled rows: written and read back by the same thread (same row mapping in every loop)
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        const int len = __ldg(alen + i);
+        const double csi = c * __ldcg(sg + i);
+        for (int k = 0; k < len; ++k) {
+            const size_t q = (size_t)k * ld + i;
+            sval[q] = csi * __ldg(aval + q) * __ldcg(sg + __ldg(acol + q));
+        }
+    }
+    XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
+    int it = 0, nsum = 0;
+    while (true) {
+        double ga = 0.0, de = 0.0;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            const double ri = sr[l];
+            double acc = ri;
+            for (int k = 0; k < len; ++k) {
+                const size_t q = (size_t)k * ld + i;
+                acc += sval[q] * __ldcg(ug + __ldg(acol + q));
+            }
+            sw[l] = acc;
+            ga += ri * ri;
+            de += acc * ri;
+        }
+        if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, (int)blockIdx.x, epoch,
+                               P.budget, P.err))
+            return;
+        if (t < 64) {
+            double g, d;
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        }
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        for (int l = t; l < nl; l += B) {
+            const double ri = sr[l];
+            const double pi = ri + beta * sp[l];
+            const double s_i = sw[l] + beta * ss[l];
+            sp[l] = pi;
+            ss[l] = s_i;
+            xg[r0 + l] += alpha * pi;
+            const double r = ri - alpha * s_i;
+            sr[l] = r;
+            ug[r0 + l] = r;
+        }
+        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+    }
+    if (S.state == 2) {
+        if (blockIdx.x == 0 && t == 0) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
+    }
+    for (int l = t; l < nl; l += B) {
+        const int i = r0 + l;
+        xg[i] = __ldcg(sg + i) * __ldcg(xg + i);
+    }
+    if (P.epi_lo < P.epi_hi) {
+        if (!grid_barrier(P.bar, epoch, P.budget, P.err, &S.ok)) return;
+        for (int l = t; l < nl; l += B) {
+            const int i = r0 + l;
+            const int len = __ldg(alen + i);
+            const double xi = __ldcg(xg + i);
+            double acc = 0.0;
+            for (int k = 0; k < len; ++k)
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+            cg_couple_row(P, i, xi, acc);
+        }
+    }
+}
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
     extern __shared__ double sm[];
@@ -1699,6 +1829,9 @@ PcgKernel pcg_general_kernel(int block) {
     return block > 512 ? k_pcg<1024> : block > 256 ? k_pcg<512> : k_pcg<256>;
 }
 PcgKernel pcg_smem_kernel(int block) { return block > 512 ? k_pcg_smem<1024> : k_pcg_smem<512>; }
+PcgKernel pcgc_scaled_kernel(int block) {
+    return block > 512 ? k_pcgc_scaled<1024> : k_pcgc_scaled<512>;
+}
 PcgKernel pcgcs_general_kernel(int block) {
     return block > 512 ? k_pcgcs<1024> : block > 256 ? k_pcgcs<512> : k_pcgcs<256>;
 }
@@ -1734,6 +1867,9 @@ void pcg_smem_attrs() {
     for (PcgKernel k : {k_pcg_scaled<512>, k_pcg_scaled<1024>})
         cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kSmemVectorsS * kSmemRowsS * sizeof(double)));
+    for (PcgKernel k : {k_pcgc_scaled<512>, k_pcgc_scaled<1024>})
+        cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmemVectorsCS * kSmemRowsC * sizeof(double)));
     for (PcgKernel k : {k_pcg_cluster<512>, k_pcg_cluster<1024>}) {
         cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(kClusterVectors * kClusterRows * sizeof(double)));
@@ -1904,9 +2040,11 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
             P.L = nblk(n, grid);
             const int blk = n >= cfg.big_rows ? 1024 : cfg.smem_block;
             pcg_smem_attrs();
+            const bool sc = cfg.scaled && P.sv && P.sval;
             cudaError_t e = cudaLaunchCooperativeKernel(
-                (const void*)pcgc_smem_kernel(blk), dim3(grid), dim3(blk), args,
-                (size_t)kSmemVectorsC * P.L * sizeof(double), s);
+                (const void*)(sc ? pcgc_scaled_kernel(blk) : pcgc_smem_kernel(blk)), dim3(grid),
+                dim3(blk), args,
+                (size_t)(sc ? kSmemVectorsCS : kSmemVectorsC) * P.L * sizeof(double), s);
             return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
         }
         int grid = std::min(cfg.max_blocks_general, nblk(n, cfg.block));

@@ -138,7 +138,8 @@ def test_step_parity_2d_square(torch_dev, tol, variant, cluster, pipe, scaled):
                          [(1, 0, 0, 1, 1), (1, 0, 0, 1, 0), (2, 0, 0, 1, 1), (2, 64, 0, 1, 1),
                           (2, 4096, 0, 1, 1),
                           (2, 0, 0, 1, 0), (2, 64, 0, 1, 0), (2, 0, 1 << 30, 1, 1),
-                          (1, 0, 0, 0, 1), (1, 0, 0, 0, 0), (2, 64, 0, 0, 1)])
+                          (1, 0, 0, 0, 1), (1, 0, 0, 0, 0), (2, 64, 0, 0, 1),
+                          (2, 64, 0, 0, 0)])
 def test_step_parity_3d_slab_with_stimulus(torch_dev, variant, rows, cluster, pipe, scaled):
     """Every CG variant: global vectors; per-block shared memory with 64 rows
     per block (many blocks, tiny chunks) and with 4096 rows per block (fewest
