@@ -18,13 +18,36 @@ __device__ __forceinline__ double ap_dIdv(const Ionic& p, double v, double w) {
     return p.ga * (3.0 * v * v - 2.0 * (1.0 + p.a) * v + p.a) + w;
 }
 // R and dR/dw, sharing the two factors
-__device__ __forceinline__ void ap_R_dRdw(const Ionic& p, double v, double w, double& R,
-                                          double& dRdw) {
-    const double inv = 1.0 / (v + p.mu2);
+__device__ __forceinline__ void ap_R_dRdw_inv(const Ionic& p, double v, double w, double inv,
+                                              double& R, double& dRdw) {
     const double E = p.eps + p.mu1 * w * inv;
     const double G = -w - p.gs * v * (v - p.a - 1.0);
     R = p.cw * E * G;
     dRdw = p.cw * (p.mu1 * inv * G - E);
+}
+__device__ __forceinline__ void ap_R_dRdw(const Ionic& p, double v, double w, double& R,
+                                          double& dRdw) {
+    ap_R_dRdw_inv(p, v, w, 1.0 / (v + p.mu2), R, dRdw);
+}
+
+// Reciprocals of x[0..N-1] with one division (Montgomery's simultaneous inversion:
+// prefix products, one reciprocal of the full product, then back-substitution),
+// 3 (N - 1) multiplications instead of N - 1 further divisions.  For positive x of
+// moderate range (no overflow or underflow of the product); each result within a
+// few ulps of 1 / x[k].
+template <int N>
+__device__ __forceinline__ void batch_reciprocal(const double* x, double* inv) {
+    double pre[N];
+    pre[0] = x[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) pre[k] = pre[k - 1] * x[k];
+    double a = 1.0 / pre[N - 1];
+#pragma unroll
+    for (int k = N - 1; k > 0; --k) {
+        inv[k] = a * pre[k - 1];
+        a *= x[k];
+    }
+    inv[0] = a;
 }
 
 // ---- P1 element geometry (Sec. 2.2) -------------------------------------------

@@ -1618,14 +1618,24 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
             amax = fmax(amax, fabs(d));
         }
         if (!w_frozen) {
-            double wm[M], gR[M], dR[M], e[M];
+            // two divisions per row instead of 2 M (FP64 division is a long sequence on this
+            // part): the M reciprocals 1 / (v + mu2), then the M reciprocals of the denominators
+            double wm[M], gR[M], dR[M], e[M], xs[M], inv[M];
             const double wz = w0[g];
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 wm[m] = W[(size_t)g * M + m];
-                if (!(vm[m] + ion.mu2 > 0.0)) raise_error(err, SDC_E_DOMAIN);
-                ap_R_dRdw(ion, vm[m], wm[m], gR[m], dR[m]);
+                xs[m] = vm[m] + ion.mu2;
+                if (!(xs[m] > 0.0)) raise_error(err, SDC_E_DOMAIN);
             }
+            batch_reciprocal<M>(xs, inv);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                ap_R_dRdw_inv(ion, vm[m], wm[m], inv[m], gR[m], dR[m]);
+                xs[m] = 1.0 - dt * co.Qh[m * kMaxM + m] * dR[m];
+                if (!(xs[m] > 0.0)) raise_error(err, SDC_E_DOMAIN);
+            }
+            batch_reciprocal<M>(xs, inv);
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 double q = 0.0;
@@ -1634,9 +1644,7 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
                 double acc = wz + dt * q - wm[m];
 #pragma unroll
                 for (int j = 0; j < m; ++j) acc += dt * co.Qh[m * kMaxM + j] * dR[j] * e[j];
-                const double den = 1.0 - dt * co.Qh[m * kMaxM + m] * dR[m];
-                if (!(den > 0.0)) raise_error(err, SDC_E_DOMAIN);
-                e[m] = acc / den;
+                e[m] = acc * inv[m];
             }
 #pragma unroll
             for (int m = 0; m < M; ++m) W[(size_t)g * M + m] = wm[m] + e[m];
