@@ -242,6 +242,12 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 FP64_LANES_PER_CYCLE = 304          # whole GPU, ncu dfma peak_sustained on GB300
+# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum): the first node solve of a slab step, k_pcg_scaled<1024> on all
+# 442,401 rows, 21 iterations = 1.735 GB of algorithmic bytes.  Scaled to the average launch
+# by algorithmic bytes.  Must be re-taken (or dropped) whenever that kernel changes.
+PCG_TRAFFIC = {"w1": {"dram_bytes": 63.63e6 + 9.97e6, "algorithmic_bytes": 1.735e9,
+                      "kernel": "k_pcg_scaled<1024>"}}
 
 
 def pcg_ops(st, M, sweeps):
@@ -381,13 +387,15 @@ def run_gb300(args):
     launches = max(1, agg_a["pcg_launches"])
     ach_ops = agg_a["pcg_ops"] / pcg_s / 1e9 if pcg_s > 0 else None
     ach_gbs = agg_a["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
-    roofline = {"kernel": "k_pcg* (restricted Jacobi-PCG, one cooperative launch per node solve)",
+    roofline = {"kernel": "k_pcg_scaled / k_pcg* (restricted Jacobi-PCG, symmetrically scaled "
+                          "form, one cooperative launch per node solve)",
                 "bound": "alu", "achieved": ach_ops, "peak": alu_peak,
                 "unit": "G FP64 lane-op/s",
                 "frac": ach_ops / alu_peak if ach_ops else None,
                 "peak_source": "304 FP64 lanes/cycle (ncu dfma peak_sustained) x %.0f MHz max SM clock"
                                % sm_max,
                 "traffic": None,
+                "traffic_source": None,
                 "algorithmic_ops_per_launch": agg_a["pcg_ops"] / launches,
                 "algorithmic_bytes_per_launch": agg_a["pcg_bytes"] / launches,
                 "avg_launch_ms": agg_a["pcg_ms"] / launches,
@@ -397,6 +405,14 @@ def run_gb300(args):
                              "frac": ach_gbs / hbm_peak if ach_gbs else None,
                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
                              if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}}
+    tr = PCG_TRAFFIC.get(args.workload)
+    if tr is not None and agg_a["pcg_launches"] > 0:
+        roofline["traffic"] = (tr["dram_bytes"] / tr["algorithmic_bytes"]
+                               * roofline["algorithmic_bytes_per_launch"])
+        roofline["traffic_source"] = (
+            "ncu DRAM bytes of one full-size %s launch (%.1f MB for %.3f GB algorithmic), "
+            "scaled to the average launch by algorithmic bytes"
+            % (tr["kernel"], tr["dram_bytes"] / 1e6, tr["algorithmic_bytes"] / 1e9))
 
     cpu = None
     parity = None
