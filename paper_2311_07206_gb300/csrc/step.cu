@@ -1212,18 +1212,19 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
 // Per row-iteration z-bar + 6 FP64 operations instead of z-bar + 8 (no u = D^-1 r,
 // no scaling of the product by c).  Each thread owns the same rows in every loop,
 // so the scaled values it writes once per solve are read back by itself.
-__device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S, int nblk,
-                                                  int bidx) {
+__device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S, int row0,
+                                                  int row1, int nblk, int bidx, unsigned* bar,
+                                                  XsRecord* part, int pstride, int* iters_out,
+                                                  double* relres_out) {
     const int t = threadIdx.x;
-    const int n = P.n;
+    const int n = row1;
     const int stride = nblk * blockDim.x;
-    const int i0 = bidx * blockDim.x + t;
+    const int i0 = row0 + bidx * blockDim.x + t;
     const bool lead = (bidx == 0 && t == 0);
     const int ld = P.ld;
     const double c = P.c;
     double* __restrict__ sg = P.sv;
     double* __restrict__ sval = P.sval;
-    XsRecord* const part = reinterpret_cast<XsRecord*>(P.part);
     unsigned epoch = 0;
     int buf = 0;
 
@@ -1243,7 +1244,7 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
         if (nblk == 1 && threadIdx.x == 0) raise_error(P.err, SDC_E_TIMEOUT);
         return;
     }
-    if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+    if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
     for (int i = i0; i < n; i += stride) {
         const int len = P.alen[i];
         const double csi = c * __ldcg(sg + i);
@@ -1268,12 +1269,12 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
             ga += ri * ri;
             de += acc * ri;
         }
-        if (!cg_publish_arrive(ga, de, S, part + buf * nblk, P.bar, nblk, bidx, epoch, P.budget,
+        if (!cg_publish_arrive(ga, de, S, part + buf * pstride, bar, nblk, bidx, epoch, P.budget,
                                P.err))
             return;
         if (t < 64) {
             double g, d;
-            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * nblk + k); }, g, d);
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         }
         __syncthreads();
@@ -1295,20 +1296,20 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
             P.x[i] += alpha * pi;
             P.r[i] = ri - alpha * si;
         }
-        if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+        if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
     }
     if (S.state == 2) {
         if (lead) raise_error(P.err, SDC_E_NONFINITE);
         return;
     }
     if (lead) {
-        *P.iters_out = it;
-        *P.relres_out = cg_relres(S);
+        *iters_out = it;
+        *relres_out = cg_relres(S);
         if (P.energy_out) *P.energy_out = S.energy;
     }
     for (int i = i0; i < n; i += stride) P.x[i] = __ldcg(sg + i) * __ldcg(P.x + i);
     if (P.epi_lo < P.epi_hi) {
-        if (!group_barrier(P.bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
+        if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
         for (int i = i0; i < n; i += stride) {
             const int len = P.alen[i];
             const double xi = __ldcg(P.x + i);
@@ -1323,7 +1324,22 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
     __shared__ CgShared S;
-    pcgc_group_scaled(P, S, (int)gridDim.x, (int)blockIdx.x);
+    pcgc_group_scaled(P, S, 0, P.n, (int)gridDim.x, (int)blockIdx.x, P.bar,
+                      reinterpret_cast<XsRecord*>(P.part), (int)gridDim.x, P.iters_out,
+                      P.relres_out);
+}
+
+// Batched form of the scaled classical arrangement (one group of blocks per instance).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgcs_batch(CgParams P, const SegBlock* __restrict__ tab,
+                                                          unsigned* __restrict__ bars,
+                                                          int* __restrict__ seg_iters,
+                                                          double* __restrict__ seg_relres) {
+    __shared__ CgShared S;
+    const SegBlock g = tab[blockIdx.x];
+    pcgc_group_scaled(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
+                      reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x,
+                      seg_iters + g.seg, seg_relres + g.seg);
 }
 
 template <int MAXT>
@@ -1858,8 +1874,8 @@ PcgKernel pcgc_general_kernel(int block) {
 PcgKernel pcgc_smem_kernel(int block) { return block > 512 ? k_pcgc_smem<1024> : k_pcgc_smem<512>; }
 // Batches: the 64-register instantiation whatever the block size, so that
 // several blocks share an SM and one cooperative wave holds more instances.
-PcgBatchKernel pcg_batch_kernel(int, bool pipelined) {
-    return pipelined ? k_pcg_batch<1024> : k_pcgc_batch<1024>;
+PcgBatchKernel pcg_batch_kernel(int, bool pipelined, bool scaled = false) {
+    return pipelined ? k_pcg_batch<1024> : scaled ? k_pcgcs_batch<1024> : k_pcgc_batch<1024>;
 }
 
 // opt-in dynamic shared memory of the on-chip variants (set once per instantiation)
@@ -2140,6 +2156,10 @@ int pcg_batch_max_blocks(int block) {
     int per2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_batch_kernel(block, true), block, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, pcg_batch_kernel(block, false), block, 0);
+    int per3 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per3, pcg_batch_kernel(block, false, true), block,
+                                                  0);
+    per2 = std::min(per2, per3);
     per = std::min(per, per2);
     return sms * per;
 }
@@ -2179,6 +2199,7 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     P.b = B.R + (size_t)m * B.ld;
     P.x = B.D + (size_t)m * B.ld;
     set_cg_vectors(P, B);
+    set_scaled_buffers(P, A, B);
     P.bar = nullptr;
     P.err = &B.sc->err;
     P.rtol = rtol;
@@ -2221,7 +2242,8 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
         const SegBlock* dtab = reinterpret_cast<const SegBlock*>(B.segtab);
         void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
         cudaError_t e = cudaLaunchCooperativeKernel(
-            (const void*)pcg_batch_kernel(cfg.batch_block, cfg.batch_pipelined),
+            (const void*)pcg_batch_kernel(cfg.batch_block, cfg.batch_pipelined,
+                                          cfg.scaled && P.sv && P.sval),
                                                     dim3((int)tab.size()),
                                                     dim3(cfg.batch_block), args, 0, s);
         if (e != cudaSuccess) return SDC_E_CUDA;

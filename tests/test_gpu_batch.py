@@ -35,14 +35,16 @@ def _instances(count=7):
     return insts
 
 
-@pytest.mark.parametrize("max_blocks", [0, 3])
-def test_batch_follows_solo_runs(torch_dev, max_blocks):
-    """max_blocks = 3 forces several waves of the batched CG launch."""
+@pytest.mark.parametrize("max_blocks,scaled", [(0, 1), (3, 1), (0, 0)])
+def test_batch_follows_solo_runs(torch_dev, max_blocks, scaled):
+    """max_blocks = 3 forces several waves of the batched CG launch; scaled = 0
+    runs the batched solves in the Jacobi form."""
     torch, dev = torch_dev
     from paper_2311_07206_gb300 import Batch, Context, default_options
     insts = _instances()
     stream = torch.cuda.current_stream(dev).cuda_stream
-    batch = Batch(insts, options=default_options(cg_max_blocks=max_blocks), stream=stream)
+    batch = Batch(insts, options=default_options(cg_max_blocks=max_blocks, cg_scaled=scaled),
+                  stream=stream)
     off = batch.offsets
     solos = [Context.from_workload(wl, stream=stream) for wl in insts]
     t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
