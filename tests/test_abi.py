@@ -117,6 +117,16 @@ def test_energy_stop_rejected_for_batches_and_bad_rho_before_device_work(lib):
     assert e.value.status == -1 and "batch" in str(e.value)
 
 
+def test_cg_scaled_validation_before_device_work(lib):
+    from paper_2311_07206_gb300 import Context, SdcError, default_options
+    import workloads as W
+    sq = W.w0_square(n=9, length=2.5)
+    for bad in (-1, 2):
+        with pytest.raises(SdcError) as e:
+            Context.from_workload(sq, options=default_options(cg_scaled=bad))
+        assert e.value.status == -1
+
+
 def test_drop_rule_validation_before_device_work(lib):
     """drop_rule 1 (the a priori drop tolerance of Sec. 4.1) needs a given
     contraction rho and is per context, not per batch."""
