@@ -73,12 +73,17 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/reference/e2e runs")
     ap.add_argument("--emi-w-frozen", action="store_true", help="w2: hold the gating at w = 0")
+    ap.add_argument("--autotune", type=int, choices=[0, 1], default=None,
+                    help="pick the node solves' launch shape with sdc_autotune before timing "
+                         "(default: on for the batch w3, off otherwise)")
     ap.add_argument("--reorder", type=int, choices=[0, 1], default=None,
                     help="library-internal Morton numbering of the dofs (default: on for the "
                          "randomly numbered tissue mesh w5, off otherwise)")
     args = ap.parse_args()
     if args.reorder is None:
         args.reorder = 1 if args.workload == "w5" else 0
+    if args.autotune is None:
+        args.autotune = 1 if args.workload == "w3" else 0
     if args.steps is None:
         args.steps = {"w1": 1000, "w2": 50, "w1l": 300, "w5": 300, "w0": 100, "w3": 100,
                       "w4": 200, "sweet": 100, "sweet_emi": 125, "order": 80}[args.workload]
@@ -298,6 +303,9 @@ def run_gb300(args):
     v0 = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    tune = None
+    if args.autotune:
+        tune = ctx.autotune(v0.clone(), w0.clone(), 0.0, wl.dt, wl.sweeps, wl.tol, trial_steps=3)
 
     def trajectory(tol, sweeps, steps, timed):
         v, w = v0.clone(), w0.clone()
@@ -435,7 +443,7 @@ def run_gb300(args):
     line = {"metric": metric_of(wl), "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms_adapt / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(wl, K, args.reorder),
+            "config": dict(config_of(wl, K, args.reorder), autotune=tune),
             "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_adapt / 1e3),
             **extras,
             "phase_ms_per_step": phase,
@@ -848,6 +856,11 @@ def run_batch(args):
         torch.cuda.synchronize(dev)
         return vs, (e0.elapsed_time(e1) if timed else None)
 
+    tune = None
+    if args.autotune:
+        # launch shape of the batched solves picked by timing steps from the start state
+        tv, tw = t64(v0), t64(w0)
+        tune = batch.autotune(tv, tw, 0.0, wl0.dt, wl0.sweeps, wl0.tol, trial_steps=10)
     run_batched(Wm, False)
     run_solo(Wm, False)
     barrier(world)
@@ -865,7 +878,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch_96_2d_instances", "n_dofs": int(batch.n),
                        "instances": len(insts), "M": wl0.M, "dt_ms": wl0.dt,
-                       "sweeps": wl0.sweeps, "TOL": wl0.tol, "l2": "inputs larger than L2"},
+                       "sweeps": wl0.sweeps, "TOL": wl0.tol, "l2": "inputs larger than L2",
+                       "autotune": tune},
             "instance_steps_per_s": world * K * len(insts) / (ms_b / 1e3),
             "active_dof_sweeps_per_s": world * ads / (ms_b / 1e3),
             "per_instance_launches": {"value": K / (ms_s / 1e3), "unit": "steps/s",

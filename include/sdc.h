@@ -117,10 +117,12 @@ typedef struct {
     int cg_pipelined;      /* arrangement of the CG iteration (the same iterates in exact
                               arithmetic): 1 pipelined (one grid synchronisation per iteration,
                               the sums overlapped with the product); 0 classical (two); -1
-                              automatic: pipelined for monodomain contexts, classical for
-                              cell-by-cell contexts, whose long ill-conditioned solves need its
-                              smaller rounding error, and for batches, whose many small groups
-                              favour its lighter rows; default -1                              */
+                              automatic: for monodomain contexts pipelined where the solve's
+                              vectors fit on chip and classical above (its lighter vector
+                              traffic wins there); classical for cell-by-cell contexts, whose
+                              long ill-conditioned solves need its smaller rounding error, and
+                              for batches, whose many small groups favour its lighter rows;
+                              default -1                                                       */
     int energy_stop;       /* 1: end the sweeps of a step once the energy norm of the sweep's
                               corrections, E_k = sum_m dv_m' A~_m dv_m with A~_m the node system
                               matrix, is at most ((1 - rho) / rho * TOL)^2 (Sec. 3.2); `sweeps`
@@ -343,6 +345,40 @@ sdc_status sdc_batch_instance_stats(const sdc_batch* batch, int sweep, int* n_ac
 /* The batch's underlying context (for sdc_get_nodes, sdc_get_active,
  * sdc_get_matrix on the stacked system); owned by the batch. */
 sdc_ctx* sdc_batch_context(sdc_batch* batch);
+
+/* ---- launch-shape autotuner --------------------------------------------------
+ * The node solves (Sec. 3.2, eq. final-sdc) dominate a step, and their best launch
+ * shape depends on the mesh, the active-set sizes the adaptivity produces and the
+ * part.  sdc_autotune times `trial_steps` steps (1..100) from the state (d_v, d_w)
+ * at (t, dt, sweeps, TOL) under candidate configurations, one knob at a time in
+ * the order below (coordinate descent, each value tried with the others at their
+ * best so far), and keeps the fastest; a value must beat the incumbent by 3 % to
+ * be adopted (each configuration is timed twice from the restored state, the
+ * better run counting).  The state arrays are restored bitwise before returning.  Every
+ * configuration computes the same iteration (results differ by rounding only).
+ *   single context: cg_pipelined {1, 0}; cg_scaled {1, 0}; shared-memory block
+ *     size {512, 1024}; rows from which the shared-memory variants use 1024
+ *     threads {0, 100000, 300000, never}; general-variant block size {256, 512,
+ *     1024}; cluster_rows {0, 2000, 5000, 10000, 20000 (within the cluster's
+ *     capacity)};
+ *   batch: arrangement {classical, pipelined}; cg_scaled {1, 0}; block size
+ *     {256, 512, 1024}; target active rows per block {256, 512, 1024, 2048, 4096}.
+ * Candidates whose cooperative grid would exceed the context's reserved
+ * per-block workspace are skipped.  Device time is measured with CUDA events on
+ * the context's stream.  Errors of a trial step are returned (the state is
+ * restored and the incumbent configuration kept).  out may be NULL. */
+typedef struct {
+    int trials;                 /* configurations timed, the starting one included   */
+    double base_ms;             /* ms per step of the starting configuration          */
+    double best_ms;             /* ms per step of the chosen configuration            */
+    int cg_pipelined, cg_scaled, smem_block, big_rows, general_block, cluster_rows;
+    int batch_pipelined, batch_block, batch_rows_per_block;   /* chosen values */
+} sdc_tune_report;
+
+sdc_status sdc_autotune(sdc_ctx* ctx, double* d_v, double* d_w, double t, double dt, int sweeps,
+                        double TOL, int trial_steps, sdc_tune_report* out);
+sdc_status sdc_batch_autotune(sdc_batch* batch, double* d_v, double* d_w, double t, double dt,
+                              int sweeps, double TOL, int trial_steps, sdc_tune_report* out);
 
 void sdc_batch_destroy(sdc_batch* batch);
 

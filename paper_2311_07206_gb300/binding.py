@@ -58,6 +58,17 @@ class sdc_stats(C.Structure):
                 ("energy", C.c_double * SDC_MAX_SWEEPS), ("tol_drop", C.c_double)]
 
 
+class sdc_tune_report(C.Structure):
+    _fields_ = [("trials", C.c_int), ("base_ms", C.c_double), ("best_ms", C.c_double),
+                ("cg_pipelined", C.c_int), ("cg_scaled", C.c_int), ("smem_block", C.c_int),
+                ("big_rows", C.c_int), ("general_block", C.c_int), ("cluster_rows", C.c_int),
+                ("batch_pipelined", C.c_int), ("batch_block", C.c_int),
+                ("batch_rows_per_block", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class sdc_tape(C.Structure):
     _fields_ = [("mode", C.c_int), ("sweeps", C.c_int), ("d_V", C.c_void_p), ("d_W", C.c_void_p),
                 ("d_act", C.c_void_p), ("n_active", C.c_int * SDC_MAX_SWEEPS)]
@@ -104,6 +115,10 @@ SIGNATURES = {
     "sdc_batch_info": (C.c_int, [_vp, _ip, _ip]),
     "sdc_batch_set_stimulus": (C.c_int, [_vp, C.c_int, _ip, C.c_int, C.c_double, C.c_double,
                                          C.c_double]),
+    "sdc_autotune": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
+                               C.c_int, C.POINTER(sdc_tune_report)]),
+    "sdc_batch_autotune": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int,
+                                     C.c_double, C.c_int, C.POINTER(sdc_tune_report)]),
     "sdc_batch_step": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_double, C.c_int, C.c_double,
                                  C.POINTER(sdc_stats)]),
     "sdc_batch_instance_stats": (C.c_int, [_vp, C.c_int, _ip, _ip]),
@@ -266,6 +281,14 @@ class Context:
                                int(sweeps), float(tol), C.byref(st) if st is not None else None),
                self._h)
         return st
+
+    def autotune(self, v, w, t, dt, sweeps, tol, trial_steps=3):
+        """Pick the node solves' launch shape by timing steps from (v, w) (restored)."""
+        rep = sdc_tune_report()
+        _check(load().sdc_autotune(self._h, _vp(_ptr(v)), _vp(_ptr(w)), float(t), float(dt),
+                                   int(sweeps), float(tol), int(trial_steps), C.byref(rep)),
+               self._h)
+        return rep.as_dict()
 
     def step_host(self, v, w, t, dt, sweeps, tol, want_stats=False):
         """One step on host numpy arrays v, w (updated in place)."""
@@ -454,6 +477,15 @@ class Batch:
                                      int(sweeps), float(tol), C.byref(st)),
                load().sdc_batch_context(self._h))
         return st
+
+    def autotune(self, v, w, t, dt, sweeps, tol, trial_steps=3):
+        """Pick the batched solves' launch shape by timing steps from (v, w) (restored)."""
+        rep = sdc_tune_report()
+        _check(load().sdc_batch_autotune(self._h, _vp(_ptr(v)), _vp(_ptr(w)), float(t),
+                                         float(dt), int(sweeps), float(tol), int(trial_steps),
+                                         C.byref(rep)),
+               load().sdc_batch_context(self._h))
+        return rep.as_dict()
 
     def instance_stats(self, sweep):
         na = np.zeros(self.count, np.int32)

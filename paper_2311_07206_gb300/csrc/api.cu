@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <functional>
 #include <vector>
 
 #include "sdc_internal.h"
@@ -110,6 +111,7 @@ int alloc_buffers(sdc_ctx* c) {
     P.cluster_rows = c->opt.cg_cluster_rows;
     P.inject_fault = c->opt.inject_fault;
     P.pipelined = c->opt.cg_pipelined != 0;
+    P.general_classical = c->opt.cg_pipelined == -1;
     P.scaled = c->opt.cg_scaled;
     P.budget = c->opt.spin_budget;
     if (P.max_blocks_general < 1 || P.sms < 1) return SDC_E_CUDA;
@@ -141,6 +143,7 @@ int alloc_buffers(sdc_ctx* c) {
         B.max_blocks = std::max(B.max_blocks, P.max_blocks_batch);
         ok = dalloc(&B.inst_off, nseg + 1) && dalloc(&B.bounds, nseg + 1) &&
              dalloc(&B.segtab, 5 * (size_t)P.max_blocks_batch) && dalloc(&B.bars, nseg) &&
+             (B.segtab_cap = P.max_blocks_batch) > 0 &&
              dalloc(&B.seg_iters, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
              dalloc(&B.seg_relres, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
              cudaMallocHost(&c->h_bounds, (nseg + 1) * sizeof(int)) == cudaSuccess;
@@ -1371,3 +1374,161 @@ void sdc_destroy(sdc_ctx* c) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// One knob of the autotuner: its candidate values and how to apply one.
+struct TuneKnob {
+    std::vector<int> values;
+    std::function<bool(PcgConfig&, int)> apply;   // false: the value is not admissible
+};
+
+sdc_status autotune_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
+                         double TOL, int trial_steps, sdc_tune_report* out) {
+    if (!c) return SDC_E_INVALID;
+    if (!d_v || !d_w) return fail(c, SDC_E_INVALID, "autotune: NULL state pointer");
+    if (trial_steps < 1 || trial_steps > 100)
+        return fail(c, SDC_E_INVALID, "autotune: trial_steps = %d outside [1, 100]", trial_steps);
+    if (!(dt > 0.0) || !std::isfinite(dt) || sweeps < 1 || sweeps > SDC_MAX_SWEEPS || !(TOL >= 0.0))
+        return fail(c, SDC_E_INVALID, "autotune: invalid dt, sweeps or TOL");
+    const size_t nb = (size_t)c->N * sizeof(double);
+    const size_t nw = (size_t)(c->is_emi ? c->emi.np : c->N) * sizeof(double);
+    double *sv = nullptr, *sw = nullptr;
+    if (cudaMalloc(&sv, nb) != cudaSuccess || cudaMalloc(&sw, nw) != cudaSuccess) {
+        cudaFree(sv);
+        return fail(c, SDC_E_NOMEM, "autotune: state copies");
+    }
+    cudaStream_t s = c->stream;
+    cudaMemcpyAsync(sv, d_v, nb, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(sw, d_w, nw, cudaMemcpyDeviceToDevice, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    sdc_status status = SDC_OK;
+    // ms per step of the context's current configuration: the better of two runs of
+    // trial_steps steps, each from the restored state
+    auto trial = [&](double& ms) -> sdc_status {
+        ms = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaMemcpyAsync(d_v, sv, nb, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(d_w, sw, nw, cudaMemcpyDeviceToDevice, s);
+            cudaEventRecord(e0, s);
+            for (int n = 0; n < trial_steps; ++n) {
+                const sdc_status st = step_impl(c, d_v, d_w, t + n * dt, dt, sweeps, TOL,
+                                                nullptr, nullptr);
+                if (st != SDC_OK) return st;
+            }
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(c, "autotune");
+            float f = 0.0f;
+            cudaEventElapsedTime(&f, e0, e1);
+            ms = std::min(ms, (double)f / trial_steps);
+        }
+        return SDC_OK;
+    };
+    PcgConfig& P = c->pcg;
+    const bool batch = c->B.nseg > 0;
+    std::vector<TuneKnob> knobs;
+    if (!batch) {
+        knobs.push_back({{1, 0}, [](PcgConfig& q, int v) { q.pipelined = v; return true; }});
+        knobs.push_back({{1, 0}, [](PcgConfig& q, int v) { q.scaled = v; return true; }});
+        knobs.push_back({{512, 1024}, [](PcgConfig& q, int v) { q.smem_block = v; return true; }});
+        knobs.push_back({{0, 100000, 300000, 0x7fffffff},
+                         [](PcgConfig& q, int v) { q.big_rows = v; return true; }});
+        const int cap = c->B.max_blocks;
+        knobs.push_back({{256, 512, 1024}, [cap](PcgConfig& q, int v) {
+                             const int g = pcg_max_blocks(v);
+                             if (g < 1 || g > cap) return false;
+                             q.block = v;
+                             q.max_blocks_general = q.max_blocks > 0 ? std::min(g, q.max_blocks) : g;
+                             return true;
+                         }});
+        const int ccap = P.cluster * kClusterRows;
+        knobs.push_back({{0, 2000, 5000, 10000, 20000}, [ccap](PcgConfig& q, int v) {
+                             if (v > ccap) return false;
+                             q.cluster_rows = v;
+                             return true;
+                         }});
+    } else {
+        knobs.push_back({{0, 1}, [](PcgConfig& q, int v) { q.batch_pipelined = v; return true; }});
+        knobs.push_back({{1, 0}, [](PcgConfig& q, int v) { q.scaled = v; return true; }});
+        const int cap = std::min(c->B.max_blocks, c->B.segtab_cap);
+        knobs.push_back({{256, 512, 1024}, [cap](PcgConfig& q, int v) {
+                             const int g = pcg_batch_max_blocks(v);
+                             if (g < 1 || g > cap) return false;
+                             q.batch_block = v;
+                             q.max_blocks_batch = q.max_blocks > 0 ? std::min(g, q.max_blocks) : g;
+                             return true;
+                         }});
+        knobs.push_back({{256, 512, 1024, 2048, 4096}, [](PcgConfig& q, int v) {
+                             q.batch_rows_per_block = v;
+                             return true;
+                         }});
+    }
+    double best = 0.0, base = 0.0;
+    int trials = 0;
+    // the first trial only warms up (first-use attributes, caches)
+    status = trial(best);
+    if (status == SDC_OK) status = trial(best);
+    base = best;
+    ++trials;
+    for (size_t k = 0; k < knobs.size() && status == SDC_OK; ++k) {
+        PcgConfig keep = P;
+        PcgConfig chosen = P;
+        for (int v : knobs[k].values) {
+            PcgConfig cand = keep;
+            if (!knobs[k].apply(cand, v)) continue;
+            P = cand;
+            double ms = 0.0;
+            status = trial(ms);
+            ++trials;
+            if (status != SDC_OK) break;
+            if (ms < 0.97 * best) {
+                best = ms;
+                chosen = cand;
+            }
+        }
+        P = chosen;
+    }
+    cudaMemcpyAsync(d_v, sv, nb, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(d_w, sw, nw, cudaMemcpyDeviceToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && status == SDC_OK)
+        status = cuda_fail(c, "autotune");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sv);
+    cudaFree(sw);
+    if (out) {
+        out->trials = trials;
+        out->base_ms = base;
+        out->best_ms = best;
+        out->cg_pipelined = P.pipelined;
+        out->cg_scaled = P.scaled;
+        out->smem_block = P.smem_block;
+        out->big_rows = P.big_rows;
+        out->general_block = P.block;
+        out->cluster_rows = P.cluster_rows;
+        out->batch_pipelined = P.batch_pipelined;
+        out->batch_block = P.batch_block;
+        out->batch_rows_per_block = P.batch_rows_per_block;
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdc_status sdc_autotune(sdc_ctx* ctx, double* d_v, double* d_w, double t, double dt, int sweeps,
+                        double TOL, int trial_steps, sdc_tune_report* out) {
+    return autotune_impl(ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+}
+
+sdc_status sdc_batch_autotune(sdc_batch* bt, double* d_v, double* d_w, double t, double dt,
+                              int sweeps, double TOL, int trial_steps, sdc_tune_report* out) {
+    if (!bt) return SDC_E_INVALID;
+    return autotune_impl(bt->ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+}
+
+}  // extern "C"
+

@@ -123,6 +123,7 @@ struct StepBuffers {
     int* inst_off = nullptr;      // [nseg + 1] first dof of each instance
     int* bounds = nullptr;        // [nseg + 1] instance boundaries in the current active list
     int* segtab = nullptr;        // per-block group table of the batched PCG launch
+    int segtab_cap = 0;           // blocks the group table holds
     unsigned* bars = nullptr;     // [nseg] barrier counters
     int* seg_iters = nullptr;     // [SDC_MAX_SWEEPS * kMaxM * nseg]
     double* seg_relres = nullptr; // same shape
@@ -167,6 +168,8 @@ struct PcgConfig {
     int inject_fault = 0;
     int pipelined = 1;              // 1: pipelined CG; 0: classical arrangement
     int scaled = 1;                 // pipelined shared-memory solves in the scaled form
+    int general_classical = 0;      // pipelined contexts: classical arrangement for the
+                                    // global-vector variant (automatic choice)
     long long budget = 0;
 };
 int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rtol, int maxit,

@@ -2053,7 +2053,11 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
     if (reinterpret_cast<uintptr_t>(P.part) % 16 != 0) return SDC_E_INVALID;
     cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
     void* args[] = {&P};
-    if (!cfg.pipelined) {
+    // automatic arrangement: the pipelined form pays off where the vectors live on chip;
+    // for the global-vector variant (solves above the on-chip capacity) its extra vector
+    // traffic outweighs the saved synchronisation
+    const bool on_chip = cfg.variant != 1 && n <= cfg.sms * kSmemRows;
+    if (!cfg.pipelined || (cfg.general_classical && !on_chip)) {
         // classical arrangement: shared-memory form when it fits, else global vectors
         if (cfg.variant != 1 && n <= cfg.sms * kSmemRowsC) {
             const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;

@@ -141,3 +141,13 @@ def test_drop_rule_validation_before_device_work(lib):
     with pytest.raises(SdcError) as e:
         Batch([sq, sq], options=default_options(drop_rule=1, sdc_rho=0.05))
     assert e.value.status == -1 and "batch" in str(e.value)
+
+
+def test_autotune_rejects_bad_arguments_without_a_device(lib):
+    """NULL context or batch is rejected before anything else."""
+    import ctypes as C
+    from paper_2311_07206_gb300 import binding as B
+    L = B.load()
+    rep = B.sdc_tune_report()
+    assert L.sdc_autotune(None, None, None, 0.0, 0.1, 4, 1e-4, 3, C.byref(rep)) == B.SDC_E_INVALID
+    assert L.sdc_batch_autotune(None, None, None, 0.0, 0.1, 4, 1e-4, 3, None) == B.SDC_E_INVALID
