@@ -105,7 +105,8 @@ typedef struct {
     int cg_cluster_max;    /* largest cluster (CTAs) for the cluster CG, 1..16; default 16      */
     int cg_max_blocks;     /* 0: no limit on the cooperative CG grid                          */
     int cg_variant;        /* 0: automatic; 1: vectors in global memory; 2: per-block vectors
-                              in shared memory whenever |I_k| <= 4096 * SM count             */
+                              in shared memory whenever they fit (3584 rows per SM for the
+                              pipelined, 4768 for the classical arrangement)                 */
     int cg_rows_per_block; /* shared-memory variant: target rows per block (0 = 512)          */
     int cg_cluster_rows;   /* solves with |I_k| <= this run on one thread-block cluster
                               (16 CTAs, distributed shared memory); default 10000, 0 = never */
