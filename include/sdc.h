@@ -151,10 +151,17 @@ typedef struct {
                               max(0, -min dI/dv) / C_m over the first sweep's linearisation
                               (zero with reaction_implicit = 0); computed on the device once
                               per step, reported in sdc_stats.tol_drop.  Not in batches      */
-    int cg_scaled;         /* 1: pipelined shared-memory solves run in the symmetrically scaled
-                              form, CG on diag^-1/2 A diag^-1/2 (the same iterates as
-                              Jacobi-PCG with fewer FP64 operations per row and six vectors on
-                              chip); 0: the Jacobi form; default 1                          */
+    int cg_scaled;         /* 1: the node solves (shared-memory, global-vector and batched
+                              variants; the cluster variant keeps the Jacobi form) run in the
+                              symmetrically scaled form, CG on diag^-1/2 A diag^-1/2: the same
+                              iterates as Jacobi-PCG with fewer FP64 operations per row and
+                              fewer vectors on chip; 0: the Jacobi form; default 1          */
+    int batch_graph;       /* batches: 1 runs each step with device-driven sweeps (|I_k| read on
+                              the device, the batched solves' block plan built on the device)
+                              captured once per (state arrays, dt, sweeps, TOL, stimulus on or
+                              off) as one CUDA graph and replayed, one host synchronisation per
+                              step; 0 host-driven sweeps.  Bitwise the same results; nnz_active
+                              is not tracked in captured steps.  Default 1                   */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */
@@ -173,6 +180,7 @@ typedef struct {
     double energy[SDC_MAX_SWEEPS];         /* E_k = sum_m dv_m' A~_m dv_m of sweep k, from the CG
                                               scalars (sum of alpha gamma over each solve)    */
     double tol_drop;                       /* the drop tolerance the step's selections used   */
+    int captured;                          /* 1: the step ran as a replayed CUDA graph        */
 } sdc_stats;
 
 /* Fill defaults (values above). */

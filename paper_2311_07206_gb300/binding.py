@@ -44,7 +44,8 @@ class sdc_options(C.Structure):
                 ("cg_rows_per_block", C.c_int), ("cg_cluster_rows", C.c_int),
                 ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
                 ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int),
-                ("reorder", C.c_int), ("drop_rule", C.c_int), ("cg_scaled", C.c_int)]
+                ("reorder", C.c_int), ("drop_rule", C.c_int), ("cg_scaled", C.c_int),
+                ("batch_graph", C.c_int)]
 
 
 class sdc_stats(C.Structure):
@@ -55,7 +56,8 @@ class sdc_stats(C.Structure):
                 ("kernel_launches", C.c_int), ("phase_launches", C.c_int * SDC_N_PHASES),
                 ("phase_ms", C.c_double * SDC_N_PHASES),
                 ("cg_ms", (C.c_double * SDC_MAX_M) * SDC_MAX_SWEEPS),
-                ("energy", C.c_double * SDC_MAX_SWEEPS), ("tol_drop", C.c_double)]
+                ("energy", C.c_double * SDC_MAX_SWEEPS), ("tol_drop", C.c_double),
+                ("captured", C.c_int)]
 
 
 class sdc_tune_report(C.Structure):

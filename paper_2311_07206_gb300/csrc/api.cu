@@ -48,6 +48,21 @@ struct sdc_ctx {
     double* wp = nullptr;
     bool stepped = false;
     std::string err;
+    // captured batched steps (batch_graph option): one executable graph per key
+    struct GraphEntry {
+        const void* v;
+        const void* w;
+        double dt, TOL, stim_on;
+        int sweeps, epoch, launches;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    int cfg_epoch = 0;            // bumped whenever the launch configuration changes
+    bool graph_broken = false;    // capture failed once: host-driven sweeps from then on
+    // captured steps run on a private stream (the caller's may be the legacy default
+    // stream, which cannot be captured), ordered after and before the caller's by events
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
 };
 
 namespace {
@@ -146,6 +161,8 @@ int alloc_buffers(sdc_ctx* c) {
              (B.segtab_cap = P.max_blocks_batch) > 0 &&
              dalloc(&B.seg_iters, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
              dalloc(&B.seg_relres, (size_t)SDC_MAX_SWEEPS * kMaxM * nseg) &&
+             dalloc(&B.plan, 2 * (size_t)nseg) && dalloc(&B.nk, SDC_MAX_SWEEPS + 1) &&
+             dalloc(&B.bounds_k, (size_t)(SDC_MAX_SWEEPS + 1) * (nseg + 1)) &&
              cudaMallocHost(&c->h_bounds, (nseg + 1) * sizeof(int)) == cudaSuccess;
         if (ok)
             cudaMemcpyAsync(B.inst_off, c->inst_off.data(), (nseg + 1) * sizeof(int),
@@ -179,6 +196,16 @@ void free_all(sdc_ctx* c) {
     if (c->h_bounds) cudaFreeHost(c->h_bounds);
     c->h_bounds = nullptr;
     cudaFree(B.sc);
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->gev_in) cudaEventDestroy(c->gev_in);
+    if (c->gev_out) cudaEventDestroy(c->gev_out);
+    c->gstream = nullptr;
+    c->gev_in = c->gev_out = nullptr;
+    cudaFree(B.plan);
+    cudaFree(B.nk);
+    cudaFree(B.bounds_k);
     free_ell(B.A[0]);
     free_ell(B.A[1]);
     free_ell(c->K.K);
@@ -275,6 +302,7 @@ void sdc_default_options(sdc_options* o) {
     o->sdc_qhat = 0;
     o->reorder = 0;
     o->drop_rule = 0;
+    o->batch_graph = 1;
     o->cg_scaled = 1;
 }
 
@@ -396,7 +424,8 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.cg_cluster_rows < 0 || o.cg_pipelined < -1 || o.cg_pipelined > 1 ||
         o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
         o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1 ||
-        o.drop_rule < 0 || o.drop_rule > 1 || o.cg_scaled < 0 || o.cg_scaled > 1)
+        o.drop_rule < 0 || o.drop_rule > 1 || o.cg_scaled < 0 || o.cg_scaled > 1 ||
+        o.batch_graph < 0 || o.batch_graph > 1)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (o.drop_rule == 1 && !(o.sdc_rho > 0.0))
         return fail(nullptr, SDC_E_INVALID, "drop_rule = 1 needs a given sdc_rho in (0, 1)");
@@ -548,6 +577,7 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
 sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, double t_on,
                             double t_off) {
     if (!c) return SDC_E_INVALID;
+    ++c->cfg_epoch;   // captured steps bake the context's data in
     if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_set_stimulus: not available for EMI contexts");
     if (n < 0 || (n > 0 && !nodes)) return fail(c, SDC_E_INVALID, "bad stimulus node list");
     for (int i = 0; i < n; ++i)
@@ -638,6 +668,155 @@ sdc_status step_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     return st;
 }
 
+// A batched step with device-driven sweeps, captured once per (state arrays, dt,
+// sweeps, TOL, stimulus on/off, launch configuration) as one CUDA graph and replayed:
+// every kernel reads |I_k| on the device (grids sized for N, rows past |I_k| idle), the
+// block plan of each batched solve is built on the device from the instance boundaries,
+// and the host synchronises once per step instead of once per sweep.  The arithmetic
+// is that of the host-driven step (same kernels; the exact sums make a solve
+// independent of how its rows are split into blocks), so the results agree bitwise.
+// Returns SDC_E_CUDA with graph_broken set when the capture itself fails.
+sdc_status step_batch_graph(sdc_ctx* c, double* d_v, double* d_w, double dt, int sweeps,
+                            double TOL, double stim_on, sdc_stats* stats) {
+    StepBuffers& B = c->B;
+    const int N = c->N, M = c->M, nseg = B.nseg;
+    if (!c->gstream) {
+        if (cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_broken = true;
+            return fail(c, SDC_E_CUDA, "batch step: private stream unavailable");
+        }
+    }
+    cudaStream_t s = c->gstream;
+    // the step follows the caller's earlier work on its stream
+    cudaEventRecord(c->gev_in, c->stream);
+    cudaStreamWaitEvent(s, c->gev_in, 0);
+    const double tol_drop = c->opt.alpha * TOL;
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+    for (const auto& g : c->graphs)
+        if (g.v == d_v && g.w == d_w && g.dt == dt && g.TOL == TOL && g.stim_on == stim_on &&
+            g.sweeps == sweeps && g.epoch == c->cfg_epoch) {
+            exec = g.exec;
+            launches = g.launches;
+        }
+    if (!exec) {
+        cudaGetLastError();
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_broken = true;
+            return fail(c, SDC_E_CUDA, "batch step: stream capture unavailable");
+        }
+        int L = 0;
+        bool ok = true;
+        const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * nseg;
+        cudaMemsetAsync(B.sc, 0, sizeof(DevScalars), s);
+        cudaMemsetAsync(B.seg_iters, 0, cnt * sizeof(int), s);
+        cudaMemsetAsync(B.seg_relres, 0, cnt * sizeof(double), s);
+        launch_graph_init(B, s);
+        launch_spread(N, M, d_v, d_w, B.V, B.W, s);
+        L += 2;
+        const Ell* A = &c->K.K;
+        int cur = 0;
+        for (int k = 0; k < sweeps && ok; ++k) {
+            const int* act = k ? c->act[k] : nullptr;
+            int* next = (k + 1 < sweeps) ? c->act[k + 1] : c->act[0];
+            const int* nd = B.nk + k;
+            const int* bd = B.bounds_k + (size_t)k * (nseg + 1);
+            launch_residual(M, N, act, c->K.K, c->K.kdiag, c->K.mass, c->stim, stim_on, B.V, B.W,
+                            d_v, dt, c->ion, c->co, c->opt.reaction_implicit, B, s, nd);
+            ++L;
+            for (int m = 0; m < M && ok; ++m) {
+                ok = launch_pcg_batch_planned(*A, m, dt, c->co, c->opt.cg_rtol, c->opt.cg_maxit, k,
+                                              c->pcg, bd, m == 0, B, s) == SDC_OK;
+                L += m == 0 ? 2 : 1;
+            }
+            launch_update(M, N, act, d_w, dt, c->ion, c->co, tol_drop, c->opt.w_frozen, B, s,
+                          nullptr, nd);
+            launch_select(N, act, next, B, s, nd);
+            cudaMemcpyAsync(B.nk + k + 1, &B.sc->count, sizeof(int), cudaMemcpyDeviceToDevice, s);
+            launch_seg_bounds(next, &B.sc->count, B, s, B.bounds_k + (size_t)(k + 1) * (nseg + 1));
+            L += 4;
+            if (k + 1 < sweeps) {
+                Ell& An = B.A[cur];
+                launch_extract(N, *A, B.map, An, B, s, nd);
+                A = &An;
+                cur ^= 1;
+                ++L;
+            }
+        }
+        launch_final(N, M, B.V, B.W, d_v, d_w, s);
+        ++L;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+        if (!ok || ec != cudaSuccess || !graph ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            c->graph_broken = true;
+            return fail(c, SDC_E_CUDA, "batch step: capture failed; host-driven sweeps from now on");
+        }
+        cudaGraphDestroy(graph);
+        if (c->graphs.size() >= 8) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back({d_v, d_w, dt, TOL, stim_on, sweeps, c->cfg_epoch, L, exec});
+        launches = L;
+    }
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) return cuda_fail(c, "batch step graph launch");
+    // later work on the caller's stream follows the step
+    cudaEventRecord(c->gev_out, s);
+    cudaStreamWaitEvent(c->stream, c->gev_out, 0);
+    std::vector<int> nk(sweeps + 1), bk((size_t)(sweeps + 1) * (nseg + 1));
+    cudaMemcpyAsync(&c->h_pin[1], &B.sc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(nk.data(), B.nk, nk.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(bk.data(), B.bounds_k, bk.size() * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(c, "batch step");
+    for (int k = 0; k < sweeps; ++k) {
+        c->n_act[k] = nk[k];
+        for (int g = 0; g < nseg; ++g)
+            c->inst_active[(size_t)k * nseg + g] =
+                bk[(size_t)k * (nseg + 1) + g + 1] - bk[(size_t)k * (nseg + 1) + g];
+    }
+    c->seg_bounds.assign(bk.begin(), bk.begin() + nseg + 1);
+    c->last_sweeps = sweeps;
+    c->stepped = true;
+    const int e = c->h_pin[1];
+    if (e != SDC_OK) return fail(c, (sdc_status)e, "batch step: %s", sdc_status_string(e));
+    if (stats) {
+        const size_t cnt = (size_t)SDC_MAX_SWEEPS * kMaxM * nseg;
+        std::vector<int> si(cnt);
+        std::vector<double> sr(cnt);
+        double mg = 0.0;
+        cudaMemcpyAsync(si.data(), B.seg_iters, cnt * sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(sr.data(), B.seg_relres, cnt * sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        stats->sweeps_run = sweeps;
+        for (int k = 0; k < sweeps; ++k) {
+            stats->n_active[k] = nk[k];
+            stats->nnz_active[k] = 0;          // not tracked in captured steps
+            for (int m = 0; m < M; ++m) {
+                int mx = 0;
+                for (int g = 0; g < nseg; ++g) {
+                    const size_t at = (size_t)(k * kMaxM + m) * nseg + g;
+                    mx = std::max(mx, si[at]);
+                    stats->cg_relres_max = std::max(stats->cg_relres_max, sr[at]);
+                }
+                stats->cg_iters[k][m] = mx;
+            }
+        }
+        stats->min_margin = mg >= 1.7976931348623157e308 ? INFINITY : mg;
+        stats->kernel_launches = launches;
+        stats->tol_drop = tol_drop;
+        stats->captured = 1;
+    }
+    return SDC_OK;
+}
+
 sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
                      double TOL, sdc_stats* stats, sdc_tape* tape) {
     if (!c) return SDC_E_INVALID;
@@ -672,6 +851,13 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         c->last_sweeps = done;
         c->stepped = true;
         return (sdc_status)st;
+    }
+    if (B.nseg > 0 && c->opt.batch_graph && !tape && !c->graph_broken &&
+        B.nseg <= c->pcg.max_blocks_batch) {
+        const sdc_status st = step_batch_graph(c, d_v, d_w, dt, sweeps, TOL, stim_on, stats);
+        if (st != SDC_E_CUDA || !c->graph_broken) return st;
+        // the capture itself failed: fall through to host-driven sweeps
+        if (stats) std::memset(stats, 0, sizeof(*stats));
     }
 
     // kernel phases: launch counts always, device time with the profile option
@@ -1208,6 +1394,7 @@ sdc_status sdc_batch_set_stimulus(sdc_batch* bt, int instance, const int* nodes,
                                   double t_on, double t_off) {
     if (!bt) return SDC_E_INVALID;
     sdc_ctx* c = bt->ctx;
+    ++c->cfg_epoch;   // captured steps bake the context's data in
     const int ninst = (int)bt->off.size() - 1;
     if (instance < 0 || instance >= ninst)
         return fail(c, SDC_E_INVALID, "instance %d out of range", instance);
@@ -1339,6 +1526,7 @@ sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0
 
 sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
     if (!c) return SDC_E_INVALID;
+    ++c->cfg_epoch;   // captured steps bake the context's data in
     if (c->B.nseg > 0) return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: not available for batches");
     if (c->is_emi) return fail(c, SDC_E_INVALID, "sdc_set_dof_scale: not available for EMI contexts");
     if (h_scale)
@@ -1359,6 +1547,7 @@ sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
 
 sdc_status sdc_set_ionic(sdc_ctx* c, const sdc_ionic* ionic) {
     if (!c || !ionic) return SDC_E_INVALID;
+    ++c->cfg_epoch;   // captured steps bake the context's data in
     if (!(ionic->mu2 > 0.0) && !c->opt.w_frozen)
         return fail(c, SDC_E_INVALID, "mu2 must be positive");
     c->ion_c = *ionic;
@@ -1479,6 +1668,7 @@ sdc_status autotune_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double 
             PcgConfig cand = keep;
             if (!knobs[k].apply(cand, v)) continue;
             P = cand;
+            ++c->cfg_epoch;
             double ms = 0.0;
             status = trial(ms);
             ++trials;
@@ -1489,6 +1679,7 @@ sdc_status autotune_impl(sdc_ctx* c, double* d_v, double* d_w, double t, double 
             }
         }
         P = chosen;
+        ++c->cfg_epoch;
     }
     cudaMemcpyAsync(d_v, sv, nb, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(d_w, sw, nw, cudaMemcpyDeviceToDevice, s);

@@ -124,6 +124,9 @@ struct StepBuffers {
     int* bounds = nullptr;        // [nseg + 1] instance boundaries in the current active list
     int* segtab = nullptr;        // per-block group table of the batched PCG launch
     int segtab_cap = 0;           // blocks the group table holds
+    int* plan = nullptr;          // [2 nseg] blocks and first block per instance (planned launch)
+    int* nk = nullptr;            // [SDC_MAX_SWEEPS + 1] |I_k| of a captured step
+    int* bounds_k = nullptr;      // [(SDC_MAX_SWEEPS + 1) (nseg + 1)] boundaries per sweep
     unsigned* bars = nullptr;     // [nseg] barrier counters
     int* seg_iters = nullptr;     // [SDC_MAX_SWEEPS * kMaxM * nseg]
     double* seg_relres = nullptr; // same shape
@@ -138,7 +141,8 @@ void launch_nodes_out(int N, int M, const double* V, const double* W, double* Vo
 void launch_residual(int M, int n, const int* act, const Ell& K, const double* kdiag,
                      const double* mass, const double* stim, double stim_on, const double* V,
                      const double* W, const double* v0, double dt, const Ionic& ion,
-                     const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s);
+                     const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s,
+                     const int* n_dev = nullptr);
 // Launch configuration of the restricted PCG solves.
 constexpr int kSmemVectorsS = 6;    // the same for the symmetrically scaled variant
 constexpr int kSmemVectorsCS = 4;   // the scaled classical shared-memory variant (kSmemRowsC rows)
@@ -207,7 +211,16 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
 int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
                      int maxit, int sweep, const PcgConfig& cfg, const std::vector<int>& bounds,
                      StepBuffers& B, cudaStream_t s);
-void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s);
+void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s,
+                       int* bounds_out = nullptr);
+// Device-planned form for captured steps: a single-block kernel apportions the fixed
+// cooperative grid (max_blocks_batch blocks) to the instances from the device boundaries
+// bounds_dev (plan = true: rebuild the table, once per sweep), blocks without a group
+// leave at once.  Needs nseg <= max_blocks_batch.
+void launch_graph_init(StepBuffers& B, cudaStream_t s);
+int launch_pcg_batch_planned(const Ell& A, int m, double dt, const Coll& co, double rtol,
+                             int maxit, int sweep, const PcgConfig& cfg, const int* bounds_dev,
+                             bool plan, StepBuffers& B, cudaStream_t s);
 int pcg_batch_max_blocks(int block);
 
 // ---- adjoint (adjoint.cu) ----
@@ -274,15 +287,17 @@ int pcg_cluster_size(int block);
 // tol_drop_dev: when set, the selection reads TOL_drop there instead of tol_drop
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
                    const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s,
-                   const double* tol_drop_dev = nullptr);
+                   const double* tol_drop_dev = nullptr, const int* n_dev = nullptr);
 // A priori drop tolerance of Sec. 4.1 into B.sc->tol_drop, from the first sweep's
 // corrections (n rows of D, M nodes) and Jacobians (nj entries per node at stride ldj).
 void launch_drop_rule(int n, int M, const double* D, int ld, int nj, const double* J, int ldj,
                       double Cm, double rho, double TOL, double dt, StepBuffers& B,
                       cudaStream_t s);
-void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s);
+// n_dev: when set, |I_k| is read on the device and n only sizes the grid (captured steps)
+void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s,
+                   const int* n_dev = nullptr);
 void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepBuffers& B,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* n_dev = nullptr);
 int pcg_max_blocks(int block);
 
 // ---- cell-by-cell (EMI) model (emi.cu) ----

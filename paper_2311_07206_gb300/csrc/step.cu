@@ -79,7 +79,8 @@ __global__ void k_residual(int n, const int* __restrict__ act, const double* __r
                            const double* __restrict__ v0, double dt, Ionic ion, Coll co,
                            int reaction_implicit, int ld, double* __restrict__ R,
                            double* __restrict__ Jout, double* __restrict__ mc,
-                           double* __restrict__ kdc) {
+                           double* __restrict__ kdc, const int* __restrict__ n_dev) {
+    if (n_dev) n = *n_dev;   // device-driven sweeps: |I_k| from the device, grid for N
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int g = act ? act[p] : p;
@@ -585,6 +586,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_batch(CgParams P, const SegBloc
                                                         double* __restrict__ seg_relres) {
     __shared__ CgShared S;
     const SegBlock g = tab[blockIdx.x];
+    if (g.nblk == 0) return;   // no group: a planned launch's spare block
     pcg_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
               reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x, seg_iters + g.seg,
               seg_relres + g.seg);
@@ -1337,6 +1339,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_batch(CgParams P, const SegBl
                                                           double* __restrict__ seg_relres) {
     __shared__ CgShared S;
     const SegBlock g = tab[blockIdx.x];
+    if (g.nblk == 0) return;   // no group: a planned launch's spare block
     pcgc_group_scaled(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
                       reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x,
                       seg_iters + g.seg, seg_relres + g.seg);
@@ -1357,6 +1360,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_batch(CgParams P, const SegBlo
                                                          double* __restrict__ seg_relres) {
     __shared__ CgShared S;
     const SegBlock g = tab[blockIdx.x];
+    if (g.nblk == 0) return;   // no group: a planned launch's spare block
     pcgc_group(P, S, g.row0, g.row1, g.nblk, (int)blockIdx.x - g.blk0, bars + g.seg,
                reinterpret_cast<XsRecord*>(P.part) + g.blk0, (int)gridDim.x, seg_iters + g.seg,
                seg_relres + g.seg);
@@ -1615,9 +1619,11 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
                          const double* __restrict__ w0, double dt, Ionic ion, Coll co,
                          double tol_drop, int w_frozen, int* __restrict__ flag,
                          int* __restrict__ blockcnt, double* __restrict__ blockmarg,
-                         int* __restrict__ err, const double* __restrict__ tol_drop_dev) {
+                         int* __restrict__ err, const double* __restrict__ tol_drop_dev,
+                         const int* __restrict__ n_dev) {
     __shared__ int wc[32];
     if (tol_drop_dev) tol_drop = *tol_drop_dev;
+    if (n_dev) n = *n_dev;
     __shared__ double wmg[32];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int keep = 0;
@@ -1731,8 +1737,9 @@ __global__ void k_scan_counts(int nb, const int* __restrict__ cnt, int* __restri
 
 __global__ void k_scatter(int n, const int* __restrict__ act, const int* __restrict__ flag,
                           const int* __restrict__ blockoff, int* __restrict__ act_next,
-                          int* __restrict__ map) {
+                          int* __restrict__ map, const int* __restrict__ n_dev) {
     __shared__ int woff[32];
+    if (n_dev) n = *n_dev;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int keep = p < n ? flag[p] : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
@@ -1761,7 +1768,8 @@ __global__ void k_scatter(int n, const int* __restrict__ act, const int* __restr
 __global__ void k_extract(int n_old, const double* __restrict__ oval, const int* __restrict__ ocol,
                           const int* __restrict__ olen, int old_ld, const int* __restrict__ map,
                           double* __restrict__ nval, int* __restrict__ ncol, int* __restrict__ nlen,
-                          int new_ld, unsigned long long* nnz) {
+                          int new_ld, unsigned long long* nnz, const int* __restrict__ n_dev) {
+    if (n_dev) n_old = *n_dev;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int cnt = 0;
     if (p < n_old) {
@@ -1834,12 +1842,15 @@ void launch_nodes_out(int N, int M, const double* V, const double* W, double* Vo
 void launch_residual(int M, int n, const int* act, const Ell& K, const double* kdiag,
                      const double* mass, const double* stim, double stim_on, const double* V,
                      const double* W, const double* v0, double dt, const Ionic& ion,
-                     const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s) {
+                     const Coll& co, int reaction_implicit, StepBuffers& B, cudaStream_t s,
+                     const int* n_dev) {
+    if (n < 1) return;
     dispatch_M(M, [&](auto mc) {
         constexpr int MM = decltype(mc)::value;
         k_residual<MM><<<nblk(n, 128), 128, 0, s>>>(n, act, K.val, K.col, K.len, K.ld, kdiag, mass,
                                                       stim, stim_on, V, W, v0, dt, ion, co,
-                                                      reaction_implicit, B.ld, B.R, B.J, B.mc, B.kdc);
+                                                      reaction_implicit, B.ld, B.R, B.J, B.mc, B.kdc,
+                                                      n_dev);
     });
 }
 
@@ -2168,28 +2179,80 @@ int pcg_batch_max_blocks(int block) {
     return sms * per;
 }
 
-void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s) {
-    k_seg_bounds<<<nblk(B.nseg + 1, 128), 128, 0, s>>>(count, act, B.nseg, B.inst_off, B.bounds);
+void launch_seg_bounds(const int* act, const int* count, StepBuffers& B, cudaStream_t s,
+                       int* bounds_out) {
+    k_seg_bounds<<<nblk(B.nseg + 1, 128), 128, 0, s>>>(count, act, B.nseg, B.inst_off,
+                                                        bounds_out ? bounds_out : B.bounds);
 }
 
-int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
-                     int maxit, int sweep, const PcgConfig& cfg, const std::vector<int>& bounds,
-                     StepBuffers& B, cudaStream_t s) {
-    const int nseg = (int)bounds.size() - 1;
-    const int Gmax = cfg.max_blocks_batch;
-    // blocks per instance: proportional to its active rows, at least one
-    std::vector<int> want(nseg, 0);
-    long long total = 0;
-    for (int g = 0; g < nseg; ++g) {
-        const int r = bounds[g + 1] - bounds[g];
-        if (r > 0) want[g] = std::max(1, nblk(r, cfg.batch_rows_per_block));
-        total += want[g];
+// Start of a captured batched step: margin, |I_0| = N and the sweep-0 boundaries.
+__global__ void k_graph_init(DevScalars* sc, int* nk, int N, const int* __restrict__ inst_off,
+                             int* __restrict__ bounds0, int nseg) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        sc->margin = DBL_MAX;
+        nk[0] = N;
     }
-    if (total > Gmax) {
-        const double f = (double)Gmax / (double)total;
-        for (int g = 0; g < nseg; ++g)
-            if (want[g] > 0) want[g] = std::max(1, (int)(want[g] * f));
+    for (int i = t; i <= nseg; i += gridDim.x * blockDim.x) bounds0[i] = inst_off[i];
+}
+
+void launch_graph_init(StepBuffers& B, cudaStream_t s) {
+    k_graph_init<<<1, 256, 0, s>>>(B.sc, B.nk, B.N, B.inst_off, B.bounds_k, B.nseg);
+}
+
+// Block plan of a batched solve from the device boundaries (one block).  Every non-empty
+// instance gets max(1, ceil(rows / rpb)) blocks; when that exceeds the grid G, each keeps
+// one block and the remaining G - (non-empty instances) are shared in proportion to the
+// extra blocks it asked for (rounded down), so the total never exceeds G (the host checks
+// nseg <= G).  Table entries past the total get nblk = 0.
+__global__ void k_batch_plan(int nseg, const int* __restrict__ bounds, int G, int rpb,
+                             SegBlock* __restrict__ tab, int* __restrict__ want,
+                             int* __restrict__ first) {
+    __shared__ int total_s;
+    if (threadIdx.x == 0) {
+        long long tot = 0, extra = 0;
+        int nonempty = 0;
+        for (int g = 0; g < nseg; ++g) {
+            const int r = bounds[g + 1] - bounds[g];
+            const int w = r > 0 ? max(1, (r + rpb - 1) / rpb) : 0;
+            want[g] = w;
+            nonempty += r > 0;
+            tot += w;
+            extra += w > 0 ? w - 1 : 0;
+        }
+        if (tot > G) {
+            const long long budget = G - nonempty;
+            for (int g = 0; g < nseg; ++g)
+                if (want[g] > 0) want[g] = 1 + (int)((long long)(want[g] - 1) * budget / extra);
+        }
+        int run = 0;
+        for (int g = 0; g < nseg; ++g) {
+            first[g] = run;
+            run += want[g];
+        }
+        total_s = run;
     }
+    __syncthreads();
+    const int total = total_s;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) {
+        SegBlock e{0, 0, 0, 0, 0};
+        if (b < total) {
+            // the last instance whose first block is <= b: a non-empty one (an empty
+            // instance shares its first block with the next non-empty instance)
+            int lo = 0, hi = nseg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (first[mid] <= b) lo = mid; else hi = mid - 1;
+            }
+            e = SegBlock{bounds[lo], bounds[lo + 1], first[lo], want[lo], lo};
+        }
+        tab[b] = e;
+    }
+}
+
+// Parameters of a batched node solve (the groups come from the block table)
+CgParams batch_params(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
+                      int maxit, const PcgConfig& cfg, StepBuffers& B) {
     CgParams P{};
     P.n = n;
     P.ld = B.ld;
@@ -2223,6 +2286,28 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
     for (int j = 0; j < kMaxM; ++j) P.qh[j] = j < co.M ? co.Qh[j * kMaxM + m] : 0.0;
     P.inject_fault = 0;
     P.L = 0;
+    return P;
+}
+
+int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, double rtol,
+                     int maxit, int sweep, const PcgConfig& cfg, const std::vector<int>& bounds,
+                     StepBuffers& B, cudaStream_t s) {
+    const int nseg = (int)bounds.size() - 1;
+    const int Gmax = cfg.max_blocks_batch;
+    // blocks per instance: proportional to its active rows, at least one
+    std::vector<int> want(nseg, 0);
+    long long total = 0;
+    for (int g = 0; g < nseg; ++g) {
+        const int r = bounds[g + 1] - bounds[g];
+        if (r > 0) want[g] = std::max(1, nblk(r, cfg.batch_rows_per_block));
+        total += want[g];
+    }
+    if (total > Gmax) {
+        const double f = (double)Gmax / (double)total;
+        for (int g = 0; g < nseg; ++g)
+            if (want[g] > 0) want[g] = std::max(1, (int)(want[g] * f));
+    }
+    CgParams P = batch_params(n, A, m, dt, co, rtol, maxit, cfg, B);
     int* seg_iters = B.seg_iters + (size_t)(sweep * kMaxM + m) * nseg;
     double* seg_relres = B.seg_relres + (size_t)(sweep * kMaxM + m) * nseg;
     cudaMemsetAsync(B.bars, 0, nseg * sizeof(unsigned), s);
@@ -2253,6 +2338,29 @@ int launch_pcg_batch(int n, const Ell& A, int m, double dt, const Coll& co, doub
         if (e != cudaSuccess) return SDC_E_CUDA;
     }
     return SDC_OK;
+}
+
+int launch_pcg_batch_planned(const Ell& A, int m, double dt, const Coll& co, double rtol,
+                             int maxit, int sweep, const PcgConfig& cfg, const int* bounds_dev,
+                             bool plan, StepBuffers& B, cudaStream_t s) {
+    const int nseg = B.nseg;
+    const int G = cfg.max_blocks_batch;
+    if (nseg < 1 || nseg > G || G > B.segtab_cap) return SDC_E_INVALID;
+    SegBlock* tab = reinterpret_cast<SegBlock*>(B.segtab);
+    if (plan)
+        k_batch_plan<<<1, 256, 0, s>>>(nseg, bounds_dev, G, cfg.batch_rows_per_block, tab, B.plan,
+                                       B.plan + nseg);
+    CgParams P = batch_params(B.N, A, m, dt, co, rtol, maxit, cfg, B);
+    int* seg_iters = B.seg_iters + (size_t)(sweep * kMaxM + m) * nseg;
+    double* seg_relres = B.seg_relres + (size_t)(sweep * kMaxM + m) * nseg;
+    cudaMemsetAsync(B.bars, 0, nseg * sizeof(unsigned), s);
+    const SegBlock* dtab = tab;
+    void* args[] = {&P, (void*)&dtab, &B.bars, &seg_iters, &seg_relres};
+    cudaError_t e = cudaLaunchCooperativeKernel(
+        (const void*)pcg_batch_kernel(cfg.batch_block, cfg.batch_pipelined,
+                                      cfg.scaled && P.sv && P.sval),
+        dim3(G), dim3(cfg.batch_block), args, 0, s);
+    return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 
 int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double* mass,
@@ -2312,12 +2420,12 @@ int launch_pcg_standalone(int n, const Ell& A, const double* kdiag, const double
 
 void launch_update(int M, int n, const int* act, const double* w0, double dt, const Ionic& ion,
                    const Coll& co, double tol_drop, int w_frozen, StepBuffers& B, cudaStream_t s,
-                   const double* tol_drop_dev) {
+                   const double* tol_drop_dev, const int* n_dev) {
     dispatch_M(M, [&](auto mc) {
         constexpr int MM = decltype(mc)::value;
         k_update<MM><<<nblk(n, kUpdateBlock), kUpdateBlock, 0, s>>>(
             n, act, B.D, B.ld, B.V, B.W, w0, dt, ion, co, tol_drop, w_frozen, B.flag, B.blockcnt,
-            B.blockmarg, &B.sc->err, tol_drop_dev);
+            B.blockmarg, &B.sc->err, tol_drop_dev, n_dev);
     });
 }
 
@@ -2369,17 +2477,19 @@ void launch_drop_rule(int n, int M, const double* D, int ld, int nj, const doubl
                                   &B.sc->tol_drop);
 }
 
-void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s) {
+void launch_select(int n, const int* act, int* act_next, StepBuffers& B, cudaStream_t s,
+                   const int* n_dev) {
     const int nb = nblk(n, kUpdateBlock);
     k_scan_counts<<<1, 1024, 0, s>>>(nb, B.blockcnt, B.blockoff, B.blockmarg, B.sc);
-    k_scatter<<<nb, kUpdateBlock, 0, s>>>(n, act, B.flag, B.blockoff, act_next, B.map);
+    k_scatter<<<nb, kUpdateBlock, 0, s>>>(n, act, B.flag, B.blockoff, act_next, B.map, n_dev);
 }
 
 void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepBuffers& B,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* n_dev) {
     cudaMemsetAsync(&B.sc->nnz, 0, sizeof(unsigned long long), s);
     k_extract<<<nblk(n_old, 256), 256, 0, s>>>(n_old, Aold.val, Aold.col, Aold.len, Aold.ld, map,
-                                               Anew.val, Anew.col, Anew.len, Anew.ld, &B.sc->nnz);
+                                               Anew.val, Anew.col, Anew.len, Anew.ld, &B.sc->nnz,
+                                               n_dev);
 }
 
 }  // namespace sdc

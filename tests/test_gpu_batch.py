@@ -107,3 +107,39 @@ def test_batch_instances_match_oracle(torch_dev):
             assert np.abs(gw[a:z] - r["w"]).max() <= RTOL * max(1.0, np.abs(r["w"]).max())
             states[b] = (r["v"], r["w"])
     batch.close()
+
+
+def test_captured_batch_step_equals_host_driven_bitwise(torch_dev):
+    """batch_graph = 1 (device-driven sweeps replayed as a CUDA graph) against
+    host-driven sweeps: the same kernels and exact sums, so the states, active
+    lists, per-instance set sizes and CG counts agree bitwise, across the end
+    of the stimulus window (a second capture)."""
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import Batch, default_options
+    insts = _instances()
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    bg = Batch(insts, options=default_options(batch_graph=1), stream=stream)
+    bh = Batch(insts, options=default_options(batch_graph=0), stream=stream)
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    v0 = np.concatenate([wl.v0 for wl in insts])
+    w0 = np.concatenate([wl.w0 for wl in insts])
+    gv, gw, hv, hw = t64(v0), t64(w0), t64(v0), t64(w0)
+    wl0 = insts[0]
+    for n in range(6):
+        t = n * wl0.dt
+        sg = bg.step(gv, gw, t, wl0.dt, wl0.sweeps, wl0.tol)
+        sh = bh.step(hv, hw, t, wl0.dt, wl0.sweeps, wl0.tol)
+        assert sg.captured == 1 and sh.captured == 0
+        assert torch.equal(gv, hv) and torch.equal(gw, hw), n
+        assert list(sg.n_active[:wl0.sweeps]) == list(sh.n_active[:wl0.sweeps])
+        for k in range(wl0.sweeps):
+            assert [sg.cg_iters[k][m] for m in range(wl0.M)] == \
+                [sh.cg_iters[k][m] for m in range(wl0.M)]
+            if sg.n_active[k]:
+                assert np.array_equal(bg.active(k), bh.active(k))
+            ng, ig = bg.instance_stats(k)
+            nh, ih = bh.instance_stats(k)
+            assert np.array_equal(ng, nh) and np.array_equal(ig, ih)
+    assert sum(sg.n_active[:wl0.sweeps]) > 0
+    bg.close()
+    bh.close()
