@@ -75,6 +75,9 @@ def lib():
         L.ora_step_forced.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
                                       C.c_double, C.c_int, C.c_double, C.POINTER(_Opts),
                                       C.POINTER(Stats), _ip, _dp, _dp, _ip, _ip]
+        L.ora_step_tangent.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(_Ionic),
+                                       C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp, _dp, _dp,
+                                       C.c_double, C.c_int, C.POINTER(_Opts), _ip, _ip, _ip]
         L.ora_step_emi.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_double, C.c_double, C.c_int,
                                    C.c_int, _ip, _ip, _dp, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
                                    C.c_double, C.POINTER(_Opts), C.POINTER(Stats), _ip]
@@ -225,6 +228,38 @@ class System:
                                    _d(w), dt, sweeps, 0.0, C.byref(opts), C.byref(st), None, None,
                                    None, _i(counts), _i(flat))
         return dict(v=v, w=w, status=rc, stats=st)
+
+    def step_tangent(self, ionic: dict, M: int, v, dv, w, dw, dt: float, sweeps: int,
+                     active_lists, dionic: dict = None, dscale_system=None,
+                     cg_rtol: float = 1e-13, cg_maxit: int = 10000, istim=None,
+                     reaction_implicit: bool = True, w_frozen: bool = False):
+        """Forward-mode derivative of step_forced along a direction: (dv, dw) of
+        the initial state, dionic of the ionic parameters, and a conductivity
+        scale direction given as the system assembled with that direction as its
+        scale (dscale_system; K is linear in the scale).  Returns dict(v, dv, w,
+        dw, status); v, w equal step_forced's result bitwise."""
+        n = self.n
+        v = np.array(v, dtype=np.float64, copy=True)
+        w = np.array(w, dtype=np.float64, copy=True)
+        dv = np.array(dv, dtype=np.float64, copy=True)
+        dw = np.array(dw, dtype=np.float64, copy=True)
+        counts = np.zeros(max(1, sweeps), np.int32)
+        counts[0] = n
+        lists = []
+        for k in range(1, sweeps):
+            lk = np.ascontiguousarray(active_lists[k], dtype=np.int32)
+            counts[k] = lk.size
+            lists.append(lk)
+        flat = np.concatenate(lists) if lists else np.zeros(1, np.int32)
+        flat = np.ascontiguousarray(flat, dtype=np.int32)
+        opts = _Opts(0.1, cg_rtol, cg_maxit, int(reaction_implicit), int(w_frozen))
+        di = C.byref(_ionic(dionic)) if dionic is not None else None
+        hd = dscale_system._h if dscale_system is not None else None
+        iters = np.zeros(MAX_SWEEPS * MAX_M, np.int32)
+        rc = lib().ora_step_tangent(self._h, hd, C.byref(_ionic(ionic)), di, M, _d(_f64(istim)),
+                                    _d(v), _d(dv), _d(w), _d(dw), dt, sweeps, C.byref(opts),
+                                    _i(counts), _i(flat), _i(iters))
+        return dict(v=v, dv=dv, w=w, dw=dw, status=rc, iters=iters)
 
     def step_emi(self, wl, u, w, sweeps=None, tol=None, cg_rtol=None, w_frozen=False,
                  want_log=False, energy_stop=False, rho=0.0, alpha=None, drop_rule=0):

@@ -1038,3 +1038,257 @@ int ora_collocation_solve(void* h, const ora_ionic* ip, int M, const double* ist
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------------------
+// Tangent (forward mode) of one step with the active sets given (derivative
+// checks of the library's discrete adjoint).  Every quantity carries a value and
+// a directional derivative (dual numbers); the step is the one of
+// ora_step_forced in the same order of operations, so the value parts equal
+// that function's results bitwise.  The direction may move the initial state
+// (dv, dw), the Aliev-Panfilov parameters (dip) and the per-node conductivity
+// scale: K is linear in the scale (K = sum_e sbar_e K_e), so the derivative of K
+// along a scale direction d is the matrix assembled with scale d on the same
+// pattern (handle hd; NULL for none).  Each CG solve differentiates its own
+// iterations, stopped by the values' test: with a tight rtol its derivative is
+// that of the exact solve to the same order.
+// --------------------------------------------------------------------------
+namespace {
+
+struct Dual {
+    double v, d;
+    Dual(double x = 0.0, double dx = 0.0) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+    const double q = a.v / b.v;
+    return Dual(q, (a.d - q * b.d) / b.v);
+}
+inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+inline Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+
+struct IonicD {
+    Dual ga, gs, a, eps, mu1, mu2, cw;
+};
+// the model of Sec. 5.1.1, written as in ion_I / ion_dIdv / ion_R / ion_dRdw
+inline Dual dion_I(const IonicD& p, Dual v, Dual w) {
+    return p.ga * v * (v - p.a) * (v - 1.0) + v * w;
+}
+inline Dual dion_dIdv(const IonicD& p, Dual v, Dual w) {
+    return p.ga * (3.0 * v * v - 2.0 * (1.0 + p.a) * v + p.a) + w;
+}
+inline Dual dion_R(const IonicD& p, Dual v, Dual w) {
+    Dual E = p.eps + p.mu1 * w / (v + p.mu2);
+    Dual G = -w - p.gs * v * (v - p.a - 1.0);
+    return p.cw * E * G;
+}
+inline Dual dion_dRdw(const IonicD& p, Dual v, Dual w) {
+    Dual E = p.eps + p.mu1 * w / (v + p.mu2);
+    Dual G = -w - p.gs * v * (v - p.a - 1.0);
+    Dual dE = p.mu1 / (v + p.mu2);
+    return p.cw * (dE * G - E);
+}
+
+// K with its derivative along the scale direction, entry by entry (same pattern)
+struct CsrD {
+    const Csr* K;
+    const Csr* Kd;   // may be null
+    Dual val(int k) const { return Dual(K->val[k], Kd ? Kd->val[k] : 0.0); }
+};
+Dual dkrow(const CsrD& K, int i, const Dual* x) {
+    Dual s = 0.0;
+    for (int k = K.K->ptr[i]; k < K.K->ptr[i + 1]; ++k) s += K.val(k) * x[K.K->col[k]];
+    return s;
+}
+Dual dkdiag(const CsrD& K, int i) {
+    for (int k = K.K->ptr[i]; k < K.K->ptr[i + 1]; ++k)
+        if (K.K->col[k] == i) return K.val(k);
+    return Dual(0.0);
+}
+
+// pcg() in dual numbers: the same iteration, stopped by the values' test
+int dpcg(const CsrD& K, double c, const std::vector<Dual>& dA, const std::vector<int>& act,
+         const std::vector<Dual>& b, std::vector<Dual>& x, double rtol, int maxit, int& iters) {
+    const int n = K.K->n;
+    std::vector<Dual> r(n), z(n), p(n), q(n);
+    for (int i : act) {
+        x[i] = 0.0;
+        r[i] = b[i];
+        z[i] = r[i] / dA[i];
+        p[i] = z[i];
+    }
+    Dual rho = 0.0;
+    for (int i : act) rho += r[i] * z[i];
+    const Dual rho0 = rho;
+    iters = 0;
+    if (rho0.v == 0.0) return ORA_OK;
+    if (!std::isfinite(rho0.v)) return ORA_NONFINITE;
+    for (int it = 1; it <= maxit; ++it) {
+        for (int i : act) {
+            Dual s = 0.0;
+            for (int k = K.K->ptr[i]; k < K.K->ptr[i + 1]; ++k) {
+                int j = K.K->col[k];
+                if (j == i) continue;
+                s += K.val(k) * p[j];
+            }
+            q[i] = dA[i] * p[i] + c * s;
+        }
+        Dual pq = 0.0;
+        for (int i : act) pq += p[i] * q[i];
+        Dual alpha = rho / pq;
+        for (int i : act) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+            z[i] = r[i] / dA[i];
+        }
+        Dual rho_new = 0.0;
+        for (int i : act) rho_new += r[i] * z[i];
+        iters = it;
+        if (!std::isfinite(rho_new.v)) return ORA_NONFINITE;
+        if (std::sqrt(rho_new.v) <= rtol * std::sqrt(rho0.v)) return ORA_OK;
+        Dual beta = rho_new / rho;
+        rho = rho_new;
+        for (int i : act) p[i] = z[i] + beta * p[i];
+    }
+    return ORA_CG_NOCONV;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Tangent of ora_step_forced (forced sets required, no energy stop or drop rule):
+// on return v, w hold the step's result and dv, dw its derivative along the
+// direction (dv, dw on entry: the initial state's direction; dip: the ionic
+// parameters' direction, NULL = none; hd: matrix of the scale direction, NULL =
+// none).  iters (optional, sweeps * ORA_MAX_M): CG iterations of each solve.
+int ora_step_tangent(void* h, void* hd, const ora_ionic* ip, const ora_ionic* dip, int M,
+                     const double* istim, double* v, double* dv, double* w, double* dw, double dt,
+                     int sweeps, const ora_opts* o, const int* forced_counts,
+                     const int* forced_lists, int* iters_out) {
+    System& S = *(System*)h;
+    const Csr& K0 = S.K;
+    const int N = K0.n;
+    Collocation col;
+    if (!make_collocation(M, col, o->qhat) || sweeps < 0 || sweeps > ORA_MAX_SWEEPS || dt <= 0 ||
+        !forced_counts)
+        return ORA_INVALID;
+    const Csr* Kd = nullptr;
+    if (hd) {
+        Kd = &((System*)hd)->K;
+        if (Kd->n != N || Kd->ptr != K0.ptr || Kd->col != K0.col) return ORA_INVALID;
+    }
+    const CsrD K{&K0, Kd};
+    const std::vector<double>& Q = col.Q;
+    const std::vector<double>& Qh = col.Qhat;
+    auto dual = [&](double x, double dx) { return Dual(x, dip ? dx : 0.0); };
+    const ora_ionic z{0, 0, 0, 0, 0, 0, 0};
+    const ora_ionic& di = dip ? *dip : z;
+    IonicD p{dual(ip->ga, di.ga), dual(ip->gs, di.gs), dual(ip->a, di.a), dual(ip->eps, di.eps),
+             dual(ip->mu1, di.mu1), dual(ip->mu2, di.mu2), dual(ip->cw, di.cw)};
+    std::vector<Dual> v0(N), w0(N);
+    for (int i = 0; i < N; ++i) {
+        v0[i] = Dual(v[i], dv[i]);
+        w0[i] = Dual(w[i], dw[i]);
+    }
+    std::vector<Dual> V((size_t)M * N), W((size_t)M * N);
+    for (int m = 0; m < M; ++m)
+        for (int i = 0; i < N; ++i) {
+            V[(size_t)m * N + i] = v0[i];
+            W[(size_t)m * N + i] = w0[i];
+        }
+    std::vector<int> act(N);
+    for (int i = 0; i < N; ++i) act[i] = i;
+    std::vector<Dual> f((size_t)M * N), J((size_t)M * N), r((size_t)M * N), delta((size_t)M * N),
+        b(N), dA(N), Kdg(N);
+    for (int i = 0; i < N; ++i) Kdg[i] = dkdiag(K, i);
+    for (int k = 0; k < sweeps; ++k) {
+        if (act.empty()) continue;   // as in ora_step_forced: an emptied set stays empty
+        {
+            for (int m = 0; m < M; ++m)
+                for (int i : act) {
+                    Dual vm = V[(size_t)m * N + i], wm = W[(size_t)m * N + i];
+                    double s = istim ? istim[i] : 0.0;
+                    f[(size_t)m * N + i] =
+                        -dkrow(K, i, &V[(size_t)m * N]) - S.mass[i] * (dion_I(p, vm, wm) - s);
+                    J[(size_t)m * N + i] = o->reaction_implicit ? dion_dIdv(p, vm, wm) : Dual(0.0);
+                }
+            for (int m = 0; m < M; ++m)
+                for (int i : act) {
+                    Dual q = 0.0;
+                    for (int j = 0; j < M; ++j) q += Q[m * M + j] * f[(size_t)j * N + i];
+                    r[(size_t)m * N + i] =
+                        S.mass[i] * v0[i] + dt * q - S.mass[i] * V[(size_t)m * N + i];
+                }
+            std::fill(delta.begin(), delta.end(), Dual(0.0));
+            for (int m = 0; m < M; ++m) {
+                for (int i : act) {
+                    Dual corr = 0.0;
+                    for (int j = 0; j < m; ++j) {
+                        const Dual* dj = &delta[(size_t)j * N];
+                        corr += Qh[m * M + j] *
+                                (dkrow(K, i, dj) + S.mass[i] * J[(size_t)j * N + i] * dj[i]);
+                    }
+                    b[i] = r[(size_t)m * N + i] - dt * corr;
+                }
+                const double c = dt * Qh[m * M + m];
+                for (int i : act) {
+                    dA[i] = S.mass[i] * (1.0 + c * J[(size_t)m * N + i]) + c * Kdg[i];
+                    if (!std::isfinite(dA[i].v)) return ORA_NONFINITE;
+                    if (!(dA[i].v > 0.0)) return ORA_DOMAIN;
+                }
+                std::vector<Dual> x(N);
+                int iters = 0;
+                const int rc = dpcg(K, c, dA, act, b, x, o->cg_rtol, o->cg_maxit, iters);
+                if (iters_out) iters_out[k * ORA_MAX_M + m] = iters;
+                if (rc != ORA_OK) return rc;
+                for (int i : act) delta[(size_t)m * N + i] = x[i];
+            }
+            for (int m = 0; m < M; ++m)
+                for (int i : act) V[(size_t)m * N + i] += delta[(size_t)m * N + i];
+            if (!o->w_frozen) {
+                for (int i : act) {
+                    Dual g[ORA_MAX_M], d[ORA_MAX_M], s[ORA_MAX_M], eps[ORA_MAX_M];
+                    for (int m = 0; m < M; ++m) {
+                        Dual vm = V[(size_t)m * N + i], wm = W[(size_t)m * N + i];
+                        if ((vm + p.mu2).v <= 0.0) return ORA_DOMAIN;
+                        g[m] = dion_R(p, vm, wm);
+                        d[m] = dion_dRdw(p, vm, wm);
+                    }
+                    for (int m = 0; m < M; ++m) {
+                        Dual q = 0.0;
+                        for (int j = 0; j < M; ++j) q += Q[m * M + j] * g[j];
+                        s[m] = w0[i] + dt * q - W[(size_t)m * N + i];
+                    }
+                    for (int m = 0; m < M; ++m) {
+                        Dual acc = s[m];
+                        for (int j = 0; j < m; ++j) acc += dt * Qh[m * M + j] * d[j] * eps[j];
+                        Dual den = 1.0 - dt * Qh[m * M + m] * d[m];
+                        if (!(den.v > 0.0)) return ORA_DOMAIN;
+                        eps[m] = acc / den;
+                    }
+                    for (int m = 0; m < M; ++m) W[(size_t)m * N + i] += eps[m];
+                }
+            }
+        }
+        // the given set of the next sweep
+        std::vector<int> next;
+        if (k + 1 < sweeps) {
+            size_t off = 0;
+            for (int kk = 1; kk <= k; ++kk) off += (size_t)forced_counts[kk];
+            next.assign(forced_lists + off, forced_lists + off + forced_counts[k + 1]);
+        }
+        act.swap(next);
+    }
+    for (int i = 0; i < N; ++i) {
+        v[i] = V[(size_t)(M - 1) * N + i].v;
+        dv[i] = V[(size_t)(M - 1) * N + i].d;
+        w[i] = W[(size_t)(M - 1) * N + i].v;
+        dw[i] = W[(size_t)(M - 1) * N + i].d;
+    }
+    return ORA_OK;
+}
+
+}  // extern "C"
