@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/reference/e2e runs")
     ap.add_argument("--emi-w-frozen", action="store_true", help="w2: hold the gating at w = 0")
+    ap.add_argument("--emi-cells", default="8,4,4",
+                    help="w2: brick cells along x,y,z (default 8,4,4 = 1,471,260 dofs)")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=None,
                     help="pick the node solves' launch shape with sdc_autotune before timing "
                          "(default: on for the batch w3, off otherwise)")
@@ -470,7 +472,8 @@ def run_emi(args):
     from paper_2311_07206_gb300 import Context, default_options
 
     frozen = bool(args.emi_w_frozen)
-    wl = emi_bricks(w_frozen=frozen)
+    cells = tuple(int(x) for x in args.emi_cells.split(","))
+    wl = emi_bricks(cells=cells, w_frozen=frozen)
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream(dev)
     opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, w_frozen=int(frozen),
