@@ -160,8 +160,8 @@ typedef struct {
                               the device, the batched solves' block plan built on the device)
                               captured once per (state arrays, dt, sweeps, TOL, stimulus on or
                               off) as one CUDA graph and replayed, one host synchronisation per
-                              step; 0 host-driven sweeps.  Bitwise the same results; nnz_active
-                              is not tracked in captured steps.  Default 1                   */
+                              step; 0 host-driven sweeps.  Bitwise the same results.
+                              Default 1                                                      */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */

@@ -742,6 +742,8 @@ sdc_status step_batch_graph(sdc_ctx* c, double* d_v, double* d_w, double dt, int
             if (k + 1 < sweeps) {
                 Ell& An = B.A[cur];
                 launch_extract(N, *A, B.map, An, B, s, nd);
+                cudaMemcpyAsync(&B.sc->nnz_k[k + 1], &B.sc->nnz, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, s);
                 A = &An;
                 cur ^= 1;
                 ++L;
@@ -794,11 +796,14 @@ sdc_status step_batch_graph(sdc_ctx* c, double* d_v, double* d_w, double dt, int
         cudaMemcpyAsync(si.data(), B.seg_iters, cnt * sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(sr.data(), B.seg_relres, cnt * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
+        std::vector<unsigned long long> nz(SDC_MAX_SWEEPS);
+        cudaMemcpyAsync(nz.data(), B.sc->nnz_k, nz.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         stats->sweeps_run = sweeps;
         for (int k = 0; k < sweeps; ++k) {
             stats->n_active[k] = nk[k];
-            stats->nnz_active[k] = 0;          // not tracked in captured steps
+            stats->nnz_active[k] = k == 0 ? c->K.nnz - N : (long long)nz[k];
             for (int m = 0; m < M; ++m) {
                 int mx = 0;
                 for (int g = 0; g < nseg; ++g) {
@@ -904,7 +909,7 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
     int n = N;
     const int* act = nullptr;      // identity for the first sweep
     const Ell* A = &c->K.K;
-    long long nnz = c->K.nnz - N;
+    const long long nnz = c->K.nnz - N;   // sweep 0; later sweeps' sizes are read at the end
     int cur = 0;                   // ping-pong index of the restricted matrix
     int status = SDC_OK;
     double energy_prev = 0.0;
@@ -1025,13 +1030,9 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         if (k + 1 < sweeps && n_next > 0) {
             Ell& An = B.A[cur];
             run(SDC_PHASE_EXTRACT, 1, [&] { launch_extract(n, *A, B.map, An, B, s); });
-            unsigned long long hn = 0;
-            cudaMemcpyAsync(&hn, &B.sc->nnz, sizeof(hn), cudaMemcpyDeviceToHost, s);
-            if (cudaStreamSynchronize(s) != cudaSuccess) {
-                status = cuda_fail(c, "extract");
-                break;
-            }
-            nnz = (long long)hn;
+            // its size is statistics only: kept on the device, read with the step's stats
+            cudaMemcpyAsync(&B.sc->nnz_k[k + 1], &B.sc->nnz, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, s);
             A = &An;
             cur ^= 1;
         }
@@ -1057,7 +1058,11 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         cudaMemcpyAsync(rr.data(), B.sc->cg_relres, rr.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(en.data(), B.sc->cg_energy, en.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&mg, &B.sc->margin, sizeof(double), cudaMemcpyDeviceToHost, s);
+        std::vector<unsigned long long> nz(SDC_MAX_SWEEPS);
+        cudaMemcpyAsync(nz.data(), B.sc->nnz_k, nz.size() * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
+        for (int kk = 1; kk < stats->sweeps_run; ++kk) stats->nnz_active[kk] = (long long)nz[kk];
         for (int kk = 0; kk < stats->sweeps_run; ++kk) {
             double E = 0.0;
             for (int m = 0; m < M; ++m) E += en[kk * kMaxM + m];

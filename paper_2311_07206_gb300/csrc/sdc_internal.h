@@ -39,6 +39,7 @@ struct DevScalars {
     unsigned long long drop_c;     // bits of max |dv| of the first sweep (drop rule 1)
     unsigned long long drop_eta;   // bits of max(0, -dI/dv) of the first sweep
     double tol_drop;               // the a priori drop tolerance of the step (drop rule 1)
+    unsigned long long nnz_k[SDC_MAX_SWEEPS];   // stored off-diagonals of K[I_k, I_k], k >= 1
 };
 
 // ELL-R matrix in column-major slots: entry t of row i at [t * ld + i],

@@ -132,6 +132,7 @@ def test_captured_batch_step_equals_host_driven_bitwise(torch_dev):
         assert sg.captured == 1 and sh.captured == 0
         assert torch.equal(gv, hv) and torch.equal(gw, hw), n
         assert list(sg.n_active[:wl0.sweeps]) == list(sh.n_active[:wl0.sweeps])
+        assert list(sg.nnz_active[:wl0.sweeps]) == list(sh.nnz_active[:wl0.sweeps])
         for k in range(wl0.sweeps):
             assert [sg.cg_iters[k][m] for m in range(wl0.M)] == \
                 [sh.cg_iters[k][m] for m in range(wl0.M)]
