@@ -94,3 +94,41 @@ def test_reorder_rejects_tapes(torch_dev):
     with pytest.raises(SdcError):
         ctx.step_taped(v, w, 0.0, wl.dt, wl.sweeps, wl.tol, tp)
     ctx.close()
+
+
+@pytest.mark.parametrize("scaled,pipe", [(1, -1), (0, 1), (1, 0)])
+def test_options_together_against_the_oracle(torch_dev, scaled, pipe):
+    """Internal Morton numbering, the energy-norm stop with a given rho, the a
+    priori drop tolerance, each CG form and arrangement, and an autotuned launch
+    shape at once, on the tissue mesh: the oracle (plain numbering, same
+    options) gives the same sweeps, drop tolerance, active sets and states."""
+    torch, dev = torch_dev
+    wl = W.w5_tissue(h=0.5)
+    ctx = _ctx(wl, torch, dev, reorder=1, energy_stop=1, sdc_rho=0.2, drop_rule=1,
+               cg_scaled=scaled, cg_pipelined=pipe)
+    S = oracle.System.from_mesh(wl.mesh, wl.sigma)
+    v, w = wl.v0.copy(), wl.w0.copy()
+    dv = torch.tensor(v, dtype=torch.float64, device=dev)
+    dw = torch.tensor(w, dtype=torch.float64, device=dev)
+    rep = ctx.autotune(dv, dw, 0.0, wl.dt, 8, wl.tol, trial_steps=1)
+    assert np.array_equal(dv.cpu().numpy(), v)
+    assert rep["trials"] >= 8
+    stopped = False
+    for n in range(4):
+        t = n * wl.dt
+        st = ctx.step(dv, dw, t, wl.dt, 8, wl.tol)
+        r = S.step(wl.ionic, wl.M, v, w, wl.dt, 8, wl.tol, cg_rtol=wl.cg_rtol,
+                   istim=wl.stim_vector(t), want_log=True, energy_stop=True, rho=0.2,
+                   drop_rule=1)
+        assert r["status"] == 0
+        assert st.sweeps_run == r["stats"].sweeps_run, n
+        stopped |= st.sweeps_run < 8
+        assert st.tol_drop == pytest.approx(r["stats"].tol_drop, rel=1e-13)
+        for k in range(st.sweeps_run):
+            if r["stats"].n_active[k]:
+                assert np.array_equal(ctx.active(k), r["active"][k]), (n, k)
+        assert _relmax(dv.cpu().numpy(), r["v"]) <= 1e-10
+        assert _relmax(dw.cpu().numpy(), r["w"]) <= 1e-10
+        v, w = r["v"], r["w"]
+    assert stopped
+    ctx.close()
