@@ -481,6 +481,9 @@ def run_emi(args):
     ctx = Context.from_emi(wl, options=opts, stream=stream.cuda_stream)
     u0 = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
+    tune = None
+    if args.autotune:
+        tune = ctx.autotune(u0.clone(), w0.clone(), 0.0, wl.dt, wl.sweeps, wl.tol, trial_steps=1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def trajectory(tol, sweeps, steps, timed):
@@ -592,7 +595,8 @@ def run_emi(args):
            "dt_ms": wl.dt, "sweeps": wl.sweeps, "TOL": wl.tol, "alpha": wl.alpha,
            "cg_rtol": wl.cg_rtol,
            "gating": "held at w = 0" if frozen else "Aliev-Panfilov on cell-bath pairs", "simulated_ms": round(K * wl.dt, 6),
-           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas"}
+           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
+           "autotune": tune}
     line = {"metric": "SDC steps/s & active-dof sweeps/s (cell-by-cell bricks), adaptive "
                       "TOL=%g vs plain; HBM GB/s" % wl.tol,
             "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": Wm,
