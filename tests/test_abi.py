@@ -117,13 +117,18 @@ def test_energy_stop_rejected_for_batches_and_bad_rho_before_device_work(lib):
     assert e.value.status == -1 and "batch" in str(e.value)
 
 
-def test_cg_scaled_validation_before_device_work(lib):
-    from paper_2311_07206_gb300 import Context, SdcError, default_options
+def test_cg_scaled_and_batch_graph_validation_before_device_work(lib):
+    from paper_2311_07206_gb300 import Batch, Context, SdcError, default_options
     import workloads as W
     sq = W.w0_square(n=9, length=2.5)
+    o = default_options()
+    assert o.cg_scaled == 1 and o.batch_graph == 1
     for bad in (-1, 2):
         with pytest.raises(SdcError) as e:
             Context.from_workload(sq, options=default_options(cg_scaled=bad))
+        assert e.value.status == -1
+        with pytest.raises(SdcError) as e:
+            Batch([sq, sq], options=default_options(batch_graph=bad))
         assert e.value.status == -1
 
 
