@@ -6,7 +6,9 @@ fixes: a single membrane with the Robin-grounded bath side reduces to the
 point Aliev-Panfilov ODE C_m v' = -I_ion(v, w) (the bath potential stays 0);
 a single gap junction between two Robin-grounded nodes reduces to the linear
 ODE v' = -(g / C_m + eps / (2 A C_m)) v, whose converged Radau step is the
-Pade(M-1, M) function.
+Pade(M-1, M) function; and on two cells, plain SDC swept to convergence equals
+the collocation solution of the whole EMI system, solved densely by Newton
+from its definition (numpy).
 """
 
 import math
@@ -87,3 +89,77 @@ def test_emi_invariants_on_two_cells():
     assert len(act[1]) < wl.n
     # the excited cell pulls the bath and the neighbour: the state moved everywhere
     assert np.abs(ad["u"] - wl.u0).max() > 1e-3
+
+
+def _emi_collocation_solve(wl, M, dt):
+    """The Radau-IIA collocation system of the cell-by-cell model written out
+    densely and solved by Newton (finite-difference Jacobian, numpy):
+        B (U_m - u0) + dt sum_j Q_mj (A U_j + b(U_j, W_j)) = 0,
+        W_m - w0 - dt sum_j Q_mj R(v_j, W_j) = 0  on the cell-bath pairs,
+    with B = sum_p area_p Cm e_p e_p', A = K + diag(robin), b = sum_p area_p
+    I_p(v_p, w_p) e_p, e_p = e_k - e_l, v_p = u_k - u_l, I_p the Aliev-Panfilov
+    current (cell-bath) or g_gap v (gap junction); gap-junction w stays w0."""
+    import scipy.sparse as sp
+    S = oracle.System.from_mesh(wl.mesh)
+    ptr, col, val, _ = S.matrix()
+    n, npair = wl.n, wl.n_pairs
+    A = sp.csr_matrix((val, col, ptr), shape=(n, n)) + sp.diags(wl.robin)
+    E = sp.csr_matrix((np.concatenate([np.ones(npair), -np.ones(npair)]),
+                       (np.concatenate([np.arange(npair)] * 2),
+                        np.concatenate([wl.pair_k, wl.pair_l]))), shape=(npair, n))
+    area = wl.pair_area
+    memb = wl.pair_kind == 0
+    p = wl.ionic
+    _, Q, _ = oracle.collocation(M)
+    u0, w0 = wl.u0, wl.w0
+    B = E.T @ sp.diags(area * wl.Cm) @ E
+
+    def I(v, w):
+        return np.where(memb, p["ga"] * v * (v - p["a"]) * (v - 1.0) + v * w, wl.g_gap * v)
+
+    def R(v, w):
+        E_ = p["eps"] + p["mu1"] * w / (v + p["mu2"])
+        G = -w - p["gs"] * v * (v - p["a"] - 1.0)
+        return np.where(memb, p["cw"] * E_ * G, 0.0)
+
+    def G(z):
+        U = z[:M * n].reshape(M, n)
+        Wp = z[M * n:].reshape(M, npair)
+        F = np.array([A @ U[j] + E.T @ (area * I(E @ U[j], Wp[j])) for j in range(M)])
+        Rv = np.array([R(E @ U[j], Wp[j]) for j in range(M)])
+        gu = np.array([B @ (U[m] - u0) + dt * Q[m] @ F for m in range(M)])
+        gw = np.array([Wp[m] - w0 - dt * Q[m] @ Rv for m in range(M)])
+        return np.concatenate([gu.ravel(), gw.ravel()])
+
+    z = np.concatenate([np.tile(u0, M), np.tile(w0, M)])
+    for _ in range(20):
+        g = G(z)
+        if np.abs(g).max() < 1e-14:
+            break
+        h = 1e-7
+        Jac = np.empty((z.size, z.size))
+        for c in range(z.size):
+            zc = z.copy()
+            zc[c] += h
+            Jac[:, c] = (G(zc) - g) / h
+        z = z - np.linalg.solve(Jac, g)
+    assert np.abs(G(z)).max() < 1e-12
+    return z[(M - 1) * n:M * n], z[M * n + (M - 1) * npair:]
+
+
+def test_converged_emi_sdc_equals_the_collocation_solve():
+    """Sec. 3.1/3.2 on the cell-by-cell system: plain SDC swept to convergence
+    reaches the fixed point, the Radau-IIA collocation solution of the EMI
+    system, solved here densely from its definition."""
+    wl = emi_tiny("two_cells")
+    wl.u0 = np.where(wl.u0 > 0.5, 0.6, 0.0)
+    wl.w0 = np.full(wl.n_pairs, 0.02)
+    M, dt = 2, 0.02
+    wl.M, wl.dt = M, dt
+    S = oracle.System.from_mesh(wl.mesh)
+    r = S.step_emi(wl, wl.u0, wl.w0, sweeps=60, tol=0.0, cg_rtol=1e-15)
+    assert r["status"] == 0
+    u_ref, w_ref = _emi_collocation_solve(wl, M, dt)
+    assert np.abs(r["u"] - u_ref).max() <= 1e-11 * max(1.0, np.abs(u_ref).max())
+    assert np.abs(r["w"] - w_ref).max() <= 1e-11
+    assert np.abs(r["u"] - wl.u0).max() > 1e-3      # the step really moves
