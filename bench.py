@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -183,6 +184,29 @@ def max_over_ranks(x, world):
 
 
 # ---------------------------------------------------------------- CPU oracle
+def host_info():
+    """The host the oracle ran on: logical cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "model": model or platform.machine()}
+
+
 def oracle_steps(wl, states, budget_s):
     """Time single oracle steps from the given (step index, v, w) states until the
     budget is used.  Returns (steps done, seconds, per-step results)."""
@@ -240,7 +264,7 @@ def run_reference(args):
             "config": config_of(wl, done),
             "active_dof_sweeps_per_s": nact / secs,
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_info()},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -432,7 +456,7 @@ def run_gb300(args):
         cpu = {"value": done / secs, "unit": "steps/s", "cores": 1, "kind": "oracle",
                "sample": "%d single steps of the same trajectory, started from the GPU states at "
                          "steps %s (single-threaded FP64 oracle)"
-                         % (done, [s for s, _ in outs])}
+                         % (done, [s for s, _ in outs]), "host": host_info()}
         diffs = []
         for s, r in outs:
             if s + 1 in snaps:
@@ -640,7 +664,7 @@ def emi_cpu_baseline(budget_s, gpu_row_iters_per_step, frozen):
             "sample": "%d oracle steps of the 2-cell instance (%d dofs) in %.1f s: %.3g CG "
                       "row-iterations/s, divided by the full workload's %.3g row-iterations per "
                       "step" % (done, wl.n, secs, rate, gpu_row_iters_per_step),
-            "sample_steps_per_s": done / secs}
+            "sample_steps_per_s": done / secs, "host": host_info()}
 
 
 
