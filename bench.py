@@ -273,12 +273,29 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 FP64_LANES_PER_CYCLE = 304          # whole GPU, ncu dfma peak_sustained on GB300
+# measured warp FP64 issue rate as a fraction of that peak (a warp FP64 instruction holds a
+# sub-partition's FP64 unit for ~76 cycles: 1.68 of 2.0 lanes per cycle per SM)
+FP64_ISSUE_FRACTION = 0.84
+SIZE_CLASSES = ((1, 10_000, "<=10k rows"), (10_001, 300_000, "10k-300k rows"),
+                (300_001, 1 << 62, ">300k rows"))
+CG_SOURCES = ("step.cu", "device_common.cuh")
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum): the first node solve of a slab step, k_pcg_scaled<1024> on all
-# 442,401 rows, 21 iterations = 1.735 GB of algorithmic bytes.  Scaled to the average launch
-# by algorithmic bytes.  Must be re-taken (or dropped) whenever that kernel changes.
+# dram__bytes_write.sum) of the first node solve of a slab step, all 442,401 rows, scaled to
+# the average launch by algorithmic bytes.  `source_sha` is the hash of the CG sources the
+# capture was taken with (kernel_source_sha()); once they change, the figure is withheld.
 PCG_TRAFFIC = {"w1": {"dram_bytes": 63.63e6 + 9.97e6, "algorithmic_bytes": 1.735e9,
-                      "kernel": "k_pcg_scaled<1024>"}}
+                      "kernel": "k_pcg_scaled<1024>", "source_sha": "6e3c3f4c039b4db9",
+                      "capture": "profiles/pcg_scaled_w1_slab_full_solve.md"}}
+
+
+def kernel_source_sha():
+    """Hash of the CG kernel sources (the code the ncu traffic figure describes)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in CG_SOURCES:
+        with open(os.path.join(ROOT, "paper_2311_07206_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def pcg_ops(st, M, sweeps):
@@ -313,7 +330,50 @@ def pcg_bytes(st, M, sweeps):
     return b
 
 
+class SolveTable:
+    """Node solves of a run grouped by active-set size: count, mean iterations,
+    device microseconds per iteration, the FP64 floor of an iteration (zbar + 8
+    operations per row at the measured issue rate) and the share of PCG time."""
+
+    def __init__(self, sm_mhz):
+        self.rate = FP64_LANES_PER_CYCLE * FP64_ISSUE_FRACTION * sm_mhz * 1e6   # lane-op/s
+        self.c = {label: [0, 0, 0.0, 0.0, 0.0] for _, _, label in SIZE_CLASSES}
+
+    def add(self, st, M):
+        for k in range(st.sweeps_run):
+            n = st.n_active[k]
+            if n == 0:
+                continue
+            ops_it = st.nnz_active[k] + n + 8.0 * n
+            label = [lb for lo, hi, lb in SIZE_CLASSES if lo <= n <= hi][0]
+            e = self.c[label]
+            for m in range(M):
+                it = st.cg_iters[k][m]
+                e[0] += 1
+                e[1] += it
+                e[2] += st.cg_ms[k][m]
+                e[3] += it * ops_it / self.rate * 1e3
+                e[4] += it * ops_it
+
+    def table(self):
+        tot = sum(e[2] for e in self.c.values()) or 1.0
+        out = []
+        for _, _, label in SIZE_CLASSES:
+            solves, iters, ms, floor_ms, ops = self.c[label]
+            if solves == 0:
+                continue
+            out.append({"class": label, "solves": solves, "mean_iters": iters / solves,
+                        "us_per_iter": 1e3 * ms / max(1, iters),
+                        "fp64_floor_us_per_iter": 1e3 * floor_ms / max(1, iters),
+                        "share_of_pcg": ms / tot,
+                        "fp64_frac": ops / (ms * 1e-3) / (self.rate / FP64_ISSUE_FRACTION)
+                        if ms > 0 else None})
+        return out
+
+
 def run_gb300(args):
+    """The headline slab (and the other monodomain workloads): timed windows of
+    adaptive SDC with the plain run, equal-error pairs, roofline and baselines."""
     import torch
 
     world, rank, local = dist_setup(args)
@@ -324,71 +384,227 @@ def run_gb300(args):
     wl = make_workload(args.workload)
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream(dev)
-    opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, reorder=args.reorder)
-    ctx = Context.from_workload(wl, options=opts, stream=stream.cuda_stream)
+
+    def new_ctx(**kw):
+        o = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, reorder=args.reorder)
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return Context.from_workload(wl, options=o, stream=stream.cuda_stream)
+
+    ctx = new_ctx()
     v0 = torch.tensor(wl.v0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    peaks = {}
+    if os.path.exists(PEAKS_FILE):
+        with open(PEAKS_FILE) as f:
+            peaks = json.load(f)
+    hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     tune = None
     if args.autotune:
         tune = ctx.autotune(v0.clone(), w0.clone(), 0.0, wl.dt, wl.sweeps, wl.tol, trial_steps=3)
 
-    def trajectory(tol, sweeps, steps, timed):
-        v, w = v0.clone(), w0.clone()
+    def trajectory(c, vs, ws, n0, steps, tol, sweeps, timed, table=None):
+        """`steps` steps of context c from (vs, ws) at step index n0 (inputs kept)."""
+        v, w = vs.clone(), ws.clone()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)] if timed else None
         agg = {"active_dof_sweeps": 0, "pcg_ms": 0.0, "pcg_launches": 0, "pcg_bytes": 0.0,
-               "pcg_ops": 0.0, "launches": 0, "phase_ms": np.zeros(5)}
-        for n in range(steps):
+               "pcg_ops": 0.0, "launches": 0, "phase_ms": np.zeros(5), "sweeps": 0}
+        for i in range(steps):
+            n = n0 + i
             if timed:
                 flush.fill_(n)
-                ev[n][0].record(stream)
-            st = ctx.step(v, w, n * wl.dt, wl.dt, sweeps, tol)
+                ev[i][0].record(stream)
+            st = c.step(v, w, n * wl.dt, wl.dt, sweeps, tol)
             if timed:
-                ev[n][1].record(stream)
+                ev[i][1].record(stream)
             agg["active_dof_sweeps"] += sum(st.n_active[:st.sweeps_run])
+            agg["sweeps"] += st.sweeps_run
             agg["pcg_ms"] += st.phase_ms[1]
             agg["pcg_launches"] += st.phase_launches[1]
             agg["pcg_bytes"] += pcg_bytes(st, wl.M, sweeps)
             agg["pcg_ops"] += pcg_ops(st, wl.M, sweeps)
             agg["launches"] += st.kernel_launches
             agg["phase_ms"] += np.array(st.phase_ms[:5])
+            if table is not None:
+                table.add(st, wl.M)
         torch.cuda.synchronize(dev)
         total_ms = sum(a.elapsed_time(b) for a, b in ev) if timed else None
         return v, w, total_ms, agg
 
-    # warm-up (untimed, discarded)
-    trajectory(wl.tol, wl.sweeps, Wm, timed=False)
-    props = torch.cuda.get_device_properties(dev)
-    dev_id = str(getattr(props, "uuid", "")) or str(local)
-    if dev_id and not dev_id.startswith("GPU-") and len(dev_id) > 8:
-        dev_id = "GPU-" + dev_id
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    clocks = Clocks(dev_id)
-    va, wa, ms_adapt, agg_a = trajectory(wl.tol, wl.sweeps, K, timed=True)
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    clk = clocks.stop()
-    ms_adapt = max_over_ranks(ms_adapt, world)
-    value = world * K / (ms_adapt / 1e3)
+    def roofline_of(agg, ms_step_total):
+        alu_peak = FP64_LANES_PER_CYCLE * sm_max * 1e6 / 1e9            # G op/s
+        pcg_s = agg["pcg_ms"] / 1e3
+        launches = max(1, agg["pcg_launches"])
+        ach_ops = agg["pcg_ops"] / pcg_s / 1e9 if pcg_s > 0 else None
+        ach_gbs = agg["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
+        avg_ms = agg["pcg_ms"] / launches
+        r = {"kernel": "k_pcg_scaled / k_pcg* (restricted Jacobi-PCG, symmetrically scaled "
+                       "form, one cooperative launch per node solve)",
+             "bound": "alu", "achieved": ach_ops, "peak": alu_peak, "unit": "G FP64 lane-op/s",
+             "frac": ach_ops / alu_peak if ach_ops else None,
+             "peak_source": "304 FP64 lanes/cycle (ncu dfma peak_sustained) x %.0f MHz max SM "
+                            "clock" % sm_max,
+             "traffic": None, "traffic_source": None,
+             "algorithmic_ops_per_launch": agg["pcg_ops"] / launches,
+             "algorithmic_bytes_per_launch": agg["pcg_bytes"] / launches,
+             "avg_launch_ms": avg_ms, "launches": agg["pcg_launches"],
+             "share_of_step": agg["pcg_ms"] / ms_step_total,
+             # algorithmic bytes over time: what the kernel moves through L2 and DRAM together
+             "effective_view": {"achieved": ach_gbs, "unit": "GB/s",
+                                "note": "algorithmic bytes / time; the solves' working set "
+                                        "is L2-resident, so this is not an HBM rate"},
+             "dram_view": None}
+        tr = PCG_TRAFFIC.get(args.workload)
+        if tr is not None and agg["pcg_launches"] > 0:
+            sha = kernel_source_sha()
+            if tr["source_sha"] == sha:
+                r["traffic"] = tr["dram_bytes"] / tr["algorithmic_bytes"] * (
+                    agg["pcg_bytes"] / launches)
+                r["traffic_source"] = (
+                    "ncu DRAM bytes of one full-size %s launch (%.1f MB for %.3f GB "
+                    "algorithmic; %s; CG sources %s), scaled to the average launch by "
+                    "algorithmic bytes" % (tr["kernel"], tr["dram_bytes"] / 1e6,
+                                           tr["algorithmic_bytes"] / 1e9, tr["capture"], sha))
+                gbs = r["traffic"] / (avg_ms / 1e3) / 1e9
+                r["dram_view"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": gbs / hbm_peak,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
+                                  if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}
+            else:
+                r["traffic_source"] = ("withheld: the CG sources (%s) changed since the ncu "
+                                       "capture (%s)" % (sha, tr["source_sha"]))
+        return r
 
-    extras = {}
-    if not args.no_extras:
-        vp, wp, ms_plain, agg_p = trajectory(0.0, wl.sweeps, K, timed=True)
-        vr, _, _, _ = trajectory(0.0, args.ref_sweeps, K, timed=False)
-        ref = vr.cpu().numpy()
-        err_a = float(np.abs(va.cpu().numpy() - ref).max())
-        err_p = float(np.abs(vp.cpu().numpy() - ref).max())
-        extras = {"plain": {"value": K / (ms_plain / 1e3), "unit": "steps/s",
-                            "ms_per_step": ms_plain / K,
-                            "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_plain / 1e3)},
-                  "speedup_vs_plain": ms_plain / ms_adapt,
-                  "err_vs_ref": {"adaptive": err_a, "plain": err_p,
+    def max_err(v, ref):
+        return float(np.abs(v.cpu().numpy() - ref).max())
+
+    def equal_error(vs, ws, n0, steps, ref, err_a, ms_a):
+        """(fixed) adaptive with the workload's sweeps against plain SDC with the fewest
+        fixed sweeps whose error is within 1.1x; the adaptive TOL is halved (up to five
+        times) until its error is within 1.1x of that partner's.  (energy_stop) the
+        energy-norm stop of Sec. 3.2 at the same TOL (rho = 0.05, at most 12 sweeps),
+        no dropping (alpha = 0) against alpha = 0.1, TOL halved on the adaptive side the
+        same way.  All errors against plain SDC with 12 sweeps from the same state."""
+        plain = {}
+        for kp in range(1, wl.sweeps + 3):
+            v, _, ms, _ = trajectory(ctx, vs, ws, n0, steps, 0.0, kp, timed=True)
+            plain[kp] = (max_err(v, ref), ms)
+        adapt = [(wl.tol, err_a, ms_a)]
+        pick = None
+        for j in range(6):
+            if j > 0:
+                tol_j = wl.tol / 2 ** j
+                v, _, ms, _ = trajectory(ctx, vs, ws, n0, steps, tol_j, wl.sweeps, timed=True)
+                adapt.append((tol_j, max_err(v, ref), ms))
+            e_a = adapt[j][1]
+            cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * e_a]
+            kp = cands[0] if cands else max(plain)
+            if e_a <= 1.1 * plain[kp][0]:
+                pick = (j, kp)
+                break
+        matched = pick is not None
+        if pick is None:
+            pick = min(((j, kp) for j in range(len(adapt)) for kp in plain),
+                       key=lambda q: abs(np.log(max(adapt[q[0]][1], 1e-300)
+                                                / max(plain[q[1]][0], 1e-300))))
+        j, kp = pick
+        # plain time at the adaptive error, interpolated log-log between the fixed-sweep runs
+        # that bracket it (None outside their range)
+        pts = sorted((e, m) for e, m in plain.values() if e > 0)
+        interp = None
+        for (e_lo, m_lo), (e_hi, m_hi) in zip(pts, pts[1:]):
+            e = adapt[j][1]
+            if e_lo <= e <= e_hi and e_hi > e_lo:
+                f = np.log(e / e_lo) / np.log(e_hi / e_lo)
+                interp = float(np.exp(np.log(m_lo) + f * np.log(m_hi / m_lo)))
+                break
+        fixed = {"adaptive": {"TOL": adapt[j][0], "sweeps": wl.sweeps, "err": adapt[j][1],
+                              "ms_per_step": adapt[j][2] / steps},
+                 "speedup_interpolated": interp / adapt[j][2] if interp else None,
+                 "interpolation": "plain ms/step at the adaptive error, log-log between the "
+                                  "two fixed-sweep plain runs whose errors bracket it",
+                 "plain": {"sweeps": kp, "err": plain[kp][0],
+                           "ms_per_step": plain[kp][1] / steps},
+                 "matched_within_1.1x": matched,
+                 "speedup": plain[kp][1] / adapt[j][2],
+                 "plain_sweep_scan": {str(k): {"err": e, "ms_per_step": m / steps}
+                                      for k, (e, m) in plain.items()},
+                 "adaptive_tol_scan": [{"TOL": t, "err": e, "ms_per_step": m / steps}
+                                       for t, e, m in adapt]}
+        # energy-norm stop pair
+        es_ctx = {a: new_ctx(alpha=a, energy_stop=1, sdc_rho=0.05) for a in (0.0, wl.alpha)}
+        v, _, ms0, agg0 = trajectory(es_ctx[0.0], vs, ws, n0, steps, wl.tol, 12, timed=True)
+        e0 = max_err(v, ref)
+        scan = []
+        for j in range(5):
+            tol_j = wl.tol / 2 ** j
+            v, _, ms1, agg1 = trajectory(es_ctx[wl.alpha], vs, ws, n0, steps, tol_j, 12,
+                                         timed=True)
+            scan.append({"TOL": tol_j, "err": max_err(v, ref), "ms_per_step": ms1 / steps,
+                         "mean_sweeps": agg1["sweeps"] / steps})
+            if scan[-1]["err"] <= 1.1 * e0:
+                break
+        best = scan[-1]
+        energy = {"non_adaptive": {"TOL": wl.tol, "alpha": 0.0, "err": e0,
+                                   "ms_per_step": ms0 / steps,
+                                   "mean_sweeps": agg0["sweeps"] / steps},
+                  "adaptive": dict(best, alpha=wl.alpha),
+                  "matched_within_1.1x": best["err"] <= 1.1 * e0,
+                  "speedup": (ms0 / steps) / best["ms_per_step"],
+                  "adaptive_tol_scan": scan}
+        for c in es_ctx.values():
+            c.close()
+        return {"fixed_sweeps": fixed, "energy_stop": energy,
+                "reference": "plain SDC, %d sweeps, same dt, same start" % args.ref_sweeps,
+                "norm": "max |v(t_end) - v_ref(t_end)|"}
+
+    def window(vs, ws, n0, steps, extras, table):
+        """Timed adaptive run of `steps` steps from (vs, ws) at step n0, then (extras) the
+        plain run, the errors, and the equal-error pairs."""
+        trajectory(ctx, vs, ws, n0, Wm, wl.tol, wl.sweeps, timed=False)   # warm-up
+        props = torch.cuda.get_device_properties(dev)
+        dev_id = str(getattr(props, "uuid", "")) or str(local)
+        if dev_id and not dev_id.startswith("GPU-") and len(dev_id) > 8:
+            dev_id = "GPU-" + dev_id
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        clocks = Clocks(dev_id)
+        va, wa, ms_a, agg_a = trajectory(ctx, vs, ws, n0, steps, wl.tol, wl.sweeps, timed=True,
+                                         table=table)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        clk = clocks.stop()
+        ms_a = max_over_ranks(ms_a, world)
+        out = {"value": world * steps / (ms_a / 1e3), "ms_per_step": ms_a / steps,
+               "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_a / 1e3),
+               "agg": agg_a, "clocks": clk, "va": va, "wa": wa}
+        if extras:
+            vp, _, ms_p, agg_p = trajectory(ctx, vs, ws, n0, steps, 0.0, wl.sweeps, timed=True)
+            vr, _, _, _ = trajectory(ctx, vs, ws, n0, steps, 0.0, args.ref_sweeps, timed=False)
+            ref = vr.cpu().numpy()
+            err_a, err_p = max_err(va, ref), max_err(vp, ref)
+            out["plain"] = {"value": steps / (ms_p / 1e3), "unit": "steps/s",
+                            "ms_per_step": ms_p / steps,
+                            "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_p / 1e3)}
+            out["speedup_vs_plain"] = ms_p / ms_a
+            out["err_vs_ref"] = {"adaptive": err_a, "plain": err_p,
                                  "reference": "plain SDC, %d sweeps, same dt" % args.ref_sweeps,
-                                 "norm": "max |v(t_K) - v_ref(t_K)|"}}
+                                 "norm": "max |v(t_K) - v_ref(t_K)|"}
+            out["equal_error"] = equal_error(vs, ws, n0, steps, ref, err_a, ms_a)
+        return out
 
-    # end to end through the host-buffer entry point (pinned host arrays)
+    # ---- window 1: the first K steps from t = 0 (the headline value)
+    table0 = SolveTable(sm_max)
+    win0 = window(v0, w0, 0, K, not args.no_extras, table0)
+    agg_a, ms_adapt = win0["agg"], win0["ms_per_step"] * K
+    value = win0["value"]
+    extras = {k: win0[k] for k in ("plain", "speedup_vs_plain", "err_vs_ref", "equal_error")
+              if k in win0}
+
+    # ---- end to end through the host-buffer entry point (pinned host arrays)
     samples = sorted({s for s in (0, K // 5, 2 * K // 5, 3 * K // 5, 4 * K // 5) if s + 1 < K})
     snaps = {}
     hv_t = torch.tensor(wl.v0, dtype=torch.float64).pin_memory()
@@ -407,50 +623,12 @@ def run_gb300(args):
            "h2d_bytes_per_step": 2 * 8 * wl.n, "d2h_bytes_per_step": 2 * 8 * wl.n,
            "api": "sdc_step_host (pinned host v, w)"}
 
-    # roofline of the dominant kernel: restricted PCG, live CUDA-event times.
-    # On GB300 the binding roof is FP64 issue (2 lanes/cycle/SM); the HBM view
-    # of the same launches is reported beside it.
-    peaks = {}
-    if os.path.exists(PEAKS_FILE):
-        with open(PEAKS_FILE) as f:
-            peaks = json.load(f)
-    hbm_peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = FP64_LANES_PER_CYCLE * sm_max * 1e6 / 1e9            # G op/s
-    pcg_s = agg_a["pcg_ms"] / 1e3
-    launches = max(1, agg_a["pcg_launches"])
-    ach_ops = agg_a["pcg_ops"] / pcg_s / 1e9 if pcg_s > 0 else None
-    ach_gbs = agg_a["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
-    roofline = {"kernel": "k_pcg_scaled / k_pcg* (restricted Jacobi-PCG, symmetrically scaled "
-                          "form, one cooperative launch per node solve)",
-                "bound": "alu", "achieved": ach_ops, "peak": alu_peak,
-                "unit": "G FP64 lane-op/s",
-                "frac": ach_ops / alu_peak if ach_ops else None,
-                "peak_source": "304 FP64 lanes/cycle (ncu dfma peak_sustained) x %.0f MHz max SM clock"
-                               % sm_max,
-                "traffic": None,
-                "traffic_source": None,
-                "algorithmic_ops_per_launch": agg_a["pcg_ops"] / launches,
-                "algorithmic_bytes_per_launch": agg_a["pcg_bytes"] / launches,
-                "avg_launch_ms": agg_a["pcg_ms"] / launches,
-                "launches": agg_a["pcg_launches"],
-                "share_of_step": agg_a["pcg_ms"] / ms_adapt,
-                "hbm_view": {"achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach_gbs / hbm_peak if ach_gbs else None,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
-                             if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}}
-    tr = PCG_TRAFFIC.get(args.workload)
-    if tr is not None and agg_a["pcg_launches"] > 0:
-        roofline["traffic"] = (tr["dram_bytes"] / tr["algorithmic_bytes"]
-                               * roofline["algorithmic_bytes_per_launch"])
-        roofline["traffic_source"] = (
-            "ncu DRAM bytes of one full-size %s launch (%.1f MB for %.3f GB algorithmic), "
-            "scaled to the average launch by algorithmic bytes"
-            % (tr["kernel"], tr["dram_bytes"] / 1e6, tr["algorithmic_bytes"] / 1e9))
+    roofline = roofline_of(agg_a, ms_adapt)
+    roofline["size_classes"] = table0.table()
 
     cpu = None
     parity = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         states = [(s, snaps[s][0], snaps[s][1]) for s in samples if s in snaps]
         done, secs, outs = oracle_steps(wl, states, args.cpu_budget)
         cpu = {"value": done / secs, "unit": "steps/s", "cores": 1, "kind": "oracle",
@@ -464,17 +642,69 @@ def run_gb300(args):
                 diffs.append(float(np.abs(gv - r["v"]).max() / max(1.0, np.abs(r["v"]).max())))
         parity = {"max_rel_diff_v_vs_oracle": max(diffs) if diffs else None, "steps": len(diffs)}
 
+    # ---- window 2: the propagating front, from the state at t = 20 ms (slab only)
+    win20 = None
+    if args.workload == "w1" and not args.no_extras:
+        n20 = int(round(20.0 / wl.dt))
+        steps20 = max(1, min(K, wl.steps - n20))
+        v20, w20 = v0.clone(), w0.clone()
+        t_adv = time.perf_counter()
+        n_adv = 0
+        while n_adv < n20 and time.perf_counter() - t_adv < 30.0:
+            ctx.step(v20, w20, n_adv * wl.dt, wl.dt, wl.sweeps, wl.tol, want_stats=False)
+            n_adv += 1
+        torch.cuda.synchronize(dev)
+        table20 = SolveTable(sm_max)
+        w2 = window(v20, w20, n_adv, steps20, True, table20)
+        rf = roofline_of(w2["agg"], w2["ms_per_step"] * steps20)
+        rf["size_classes"] = table20.table()
+        win20 = {"t_start_ms": n_adv * wl.dt, "steps": steps20,
+                 "advance": "untimed adaptive steps from t = 0 (capped at 30 s)",
+                 "value": w2["value"], "unit": "steps/s", "ms_per_step": w2["ms_per_step"],
+                 "active_dof_sweeps_per_s": w2["active_dof_sweeps_per_s"],
+                 **{k: w2[k] for k in ("plain", "speedup_vs_plain", "err_vs_ref", "equal_error")},
+                 "phase_ms_per_step": dict(zip(("residual", "pcg", "update", "select",
+                                                "extract"),
+                                               (w2["agg"]["phase_ms"] / steps20).round(4)
+                                               .tolist())),
+                 "roofline": rf, "clocks": w2["clocks"]}
+        if rank == 0 and world == 1:
+            # one oracle step from the window's start state against the library's step
+            import oracle
+            S = oracle.System.from_mesh(wl.mesh, wl.sigma, wl.dof_scale)
+            hv20, hw20 = v20.cpu().numpy(), w20.cpu().numpy()
+            vg, wg = v20.clone(), w20.clone()
+            ctx.step(vg, wg, n_adv * wl.dt, wl.dt, wl.sweeps, wl.tol)
+            acts_g = [ctx.active(k) for k in range(wl.sweeps)]
+            t0 = time.perf_counter()
+            r = S.step(wl.ionic, wl.M, hv20, hw20, wl.dt, wl.sweeps, wl.tol, alpha=wl.alpha,
+                       cg_rtol=wl.cg_rtol, istim=wl.stim_vector(n_adv * wl.dt), want_log=True)
+            secs = time.perf_counter() - t0
+            vgn, wgn = vg.cpu().numpy(), wg.cpu().numpy()
+            same = (r["status"] == 0 and len(r["active"]) <= len(acts_g) and all(
+                np.array_equal(a, b) for a, b in zip(r["active"], acts_g)))
+            win20["oracle_step"] = {
+                "status": r["status"], "seconds": secs,
+                "max_rel_diff_v": float(np.abs(vgn - r["v"]).max()
+                                        / max(1.0, np.abs(r["v"]).max())),
+                "max_rel_diff_w": float(np.abs(wgn - r["w"]).max()
+                                        / max(1.0, np.abs(r["w"]).max())),
+                "active_sets_identical": bool(same),
+                "n_active": list(r["stats"].n_active[:r["stats"].sweeps_run])}
+
     phase = dict(zip(("residual", "pcg", "update", "select", "extract"),
                      (agg_a["phase_ms"] / K).round(4).tolist()))
     line = {"metric": metric_of(wl), "value": value, "unit": "steps/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms_adapt / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(config_of(wl, K, args.reorder), autotune=tune),
-            "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_adapt / 1e3),
+            "active_dof_sweeps_per_s": win0["active_dof_sweeps_per_s"],
             **extras,
             "phase_ms_per_step": phase,
             "roofline": roofline, "cpu_baseline": cpu, "oracle_parity_on_sample": parity,
-            "e2e": e2e, "clocks": clk, "gpu_launches": agg_a["launches"]}
+            "e2e": e2e, "clocks": win0["clocks"], "gpu_launches": agg_a["launches"]}
+    if win20 is not None:
+        line["window_t20"] = win20
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -604,13 +834,12 @@ def run_emi(args):
                 "algorithmic_bytes_per_launch": agg_a["pcg_bytes"] / launches,
                 "avg_launch_ms": agg_a["pcg_ms"] / launches, "launches": agg_a["pcg_launches"],
                 "share_of_step": agg_a["pcg_ms"] / ms_adapt,
-                "hbm_view": {"achieved": ach_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": ach_gbs / hbm_peak if ach_gbs else None,
-                             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"
-                             if "hbm_gbs" in peaks else "fallback 6.8 TB/s"}}
+                "effective_view": {"achieved": ach_gbs, "unit": "GB/s",
+                                   "note": "algorithmic bytes / time (L2 and DRAM together); "
+                                           "no DRAM capture is stored for this workload"}}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = emi_cpu_baseline(args.cpu_budget, agg_a["row_iters"] / K, frozen)
 
     phase = dict(zip(("residual", "pcg", "update", "select", "extract"),
@@ -660,10 +889,12 @@ def emi_cpu_baseline(budget_s, gpu_row_iters_per_step, frozen):
         done += 1
     rate = row_iters / secs
     return {"value": rate / gpu_row_iters_per_step, "unit": "steps/s", "cores": 1,
-            "kind": "oracle",
-            "sample": "%d oracle steps of the 2-cell instance (%d dofs) in %.1f s: %.3g CG "
-                      "row-iterations/s, divided by the full workload's %.3g row-iterations per "
-                      "step" % (done, wl.n, secs, rate, gpu_row_iters_per_step),
+            "kind": "oracle", "same_config": False,
+            "sample": "different configuration: %d oracle steps of a 2-cell instance of the same "
+                      "construction (%d dofs) in %.1f s, %.3g CG row-iterations/s, divided by "
+                      "the full workload's %.3g row-iterations per step (one oracle step of the "
+                      "full workload takes minutes)"
+                      % (done, wl.n, secs, rate, gpu_row_iters_per_step),
             "sample_steps_per_s": done / secs, "host": host_info()}
 
 

@@ -451,7 +451,8 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
  *     sdc_last_error(NULL), and nothing is launched.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
- *     stream capture starts on the device.
+ *     stream capture starts on the device.  After cudaDeviceReset the next
+ *     call looks the address up again in the device's new context.
  *   - Every call on a device uses the same array; calls that overlap on the GPU
  *     (other streams, other host threads) race.  Serialise them.
  * Meant for host frameworks that hand out all device memory from their own

@@ -88,21 +88,35 @@ def replayed_loss(ctx, wl, v0, w0, steps, probes, targets, tapes):
 
 class TrajectoryLoss(torch.autograd.Function):
     """L(s, k, a) for a context, a workload and probe targets, differentiated by
-    the discrete adjoint with checkpoints every `checkpoint_every` steps."""
+    the discrete adjoint with checkpoints every `checkpoint_every` steps.
+
+    The context's parameters may change between forward and backward (another
+    application of this function, a finite-difference probe): backward sets the
+    forward's (s, k, a) for its recomputation and adjoint, then puts back the
+    parameters the context held when backward started."""
 
     @staticmethod
     def forward(fctx, scale, ka, ctx, wl, steps, probes, targets, checkpoint_every):
         device = scale.device
-        _set_params(ctx, wl, scale, ka[0].item(), ka[1].item())
+        k, a = ka[0].item(), ka[1].item()
+        _set_params(ctx, wl, scale, k, a)
         v0 = torch.tensor(wl.v0, dtype=torch.float64, device=device)
         w0 = torch.tensor(wl.w0, dtype=torch.float64, device=device)
         loss, ckpts = trajectory_loss(ctx, wl, v0, w0, steps, probes, targets, checkpoint_every)
         fctx.save = (ctx, wl, ckpts, steps, probes, targets, device)
+        fctx.params = (scale.detach().clone(), k, a)
         return torch.tensor(loss, dtype=torch.float64, device=device)
 
     @staticmethod
     def backward(fctx, gout):
         ctx, wl, ckpts, steps, probes, targets, device = fctx.save
-        gs, gi = trajectory_grad(ctx, wl, ckpts, steps, probes, targets, device)
+        prev_scale, prev_ionic = ctx.dof_scale, ctx.ionic
+        _set_params(ctx, wl, *fctx.params)
+        try:
+            gs, gi = trajectory_grad(ctx, wl, ckpts, steps, probes, targets, device)
+        finally:
+            ctx.set_dof_scale(prev_scale)
+            if prev_ionic is not None:
+                ctx.set_ionic(prev_ionic)
         gka = torch.tensor([gi[0] + gi[1], gi[2]], dtype=torch.float64, device=device)
         return gout * gs, gout * gka, None, None, None, None, None, None

@@ -241,6 +241,10 @@ class Context:
         self._h = h
         self.M = int(M)
         self.n = int(xyz.shape[0])
+        # the parameters last handed to the library (read back by the autograd
+        # driver, which must restore them around its recomputation)
+        self.dof_scale = None if ds is None else ds.copy()
+        self.ionic = {k: getattr(ion, k) for k, _ in sdc_ionic._fields_}
 
     @classmethod
     def from_workload(cls, wl, options=None, stream=0):
@@ -335,12 +339,14 @@ class Context:
                                        gi), self._h)
 
     def set_dof_scale(self, scale):
-        sc = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
+        sc = None if scale is None else np.array(scale, dtype=np.float64, copy=True)
         _check(load().sdc_set_dof_scale(self._h, None if sc is None else sc.ctypes.data_as(_dp)),
                self._h)
+        self.dof_scale = sc
 
     def set_ionic(self, ionic):
         _check(load().sdc_set_ionic(self._h, C.byref(ionic_struct(ionic))), self._h)
+        self.ionic = dict(ionic)
 
     def nodes(self, V, W):
         _check(load().sdc_get_nodes(self._h, _vp(_ptr(V)), _vp(_ptr(W))), self._h)

@@ -19,7 +19,9 @@
 //   * host code cannot use the array's name as a device address, so the first
 //     call on each device looks the address up (cudaGetSymbolAddress, with that
 //     device current) and caches it; make that first call before any stream
-//     capture is started on the device.
+//     capture is started on the device.  The cache is keyed by the device's
+//     context as well: after cudaDeviceReset the array lives at a new address
+//     in the new context, and the first call there looks it up again.
 
 #include <cstdio>
 #include <mutex>
@@ -39,6 +41,26 @@ static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // context id the address belongs to
+
+// Unique id of the calling thread's current context (cuCtxGetId through the
+// runtime's driver entry point, so the library needs no link to libcuda);
+// 0 when there is none yet or the query is unavailable.
+unsigned long long current_context_id() {
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetId fn = []() -> GetId {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return (GetId)p;
+    }();
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != 0) return 0;
+    return id;
+}
 
 sdc_status reject(sdc_status st, const char* msg) {
     sdc::set_thread_error(msg);
@@ -72,7 +94,8 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
     double* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long ctx_id = current_context_id();
+        if (!g_scratch_addr[dev] || ctx_id == 0 || ctx_id != g_scratch_ctx[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
             if (e != cudaSuccess || !p) {
@@ -83,6 +106,8 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
                 return reject(SDC_E_CUDA, buf);
             }
             g_scratch_addr[dev] = (double*)p;
+            // the lookup made the device's context current if it was not yet
+            g_scratch_ctx[dev] = current_context_id();
         }
         base = g_scratch_addr[dev];
     }

@@ -244,3 +244,37 @@ def test_checkpoint_interval_does_not_change_the_gradient(torch_dev):
         assert L == grads[0][0]
         assert np.array_equal(gs, grads[0][1]) and np.array_equal(gka, grads[0][2])
     ctx.close()
+
+
+def test_backward_uses_the_forward_parameters(torch_dev):
+    """Two applications with different parameters before the first backward:
+    the first gradient equals the one taken alone, and backward leaves the
+    context with the parameters it held before (the second application's)."""
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300.autodiff import TrajectoryLoss
+    steps = 3
+    wl, ctx, probes, targets, rng, t64 = _setup(torch, dev, "2d", steps)
+    k0, a0 = wl.ionic["ga"], wl.ionic["a"]
+    s0 = wl.dof_scale.copy()
+    s1 = s0 * (1.0 + 0.05 * rng.standard_normal(wl.n))
+
+    def grad_at(sc, k, a):
+        scale = t64(sc).requires_grad_(True)
+        ka = t64([k, a]).requires_grad_(True)
+        return scale, ka, TrajectoryLoss.apply(scale, ka, ctx, wl, steps, probes, targets, 2)
+
+    scale, ka, L = grad_at(s0, k0, a0)
+    L.backward()
+    alone = (scale.grad.cpu().numpy().copy(), ka.grad.cpu().numpy().copy())
+
+    scale_a, ka_a, La = grad_at(s0, k0, a0)
+    scale_b, ka_b, Lb = grad_at(s1, 1.1 * k0, 0.9 * a0)
+    assert La.item() != Lb.item()
+    La.backward()
+    assert np.array_equal(scale_a.grad.cpu().numpy(), alone[0])
+    assert np.array_equal(ka_a.grad.cpu().numpy(), alone[1])
+    assert np.array_equal(ctx.dof_scale, s1)
+    assert ctx.ionic["ga"] == 1.1 * k0 and ctx.ionic["a"] == 0.9 * a0
+    Lb.backward()
+    assert np.all(np.isfinite(scale_b.grad.cpu().numpy()))
+    ctx.close()
