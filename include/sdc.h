@@ -107,7 +107,7 @@ typedef struct {
     int cg_variant;        /* 0: automatic; 1: vectors in global memory; 2: per-block vectors
                               in shared memory whenever they fit (3584 rows per SM for the
                               pipelined, 4768 for the classical arrangement)                 */
-    int cg_rows_per_block; /* shared-memory variant: target rows per block (0 = 512)          */
+    int cg_rows_per_block; /* shared-memory variant: target rows per block (0 = 256)          */
     int cg_cluster_rows;   /* solves with |I_k| <= this run on one thread-block cluster
                               (16 CTAs, distributed shared memory); default 10000, 0 = never */
     int profile;           /* 1: bracket every kernel launch with CUDA events on the context's

@@ -236,17 +236,41 @@ __device__ __forceinline__ int xs_field(double v) {
     return f < 1 ? 1 : f;
 }
 
+// 128-bit integers are handled as two 64-bit halves: variable shifts and the
+// final rounding run as a few 64-bit integer instructions, and nothing here
+// issues on the FP64 pipe, which the product warps keep busy meanwhile.
+__device__ __forceinline__ __int128 xs_make(unsigned long long hi, unsigned long long lo) {
+    return (__int128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// q >> d (arithmetic), 0 <= d <= 126
+__device__ __forceinline__ __int128 xs_sar(__int128 q, int d) {
+    const long long hi = (long long)((unsigned __int128)q >> 64);
+    const unsigned long long lo = (unsigned long long)q;
+    if (d == 0) return q;
+    if (d < 64)
+        return xs_make((unsigned long long)(hi >> d), (lo >> d) | ((unsigned long long)hi << (64 - d)));
+    return xs_make((unsigned long long)(hi >> 63), (unsigned long long)(hi >> (d - 64)));
+}
+
 // v as a signed fixed-point integer at the scale of field F (F >= field of v)
 __device__ __forceinline__ __int128 xs_fixed(double v, int F) {
     const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
     const int f = (int)(bits >> 52) & 0x7ff;
     const unsigned long long mant = (bits & 0xfffffffffffffull) | (f > 0 ? (1ull << 52) : 0ull);
     const int sh = 48 - (F - (f < 1 ? 1 : f));
-    unsigned __int128 q;
-    if (sh >= 0) q = (unsigned __int128)mant << sh;
-    else q = -sh >= 53 ? 0 : (unsigned __int128)(mant >> -sh);
-    const __int128 sq = (__int128)q;
-    return (bits >> 63) ? -sq : sq;
+    unsigned long long hi = 0, lo;
+    if (sh >= 0) {          // sh <= 48: mant << sh spans both halves
+        lo = mant << sh;
+        hi = sh > 0 ? mant >> (64 - sh) : 0ull;
+    } else {
+        lo = -sh >= 53 ? 0ull : mant >> -sh;
+    }
+    if (bits >> 63) {       // two's complement negation
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    return xs_make(hi, lo);
 }
 
 // exact warp sum of a signed 128-bit value (full warp): seven limbs summed
@@ -264,25 +288,50 @@ __device__ __forceinline__ __int128 xs_warp_sum(__int128 q) {
     return (__int128)tot;
 }
 
-// q 2^(F - 1123) rounded to the nearest double (ties to even)
+// q 2^(F - 1123) rounded to the nearest double (ties to even).  A normal
+// result is assembled from its bits with integer instructions; subnormal and
+// overflowing results take ldexp.
 __device__ __forceinline__ double xs_to_double(__int128 q, int F) {
     if (F >= 2047) return __longlong_as_double(0x7ff8000000000000ll);
     if (q == 0) return 0.0;
     const bool neg = q < 0;
-    const unsigned __int128 a = neg ? (unsigned __int128)(-q) : (unsigned __int128)q;
-    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    unsigned long long hi = (unsigned long long)((unsigned __int128)q >> 64);
+    unsigned long long lo = (unsigned long long)q;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
     const int L = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
     unsigned long long mant;
     int e = F - 1123;
     if (L <= 52) {
         mant = lo;
     } else {
-        const int sh = L - 52;
-        mant = (unsigned long long)(a >> sh);
-        const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
-        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+        const int sh = L - 52;     // 1 .. 75: drop sh bits, round to nearest even
+        bool up;
+        if (sh < 64) {
+            mant = (lo >> sh) | (hi << (64 - sh));
+            const unsigned long long r = lo & ((1ull << sh) - 1ull), h = 1ull << (sh - 1);
+            up = r > h || (r == h && (mant & 1ull));
+        } else {
+            mant = hi >> (sh - 64);
+            const unsigned long long rh = hi & ((1ull << (sh - 64)) - 1ull), rl = lo;
+            const unsigned long long hh = sh == 64 ? 0ull : 1ull << (sh - 65);
+            const unsigned long long hl = sh == 64 ? 1ull << 63 : 0ull;
+            const bool gt = rh > hh || (rh == hh && rl > hl);
+            const bool eq = rh == hh && rl == hl;
+            up = gt || (eq && (mant & 1ull));
+        }
+        if (up) ++mant;
         e += sh;
+    }
+    const int lead = 63 - __clzll((long long)mant);     // mant <= 2^53
+    const int biased = lead + e + 1023;
+    if (biased >= 1 && biased <= 2046) {
+        const unsigned long long frac =
+            (lead <= 52 ? mant << (52 - lead) : mant >> (lead - 52)) & 0xfffffffffffffull;
+        return __longlong_as_double(
+            (long long)(((unsigned long long)biased << 52) | frac | (neg ? 1ull << 63 : 0ull)));
     }
     const double d = ldexp((double)mant, e);
     return neg ? -d : d;
@@ -347,33 +396,82 @@ __device__ __forceinline__ void xs_store(XsRecord* r, int fa, int fb, __int128 q
     r->fb = fb;
 }
 
-// Exact totals of n records (one warp, all lanes get the result): the common
-// field is the largest block field; block sums are aligned by an arithmetic
-// right shift (truncation below 2^-101 of the largest term) and added.
+// Exact totals of n records, computed by warps 0 and 1 together (all 64
+// threads call it; all get the result).  The common field is the largest block
+// field; block sums are aligned by an arithmetic right shift (truncation below
+// 2^-101 of the largest term) and added.  Thread t takes records t, t + 64, ...:
+// up to 64 * kXsInFlight records are loaded once, every load issued before the
+// first is used, and reduced from registers (one memory round trip, not one per
+// record and pass); larger groups take two passes.  The two warps exchange their
+// largest fields and partial sums through X and a 64-thread named barrier.
+// Integer addition is exact, so the totals do not depend on the split.
+constexpr int kXsInFlight = 3;
+
+__device__ __forceinline__ void xs_pair_barrier() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+__device__ __forceinline__ void xs_accumulate(const XsRecord& r, int fa, int fb, __int128& sa,
+                                              __int128& sb) {
+    const __int128 qa = xs_make(r.ahi, r.alo);
+    const __int128 qb = xs_make(r.bhi, r.blo);
+    const int da = fa - r.fa, db = fb - r.fb;
+    sa += da >= 127 ? (qa < 0 ? (__int128)-1 : (__int128)0) : xs_sar(qa, da);
+    sb += db >= 127 ? (qb < 0 ? (__int128)-1 : (__int128)0) : xs_sar(qb, db);
+}
+
 template <class Load>
-__device__ __forceinline__ void xs_group_total(int n, Load&& load, double& ta, double& tb) {
-    const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void xs_group_total(int n, Load&& load, XsScratch& X, double& ta,
+                                               double& tb) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int fa = 1, fb = 1;
-    for (int i = lane; i < n; i += 32) {
-        const XsRecord r = load(i);
-        fa = max(fa, r.fa);
-        fb = max(fb, r.fb);
-    }
-    fa = __reduce_max_sync(0xffffffffu, fa);
-    fb = __reduce_max_sync(0xffffffffu, fb);
     __int128 sa = 0, sb = 0;
-    for (int i = lane; i < n; i += 32) {
-        const XsRecord r = load(i);
-        const __int128 qa = (__int128)(((unsigned __int128)r.ahi << 64) | r.alo);
-        const __int128 qb = (__int128)(((unsigned __int128)r.bhi << 64) | r.blo);
-        const int da = fa - r.fa, db = fb - r.fb;
-        sa += da >= 127 ? (qa < 0 ? (__int128)-1 : (__int128)0) : (qa >> da);
-        sb += db >= 127 ? (qb < 0 ? (__int128)-1 : (__int128)0) : (qb >> db);
+    auto exchange_fields = [&]() {
+        fa = __reduce_max_sync(0xffffffffu, fa);
+        fb = __reduce_max_sync(0xffffffffu, fb);
+        if (lane == 0) {
+            X.fmax[w] = fa;
+            X.fmax[2 + w] = fb;
+        }
+        xs_pair_barrier();
+        fa = max(X.fmax[0], X.fmax[1]);
+        fb = max(X.fmax[2], X.fmax[3]);
+    };
+    if (n <= 64 * kXsInFlight) {
+        XsRecord r[kXsInFlight];
+#pragma unroll
+        for (int k = 0; k < kXsInFlight; ++k) {
+            if (t + 64 * k < n) {
+                r[k] = load(t + 64 * k);
+            } else {
+                r[k].alo = r[k].ahi = r[k].blo = r[k].bhi = 0ull;
+                r[k].fa = r[k].fb = 1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kXsInFlight; ++k) {
+            fa = max(fa, r[k].fa);
+            fb = max(fb, r[k].fb);
+        }
+        exchange_fields();
+#pragma unroll
+        for (int k = 0; k < kXsInFlight; ++k) xs_accumulate(r[k], fa, fb, sa, sb);
+    } else {
+        for (int i = t; i < n; i += 64) {
+            const XsRecord r = load(i);
+            fa = max(fa, r.fa);
+            fb = max(fb, r.fb);
+        }
+        exchange_fields();
+        for (int i = t; i < n; i += 64) xs_accumulate(load(i), fa, fb, sa, sb);
     }
     sa = xs_warp_sum(sa);
     sb = xs_warp_sum(sb);
-    ta = xs_to_double(sa, fa);
-    tb = xs_to_double(sb, fb);
+    if (lane == 0) {
+        X.q[w] = sa;
+        X.q[2 + w] = sb;
+    }
+    xs_pair_barrier();
+    ta = xs_to_double(X.q[0] + X.q[1], fa);
+    tb = xs_to_double(X.q[2] + X.q[3], fb);
 }
 
 }  // namespace sdc

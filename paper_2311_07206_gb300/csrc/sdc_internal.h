@@ -150,6 +150,9 @@ constexpr int kSmemVectorsCS = 4;   // the scaled classical shared-memory varian
 constexpr int kSmemRowsS = 4800;    // rows per block of the symmetrically scaled variant
 constexpr int kSmemVectors = 8;     // per-row doubles in shared memory, shared-memory variant
 constexpr int kSmemRows = 3584;     // rows per block of the shared-memory variant
+// target rows per block of the shared-memory variants below their capacity: one row
+// per product thread of a 512-thread block, spread over up to one block per SM
+constexpr int kSmemRowsDefault = 256;
 constexpr int kClusterVectors = 10; // per-row doubles in shared memory, cluster variant
 constexpr int kClusterRows = 2848;  // rows per CTA of the cluster variant
 constexpr int kSmemVectorsC = 6;    // classical arrangement, shared-memory form

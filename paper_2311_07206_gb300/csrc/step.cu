@@ -185,6 +185,43 @@ __device__ __forceinline__ void cg_couple_row(const CgParams& P, int i, double x
     }
 }
 
+// Off-diagonal product of row i over its ELL slots, acc + sum_k val(k) x(col(k))
+// in slot order (the same FMAs, in the same order, as a plain slot loop).  The
+// column and value loads of CH slots, and then their gathers, are all issued
+// before the first multiply, so a row costs two memory round trips per CH slots
+// instead of two per slot: the latency that bounds an iteration when a thread
+// has one or two rows.  CH follows the register budget of the block size
+// (1024-thread blocks have 64 registers per thread).
+template <int MAXT>
+struct EllChunk {
+    static constexpr int value = MAXT > 512 ? 3 : 6;
+};
+
+template <int CH, class Val, class Gather>
+__device__ __forceinline__ double ell_row_dot(double acc, int len, size_t i, int ld,
+                                              const int* __restrict__ col, Val&& val,
+                                              Gather&& gather) {
+    for (int k0 = 0; k0 < len; k0 += CH) {
+        int j[CH];
+        double a[CH], x[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) {
+            if (k0 + k < len) {
+                const size_t q = (size_t)(k0 + k) * ld + i;
+                j[k] = __ldg(col + q);
+                a[k] = val(q);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+            if (k0 + k < len) x[k] = gather(j[k]);
+#pragma unroll
+        for (int k = 0; k < CH; ++k)
+            if (k0 + k < len) acc += a[k] * x[k];
+    }
+    return acc;
+}
+
 // Shared per-block state of a CG solve.  The scalars are derived by lane 0
 // of warps 0 and 1 from each pair of grid-wide sums (a few FP64 operations
 // per block, not per thread: the FP64 pipe is the scarce unit on this part).
@@ -356,7 +393,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         const double* mc = mbuf[nsum & 1];
         auto totals = [&]() {
             double g, d;
-            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         };
         if (sp0 > 0 && t < 64) totals();
@@ -491,7 +528,7 @@ __device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S,
         const double* mc = mbuf[nsum & 1];
         auto totals = [&]() {
             double g, d;
-            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * nblk + k); }, g, d);
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * nblk + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         };
         if (sp0 > 0 && t < 64) totals();
@@ -686,7 +723,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
         const double* mc = P.m + (nsum & 1) * (size_t)ld;
         auto totals = [&]() {
             double g, d;
-            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         };
         if (sp0 > 0 && t < 64) totals();
@@ -832,12 +869,32 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
         const double csi = c * __ldcg(sg + i);
         const double ri = SR(l);
         double acc = ri;
-        for (int k = 0; k < len; ++k) {
-            const size_t q = (size_t)k * ld + i;
-            const int j = __ldg(acol + q);
-            const double a = csi * __ldg(aval + q) * __ldcg(sg + j);
-            sval[q] = a;
-            acc += a * __ldcg(ug + j);
+        for (int k0 = 0; k0 < len; k0 += EllChunk<MAXT>::value) {
+            int j[EllChunk<MAXT>::value];
+            double av[EllChunk<MAXT>::value], sj[EllChunk<MAXT>::value], uj[EllChunk<MAXT>::value];
+#pragma unroll
+            for (int k = 0; k < EllChunk<MAXT>::value; ++k) {
+                if (k0 + k < len) {
+                    const size_t q = (size_t)(k0 + k) * ld + i;
+                    j[k] = __ldg(acol + q);
+                    av[k] = __ldg(aval + q);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < EllChunk<MAXT>::value; ++k) {
+                if (k0 + k < len) {
+                    sj[k] = __ldcg(sg + j[k]);
+                    uj[k] = __ldcg(ug + j[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < EllChunk<MAXT>::value; ++k) {
+                if (k0 + k < len) {
+                    const double a = csi * av[k] * sj[k];
+                    sval[(size_t)(k0 + k) * ld + i] = a;
+                    acc += a * uj[k];
+                }
+            }
         }
         SW(l) = acc;
         ga += ri * ri;
@@ -852,7 +909,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
         const double* mc = P.m + (nsum & 1) * (size_t)ld;
         auto totals = [&]() {
             double g, d;
-            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         };
         if (sp0 > 0 && t < 64) totals();
@@ -860,12 +917,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
             for (int l = t - sp0; l < nl; l += B - sp0) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
-                double acc = SW(l);
-                for (int k = 0; k < len; ++k) {
-                    const size_t q = (size_t)k * ld + i;
-                    acc += __ldcg(sval + q) * __ldcg(mc + __ldg(acol + q));
-                }
-                SN(l) = acc;
+                SN(l) = ell_row_dot<EllChunk<MAXT>::value>(SW(l), len, (size_t)i, ld, acol,
+                                    [&](size_t q) { return __ldcg(sval + q); },
+                                    [&](int j) { return __ldcg(mc + j); });
             }
         }
         if (sp0 == 0 && t < 64) totals();
@@ -920,9 +974,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
             const int i = r0 + l;
             const int len = __ldg(alen + i);
             const double xi = __ldcg(xg + i);
-            double acc = 0.0;
-            for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+            const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                                           [&](size_t q) { return __ldg(aval + q); },
+                                           [&](int j) { return __ldcg(xg + j); });
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -1001,12 +1055,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
     for (int l = t; l < nl; l += B) {
         const int i = r0 + l;
         const int len = __ldg(alen + i);
-        double acc = 0.0;
-        for (int k = 0; k < len; ++k) {
-            const int j = __ldg(acol + (size_t)k * ld + i);
-            const int owner = j / L;
-            acc += __ldg(aval + (size_t)k * ld + i) * mr[1][owner][j - owner * L];
-        }
+        const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                                       [&](size_t q) { return __ldg(aval + q); },
+                                       [&](int j) {
+                                           const int owner = j / L;
+                                           return mr[1][owner][j - owner * L];
+                                       });
         const double ri = sr[l], ui = su[l];
         const double wi = ri + c * acc;
         sw[l] = wi;
@@ -1026,7 +1080,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
         const int cb = nsum & 1;
         auto totals = [&]() {
             double g, d;
-            xs_group_total(C, [&](int k) { return pr[k][buf]; }, g, d);
+            xs_group_total(C, [&](int k) { return pr[k][buf]; }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         };
         if (sp0 > 0 && t < 64) totals();
@@ -1034,12 +1088,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
             for (int l = t - sp0; l < nl; l += B - sp0) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
-                double acc = 0.0;
-                for (int k = 0; k < len; ++k) {
-                    const int j = __ldg(acol + (size_t)k * ld + i);
-                    const int owner = j / L;
-                    acc += __ldg(aval + (size_t)k * ld + i) * mr[cb][owner][j - owner * L];
-                }
+                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                                               [&](size_t q) { return __ldg(aval + q); },
+                                               [&](int j) {
+                                                   const int owner = j / L;
+                                                   return mr[cb][owner][j - owner * L];
+                                               });
                 sn[l] = sw[l] + c * acc;
             }
         }
@@ -1092,9 +1146,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
                 const double xi = __ldcg(xg + i);
-                double acc = 0.0;
-                for (int k = 0; k < len; ++k)
-                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                                               [&](size_t q) { return __ldg(aval + q); },
+                                               [&](int j) { return __ldcg(xg + j); });
                 cg_couple_row(P, i, xi, acc);
             }
         }
@@ -1161,7 +1215,7 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
             return;
         if (t < 64) {
             double g, d;
-            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         }
         __syncthreads();
@@ -1276,7 +1330,7 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
             return;
         if (t < 64) {
             double g, d;
-            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, g, d);
+            xs_group_total(nblk, [&](int k) { return xs_load_cg(part + buf * pstride + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         }
         __syncthreads();
@@ -1445,7 +1499,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_scaled(CgParams P) {
             return;
         if (t < 64) {
             double g, d;
-            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         }
         __syncthreads();
@@ -1563,7 +1617,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
             return;
         if (t < 64) {
             double g, d;
-            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, g, d);
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, S.xs, g, d);
             if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
         }
         __syncthreads();
@@ -2071,7 +2125,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
     if (!cfg.pipelined || (cfg.general_classical && !on_chip)) {
         // classical arrangement: shared-memory form when it fits, else global vectors
         if (cfg.variant != 1 && n <= cfg.sms * kSmemRowsC) {
-            const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+            const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : kSmemRowsDefault;
             int grid = std::max(nblk(n, kSmemRowsC), nblk(n, rpb));
             grid = std::min(grid, cfg.sms);
             if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
@@ -2123,7 +2177,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
     // leave too little L1 for the irregular gathers and the global-vector kernel is faster
     // (16.1 against 18.9 ms of PCG per step)
     if (cfg.variant != 1 && cfg.scaled && P.sv && P.sval && n <= cfg.sms * kSmemRows) {
-        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : kSmemRowsDefault;
         int grid = std::max(nblk(n, kSmemRowsS), nblk(n, rpb));
         grid = std::min(grid, cfg.sms);
         if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
@@ -2139,7 +2193,7 @@ int launch_pcg_params(CgParams& P, const PcgConfig& cfg, StepBuffers& B, cudaStr
     // shared-memory variant: one block per SM at most, each owning <= kSmemRows rows
     const bool smem_ok = cfg.variant != 1 && n <= cfg.sms * kSmemRows;
     if (smem_ok && cfg.variant != 1) {
-        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : 512;
+        const int rpb = cfg.rows_per_block > 0 ? cfg.rows_per_block : kSmemRowsDefault;
         int grid = std::max(nblk(n, kSmemRows), nblk(n, rpb));
         grid = std::min(grid, cfg.sms);
         if (cfg.max_blocks > 0) grid = std::min(grid, cfg.max_blocks);
