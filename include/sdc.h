@@ -254,7 +254,7 @@ sdc_status sdc_get_matrix(const sdc_ctx* ctx, int* row_ptr, int* col, double* va
  * d_len[i] <= width entries, entry t at d_val[t * ld + i], column
  * d_col[t * ld + i] in [0, n); ld >= n.  Every array is caller-owned device
  * memory of the current device; d_x receives the solution.  The workspace
- * (10 n doubles plus a few per SM) is allocated and freed inside the call, which
+ * (8 n + 2 ld doubles plus a few per SM) is allocated and freed inside the call, which
  * synchronises `stream` (a cudaStream_t, NULL = legacy default).  iters and
  * relres (host, may be NULL) receive the iteration count and the final
  * sqrt(r'z / r0'z0).  Errors: SDC_E_INVALID (nothing launched),
@@ -447,8 +447,8 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
  * and errors as sdc_pcg_solve, but no device memory is allocated or freed:
  * the workspace is a static array of the library, reserved (about 5.6 MB) on
  * every GPU that loads the library until the process exits.
- *   - n <= SDC_PCG_NOALLOC_MAX_ROWS, else SDC_E_INVALID with a message from
- *     sdc_last_error(NULL), and nothing is launched.
+ *   - n <= SDC_PCG_NOALLOC_MAX_ROWS and 9 n + ld <= 10 SDC_PCG_NOALLOC_MAX_ROWS, else
+ *     SDC_E_INVALID with a message from sdc_last_error(NULL), and nothing is launched.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
  *     stream capture starts on the device.  After cudaDeviceReset the next

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsdc_gb300.so")
+# SDC_GB300_LIB selects another build of the library, e.g. the checked build
+# libsdc_gb300_checked.so (every kernel gather tested against its bound)
+LIB_PATH = os.environ.get("SDC_GB300_LIB") or os.path.join(HERE, "libsdc_gb300.so")
 
 SDC_MAX_M = 8
 SDC_MAX_SWEEPS = 64

@@ -135,11 +135,11 @@ __global__ void k_adj_wsweep(int n, const int* __restrict__ act, const double* _
                              const double* __restrict__ Wo, const double* __restrict__ Wn,
                              double dt, Ionic ion, Coll co, double* __restrict__ Vb,
                              double* __restrict__ Wb, double* __restrict__ lw0,
-                             double* __restrict__ part3) {
+                             double* __restrict__ part3, int N) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double gga = 0.0, ggs = 0.0, ga_ = 0.0;
     if (p < n) {
-        const int g = act ? act[p] : p;
+        const int g = act ? sdc_idx(act[p], N, 201) : p;
         ApDer d[M];
         double eps[M], den[M], eb[M], Nb[M], sb[M], gb[M], db[M];
 #pragma unroll
@@ -195,10 +195,10 @@ __global__ void k_adj_prep(int n, const int* __restrict__ act, const double* __r
                            const double* __restrict__ Vb, Ionic ion, int reaction_implicit,
                            int ld, double* __restrict__ J, double* __restrict__ D,
                            double* __restrict__ mc, double* __restrict__ kdc,
-                           double* __restrict__ Db, double* __restrict__ Jb) {
+                           double* __restrict__ Db, double* __restrict__ Jb, int N) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int g = act ? act[p] : p;
+    const int g = act ? sdc_idx(act[p], N, 202) : p;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const double v = Vo[(size_t)g * M + m], w = Wo[(size_t)g * M + m];
@@ -222,7 +222,7 @@ __global__ void k_adj_node_post(int n, const int* __restrict__ act, int m, doubl
                                 double* __restrict__ vkfull) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int g = act ? act[p] : p;
+    const int g = act ? sdc_idx(act[p], N, 203) : p;
     const double xb = x[p];
     const double cm = dt * co.Qh[m * kMaxM + m];
     const double dm = D[(size_t)m * ld + p];
@@ -249,7 +249,7 @@ __global__ void k_adj_residual(int n, const int* __restrict__ act, int ld, int N
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double gga = 0.0, ggs = 0.0, ga_ = 0.0;
     if (p < n) {
-        const int g = act ? act[p] : p;
+        const int g = act ? sdc_idx(act[p], N, 204) : p;
         const double mi = mass[g];
         double rb[M], fb[M];
         double rsum = 0.0;
@@ -292,7 +292,7 @@ __global__ void k_adj_kfull(int N, const double* __restrict__ kval, const int* _
     const int len = klen[i];
     for (int t = 0; t < len; ++t) {
         const double a = kval[(size_t)t * ldk + i];
-        const int j = kcol[(size_t)t * ldk + i];
+        const int j = sdc_idx(kcol[(size_t)t * ldk + i], N, 205);
 #pragma unroll
         for (int m = 0; m < M; ++m) acc[m] += a * ffull[(size_t)m * N + j];
     }
@@ -369,24 +369,25 @@ __global__ void k_adj_spread_back(int N, int M, const double* __restrict__ Vb,
     lw0[i] += b;
 }
 
-__global__ void k_pos_set(int n, const int* __restrict__ act, int* __restrict__ pos, int reset) {
+__global__ void k_pos_set(int n, const int* __restrict__ act, int* __restrict__ pos, int reset,
+                          int N) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    pos[act[q]] = reset ? -1 : q;
+    pos[sdc_idx(act[q], N, 206)] = reset ? -1 : q;
 }
 
 // restricted matrix of an arbitrary active list, straight from the global K
 __global__ void k_extract_global(int n, const int* __restrict__ act, const int* __restrict__ pos,
                                  const double* __restrict__ kval, const int* __restrict__ kcol,
                                  const int* __restrict__ klen, int ldk, double* __restrict__ nval,
-                                 int* __restrict__ ncol, int* __restrict__ nlen, int ldn) {
+                                 int* __restrict__ ncol, int* __restrict__ nlen, int ldn, int N) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const int g = act[q];
+    const int g = sdc_idx(act[q], N, 207);
     const int len = klen[g];
     int c = 0;
     for (int t = 0; t < len; ++t) {
-        const int jn = pos[kcol[(size_t)t * ldk + g]];
+        const int jn = pos[sdc_idx(kcol[(size_t)t * ldk + g], N, 208)];
         if (jn >= 0) {
             nval[(size_t)c * ldn + q] = kval[(size_t)t * ldk + g];
             ncol[(size_t)c * ldn + q] = jn;
@@ -398,10 +399,10 @@ __global__ void k_extract_global(int n, const int* __restrict__ act, const int* 
 
 // old compact row -> position in a replayed next list (pos holds that list)
 __global__ void k_replay_map(int n_old, const int* __restrict__ act_old,
-                             const int* __restrict__ pos, int* __restrict__ map) {
+                             const int* __restrict__ pos, int* __restrict__ map, int N) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_old) return;
-    map[p] = pos[act_old ? act_old[p] : p];
+    map[p] = pos[act_old ? sdc_idx(act_old[p], N, 209) : p];
 }
 
 template <class F>
@@ -421,20 +422,22 @@ void dispatch_M(int M, F&& f) {
 
 }  // namespace
 
-void launch_pos_set(int n, const int* act, int* pos, int reset, cudaStream_t s) {
-    if (n > 0) k_pos_set<<<nb(n, kAdjBlock), kAdjBlock, 0, s>>>(n, act, pos, reset);
+void launch_pos_set(int n, const int* act, int* pos, int reset, int N, cudaStream_t s) {
+    if (n > 0) k_pos_set<<<nb(n, kAdjBlock), kAdjBlock, 0, s>>>(n, act, pos, reset, N);
 }
 
-void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s) {
-    if (n_old > 0) k_replay_map<<<nb(n_old, kAdjBlock), kAdjBlock, 0, s>>>(n_old, act_old, pos, map);
+void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, int N,
+                       cudaStream_t s) {
+    if (n_old > 0)
+        k_replay_map<<<nb(n_old, kAdjBlock), kAdjBlock, 0, s>>>(n_old, act_old, pos, map, N);
 }
 
-void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, Ell& out,
+void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, Ell& out, int N,
                            cudaStream_t s) {
     if (n > 0)
         k_extract_global<<<nb(n, kAdjBlock), kAdjBlock, 0, s>>>(n, act, pos, K.val, K.col, K.len,
                                                                 K.ld, out.val, out.col, out.len,
-                                                                out.ld);
+                                                                out.ld, N);
 }
 
 int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaStream_t s) {
@@ -460,21 +463,21 @@ int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaSt
         // restricted matrix of I_k
         const Ell* A = &K;
         if (act) {
-            launch_pos_set(n, act, W.pos, 0, s);
-            launch_extract_global(n, act, W.pos, K, B.A[0], s);
-            launch_pos_set(n, act, W.pos, 1, s);
+            launch_pos_set(n, act, W.pos, 0, N, s);
+            launch_extract_global(n, act, W.pos, K, B.A[0], N, s);
+            launch_pos_set(n, act, W.pos, 1, N, s);
             A = &B.A[0];
         }
         dispatch_M(M, [&](auto mc) {
             constexpr int MM = decltype(mc)::value;
             if (!a.w_frozen) {
                 k_adj_wsweep<MM><<<nbk, kAdjBlock, 0, s>>>(n, act, Vn, Wo, Wn, a.dt, a.ion, a.co,
-                                                           W.Vb, W.Wb, a.lam_w0, W.part3);
+                                                           W.Vb, W.Wb, a.lam_w0, W.part3, N);
                 k_sum3<<<1, 32, 0, s>>>(nbk, W.part3, W.iacc);
             }
             k_adj_prep<MM><<<nbk, kAdjBlock, 0, s>>>(n, act, Vo, Wo, Vn, a.kdiag, a.mass, W.Vb,
                                                      a.ion, a.reaction_implicit, ld, B.J, B.D,
-                                                     B.mc, B.kdc, B.R, W.Jb);
+                                                     B.mc, B.kdc, B.R, W.Jb, N);
         });
         cudaMemsetAsync(W.bfull, 0, (size_t)M * N * sizeof(double), s);
         cudaMemsetAsync(W.vkfull, 0, (size_t)M * N * sizeof(double), s);
@@ -529,4 +532,8 @@ int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaSt
     return SDC_OK;
 }
 
+}  // namespace sdc
+
+namespace sdc {
+SDC_CHECK_READER(check_take_adjoint)
 }  // namespace sdc

@@ -87,6 +87,34 @@ sdc_status fail(sdc_ctx* c, sdc_status st, const char* fmt, ...) {
     return st;
 }
 
+}  // namespace
+
+namespace sdc {
+sdc_status check_outcome(sdc_ctx* c, void* stream, sdc_status st) {
+#if SDC_CHECKED
+    unsigned long long (*const take[4])(void*, unsigned*) = {check_take_step, check_take_emi,
+                                                             check_take_adjoint,
+                                                             check_take_assembly};
+    const char* const name[4] = {"step", "cell-by-cell", "adjoint", "assembly"};
+    for (int k = 0; k < 4; ++k) {
+        unsigned cnt = 0;
+        const unsigned long long f = take[k](stream, &cnt);
+        if (f || cnt)
+            return fail(c, SDC_E_INVALID,
+                        "checked build: %u gathered indices outside their bounds in the %s "
+                        "kernels, the first at check site %u (index %d)",
+                        cnt, name[k], (unsigned)(f >> 32), (int)(unsigned)(f & 0xffffffffu));
+    }
+#else
+    (void)c;
+    (void)stream;
+#endif
+    return st;
+}
+}  // namespace sdc
+
+namespace {
+
 sdc_status cuda_fail(sdc_ctx* c, const char* where) {
     cudaError_t e = cudaGetLastError();
     return fail(c, SDC_E_CUDA, "%s: %s", where, cudaGetErrorString(e));
@@ -561,7 +589,8 @@ extern "C" {
 
 sdc_status sdc_create(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ionic, int M,
                       const sdc_options* opt, void* stream) {
-    return create_impl(out, mesh, ionic, M, opt, stream, nullptr);
+    const sdc_status st = create_impl(out, mesh, ionic, M, opt, stream, nullptr);
+    return check_outcome(out ? *out : nullptr, stream, st);
 }
 
 sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* emi,
@@ -571,7 +600,8 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
         if (out) *out = nullptr;
         return SDC_E_INVALID;
     }
-    return create_impl(out, mesh, ionic, M, opt, stream, nullptr, emi);
+    const sdc_status st = create_impl(out, mesh, ionic, M, opt, stream, nullptr, emi);
+    return check_outcome(out ? *out : nullptr, stream, st);
 }
 
 sdc_status sdc_set_stimulus(sdc_ctx* c, const int* nodes, int n, double amp, double t_on,
@@ -610,7 +640,8 @@ extern "C" {
 
 sdc_status sdc_step(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
                     double TOL, sdc_stats* stats) {
-    return step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats, nullptr);
+    const sdc_status st = step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats, nullptr);
+    return c ? check_outcome(c, c->stream, st) : st;
 }
 
 sdc_status sdc_step_taped(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, int sweeps,
@@ -632,8 +663,9 @@ sdc_status sdc_step_taped(sdc_ctx* c, double* d_v, double* d_w, double t, double
                     return fail(c, SDC_E_INVALID, "replay: active sets are not nested");
         }
     }
-    return step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats,
-                     tape && tape->mode != SDC_TAPE_OFF ? tape : nullptr);
+    const sdc_status st = step_impl(c, d_v, d_w, t, dt, sweeps, TOL, stats,
+                                    tape && tape->mode != SDC_TAPE_OFF ? tape : nullptr);
+    return check_outcome(c, c->stream, st);
 }
 
 }  // extern "C"
@@ -976,9 +1008,9 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
             if (nn > 0)
                 cudaMemcpyAsync(next, tape->d_act + (size_t)(k + 1) * N, (size_t)nn * sizeof(int),
                                 cudaMemcpyDeviceToDevice, s);
-            launch_pos_set(nn, next, c->AW.pos, 0, s);
-            launch_replay_map(n, act, c->AW.pos, B.map, s);
-            launch_pos_set(nn, next, c->AW.pos, 1, s);
+            launch_pos_set(nn, next, c->AW.pos, 0, c->N, s);
+            launch_replay_map(n, act, c->AW.pos, B.map, c->N, s);
+            launch_pos_set(nn, next, c->AW.pos, 1, c->N, s);
             cudaMemcpyAsync(&B.sc->count, &tape->n_active[k + 1 < sweeps ? k + 1 : 0], sizeof(int),
                             cudaMemcpyHostToDevice, s);
             launches[SDC_PHASE_SELECT] += 3;
@@ -1253,10 +1285,25 @@ sdc_status sdc_get_matrix(const sdc_ctx* cc, int* row_ptr, int* col, double* val
     return SDC_OK;
 }
 
+static sdc_status pcg_solve_body(int n, const double* d_val, const int* d_col, const int* d_len,
+                                 int ld, int width, const double* d_kdiag, const double* d_mass,
+                                 const double* d_J, double c, const double* d_b, double* d_x,
+                                 double rtol, int maxit, int* iters, double* relres, void* stream);
+
 sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int* d_len, int ld,
                          int width, const double* d_kdiag, const double* d_mass, const double* d_J,
                          double c, const double* d_b, double* d_x, double rtol, int maxit,
                          int* iters, double* relres, void* stream) {
+    const sdc_status st = pcg_solve_body(n, d_val, d_col, d_len, ld, width, d_kdiag, d_mass, d_J,
+                                         c, d_b, d_x, rtol, maxit, iters, relres, stream);
+    return check_outcome(nullptr, stream, st);
+}
+
+static sdc_status pcg_solve_body(int n, const double* d_val, const int* d_col, const int* d_len,
+                                 int ld, int width, const double* d_kdiag, const double* d_mass,
+                                 const double* d_J, double c, const double* d_b, double* d_x,
+                                 double rtol, int maxit, int* iters, double* relres,
+                                 void* stream) {
     g_create_error.clear();
     if (n < 1 || ld < n || width < 0 || !d_len || !d_kdiag || !d_mass || !d_J || !d_b || !d_x ||
         (width > 0 && (!d_val || !d_col)) || !(rtol > 0.0) || maxit < 1 || !std::isfinite(c))
@@ -1264,9 +1311,10 @@ sdc_status sdc_pcg_solve(int n, const double* d_val, const int* d_col, const int
     cudaStream_t s = (cudaStream_t)stream;
     const int block = 256;
     const int maxb = pcg_max_blocks(block);
-    // workspace: 10 vectors, 12 * maxb for the partial-sum records (16-byte aligned:
-    // they are read with 16-byte loads), then the scalars
-    const size_t po = ((size_t)10 * n + 1) & ~(size_t)1;
+    // workspace: 8 vectors of n, the published m in two buffers ld apart (the kernels
+    // offset the second by the matrix's ld), 12 * maxb for the partial-sum records
+    // (16-byte aligned: they are read with 16-byte loads), then the scalars
+    const size_t po = ((size_t)8 * n + 2 * (size_t)ld + 1) & ~(size_t)1;
     const size_t nd = po + 12 * (size_t)maxb + 2;
     char* ws = nullptr;
     if (cudaMalloc(&ws, nd * sizeof(double) + 64) != cudaSuccess)
@@ -1385,7 +1433,7 @@ sdc_status sdc_batch_create(sdc_batch** out, const sdc_mesh* meshes, int n_insta
     bt->off = off;
     bt->amp.assign((size_t)nodes, 0.0);
     *out = bt;
-    return SDC_OK;
+    return check_outcome(nullptr, stream, SDC_OK);
 }
 
 sdc_status sdc_batch_info(const sdc_batch* bt, int* n_instances, int* offsets) {
@@ -1471,11 +1519,25 @@ size_t sdc_tape_bytes(const sdc_ctx* c, int sweeps) {
     return (size_t)2 * sweeps * c->N * c->M * sizeof(double) + (size_t)sweeps * c->N * sizeof(int);
 }
 
+static sdc_status step_adjoint_body(sdc_ctx* c, const sdc_tape* tape, const double* d_v0,
+                                    const double* d_w0, double dt, const double* d_lam_v,
+                                    const double* d_lam_w, double* d_lam_v0, double* d_lam_w0,
+                                    double* d_grad_scale, double* grad_ionic);
+
 sdc_status sdc_step_adjoint(sdc_ctx* c, const sdc_tape* tape, const double* d_v0,
                             const double* d_w0, double dt, const double* d_lam_v,
                             const double* d_lam_w, double* d_lam_v0, double* d_lam_w0,
                             double* d_grad_scale, double* grad_ionic) {
     if (!c) return SDC_E_INVALID;
+    const sdc_status st = step_adjoint_body(c, tape, d_v0, d_w0, dt, d_lam_v, d_lam_w, d_lam_v0,
+                                            d_lam_w0, d_grad_scale, grad_ionic);
+    return check_outcome(c, c->stream, st);
+}
+
+static sdc_status step_adjoint_body(sdc_ctx* c, const sdc_tape* tape, const double* d_v0,
+                                    const double* d_w0, double dt, const double* d_lam_v,
+                                    const double* d_lam_w, double* d_lam_v0, double* d_lam_w0,
+                                    double* d_grad_scale, double* grad_ionic) {
     if (!tape || tape->sweeps < 1 || tape->sweeps > SDC_MAX_SWEEPS || !tape->d_V || !tape->d_W ||
         (tape->sweeps > 1 && !tape->d_act))
         return fail(c, SDC_E_INVALID, "sdc_step_adjoint: missing or empty tape");
@@ -1547,7 +1609,7 @@ sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
     }
     const int rc = reassemble_device(c->K, h_scale, c->opt.drop_rel, c->stream, why);
     if (rc != SDC_OK) return fail(c, (sdc_status)rc, "%s", why.c_str());
-    return SDC_OK;
+    return check_outcome(c, c->stream, SDC_OK);
 }
 
 sdc_status sdc_set_ionic(sdc_ctx* c, const sdc_ionic* ionic) {
@@ -1717,13 +1779,15 @@ extern "C" {
 
 sdc_status sdc_autotune(sdc_ctx* ctx, double* d_v, double* d_w, double t, double dt, int sweeps,
                         double TOL, int trial_steps, sdc_tune_report* out) {
-    return autotune_impl(ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+    const sdc_status st = autotune_impl(ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+    return ctx ? check_outcome(ctx, ctx->stream, st) : st;
 }
 
 sdc_status sdc_batch_autotune(sdc_batch* bt, double* d_v, double* d_w, double t, double dt,
                               int sweeps, double TOL, int trial_steps, sdc_tune_report* out) {
     if (!bt) return SDC_E_INVALID;
-    return autotune_impl(bt->ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+    const sdc_status st = autotune_impl(bt->ctx, d_v, d_w, t, dt, sweeps, TOL, trial_steps, out);
+    return check_outcome(bt->ctx, bt->ctx->stream, st);
 }
 
 }  // extern "C"

@@ -38,6 +38,11 @@ __global__ void k_assemble_rows(int N, int dim, const double* __restrict__ xyz,
         const int e = n2e[k];
         const int a = n2e_loc[k];
         const int* vt = elem + (size_t)e * nv;
+#if SDC_CHECKED
+        bool bad = false;
+        for (int b = 0; b < nv; ++b) bad |= sdc_idx(vt[b], N, 301) != vt[b];
+        if (bad) return;
+#endif
         double grad[4][3];
         double vol;
         if (!p1_gradients(dim, xyz, vt, grad, vol)) {
@@ -328,4 +333,8 @@ int reassemble_device(AssemblyOut& out, const double* h_scale, double drop_rel, 
     return rc;
 }
 
+}  // namespace sdc
+
+namespace sdc {
+SDC_CHECK_READER(check_take_assembly)
 }  // namespace sdc

@@ -93,6 +93,63 @@ __device__ __forceinline__ bool p1_gradients(int dim, const double* __restrict__
     return true;
 }
 
+// ---- checked builds -------------------------------------------------------------
+// Built with SDC_CHECKED=1 (libsdc_gb300_checked.so), every gathered index of the
+// kernels goes through sdc_idx(j, bound, site): an index outside [0, bound) is recorded
+// in this translation unit's check words (the check site and the index of the first
+// failure, and a count) and replaced by 0, an in-bounds index, so the kernel runs on to
+// its end over bounded loops; the library's entry points turn a record into
+// SDC_E_INVALID after the call.  Without the flag sdc_idx returns j unchanged and the
+// check compiles away.
+#if SDC_CHECKED
+static __device__ unsigned long long g_check_first;   // (site << 32) | index, 0: none
+static __device__ unsigned int g_check_count;
+#endif
+__device__ __forceinline__ int sdc_idx(int j, int bound, int site) {
+#if SDC_CHECKED
+    if ((unsigned)j >= (unsigned)bound) {
+        atomicCAS(&g_check_first, 0ull, ((unsigned long long)(unsigned)site << 32) | (unsigned)j);
+        atomicAdd(&g_check_count, 1u);
+        return 0;
+    }
+#else
+    (void)bound;
+    (void)site;
+#endif
+    return j;
+}
+
+// Host side: read and clear this translation unit's check words after the work on
+// `stream`; returns the first failure record (0: none) and sets *count.
+#if SDC_CHECKED
+#define SDC_CHECK_READER(fn)                                                               \
+    unsigned long long fn(void* stream, unsigned* count) {                                  \
+        unsigned long long first = 0, zero = 0;                                             \
+        unsigned cnt = 0, zc = 0;                                                           \
+        cudaStream_t s = (cudaStream_t)stream;                                              \
+        cudaMemcpyFromSymbolAsync(&first, g_check_first, sizeof first, 0,                   \
+                                  cudaMemcpyDeviceToHost, s);                               \
+        cudaMemcpyFromSymbolAsync(&cnt, g_check_count, sizeof cnt, 0, cudaMemcpyDeviceToHost, \
+                                  s);                                                       \
+        cudaStreamSynchronize(s);                                                           \
+        if (first || cnt) {                                                                 \
+            cudaMemcpyToSymbolAsync(g_check_first, &zero, sizeof zero, 0,                   \
+                                    cudaMemcpyHostToDevice, s);                             \
+            cudaMemcpyToSymbolAsync(g_check_count, &zc, sizeof zc, 0, cudaMemcpyHostToDevice, \
+                                    s);                                                     \
+            cudaStreamSynchronize(s);                                                       \
+        }                                                                                   \
+        if (count) *count = cnt;                                                            \
+        return first;                                                                       \
+    }
+#else
+#define SDC_CHECK_READER(fn)                                \
+    unsigned long long fn(void*, unsigned* count) {          \
+        if (count) *count = 0;                               \
+        return 0;                                            \
+    }
+#endif
+
 // ---- error flag: first error wins ---------------------------------------------
 __device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
 

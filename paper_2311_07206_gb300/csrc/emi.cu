@@ -55,10 +55,10 @@ __global__ void k_emi_pair_eval(int NP, const int* __restrict__ pk, const int* _
                                 const int* __restrict__ pkind, const double* __restrict__ V,
                                 const double* __restrict__ Wp, Ionic ion, double g_gap,
                                 int reaction_implicit, double* __restrict__ Ip,
-                                double* __restrict__ Jp) {
+                                double* __restrict__ Jp, int N) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
-    const int k = pk[p], l = pl[p], kind = pkind[p];
+    const int k = sdc_idx(pk[p], N, 101), l = sdc_idx(pl[p], N, 102), kind = pkind[p];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const double v = V[(size_t)k * M + m] - V[(size_t)l * M + m];
@@ -86,10 +86,10 @@ __global__ void k_emi_residual(int n, const int* __restrict__ act, const double*
                                const double* __restrict__ Ip, int NP, const double* __restrict__ V,
                                const double* __restrict__ u0, double Cm, double dt, Coll co,
                                int ld, double* __restrict__ R, double* __restrict__ J,
-                               double* __restrict__ kdc) {
+                               double* __restrict__ kdc, int N) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const int g = act ? act[q] : q;
+    const int g = act ? sdc_idx(act[q], N, 103) : q;
     const double kd = kdiag[g] + (robin ? robin[g] : 0.0);
     double f[M], bt[M];
 #pragma unroll
@@ -100,13 +100,13 @@ __global__ void k_emi_residual(int n, const int* __restrict__ act, const double*
     const int len = klen[g];
     for (int t = 0; t < len; ++t) {
         const double a = kval[(size_t)t * ldk + g];
-        const int j = kcol[(size_t)t * ldk + g];
+        const int j = sdc_idx(kcol[(size_t)t * ldk + g], N, 104);
 #pragma unroll
         for (int m = 0; m < M; ++m) f[m] -= a * V[(size_t)j * M + m];
     }
     const double u0g = u0[g];
     for (int e = np_ptr[g]; e < np_ptr[g + 1]; ++e) {
-        const int pid = np_pid[e], j = np_part[e];
+        const int pid = sdc_idx(np_pid[e], NP, 105), j = sdc_idx(np_part[e], N, 106);
         const double A = parea[pid], s = (double)np_sign[e];
         const double du0 = u0g - u0[j];
 #pragma unroll
@@ -137,22 +137,23 @@ __global__ void k_emi_build(int n, const int* __restrict__ act, const double* __
                             const double* __restrict__ Jpm, const int* __restrict__ pos,
                             double Cm, double c, double* __restrict__ eval,
                             int* __restrict__ ecol, int* __restrict__ elen,
-                            double* __restrict__ mc, unsigned long long* __restrict__ slots) {
+                            double* __restrict__ mc, unsigned long long* __restrict__ slots,
+                            int N) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     int added = 0;
     if (q < n) {
-    const int g = act ? act[q] : q;
+    const int g = act ? sdc_idx(act[q], N, 107) : q;
     int cnt = alen[q];
     for (int t = 0; t < cnt; ++t) {
         eval[(size_t)t * ld + q] = aval[(size_t)t * lda + q];
-        ecol[(size_t)t * ld + q] = acol[(size_t)t * lda + q];
+        ecol[(size_t)t * ld + q] = sdc_idx(acol[(size_t)t * lda + q], n, 108);
     }
     double pd = 0.0;
     for (int e = np_ptr[g]; e < np_ptr[g + 1]; ++e) {
         const int pid = np_pid[e];
         const double coef = parea[pid] * (Cm + c * Jpm[pid]);
         pd += coef;
-        const int jq = pos[np_part[e]];
+        const int jq = pos[sdc_idx(np_part[e], N, 109)];
         if (jq >= 0) {
             eval[(size_t)cnt * ld + q] = -coef / c;
             ecol[(size_t)cnt * ld + q] = jq;
@@ -179,18 +180,19 @@ __global__ void k_emi_couple(int n, const int* __restrict__ act, int m, int M,
                              const int* __restrict__ np_part, const double* __restrict__ parea,
                              const double* __restrict__ Jpm, const int* __restrict__ pos,
                              const double* __restrict__ x, double dt, Coll co,
-                             double* __restrict__ R) {
+                             double* __restrict__ R, int N) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
-    const int g = act ? act[q] : q;
+    const int g = act ? sdc_idx(act[q], N, 110) : q;
     const double xq = x[q];
     double acc = kdc[q] * xq;
     const int len = alen[q];
-    for (int t = 0; t < len; ++t) acc += aval[(size_t)t * lda + q] * x[acol[(size_t)t * lda + q]];
+    for (int t = 0; t < len; ++t)
+        acc += aval[(size_t)t * lda + q] * x[sdc_idx(acol[(size_t)t * lda + q], n, 111)];
     for (int e = np_ptr[g]; e < np_ptr[g + 1]; ++e) {
         const int pid = np_pid[e];
-        const int jq = pos[np_part[e]];
-        acc += parea[pid] * Jpm[pid] * (xq - (jq >= 0 ? x[jq] : 0.0));
+        const int jq = pos[sdc_idx(np_part[e], N, 112)];
+        acc += parea[pid] * Jpm[pid] * (xq - (jq >= 0 ? x[sdc_idx(jq, n, 113)] : 0.0));
     }
     for (int mm = m + 1; mm < M; ++mm) R[(size_t)mm * ld + q] -= dt * co.Qh[mm * kMaxM + m] * acc;
 }
@@ -202,10 +204,10 @@ __global__ void k_emi_wsweep(int NP, const int* __restrict__ pk, const int* __re
                              const int* __restrict__ pkind, const int* __restrict__ pos,
                              const double* __restrict__ V, double* __restrict__ Wp,
                              const double* __restrict__ w0, double dt, Ionic ion, Coll co,
-                             int* __restrict__ err) {
+                             int* __restrict__ err, int N) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NP) return;
-    const int k = pk[p], l = pl[p];
+    const int k = sdc_idx(pk[p], N, 114), l = sdc_idx(pl[p], N, 115);
     if (pkind[p] != 0 || (pos[k] < 0 && pos[l] < 0)) return;
     double wm[M], gR[M], dR[M], e[M];
 #pragma unroll
@@ -419,7 +421,7 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         cur_m = -1;
         // compact positions of the current list (partners outside it read -1)
         run(SDC_PHASE_SELECT, 1, [&] {
-            if (act) launch_pos_set(n, act, E.pos, 0, s);
+            if (act) launch_pos_set(n, act, E.pos, 0, B.N, s);
             else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 0);
         });
         run(SDC_PHASE_RESIDUAL, 2, [&] {
@@ -427,11 +429,11 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
                 constexpr int MM = decltype(mc)::value;
                 k_emi_pair_eval<MM><<<nbk(NP, 256), 256, 0, s>>>(
                     NP, E.pk, E.pl, E.pkind, B.V, E.Wp, *a.ion, E.g_gap, a.opt->reaction_implicit,
-                    E.Ip, E.Jp);
+                    E.Ip, E.Jp, B.N);
                 k_emi_residual<MM><<<nbk(n, 128), 128, 0, s>>>(
                     n, act, a.K->K.val, a.K->K.col, a.K->K.len, a.K->K.ld, a.K->kdiag, E.robin,
                     E.np_ptr, E.np_pid, E.np_part, E.np_sign, E.parea, E.Ip, NP, B.V, d_u, E.Cm,
-                    dt, co, B.ld, B.R, B.J, B.kdc);
+                    dt, co, B.ld, B.R, B.J, B.kdc, B.N);
             });
         });
         cudaMemsetAsync(E.slots, 0, sizeof(unsigned long long), s);
@@ -443,7 +445,7 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
                 k_emi_build<<<nbk(n, 128), 128, 0, s>>>(
                     n, act, A->val, A->col, A->len, A->ld, B.ld, E.np_ptr, E.np_pid, E.np_part,
                     E.parea, Jm, E.pos, E.Cm, c, E.A.val, E.A.col, E.A.len, B.mc,
-                    m == 0 ? E.slots : nullptr);
+                    m == 0 ? E.slots : nullptr, B.N);
             });
             PcgRole role{};
             role.b = B.R + (size_t)m * B.ld;
@@ -469,7 +471,7 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
                     k_emi_couple<<<nbk(n, 128), 128, 0, s>>>(
                         n, act, m, M, A->val, A->col, A->len, A->ld, B.ld, B.kdc, E.np_ptr,
                         E.np_pid, E.np_part, E.parea, Jm, E.pos, B.D + (size_t)m * B.ld, dt, co,
-                        B.R);
+                        B.R, B.N);
                 });
             }
         }
@@ -489,12 +491,12 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
                     constexpr int MM = decltype(mc)::value;
                     k_emi_wsweep<MM><<<nbk(NP, 256), 256, 0, s>>>(
                         NP, E.pk, E.pl, E.pkind, E.pos, B.V, E.Wp, d_w, dt, *a.ion, co,
-                        &B.sc->err);
+                        &B.sc->err, B.N);
                 });
         });
         int* next = (k + 1 < sweeps) ? (*a.act)[k + 1] : (*a.act)[0];
         run(SDC_PHASE_SELECT, 3, [&] {
-            if (act) launch_pos_set(n, act, E.pos, 1, s);
+            if (act) launch_pos_set(n, act, E.pos, 1, B.N, s);
             else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 1);
             launch_select(n, act, next, B, s);
         });
@@ -607,4 +609,8 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
     return status;
 }
 
+}  // namespace sdc
+
+namespace sdc {
+SDC_CHECK_READER(check_take_emi)
 }  // namespace sdc

@@ -83,6 +83,14 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
                  kMaxRows);
         return reject(SDC_E_INVALID, buf);
     }
+    // the published m takes two buffers ld apart after the eight other vectors
+    if (n > 0 && ld > 0 && 9 * (size_t)n + (size_t)ld > kVecDoubles) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "sdc_pcg_solve_noalloc: ld = %d too large for n = %d in the static workspace "
+                 "(9 n + ld must not exceed %zu)", ld, n, kVecDoubles);
+        return reject(SDC_E_INVALID, buf);
+    }
     if (n < 1 || ld < n || width < 0 || !d_len || !d_kdiag || !d_mass || !d_J || !d_b || !d_x ||
         (width > 0 && (!d_val || !d_col)) || !(rtol > 0.0) || maxit < 1 || !(c - c == 0.0))
         return reject(SDC_E_INVALID, "sdc_pcg_solve_noalloc: invalid arguments");
@@ -149,6 +157,11 @@ extern "C" sdc_status sdc_pcg_solve_noalloc(int n, const double* d_val, const in
         return reject(SDC_E_CUDA, "sdc_pcg_solve_noalloc: reading the status failed");
     if (iters) *iters = h[2];
     if (relres) *relres = hr;
+    {
+        // checked builds: an index outside its bound is reported before any CG status
+        const sdc_status chk = sdc::check_outcome(nullptr, s, SDC_OK);
+        if (chk != SDC_OK) return chk;
+    }
     if (h[1] != 0) {
         char buf[120];
         snprintf(buf, sizeof buf, "sdc_pcg_solve_noalloc: %s", sdc_status_string(h[1]));

@@ -87,6 +87,23 @@ int reassemble_device(AssemblyOut& out, const double* h_scale, double drop_rel, 
 void free_mesh_dev(MeshDev& m);
 
 // ---- step kernels (step.cu) ----
+// SDC_CHECKED=1 builds the checked library (index checks in every kernel gather).
+#ifndef SDC_CHECKED
+#define SDC_CHECKED 0
+#endif
+
+// Check words of the checked build (SDC_CHECKED=1), one reader per translation unit
+// that runs kernels: read and clear after the work on `stream`; the first failure
+// record is (check site << 32) | index, 0 when none (always 0 in normal builds).
+unsigned long long check_take_step(void* stream, unsigned* count);
+unsigned long long check_take_emi(void* stream, unsigned* count);
+unsigned long long check_take_adjoint(void* stream, unsigned* count);
+unsigned long long check_take_assembly(void* stream, unsigned* count);
+// The status of a call after its device work on `stream`: in checked builds an index
+// recorded outside its bound turns it into SDC_E_INVALID (message on ctx, or on the
+// calling thread when ctx is NULL); otherwise st unchanged.
+sdc_status check_outcome(sdc_ctx* ctx, void* stream, sdc_status st);
+
 struct StepBuffers {
     int N = 0, M = 0, ld = 0;
     double* V = nullptr;      // [N][M] node-interleaved collocation iterates of v
@@ -264,10 +281,11 @@ struct AdjointBuffers {
     double* relres = nullptr;
 };
 int adjoint_step(const AdjointArgs& a, StepBuffers& B, AdjointBuffers& W, cudaStream_t s);
-void launch_pos_set(int n, const int* act, int* pos, int reset, cudaStream_t s);
-void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, Ell& out,
+void launch_pos_set(int n, const int* act, int* pos, int reset, int N, cudaStream_t s);
+void launch_extract_global(int n, const int* act, const int* pos, const Ell& K, Ell& out, int N,
                            cudaStream_t s);
-void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, cudaStream_t s);
+void launch_replay_map(int n_old, const int* act_old, const int* pos, int* map, int N,
+                       cudaStream_t s);
 
 // Workspace of one standalone PCG solve (caller-provided device memory).
 // r, u, w, p, s, z, nv, idA: n doubles each; m: 2 n doubles;

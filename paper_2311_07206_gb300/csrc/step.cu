@@ -55,18 +55,18 @@ __global__ void k_nodes_out(int N, int M, const double* __restrict__ V, const do
 __global__ void k_perm_gather(int N, const int* __restrict__ perm, const double* __restrict__ src,
                               double* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) dst[i] = src[perm[i]];
+    if (i < N) dst[i] = src[sdc_idx(perm[i], N, 1)];
 }
 __global__ void k_perm_scatter(int N, const int* __restrict__ perm, const double* __restrict__ src,
                                double* __restrict__ dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) dst[perm[i]] = src[i];
+    if (i < N) dst[sdc_idx(perm[i], N, 2)] = src[i];
 }
 __global__ void k_nodes_out_perm(int N, int M, const int* __restrict__ perm,
                                  const double* __restrict__ X, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int o = perm[i];
+    const int o = sdc_idx(perm[i], N, 3);
     for (int m = 0; m < M; ++m) out[(size_t)m * N + o] = X[(size_t)i * M + m];
 }
 
@@ -79,11 +79,11 @@ __global__ void k_residual(int n, const int* __restrict__ act, const double* __r
                            const double* __restrict__ v0, double dt, Ionic ion, Coll co,
                            int reaction_implicit, int ld, double* __restrict__ R,
                            double* __restrict__ Jout, double* __restrict__ mc,
-                           double* __restrict__ kdc, const int* __restrict__ n_dev) {
+                           double* __restrict__ kdc, const int* __restrict__ n_dev, int N) {
     if (n_dev) n = *n_dev;   // device-driven sweeps: |I_k| from the device, grid for N
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int g = act ? act[p] : p;
+    const int g = act ? sdc_idx(act[p], N, 4) : p;
     const double kd = kdiag[g];
     double vm[M], kv[M];
 #pragma unroll
@@ -94,7 +94,7 @@ __global__ void k_residual(int n, const int* __restrict__ act, const double* __r
     const int len = klen[g];
     for (int t = 0; t < len; ++t) {
         const double a = kval[(size_t)t * ldk + g];
-        const int j = kcol[(size_t)t * ldk + g];
+        const int j = sdc_idx(kcol[(size_t)t * ldk + g], N, 5);
 #pragma unroll
         for (int m = 0; m < M; ++m) kv[m] += a * V[(size_t)j * M + m];
     }
@@ -199,7 +199,7 @@ struct EllChunk {
 
 template <int CH, class Val, class Gather>
 __device__ __forceinline__ double ell_row_dot(double acc, int len, size_t i, int ld,
-                                              const int* __restrict__ col, Val&& val,
+                                              const int* __restrict__ col, int ncol, Val&& val,
                                               Gather&& gather) {
     for (int k0 = 0; k0 < len; k0 += CH) {
         int j[CH];
@@ -208,7 +208,7 @@ __device__ __forceinline__ double ell_row_dot(double acc, int len, size_t i, int
         for (int k = 0; k < CH; ++k) {
             if (k0 + k < len) {
                 const size_t q = (size_t)(k0 + k) * ld + i;
-                j[k] = __ldg(col + q);
+                j[k] = sdc_idx(__ldg(col + q), ncol, 6);
                 a[k] = val(q);
             }
         }
@@ -377,7 +377,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         const int len = P.alen[i];
         double acc = 0.0;
         for (int k = 0; k < len; ++k)
-            acc += P.aval[(size_t)k * ld + i] * __ldcg(P.u + P.acol[(size_t)k * ld + i]);
+            acc += P.aval[(size_t)k * ld + i] * __ldcg(P.u + sdc_idx(P.acol[(size_t)k * ld + i], P.n, 11));
         const double ri = P.r[i], ui = P.u[i];
         const double wi = ri + c * acc;
         P.w[i] = wi;
@@ -402,7 +402,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
                 const int len = P.alen[i];
                 double acc = 0.0;
                 for (int k = 0; k < len; ++k)
-                    acc += P.aval[(size_t)k * ld + i] * __ldcg(mc + P.acol[(size_t)k * ld + i]);
+                    acc += P.aval[(size_t)k * ld + i] * __ldcg(mc + sdc_idx(P.acol[(size_t)k * ld + i], P.n, 12));
                 P.nv[i] = P.w[i] + c * acc;
             }
         }
@@ -456,7 +456,7 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + sdc_idx(P.acol[(size_t)k * ld + i], P.n, 13));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -510,7 +510,7 @@ __device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S,
         double acc = ri;
         for (int k = 0; k < len; ++k) {
             const size_t q = (size_t)k * ld + i;
-            const int j = P.acol[q];
+            const int j = sdc_idx(P.acol[q], P.n, 14);
             const double a = csi * P.aval[q] * __ldcg(sg + j);
             sval[q] = a;
             acc += a * __ldcg(P.u + j);
@@ -538,7 +538,7 @@ __device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S,
                 double acc = P.w[i];
                 for (int k = 0; k < len; ++k) {
                     const size_t q = (size_t)k * ld + i;
-                    acc += __ldcg(sval + q) * __ldcg(mc + P.acol[q]);
+                    acc += __ldcg(sval + q) * __ldcg(mc + sdc_idx(P.acol[q], P.n, 15));
                 }
                 P.nv[i] = acc;
             }
@@ -592,7 +592,7 @@ __device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S,
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + sdc_idx(P.acol[(size_t)k * ld + i], P.n, 16));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
         const int len = __ldg(alen + i);
         double acc = 0.0;
         for (int k = 0; k < len; ++k)
-            acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + __ldg(acol + (size_t)k * ld + i));
+            acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 41));
         const double ri = SR(l), ui = SU(l);
         const double wi = ri + c * acc;
         SW(l) = wi;
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
                 const int len = __ldg(alen + i);
                 double acc = 0.0;
                 for (int k = 0; k < len; ++k)
-                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(mc + __ldg(acol + (size_t)k * ld + i));
+                    acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(mc + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 42));
                 SN(l) = SW(l) + c * acc;
             }
         }
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_smem(CgParams P) {
             const double xi = __ldcg(xg + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 43));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
             for (int k = 0; k < EllChunk<MAXT>::value; ++k) {
                 if (k0 + k < len) {
                     const size_t q = (size_t)(k0 + k) * ld + i;
-                    j[k] = __ldg(acol + q);
+                    j[k] = sdc_idx(__ldg(acol + q), P.n, 44);
                     av[k] = __ldg(aval + q);
                 }
             }
@@ -917,7 +917,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
             for (int l = t - sp0; l < nl; l += B - sp0) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
-                SN(l) = ell_row_dot<EllChunk<MAXT>::value>(SW(l), len, (size_t)i, ld, acol,
+                SN(l) = ell_row_dot<EllChunk<MAXT>::value>(SW(l), len, (size_t)i, ld, acol, P.n,
                                     [&](size_t q) { return __ldcg(sval + q); },
                                     [&](int j) { return __ldcg(mc + j); });
             }
@@ -974,7 +974,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_scaled(CgParams P) {
             const int i = r0 + l;
             const int len = __ldg(alen + i);
             const double xi = __ldcg(xg + i);
-            const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+            const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol, P.n,
                                            [&](size_t q) { return __ldg(aval + q); },
                                            [&](int j) { return __ldcg(xg + j); });
             cg_couple_row(P, i, xi, acc);
@@ -1055,7 +1055,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
     for (int l = t; l < nl; l += B) {
         const int i = r0 + l;
         const int len = __ldg(alen + i);
-        const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+        const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol, P.n,
                                        [&](size_t q) { return __ldg(aval + q); },
                                        [&](int j) {
                                            const int owner = j / L;
@@ -1088,7 +1088,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
             for (int l = t - sp0; l < nl; l += B - sp0) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
-                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol, P.n,
                                                [&](size_t q) { return __ldg(aval + q); },
                                                [&](int j) {
                                                    const int owner = j / L;
@@ -1146,7 +1146,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcg_cluster(CgParams P) {
                 const int i = r0 + l;
                 const int len = __ldg(alen + i);
                 const double xi = __ldcg(xg + i);
-                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol,
+                const double acc = ell_row_dot<EllChunk<MAXT>::value>(0.0, len, (size_t)i, ld, acol, P.n,
                                                [&](size_t q) { return __ldg(aval + q); },
                                                [&](int j) { return __ldcg(xg + j); });
                 cg_couple_row(P, i, xi, acc);
@@ -1202,7 +1202,7 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
             const int len = P.alen[i];
             double acc = 0.0;
             for (int t = 0; t < len; ++t)
-                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.u + P.acol[(size_t)t * ld + i]);
+                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.u + sdc_idx(P.acol[(size_t)t * ld + i], P.n, 17));
             const double ri = P.r[i];
             const double ui = P.u[i];
             const double wi = ri + c * acc;
@@ -1257,7 +1257,7 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
             for (int t = 0; t < len; ++t)
-                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.x + P.acol[(size_t)t * ld + i]);
+                acc += P.aval[(size_t)t * ld + i] * __ldcg(P.x + sdc_idx(P.acol[(size_t)t * ld + i], P.n, 18));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -1306,7 +1306,7 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
         const double csi = c * __ldcg(sg + i);
         for (int k = 0; k < len; ++k) {
             const size_t q = (size_t)k * ld + i;
-            sval[q] = csi * P.aval[q] * __ldcg(sg + P.acol[q]);
+            sval[q] = csi * P.aval[q] * __ldcg(sg + sdc_idx(P.acol[q], P.n, 19));
         }
     }
     int it = 0, nsum = 0;
@@ -1319,7 +1319,7 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
             double acc = ri;
             for (int k = 0; k < len; ++k) {
                 const size_t q = (size_t)k * ld + i;
-                acc += sval[q] * __ldcg(P.r + P.acol[q]);
+                acc += sval[q] * __ldcg(P.r + sdc_idx(P.acol[q], P.n, 20));
             }
             P.w[i] = acc;
             ga += ri * ri;
@@ -1371,7 +1371,7 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
             const double xi = __ldcg(P.x + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + P.acol[(size_t)k * ld + i]);
+                acc += P.aval[(size_t)k * ld + i] * __ldcg(P.x + sdc_idx(P.acol[(size_t)k * ld + i], P.n, 21));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -1474,7 +1474,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_scaled(CgParams P) {
         const double csi = c * __ldcg(sg + i);
         for (int k = 0; k < len; ++k) {
             const size_t q = (size_t)k * ld + i;
-            sval[q] = csi * __ldg(aval + q) * __ldcg(sg + __ldg(acol + q));
+            sval[q] = csi * __ldg(aval + q) * __ldcg(sg + sdc_idx(__ldg(acol + q), P.n, 45));
         }
     }
     XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
@@ -1488,7 +1488,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_scaled(CgParams P) {
             double acc = ri;
             for (int k = 0; k < len; ++k) {
                 const size_t q = (size_t)k * ld + i;
-                acc += sval[q] * __ldcg(ug + __ldg(acol + q));
+                acc += sval[q] * __ldcg(ug + sdc_idx(__ldg(acol + q), P.n, 46));
             }
             sw[l] = acc;
             ga += ri * ri;
@@ -1546,7 +1546,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_scaled(CgParams P) {
             const double xi = __ldcg(xg + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 47));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -1605,7 +1605,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
             const int len = __ldg(alen + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + __ldg(acol + (size_t)k * ld + i));
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(ug + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 48));
             const double ri = sr[l], ui = su[l];
             const double wi = ri + c * acc;
             sw[l] = wi;
@@ -1661,7 +1661,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgc_smem(CgParams P) {
             const double xi = __ldcg(xg + i);
             double acc = 0.0;
             for (int k = 0; k < len; ++k)
-                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + __ldg(acol + (size_t)k * ld + i));
+                acc += __ldg(aval + (size_t)k * ld + i) * __ldcg(xg + sdc_idx(__ldg(acol + (size_t)k * ld + i), P.n, 49));
             cg_couple_row(P, i, xi, acc);
         }
     }
@@ -1674,7 +1674,7 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
                          double tol_drop, int w_frozen, int* __restrict__ flag,
                          int* __restrict__ blockcnt, double* __restrict__ blockmarg,
                          int* __restrict__ err, const double* __restrict__ tol_drop_dev,
-                         const int* __restrict__ n_dev) {
+                         const int* __restrict__ n_dev, int N) {
     __shared__ int wc[32];
     if (tol_drop_dev) tol_drop = *tol_drop_dev;
     if (n_dev) n = *n_dev;
@@ -1683,7 +1683,7 @@ __global__ void k_update(int n, const int* __restrict__ act, const double* __res
     int keep = 0;
     double margin = DBL_MAX;
     if (p < n) {
-        const int g = act ? act[p] : p;
+        const int g = act ? sdc_idx(act[p], N, 61) : p;
         double vm[M];
         double amax = 0.0;
 #pragma unroll
@@ -1831,7 +1831,7 @@ __global__ void k_extract(int n_old, const double* __restrict__ oval, const int*
         if (qrow >= 0) {
             const int len = olen[p];
             for (int t = 0; t < len; ++t) {
-                const int jn = map[ocol[(size_t)t * old_ld + p]];
+                const int jn = map[sdc_idx(ocol[(size_t)t * old_ld + p], n_old, 62)];
                 if (jn >= 0) {
                     nval[(size_t)cnt * new_ld + qrow] = oval[(size_t)t * old_ld + p];
                     ncol[(size_t)cnt * new_ld + qrow] = jn;
@@ -1904,7 +1904,7 @@ void launch_residual(int M, int n, const int* act, const Ell& K, const double* k
         k_residual<MM><<<nblk(n, 128), 128, 0, s>>>(n, act, K.val, K.col, K.len, K.ld, kdiag, mass,
                                                       stim, stim_on, V, W, v0, dt, ion, co,
                                                       reaction_implicit, B.ld, B.R, B.J, B.mc, B.kdc,
-                                                      n_dev);
+                                                      n_dev, B.N);
     });
 }
 
@@ -2479,7 +2479,7 @@ void launch_update(int M, int n, const int* act, const double* w0, double dt, co
         constexpr int MM = decltype(mc)::value;
         k_update<MM><<<nblk(n, kUpdateBlock), kUpdateBlock, 0, s>>>(
             n, act, B.D, B.ld, B.V, B.W, w0, dt, ion, co, tol_drop, w_frozen, B.flag, B.blockcnt,
-            B.blockmarg, &B.sc->err, tol_drop_dev, n_dev);
+            B.blockmarg, &B.sc->err, tol_drop_dev, n_dev, B.N);
     });
 }
 
@@ -2546,4 +2546,8 @@ void launch_extract(int n_old, const Ell& Aold, const int* map, Ell& Anew, StepB
                                                n_dev);
 }
 
+}  // namespace sdc
+
+namespace sdc {
+SDC_CHECK_READER(check_take_step)
 }  // namespace sdc

@@ -156,3 +156,13 @@ def test_autotune_rejects_bad_arguments_without_a_device(lib):
     rep = B.sdc_tune_report()
     assert L.sdc_autotune(None, None, None, 0.0, 0.1, 4, 1e-4, 3, C.byref(rep)) == B.SDC_E_INVALID
     assert L.sdc_batch_autotune(None, None, None, 0.0, 0.1, 4, 1e-4, 3, None) == B.SDC_E_INVALID
+
+
+def test_checked_build_exports_every_declared_symbol(lib):
+    """The checked build (SDC_CHECKED=1: index checks in every kernel gather) links
+    and exposes the same entry points as the library."""
+    import ctypes
+    from paper_2311_07206_gb300 import build as b
+    chk = ctypes.CDLL(b.build(checked=True))
+    for n in _declared():
+        assert hasattr(chk, n), n

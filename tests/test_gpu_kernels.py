@@ -88,6 +88,35 @@ def test_pcg_solve_matches_dense_solve(torch_dev, system):
     assert 0 < it < 1000 and rr <= 1e-13
 
 
+@pytest.mark.parametrize("n", [40, 300, 1000])
+def test_pcg_solve_small_systems_with_padded_ld(torch_dev, n):
+    """One to four blocks, and an ELL leading dimension above n (rounded up to 32,
+    and 64 more): the second buffer of the published m vector lies ld after the
+    first, so the workspace must hold 2 ld for it."""
+    torch, dev = torch_dev
+    from paper_2311_07206_gb300 import binding
+    K, mass, rp, ci, val = _laplacian_system(n, seed=n)
+    rng = np.random.default_rng(n)
+    J = rng.uniform(-0.5, 2.0, n)
+    c = 0.1
+    b = rng.standard_normal(n)
+    A = np.diag(mass * (1 + c * J)) + c * K
+    ref = np.linalg.solve(A, b)
+    kdiag, ev, ec, el, ld, width = binding.csr_to_ell(rp, ci, val, n)
+    for pad in (0, 64):
+        ld2 = ld + pad
+        ev2 = np.zeros((ev.shape[0], ld2))
+        ec2 = np.zeros((ec.shape[0], ld2), np.int32)
+        ev2[:, :ld], ec2[:, :ld] = ev, ec
+        t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device=dev)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        it, rr = binding.pcg_solve(n, t(ev2), t(ec2, torch.int32), t(el, torch.int32), ld2, width,
+                                   t(kdiag), t(mass), t(J), c, t(b), x, rtol=1e-13, maxit=2000,
+                                   stream=torch.cuda.current_stream(dev).cuda_stream)
+        assert np.abs(x.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+        assert 0 < it < 200 and rr <= 1e-13
+
+
 def test_pcg_solve_zero_rhs_and_errors(torch_dev):
     torch, dev = torch_dev
     from paper_2311_07206_gb300 import SdcError, binding

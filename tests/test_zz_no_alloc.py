@@ -76,3 +76,15 @@ def test_noalloc_rejects_oversized_system(torch_dev):
         binding.pcg_solve_noalloc(n, 0, 0, 0, n, 1, 0, 0, 0, 0.1, 0, 0)
     assert e.value.status == binding.SDC_E_INVALID
     assert "static workspace" in str(e.value)
+
+
+def test_noalloc_rejects_an_ld_beyond_the_workspace(torch_dev):
+    """The published m vector takes two buffers ld apart in the static array:
+    9 n + ld beyond its ten vectors is refused before any device work."""
+    from paper_2311_07206_gb300 import SdcError, binding
+    n = 1000
+    ld = 10 * binding.SDC_PCG_NOALLOC_MAX_ROWS
+    with pytest.raises(SdcError) as e:
+        binding.pcg_solve_noalloc(n, 0, 0, 0, ld, 1, 0, 0, 0, 0.1, 0, 0)
+    assert e.value.status == binding.SDC_E_INVALID
+    assert "too large" in str(e.value)
