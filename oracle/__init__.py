@@ -80,7 +80,10 @@ def lib():
                                        C.c_double, C.c_int, C.POINTER(_Opts), _ip, _ip, _ip]
         L.ora_step_emi.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_double, C.c_double, C.c_int,
                                    C.c_int, _ip, _ip, _dp, _ip, _dp, _dp, _dp, C.c_double, C.c_int,
-                                   C.c_double, C.POINTER(_Opts), C.POINTER(Stats), _ip]
+                                   C.c_double, C.POINTER(_Opts), C.POINTER(Stats), _ip, _ip]
+        L.ora_pcg_csr.argtypes = [C.c_int, _ip, _ip, _dp, C.c_int, _ip, _ip, _dp, _dp, C.c_double,
+                                  C.c_int, _ip]
+        L.ora_two_level_apply.argtypes = [C.c_int, _ip, _ip, _dp, C.c_int, _ip, _ip, _dp, _dp]
         L.ora_collocation_solve.argtypes = [C.c_void_p, C.POINTER(_Ionic), C.c_int, _dp, _dp, _dp,
                                             C.c_double, _dp, _dp, _ip]
         _lib = L
@@ -110,6 +113,34 @@ def collocation(M: int):
     if rc != OK:
         raise ValueError("ora_collocation(M=%d) failed: %d" % (M, rc))
     return tau, Q, Qh
+
+
+def pcg_csr(ptr, col, val, b, act=None, dom=None, rtol=1e-10, maxit=100000):
+    """PCG on an explicit CSR matrix restricted to `act` (all rows when None):
+    Jacobi, plus the two-level coarse part over the labels `dom` when given.
+    Returns (x, iterations, status)."""
+    ptr, col, val, b = _i32(ptr), _i32(col), _f64(val), _f64(b)
+    n = len(b)
+    act = _i32(np.arange(n) if act is None else act)
+    x = np.zeros(n)
+    it = C.c_int(0)
+    rc = lib().ora_pcg_csr(n, _i(ptr), _i(col), _d(val), len(act), _i(act), _i(_i32(dom)), _d(b),
+                           _d(x), rtol, maxit, C.byref(it))
+    return x, it.value, rc
+
+
+def two_level_apply(ptr, col, val, r, dom, act=None):
+    """z = D^-1 r + Z E^-1 Z' r of the two-level preconditioner (Sec. 6) on an explicit
+    CSR matrix restricted to `act`, Z the indicator vectors of the labels `dom`."""
+    ptr, col, val, r = _i32(ptr), _i32(col), _f64(val), _f64(r)
+    n = len(r)
+    act = _i32(np.arange(n) if act is None else act)
+    z = np.zeros(n)
+    rc = lib().ora_two_level_apply(n, _i(ptr), _i(col), _d(val), len(act), _i(act),
+                                   _i(_i32(dom)), _d(r), _d(z))
+    if rc != OK:
+        raise ValueError("ora_two_level_apply failed: %d" % rc)
+    return z
 
 
 def _ionic(p: dict) -> _Ionic:
@@ -262,11 +293,14 @@ class System:
         return dict(v=v, dv=dv, w=w, dw=dw, status=rc, iters=iters)
 
     def step_emi(self, wl, u, w, sweeps=None, tol=None, cg_rtol=None, w_frozen=False,
-                 want_log=False, energy_stop=False, rho=0.0, alpha=None, drop_rule=0):
+                 want_log=False, energy_stop=False, rho=0.0, alpha=None, drop_rule=0,
+                 coarse=False):
         """One SDC step of a cell-by-cell workload (K of this system = the
         subdomain stiffness; pairs, Robin and membrane data from `wl`).
         `energy_stop` ends the sweeps by the energy-norm test of Sec. 3.2
-        (`rho` given, or estimated from successive sweep energies when 0)."""
+        (`rho` given, or estimated from successive sweep energies when 0).
+        `coarse` solves the node systems with the two-level preconditioner over
+        the workload's subdomain labels (Sec. 6) instead of Jacobi alone."""
         n = self.n
         sweeps = wl.sweeps if sweeps is None else sweeps
         tol = wl.tol if tol is None else tol
@@ -281,7 +315,8 @@ class System:
         pk, pl, pa, pkd = _i32(wl.pair_k), _i32(wl.pair_l), _f64(wl.pair_area), _i32(wl.pair_kind)
         rc = lib().ora_step_emi(self._h, C.byref(_ionic(wl.ionic)), wl.Cm, wl.g_gap, wl.M,
                                 wl.n_pairs, _i(pk), _i(pl), _d(pa), _i(pkd), _d(rob), _d(u),
-                                _d(w), wl.dt, sweeps, tol, C.byref(opts), C.byref(st), _i(log))
+                                _d(w), wl.dt, sweeps, tol, C.byref(opts), C.byref(st), _i(log),
+                                _i(_i32(wl.labels)) if coarse else None)
         out = dict(u=u, w=w, status=rc, stats=st)
         if want_log:
             lists, pos = [], 0

@@ -16,6 +16,8 @@
 //     nested algebraic active sets I_{k+1} = {i in I_k : |dv_i| >= TOL_drop}
 //                                                  [Sec. 3.2, eq. final-sdc; Sec. 4.2]
 //   * Jacobi-preconditioned CG on the restricted systems            [Sec. 4.2]
+//   * for cell-by-cell systems, optionally the additive two-level
+//     preconditioner over the subdomains (block preconditioning)     [Sec. 6]
 //   * a dense Newton solve of the full collocation system (tiny meshes),
 //     the fixed point the SDC sweeps converge to                     [Sec. 3.1]
 //
@@ -363,19 +365,96 @@ int pcg(const Csr& K, double c, const std::vector<double>& dA, const std::vector
     return ORA_CG_NOCONV;
 }
 
-// Jacobi PCG with the operator given as a function y = A x on the active rows
-// (x is zero off the active set), same iteration and stopping rule as pcg().
+// Additive two-level preconditioner for the cell-by-cell node systems (the block
+// preconditioning Sec. 6 proposes for EMI systems): blocks are the subdomains (each
+// cell, the extracellular space), and the blocks selected are those holding active
+// dofs.  With Z the n x q matrix of their indicator vectors restricted to the active
+// set and E = Z' A Z (q x q, symmetric positive definite),
+//     z = D^-1 r + Z E^-1 Z' r.
+// The Jacobi part is the one-level preconditioner of pcg(); the coarse part removes
+// the near-constant modes of the floating subdomains.
+struct TwoLevel {
+    int q = 0;                  // selected subdomains (coarse vectors)
+    std::vector<int> cls;       // per dof: coarse index, -1 outside the coarse space
+    std::vector<double> L;      // Cholesky factor of E, q x q row-major, lower
+
+    // dom[i]: subdomain label of dof i (labels >= 0; -1: in no block).  Returns
+    // false when E is not positive definite.
+    template <class Op>
+    bool build(int n, const int* dom, const std::vector<int>& act, Op apply) {
+        std::vector<int> labels;
+        for (int i : act)
+            if (dom[i] >= 0) labels.push_back(dom[i]);
+        std::sort(labels.begin(), labels.end());
+        labels.erase(std::unique(labels.begin(), labels.end()), labels.end());
+        q = (int)labels.size();
+        cls.assign(n, -1);
+        for (int i : act)
+            if (dom[i] >= 0)
+                cls[i] = (int)(std::lower_bound(labels.begin(), labels.end(), dom[i]) -
+                               labels.begin());
+        // E = Z' A Z, one column per application of A to an indicator vector
+        std::vector<double> E((size_t)q * q, 0.0), zb(n, 0.0), y(n, 0.0);
+        for (int b = 0; b < q; ++b) {
+            for (int i : act) zb[i] = cls[i] == b ? 1.0 : 0.0;
+            apply(zb, y);
+            for (int i : act)
+                if (cls[i] >= 0) E[(size_t)cls[i] * q + b] += y[i];
+        }
+        // Cholesky E = L L'
+        L.assign((size_t)q * q, 0.0);
+        for (int a = 0; a < q; ++a) {
+            for (int b = 0; b <= a; ++b) {
+                double s = E[(size_t)a * q + b];
+                for (int k = 0; k < b; ++k) s -= L[(size_t)a * q + k] * L[(size_t)b * q + k];
+                if (a == b) {
+                    if (!(s > 0.0)) return false;
+                    L[(size_t)a * q + a] = std::sqrt(s);
+                } else {
+                    L[(size_t)a * q + b] = s / L[(size_t)b * q + b];
+                }
+            }
+        }
+        return true;
+    }
+
+    // z += Z E^-1 Z' r on the active rows
+    void add(const std::vector<int>& act, const std::vector<double>& r,
+             std::vector<double>& z) const {
+        if (q == 0) return;
+        std::vector<double> t(q, 0.0), y(q, 0.0);
+        for (int i : act)
+            if (cls[i] >= 0) t[cls[i]] += r[i];
+        for (int a = 0; a < q; ++a) {           // L y' = t
+            double s = t[a];
+            for (int k = 0; k < a; ++k) s -= L[(size_t)a * q + k] * y[k];
+            y[a] = s / L[(size_t)a * q + a];
+        }
+        for (int a = q - 1; a >= 0; --a) {      // L' y = y'
+            double s = y[a];
+            for (int k = a + 1; k < q; ++k) s -= L[(size_t)k * q + a] * y[k];
+            y[a] = s / L[(size_t)a * q + a];
+        }
+        for (int i : act)
+            if (cls[i] >= 0) z[i] += y[cls[i]];
+    }
+};
+
+// PCG with the operator given as a function y = A x on the active rows (x is zero
+// off the active set), same iteration and stopping rule as pcg(): Jacobi
+// preconditioner, and the coarse part of a two-level one when tl is given.
 template <class Op>
 int pcg_op(int n, Op apply, const std::vector<double>& diag, const std::vector<int>& act,
            const std::vector<double>& b, std::vector<double>& x, double rtol, int maxit,
-           int& iters, double& relres) {
+           int& iters, double& relres, const TwoLevel* tl = nullptr) {
     std::vector<double> r(n, 0.0), z(n, 0.0), p(n, 0.0), q(n, 0.0);
     for (int i : act) {
         x[i] = 0.0;
         r[i] = b[i];
         z[i] = r[i] / diag[i];
-        p[i] = z[i];
     }
+    if (tl) tl->add(act, r, z);
+    for (int i : act) p[i] = z[i];
     double rho = 0.0;
     for (int i : act) rho += r[i] * z[i];
     const double rho0 = rho;
@@ -393,6 +472,7 @@ int pcg_op(int n, Op apply, const std::vector<double>& diag, const std::vector<i
             r[i] -= alpha * q[i];
             z[i] = r[i] / diag[i];
         }
+        if (tl) tl->add(act, r, z);
         double rho_new = 0.0;
         for (int i : act) rho_new += r[i] * z[i];
         iters = it;
@@ -729,10 +809,75 @@ int ora_step_forced(void* h, const ora_ionic* ip, int M, const double* istim, do
 // pair Jacobian sum_p area_p dI_p/dv (e_k - e_l)(e_k - e_l)^T in place of the
 // lumped ionic Jacobian; the gating sweep runs over the pairs with an active
 // endpoint; selection uses |du| of every potential dof.
+// PCG on an explicit CSR matrix A (rows ptr/col/val, n x n, symmetric positive
+// definite on the active rows act[0..n_act)): Jacobi, plus the two-level coarse part
+// over the subdomain labels dom when dom is given.  x: n entries (zero off the
+// active set on return).
+int ora_pcg_csr(int n, const int* ptr, const int* col, const double* val, int n_act,
+                const int* act_list, const int* dom, const double* b_in, double* x_out,
+                double rtol, int maxit, int* iters_out) {
+    std::vector<int> act(act_list, act_list + n_act);
+    std::vector<char> on(n, 0);
+    for (int i : act) on[i] = 1;
+    std::vector<double> diag(n, 0.0), b(n, 0.0), x(n, 0.0);
+    for (int i : act) {
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] == i) diag[i] += val[k];
+        b[i] = b_in[i];
+        if (!(diag[i] > 0.0)) return ORA_DOMAIN;
+    }
+    auto apply = [&](const std::vector<double>& v, std::vector<double>& y) {
+        for (int i : act) {
+            double s = 0.0;
+            for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+                if (on[col[k]]) s += val[k] * v[col[k]];
+            y[i] = s;
+        }
+    };
+    TwoLevel tl;
+    if (dom && !tl.build(n, dom, act, apply)) return ORA_DOMAIN;
+    int iters = 0;
+    double relres = 0.0;
+    const int rc = pcg_op(n, apply, diag, act, b, x, rtol, maxit, iters, relres,
+                          dom ? &tl : nullptr);
+    for (int i = 0; i < n; ++i) x_out[i] = x[i];
+    if (iters_out) *iters_out = iters;
+    return rc;
+}
+
+// z = D^-1 r + Z E^-1 Z' r of the two-level preconditioner on an explicit CSR matrix
+// restricted to act[0..n_act) (z: n entries).
+int ora_two_level_apply(int n, const int* ptr, const int* col, const double* val, int n_act,
+                        const int* act_list, const int* dom, const double* r_in, double* z_out) {
+    std::vector<int> act(act_list, act_list + n_act);
+    std::vector<char> on(n, 0);
+    for (int i : act) on[i] = 1;
+    auto apply = [&](const std::vector<double>& v, std::vector<double>& y) {
+        for (int i : act) {
+            double s = 0.0;
+            for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+                if (on[col[k]]) s += val[k] * v[col[k]];
+            y[i] = s;
+        }
+    };
+    TwoLevel tl;
+    if (!tl.build(n, dom, act, apply)) return ORA_DOMAIN;
+    std::vector<double> r(r_in, r_in + n), z(n, 0.0);
+    for (int i : act) {
+        double d = 0.0;
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] == i) d += val[k];
+        z[i] = r[i] / d;
+    }
+    tl.add(act, r, z);
+    for (int i = 0; i < n; ++i) z_out[i] = z[i];
+    return ORA_OK;
+}
+
 int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, int n_pairs,
                  const int* pk, const int* pl, const double* parea, const int* pkind,
                  const double* robin, double* u, double* w, double dt, int sweeps, double tol,
-                 const ora_opts* o, ora_stats* st, int* active_log) {
+                 const ora_opts* o, ora_stats* st, int* active_log, const int* dom) {
     System& S = *(System*)h;
     const Csr& K = S.K;
     const int N = K.n, NP = n_pairs;
@@ -849,7 +994,11 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
             std::vector<double> x(N, 0.0);
             int iters = 0;
             double relres = 0.0;
-            const int rc = pcg_op(N, apply, diag, act, b, x, o->cg_rtol, o->cg_maxit, iters, relres);
+            // dom given: the two-level preconditioner over the subdomains of the active set
+            TwoLevel tl;
+            if (dom && !tl.build(N, dom, act, apply)) return ORA_DOMAIN;
+            const int rc = pcg_op(N, apply, diag, act, b, x, o->cg_rtol, o->cg_maxit, iters, relres,
+                                  dom ? &tl : nullptr);
             if (st) {
                 st->cg_iters[k * ORA_MAX_M + m] = iters;
                 st->cg_relres_max = std::max(st->cg_relres_max, relres);
