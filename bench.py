@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--emi-w-frozen", action="store_true", help="w2: hold the gating at w = 0")
     ap.add_argument("--emi-cells", default="8,4,4",
                     help="w2: brick cells along x,y,z (default 8,4,4 = 1,471,260 dofs)")
+    ap.add_argument("--emi-coarse", default="16,4,4",
+                    help="w2: two-level preconditioner of the node solves over blocks = the "
+                         "cells and the extracellular space cut into this many boxes "
+                         "(x,y,z); 'off' for Jacobi alone")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=None,
                     help="pick the node solves' launch shape with sdc_autotune before timing "
                          "(default: on for the batch w3, off otherwise)")
@@ -733,6 +737,11 @@ def run_emi(args):
     opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, w_frozen=int(frozen),
                            cg_maxit=100000)
     ctx = Context.from_emi(wl, options=opts, stream=stream.cuda_stream)
+    blocks = None
+    if args.emi_coarse != "off":
+        from workloads.emi import coarse_blocks
+        blocks = coarse_blocks(wl, split=tuple(int(x) for x in args.emi_coarse.split(",")))
+        ctx.set_coarse_blocks(blocks)
     u0 = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
     tune = None
@@ -848,6 +857,9 @@ def run_emi(args):
            "dt_ms": wl.dt, "sweeps": wl.sweeps, "TOL": wl.tol, "alpha": wl.alpha,
            "cg_rtol": wl.cg_rtol,
            "gating": "held at w = 0" if frozen else "Aliev-Panfilov on cell-bath pairs", "simulated_ms": round(K * wl.dt, 6),
+           "preconditioner": ("two-level: Jacobi + %d blocks (cells, extracellular space in "
+                              "%s boxes)" % (int(blocks.max()) + 1, args.emi_coarse)
+                              if blocks is not None else "Jacobi"),
            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
            "autotune": tune}
     line = {"metric": "SDC steps/s & active-dof sweeps/s (cell-by-cell bricks), adaptive "

@@ -439,6 +439,28 @@ typedef struct {
 sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* emi,
                           const sdc_ionic* ionic, int M, const sdc_options* opt, void* stream);
 
+/* Two-level preconditioner of the node solves of a cell-by-cell context.  Sec. 6
+ * proposes block preconditioners with a selection of the blocks for EMI systems,
+ * whose Jacobi-preconditioned solves run for hundreds to thousands of iterations:
+ * their slow modes are nearly constant on each floating cell and vary slowly over
+ * the extracellular space.  Given blocks (every dof in one block: each cell, and
+ * pieces of the extracellular space), each node system A (Sec. 3.2, restricted to
+ * the active set I_k) is solved by CG preconditioned with
+ *     z = D^-1 r + Z E^-1 Z' r,    E = Z' A Z,
+ * Z the indicator vectors of the blocks that hold active dofs (the block selection);
+ * D^-1 alone is the default Jacobi preconditioner.  E is formed per node solve in
+ * exact 64-bit fixed point (terms rounded at 2^-41 of the largest diagonal entry) and
+ * inverted by Gauss-Jordan elimination on the device; results stay bitwise
+ * reproducible.
+ *   block_of_dof  host, n_nodes labels in [0, n_blocks) (copied)
+ *   n_blocks      1 .. SDC_MAX_COARSE_BLOCKS; block_of_dof NULL or n_blocks 0
+ *                 switches the two-level preconditioner off
+ * Cell-by-cell contexts only (else SDC_E_INVALID); SDC_E_NOMEM when device memory
+ * is short.  Each node solve then costs one more grid barrier per CG iteration, and
+ * a factorisation of E (one grid barrier per block) per solve. */
+#define SDC_MAX_COARSE_BLOCKS 1024
+sdc_status sdc_set_coarse_blocks(sdc_ctx* ctx, const int* block_of_dof, int n_blocks);
+
 /* Largest n accepted by sdc_pcg_solve_noalloc. */
 #define SDC_PCG_NOALLOC_MAX_ROWS 65536
 

@@ -299,8 +299,9 @@ class System:
         subdomain stiffness; pairs, Robin and membrane data from `wl`).
         `energy_stop` ends the sweeps by the energy-norm test of Sec. 3.2
         (`rho` given, or estimated from successive sweep energies when 0).
-        `coarse` solves the node systems with the two-level preconditioner over
-        the workload's subdomain labels (Sec. 6) instead of Jacobi alone."""
+        `coarse` solves the node systems with the two-level preconditioner (Sec. 6)
+        instead of Jacobi alone, over the workload's subdomain labels (True) or the
+        block labels given as an array."""
         n = self.n
         sweeps = wl.sweeps if sweeps is None else sweeps
         tol = wl.tol if tol is None else tol
@@ -312,11 +313,14 @@ class System:
                      int(energy_stop), rho, 0, int(drop_rule))
         log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
         rob = _f64(wl.robin)
+        dom = None
+        if coarse is not None and coarse is not False:
+            dom = _i32(wl.labels if coarse is True else coarse)
         pk, pl, pa, pkd = _i32(wl.pair_k), _i32(wl.pair_l), _f64(wl.pair_area), _i32(wl.pair_kind)
         rc = lib().ora_step_emi(self._h, C.byref(_ionic(wl.ionic)), wl.Cm, wl.g_gap, wl.M,
                                 wl.n_pairs, _i(pk), _i(pl), _d(pa), _i(pkd), _d(rob), _d(u),
                                 _d(w), wl.dt, sweeps, tol, C.byref(opts), C.byref(st), _i(log),
-                                _i(_i32(wl.labels)) if coarse else None)
+                                _i(dom))
         out = dict(u=u, w=w, status=rc, stats=st)
         if want_log:
             lists, pos = [], 0

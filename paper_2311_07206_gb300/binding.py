@@ -21,6 +21,7 @@ SDC_MAX_M = 8
 SDC_MAX_SWEEPS = 64
 SDC_N_PHASES = 5
 SDC_PCG_NOALLOC_MAX_ROWS = 65536
+SDC_MAX_COARSE_BLOCKS = 1024
 PHASES = ("residual", "pcg", "update", "select", "extract")
 SDC_OK, SDC_E_INVALID, SDC_E_CUDA, SDC_E_NOMEM = 0, -1, -2, -3
 SDC_E_CG_NOCONV, SDC_E_TIMEOUT, SDC_E_NONFINITE, SDC_E_DOMAIN = -4, -5, -6, -7
@@ -135,6 +136,7 @@ SIGNATURES = {
                                    _vp, _vp, _dp]),
     "sdc_set_dof_scale": (C.c_int, [_vp, _dp]),
     "sdc_set_ionic": (C.c_int, [_vp, C.POINTER(sdc_ionic)]),
+    "sdc_set_coarse_blocks": (C.c_int, [_vp, _ip, C.c_int]),
     "sdc_last_error": (C.c_char_p, [_vp]),
     "sdc_status_string": (C.c_char_p, [C.c_int]),
     "sdc_destroy": (None, [_vp]),
@@ -345,6 +347,16 @@ class Context:
         _check(load().sdc_set_dof_scale(self._h, None if sc is None else sc.ctypes.data_as(_dp)),
                self._h)
         self.dof_scale = sc
+
+    def set_coarse_blocks(self, labels, n_blocks=None):
+        """Two-level preconditioner of the cell-by-cell node solves over the given
+        block of each dof (None: back to Jacobi)."""
+        if labels is None:
+            _check(load().sdc_set_coarse_blocks(self._h, None, 0), self._h)
+            return
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        nb = int(lab.max()) + 1 if n_blocks is None else int(n_blocks)
+        _check(load().sdc_set_coarse_blocks(self._h, lab.ctypes.data_as(_ip), nb), self._h)
 
     def set_ionic(self, ionic):
         _check(load().sdc_set_ionic(self._h, C.byref(ionic_struct(ionic))), self._h)

@@ -23,7 +23,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libsdc_gb300.so")
 CHECKED_LIB = os.path.join(HERE, "libsdc_gb300_checked.so")
-SOURCES = ["api.cu", "assembly.cu", "step.cu", "adjoint.cu", "emi.cu", "noalloc.cu", "radau.cpp"]
+SOURCES = ["api.cu", "assembly.cu", "step.cu", "adjoint.cu", "emi.cu", "coarse.cu", "noalloc.cu",
+           "radau.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr"]

@@ -41,6 +41,7 @@ struct sdc_ctx {
     AdjointBuffers AW;            // adjoint workspace, allocated on first use
     bool is_emi = false;          // cell-by-cell model (sdc_create_emi)
     EmiDev emi;
+    CoarseDev coarse;             // blocks of the two-level preconditioner (q = 0: off)
     // internal dof numbering (reorder option): perm[new] = old, inv[old] = new
     std::vector<int> h_perm, h_inv;
     int* d_perm = nullptr;
@@ -92,11 +93,12 @@ sdc_status fail(sdc_ctx* c, sdc_status st, const char* fmt, ...) {
 namespace sdc {
 sdc_status check_outcome(sdc_ctx* c, void* stream, sdc_status st) {
 #if SDC_CHECKED
-    unsigned long long (*const take[4])(void*, unsigned*) = {check_take_step, check_take_emi,
+    unsigned long long (*const take[5])(void*, unsigned*) = {check_take_step, check_take_emi,
                                                              check_take_adjoint,
-                                                             check_take_assembly};
-    const char* const name[4] = {"step", "cell-by-cell", "adjoint", "assembly"};
-    for (int k = 0; k < 4; ++k) {
+                                                             check_take_assembly,
+                                                             check_take_coarse};
+    const char* const name[5] = {"step", "cell-by-cell", "adjoint", "assembly", "coarse"};
+    for (int k = 0; k < 5; ++k) {
         unsigned cnt = 0;
         const unsigned long long f = take[k](stream, &cnt);
         if (f || cnt)
@@ -240,6 +242,7 @@ void free_all(sdc_ctx* c) {
     free_mesh_dev(c->K.mesh);
     free_adjoint(c->AW);
     emi_free(c->emi);
+    coarse_free(c->coarse);
     cudaFree(c->d_perm);
     cudaFree(c->vp);
     cudaFree(c->wp);
@@ -883,7 +886,8 @@ sdc_status step_core(sdc_ctx* c, double* d_v, double* d_w, double t, double dt, 
         if (tape) return fail(c, SDC_E_INVALID, "tapes are not available for EMI contexts");
         int done = sweeps;
         EmiStepArgs ea{N, M, s, &c->K, &B, &c->emi, &c->act, &c->n_act, &c->pcg, &c->opt, &c->co,
-                       &c->ion, c->h_pin, &c->err, &c->events, &done};
+                       &c->ion, c->h_pin, &c->err, &c->events, &done,
+                       c->coarse.q > 0 ? &c->coarse : nullptr};
         const int st = emi_step(ea, d_v, d_w, dt, sweeps, TOL, stats);
         c->last_sweeps = done;
         c->stepped = true;
@@ -1610,6 +1614,21 @@ sdc_status sdc_set_dof_scale(sdc_ctx* c, const double* h_scale) {
     const int rc = reassemble_device(c->K, h_scale, c->opt.drop_rel, c->stream, why);
     if (rc != SDC_OK) return fail(c, (sdc_status)rc, "%s", why.c_str());
     return check_outcome(c, c->stream, SDC_OK);
+}
+
+sdc_status sdc_set_coarse_blocks(sdc_ctx* c, const int* block_of_dof, int n_blocks) {
+    if (!c) return SDC_E_INVALID;
+    if (!c->is_emi)
+        return fail(c, SDC_E_INVALID, "sdc_set_coarse_blocks: cell-by-cell contexts only");
+    if (!block_of_dof || n_blocks == 0) {
+        coarse_free(c->coarse);
+        return SDC_OK;
+    }
+    std::string why;
+    const int rc = coarse_setup(c->coarse, block_of_dof, c->N, n_blocks, c->B.ld, &c->B.sc->err,
+                                c->stream, why);
+    if (rc != SDC_OK) return fail(c, (sdc_status)rc, "%s", why.c_str());
+    return SDC_OK;
 }
 
 sdc_status sdc_set_ionic(sdc_ctx* c, const sdc_ionic* ionic) {

@@ -99,6 +99,7 @@ unsigned long long check_take_step(void* stream, unsigned* count);
 unsigned long long check_take_emi(void* stream, unsigned* count);
 unsigned long long check_take_adjoint(void* stream, unsigned* count);
 unsigned long long check_take_assembly(void* stream, unsigned* count);
+unsigned long long check_take_coarse(void* stream, unsigned* count);
 // The status of a call after its device work on `stream`: in checked builds an index
 // recorded outside its bound turns it into SDC_E_INVALID (message on ctx, or on the
 // calling thread when ctx is NULL); otherwise st unchanged.
@@ -226,6 +227,50 @@ struct PcgRole {
 };
 int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,
                     int maxit, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
+
+// ---- two-level preconditioner of the cell-by-cell node solves (Sec. 6) ----------
+// Blocks (labels per dof, every dof in one block) give the coarse space Z of the
+// additive two-level preconditioner z = D^-1 r + Z E^-1 Z' r, E = Z' A Z, over the
+// blocks that hold active dofs.
+constexpr int kMaxCoarseBlocks = SDC_MAX_COARSE_BLOCKS;
+struct CoarseDev {
+    int q = 0;                           // blocks
+    int N = 0;
+    int* lab = nullptr;                  // [N] block of each dof
+    int* gperm = nullptr;                // [N] dofs sorted by (block, dof)
+    int* lab_c = nullptr;                // [ld] block of each compact row of the sweep
+    int* crow = nullptr;                 // [ld] compact rows sorted by (block, row)
+    int* boff = nullptr;                 // [q + 1] first position of each block in crow
+    int* chunk_cnt = nullptr;            // compaction scratch: per-chunk counts and offsets
+    int* chunk_off = nullptr;
+    int* cta_ptr = nullptr;              // [G + 1] blocks of each CTA of the CG launch ...
+    int* cta_lab = nullptr;              // [q]     ... in cta_lab[cta_ptr[b] .. cta_ptr[b+1])
+    unsigned long long* Eacc = nullptr;  // [q * q] E in 64-bit fixed point
+    double* Einv = nullptr;              // [q * q] E^-1, row-major
+    double* piv = nullptr;               // [2 q] pivot rows of the inversion
+    double* tvec = nullptr;              // [q] coarse residual of the current iteration
+    unsigned long long* dmax = nullptr;  // largest diagonal of the node operator (bits)
+    unsigned* bar = nullptr;             // grid barrier counter of the inversion
+    int* err = nullptr;                  // shared with the step's error word
+    std::vector<int> h_boff, h_cta_ptr, h_cta_lab;
+    int G = 0;                           // CTAs of the coarse CG launch
+};
+// labels: host, N entries in [0, q).  Allocates and uploads; returns an sdc_status.
+int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err, cudaStream_t s,
+                 std::string& why);
+void coarse_free(CoarseDev& C);
+// Per sweep: block of each compact row, rows sorted by block, block ranges and the
+// assignment of blocks to the CTAs of the CG launch (balanced by rows).  pos: dof ->
+// compact row (-1 outside the active set).  Synchronises the stream (reads the block
+// ranges).
+int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, int G, cudaStream_t s);
+// Per node solve: E = Z' A Z of the operator diag(mc (1 + c J) + c kdc) + c A_off on the
+// active rows (exact fixed-point accumulation) and its inverse.
+int coarse_factor(CoarseDev& C, int n, const Ell& A, const double* mc, const double* J,
+                  const double* kdc, double c, long long budget, cudaStream_t s);
+// The node solve with the two-level preconditioner (classical scaled arrangement).
+int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int maxit,
+                      const CoarseDev& C, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s);
 
 // Batched PCG: independent solves of the instances whose compact rows are
 // [bounds[s], bounds[s+1]); empty instances are skipped.
@@ -359,6 +404,7 @@ struct EmiStepArgs {
     std::string* err;
     std::vector<cudaEvent_t>* events;   // profiling event pool (profile option)
     int* sweeps_done;           // out: sweeps run (fewer after an energy-norm stop)
+    CoarseDev* coarse;          // two-level preconditioner blocks, or null (Jacobi)
 };
 int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int sweeps, double TOL,
              sdc_stats* stats);

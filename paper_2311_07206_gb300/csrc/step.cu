@@ -1386,6 +1386,186 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
 }
 
 // Batched form of the scaled classical arrangement (one group of blocks per instance).
+// ---- two-level preconditioner (cell-by-cell node solves, Sec. 6) ------------------
+// The classical scaled arrangement of pcgc_group_scaled with the preconditioned
+// residual u = r + Y E^-1 Y' r in place of u = r: in the scaled variables x = S x~
+// the block indicators Z become Y = S^-1 Z (Y_i = sqrt(d_i) on the rows of its block)
+// and D^-1 becomes the identity.  Every row of block a is handled by the CTA that owns
+// a (cta_lab), so a CTA forms the coarse residual t_a = sum_{i in a} Y_i r_i of its
+// blocks by exact sums in a fixed order, publishes it, and after one grid barrier
+// computes y_a = (E^-1 t)_a for its own blocks and u on their rows.  Per iteration:
+// the product and the two dot products (one grid sum), the update, the coarse
+// residual (one grid barrier), u (one grid barrier that also publishes it).
+struct CoarseParams {
+    int q;
+    const int* lab_c;
+    const int* crow;
+    const int* boff;
+    const int* cta_ptr;
+    const int* cta_lab;
+    const double* Einv;
+    double* tvec;
+};
+
+// exact block sums of (a, b) returned in every thread (tot: 2 doubles of shared memory)
+__device__ __forceinline__ void xs_block_total2(double a, double b, XsScratch& X, double* tot,
+                                                double& ta, double& tb) {
+    int fa, fb;
+    __int128 qa, qb;
+    xs_block_sum2(a, b, X, fa, fb, qa, qb);
+    if (threadIdx.x == 0) {
+        tot[0] = xs_to_double(qa, fa);
+        tot[1] = xs_to_double(qb, fb);
+    }
+    __syncthreads();
+    ta = tot[0];
+    tb = tot[1];
+    __syncthreads();
+}
+
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarseParams C) {
+    __shared__ CgShared S;
+    __shared__ double tot[2];
+    __shared__ double ysh[kMaxCoarseBlocks];
+    const int t = threadIdx.x, B = blockDim.x, G = gridDim.x, bidx = blockIdx.x;
+    const bool lead = bidx == 0 && t == 0;
+    const int ld = P.ld, n = P.n;
+    const double c = P.c;
+    double* __restrict__ sg = P.sv;     // diag^-1/2
+    double* __restrict__ yv = P.idA;    // diag^1/2: the block indicators in scaled variables
+    double* __restrict__ sval = P.sval;
+    XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
+    const int e0 = C.cta_ptr[bidx], e1 = C.cta_ptr[bidx + 1];
+    unsigned epoch = 0;
+    int buf = 0;
+    // f(e, i) over the rows of this CTA: block cta_lab[e], compact row i
+    auto for_rows = [&](auto&& f) {
+        for (int e = e0; e < e1; ++e) {
+            const int a = C.cta_lab[e];
+            const int k1 = C.boff[a + 1];
+            for (int k = C.boff[a] + t; k < k1; k += B) f(e, sdc_idx(C.crow[k], n, 70));
+        }
+    };
+    for_rows([&](int, int i) {
+        const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
+        double si = 0.0;
+        if (!isfinite(d)) raise_error(P.err, SDC_E_NONFINITE);
+        else if (!(d > 0.0)) raise_error(P.err, SDC_E_DOMAIN);
+        else si = rsqrt(d);
+        sg[i] = si;
+        yv[i] = d * si;
+        P.r[i] = si * P.b[i];
+        P.p[i] = 0.0;
+        P.s[i] = 0.0;
+        P.x[i] = 0.0;
+    });
+    if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return;
+    for_rows([&](int, int i) {
+        const int len = P.alen[i];
+        const double csi = c * sg[i];
+        for (int k = 0; k < len; ++k) {
+            const size_t q = (size_t)k * ld + i;
+            sval[q] = csi * P.aval[q] * __ldcg(sg + sdc_idx(P.acol[q], n, 71));
+        }
+    });
+    // u = r + Y E^-1 Y' r on this CTA's rows, published by the closing grid barrier
+    auto precondition = [&]() -> bool {
+        for (int e = e0; e < e1; e += 2) {
+            const int a = C.cta_lab[e], a2 = e + 1 < e1 ? C.cta_lab[e + 1] : -1;
+            double pa = 0.0, pb = 0.0;
+            for (int k = C.boff[a] + t; k < C.boff[a + 1]; k += B) {
+                const int i = C.crow[k];
+                pa += yv[i] * P.r[i];
+            }
+            if (a2 >= 0)
+                for (int k = C.boff[a2] + t; k < C.boff[a2 + 1]; k += B) {
+                    const int i = C.crow[k];
+                    pb += yv[i] * P.r[i];
+                }
+            double ta, tb;
+            xs_block_total2(pa, pb, S.xs, tot, ta, tb);
+            if (t == 0) {
+                C.tvec[a] = ta;
+                if (a2 >= 0) C.tvec[a2] = tb;
+            }
+        }
+        if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return false;
+        for (int e = e0; e < e1; e += 2) {
+            const int a = C.cta_lab[e], a2 = e + 1 < e1 ? C.cta_lab[e + 1] : -1;
+            double pa = 0.0, pb = 0.0;
+            for (int j = t; j < C.q; j += B) {
+                const double tj = __ldcg(C.tvec + j);
+                pa += __ldg(C.Einv + (size_t)a * C.q + j) * tj;
+                if (a2 >= 0) pb += __ldg(C.Einv + (size_t)a2 * C.q + j) * tj;
+            }
+            double ya, yb;
+            xs_block_total2(pa, pb, S.xs, tot, ya, yb);
+            if (t == 0) {
+                ysh[e - e0] = ya;
+                if (a2 >= 0) ysh[e + 1 - e0] = yb;
+            }
+        }
+        __syncthreads();
+        for_rows([&](int e, int i) { P.u[i] = P.r[i] + yv[i] * ysh[e - e0]; });
+        return group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok);
+    };
+    if (!precondition()) return;
+    int it = 0, nsum = 0;
+    while (true) {
+        // w = (I + c S K_off S) u, r.u, w.u
+        double ga = 0.0, de = 0.0;
+        for_rows([&](int, int i) {
+            const int len = P.alen[i];
+            const double ui = __ldcg(P.u + i);
+            double acc = ui;
+            for (int k = 0; k < len; ++k) {
+                const size_t q = (size_t)k * ld + i;
+                acc += sval[q] * __ldcg(P.u + sdc_idx(P.acol[q], n, 72));
+            }
+            P.w[i] = acc;
+            ga += P.r[i] * ui;
+            de += acc * ui;
+        });
+        if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, bidx, epoch, P.budget, P.err))
+            return;
+        if (t < 64) {
+            double g, d;
+            xs_group_total(G, [&](int k) { return xs_load_cg(rec + buf * G + k); }, S.xs, g, d);
+            if ((t & 31) == 0) cg_scalars(S, t >> 5, nsum, g, d, P.rtol);
+        }
+        __syncthreads();
+        ++nsum;
+        buf ^= 1;
+        if (S.state != 0) break;
+        if (it >= P.maxit) {
+            if (lead) raise_error(P.err, SDC_E_CG_NOCONV);
+            break;
+        }
+        ++it;
+        const double alpha = S.alpha, beta = S.beta;
+        for_rows([&](int, int i) {
+            const double pi = P.u[i] + beta * P.p[i];
+            const double si = P.w[i] + beta * P.s[i];
+            P.p[i] = pi;
+            P.s[i] = si;
+            P.x[i] += alpha * pi;
+            P.r[i] -= alpha * si;
+        });
+        if (!precondition()) return;
+    }
+    if (S.state == 2) {
+        if (lead) raise_error(P.err, SDC_E_NONFINITE);
+        return;
+    }
+    if (lead) {
+        *P.iters_out = it;
+        *P.relres_out = cg_relres(S);
+        if (P.energy_out) *P.energy_out = S.energy;
+    }
+    for_rows([&](int, int i) { P.x[i] = sg[i] * P.x[i]; });
+}
+
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_batch(CgParams P, const SegBlock* __restrict__ tab,
                                                           unsigned* __restrict__ bars,
@@ -2070,6 +2250,50 @@ int launch_pcg(int n, const Ell& A, int m, double dt, const Coll& co, double rto
     P.inject_fault = cfg.inject_fault;
     P.L = 0;
     return launch_pcg_params(P, cfg, B, s);
+}
+
+int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int maxit,
+                      const CoarseDev& C, const PcgConfig& cfg, StepBuffers& B, cudaStream_t s) {
+    CgParams P{};
+    P.n = n;
+    P.ld = B.ld;
+    P.aval = A.val;
+    P.acol = A.col;
+    P.alen = A.len;
+    P.mc = B.mc;
+    P.kdc = B.kdc;
+    P.J = role.J;
+    P.c = role.c;
+    P.b = role.b;
+    P.x = role.x;
+    set_cg_vectors(P, B);
+    set_scaled_buffers(P, A, B);
+    if (!P.sv || !P.sval || role.epi_lo < role.epi_hi || C.G < 1 || C.q < 1) return SDC_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(P.part) % 16 != 0 || C.G > B.max_blocks) return SDC_E_INVALID;
+    P.bar = &B.sc->bar;
+    P.err = &B.sc->err;
+    P.rtol = rtol;
+    P.maxit = maxit;
+    P.budget = cfg.budget;
+    P.iters_out = role.iters_out;
+    P.relres_out = role.relres_out;
+    P.energy_out = role.energy_out;
+    P.M = 1;
+    cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
+    CoarseParams CP;
+    CP.q = C.q;
+    CP.lab_c = C.lab_c;
+    CP.crow = C.crow;
+    CP.boff = C.boff;
+    CP.cta_ptr = C.cta_ptr;
+    CP.cta_lab = C.cta_lab;
+    CP.Einv = C.Einv;
+    CP.tvec = C.tvec;
+    void* args[] = {&P, &CP};
+    const int blk = cfg.block > 512 ? 1024 : 512;
+    const void* k = blk > 512 ? (const void*)k_pcgcs_coarse<1024> : (const void*)k_pcgcs_coarse<512>;
+    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(C.G), dim3(blk), args, 0, s);
+    return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 
 int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, double rtol,

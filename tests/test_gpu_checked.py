@@ -8,8 +8,8 @@ replaced by an in-bounds one, and turns the call's status into SDC_E_INVALID.
    loads the checked build (SDC_GB300_LIB): 2D and 3D steps against the oracle,
    the 3- and 4-node meshes and the ragged 33 x 31 and 3D meshes, every M,
    empty sets, error statuses and the bounded-wait fault path, the cell-by-cell
-   two-cell, grid and branched cases, the PCG kernel tests, batches and the
-   adjoint.  No check may fire (a firing check fails the call), and every parity
+   two-cell, grid and branched cases with and without the two-level
+   preconditioner, the PCG kernel tests, batches and the adjoint.  No check may fire (a firing check fails the call), and every parity
    bar is the test's own.
 2. A node system one of whose column indices lies outside the matrix is solved
    by the checked build only: the call returns SDC_E_INVALID naming the check
@@ -47,7 +47,8 @@ def _env(lib):
 
 def test_small_cases_pass_under_the_checked_build(checked_lib):
     files = ["tests/test_gpu_parity.py", "tests/test_gpu_kernels.py", "tests/test_gpu_emi.py",
-             "tests/test_gpu_batch.py", "tests/test_gpu_adjoint.py"]
+             "tests/test_gpu_emi_coarse.py", "tests/test_gpu_batch.py",
+             "tests/test_gpu_adjoint.py"]
     r = subprocess.run([sys.executable, "-m", "pytest", *files, "-q", "-x",
                         "-m", "gpu and not slow", "-k", "not full_size"],
                        cwd=ROOT, env=_env(checked_lib), capture_output=True, text=True,

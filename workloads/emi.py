@@ -343,6 +343,32 @@ def emi_branched_2d(h=1.25, dt=0.02, sweeps=12, tol=1e-4, steps=125, name=None) 
                        meta={"seed": SEED_BASE + 2, "w_frozen": True, "labels": lab.shape})
 
 
+def coarse_blocks(wl, split=(16, 4, 4), min_dofs=None) -> np.ndarray:
+    """Blocks of the two-level preconditioner of the node solves: each subdomain (a
+    cell) is one block, and each subdomain with more than `min_dofs` dofs (default:
+    four times the median subdomain) is cut by a grid of split[0] x split[1] (x
+    split[2]) boxes over its bounding box.  Returns consecutive labels 0 .. nb-1."""
+    lab = np.asarray(wl.labels)
+    xyz = wl.mesh.xyz
+    dim = xyz.shape[1]
+    sizes = np.bincount(lab)
+    if min_dofs is None:
+        min_dofs = 4 * int(np.median(sizes[sizes > 0]))
+    key = lab.astype(np.int64) * 0
+    big = np.nonzero(sizes > min_dofs)[0]
+    for b in big:
+        sel = lab == b
+        lo, hi = xyz[sel].min(axis=0), xyz[sel].max(axis=0)
+        cells = np.array(split[:dim], dtype=np.int64)
+        ijk = np.floor((xyz[sel] - lo) / ((hi - lo) / cells + 1e-12)).astype(np.int64)
+        ijk = np.minimum(ijk, cells - 1)
+        flat = np.ravel_multi_index(tuple(ijk.T), tuple(cells))
+        key[sel] = 1 + flat
+    # consecutive labels in (subdomain, box) order
+    _, out = np.unique(lab.astype(np.int64) * (1 << 32) + key, return_inverse=True)
+    return out.astype(np.int32)
+
+
 def emi_tiny(kind="pair"):
     """Small EMI problems for exact checks."""
     if kind == "two_cells":
