@@ -14,21 +14,22 @@
 //   - lab_c: the block of each compact row;
 //   - crow: the compact rows sorted by (block, row), a stable compaction of the dofs
 //     sorted by (block, dof) (set up once) by the active flag; boff: block ranges;
-//   - the assignment of blocks to the CTAs of the CG launch, balanced by rows
-//     (largest block first onto the least loaded CTA), on the host.
+//   - the rows of the CG launch: CTA b takes the positions [cut[b], cut[b + 1]) of
+//     crow, ranges of equal weight (ELL row length + kRowWeight: the product's work
+//     per row), cut at block boundaries into pieces (host).
 // Work per node solve:
 //   - E = Z' A Z accumulated in 64-bit fixed point (terms rounded at 2^-41 of the
 //     largest diagonal entry; integer sums are exact, so E does not depend on the
 //     order of the atomic additions), then converted;
 //   - E^-1 by Gauss-Jordan elimination (E is symmetric positive definite: no
-//     pivoting), one grid barrier per pivot, in one cooperative launch.
+//     pivoting), kInvPanel pivots per step and one grid barrier per step, in one
+//     cooperative launch.
 // The CG itself is k_pcgcs_coarse (step.cu).
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <numeric>
-#include <queue>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,9 @@ namespace {
 
 constexpr int kChunk = 1024;    // dofs per compaction chunk (= threads per block)
 constexpr int kFracBits = 40;   // fixed-point fraction bits below the largest diagonal
+constexpr int kRowWeight = 4;   // per-row work of a CG iteration beside the row's slots
+constexpr int kRowsPerCta = 512;    // fewest active rows per CTA of the coarse CG launch:
+                                    // small active sets take fewer CTAs (cheaper grid syncs)
 
 inline int nb(int n, int b) { return (n + b - 1) / b; }
 
@@ -111,6 +115,71 @@ __global__ void k_coarse_scatter(int N, const int* __restrict__ gperm, const int
     }
 }
 
+// weight of compact position k: the ELL length of its row plus kRowWeight
+__device__ __forceinline__ int row_weight(int k, int n, const int* __restrict__ crow,
+                                          const int* __restrict__ act, const int* __restrict__ len,
+                                          int N) {
+    if (k >= n) return 0;
+    const int p = sdc_idx(crow[k], n, 87);
+    return len[act ? sdc_idx(act[p], N, 88) : p] + kRowWeight;
+}
+
+// inclusive block scan of one int per thread (kChunk threads)
+__device__ __forceinline__ int block_incl_scan(int v, int* wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int x = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        wsum[lane] = x;
+    }
+    __syncthreads();
+    return v + (wid ? wsum[wid - 1] : 0);
+}
+
+// weight of each chunk of kChunk positions of crow
+__global__ void k_coarse_wchunk(int n, const int* __restrict__ crow, const int* __restrict__ act,
+                                const int* __restrict__ len, int N, int* __restrict__ wcnt) {
+    __shared__ int wsum[32];
+    const int k = blockIdx.x * kChunk + threadIdx.x;
+    const int v = block_incl_scan(row_weight(k, n, crow, act, len, N), wsum);
+    if (threadIdx.x == kChunk - 1) wcnt[blockIdx.x] = v;
+}
+
+// cut[b] (block b - 1 of the grid, 1 <= b < G): the first position whose inclusive
+// weight prefix exceeds W b / G (W: the total weight)
+__global__ void k_coarse_cuts(int n, int G, const int* __restrict__ crow, const int* __restrict__ act,
+                              const int* __restrict__ len, int N, int ncn,
+                              const int* __restrict__ wcnt, const int* __restrict__ woff,
+                              int* __restrict__ cut) {
+    __shared__ int wsum[32];
+    __shared__ int first;
+    const int b = blockIdx.x + 1;
+    const long long W = (long long)woff[ncn - 1] + wcnt[ncn - 1];
+    const long long T = W * b / G;
+    int lo = 0, hi = ncn - 1;   // the last chunk c with woff[c] <= T
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (woff[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    if (threadIdx.x == 0) first = n;
+    const int k = lo * kChunk + threadIdx.x;
+    const long long incl = woff[lo] + block_incl_scan(row_weight(k, n, crow, act, len, N), wsum);
+    if (k < n && incl > T) atomicMin(&first, k);
+    __syncthreads();
+    if (threadIdx.x == 0) cut[b] = first;
+}
+
 // boff[a] = first position k with lab_c[crow[k]] >= a (crow sorted by block)
 __global__ void k_coarse_bounds(int q, int n, const int* __restrict__ crow,
                                 const int* __restrict__ lab_c, int* __restrict__ boff) {
@@ -179,8 +248,7 @@ __global__ void k_coarse_E(int n, int q, const int* __restrict__ lab_c, const do
 // E from fixed point; a block without active rows gets a unit diagonal (decoupled)
 __global__ void k_coarse_convert(int q, const unsigned long long* __restrict__ Eacc,
                                  const unsigned long long* __restrict__ dmax,
-                                 const int* __restrict__ boff, double* __restrict__ E,
-                                 double* __restrict__ piv) {
+                                 const int* __restrict__ boff, double* __restrict__ E) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= q * q) return;
     const int a = k / q, b = k - a * q;
@@ -188,40 +256,111 @@ __global__ void k_coarse_convert(int q, const unsigned long long* __restrict__ E
     double v = (double)(long long)Eacc[k] * inv;
     if (boff[a + 1] == boff[a] || boff[b + 1] == boff[b]) v = a == b ? 1.0 : 0.0;
     E[k] = v;
-    if (a == 0) piv[b] = v;   // row 0: the first pivot row
 }
 
-// In-place Gauss-Jordan inversion of the q x q matrix E (row-major), rows owned
-// cyclically by the CTAs.  Step k uses the pivot row k as it stood after step k - 1
-// (piv[k & 1], written by its owner at the end of that step); the owner of row k + 1
-// copies it to piv[(k + 1) & 1] after its update.  One grid barrier per step.
-__global__ void k_coarse_invert(int q, double* __restrict__ E, double* __restrict__ piv,
-                                unsigned* bar, long long budget, int* err) {
+// In-place Gauss-Jordan inversion of the q x q matrix E (row-major, symmetric positive
+// definite: no pivoting), a panel of kInvPanel pivots at a time, rows owned cyclically
+// by the CTAs.  Step K (pivot rows and columns K = [kb, kb + bk)), with P = E_KK^-1:
+//     rows i outside K:  E_iJ <- E_iJ - E_iK P E_KJ   (J outside K),   E_iK <- -E_iK P;
+//     rows of K:         E_KJ <- P E_KJ,   E_KK <- P.
+// Every CTA forms P itself (scalar Gauss-Jordan on the bk x bk block in shared memory).
+// The rows of K are read by every CTA during the step, so their owners write the new
+// rows to T (two buffers, by step parity) and copy them back at the next step: one
+// grid barrier per step.
+constexpr int kInvPanel = 16;
+constexpr int kInvThreads = 256;   // >= kInvPanel^2: one element of P per thread
+
+__global__ void __launch_bounds__(kInvThreads) k_coarse_invert(int q, double* __restrict__ E,
+                                                               double* __restrict__ T,
+                                                               unsigned* bar, long long budget,
+                                                               int* err) {
     __shared__ int ok;
-    __shared__ double sp[kMaxCoarseBlocks];
-    const int G = gridDim.x, b = blockIdx.x, t = threadIdx.x, T = blockDim.x;
+    __shared__ double Pm[kInvPanel][kInvPanel + 1];
+    __shared__ double piv;
+    __shared__ double fv[kInvPanel];
+    __shared__ double gv[kInvPanel];
+    const int G = gridDim.x, c = blockIdx.x, t = threadIdx.x, NT = blockDim.x;
     unsigned epoch = 0;
-    if (!group_barrier(bar, G, epoch, budget, err, &ok)) return;   // piv[0] visible
-    for (int k = 0; k < q; ++k) {
-        const double* pk = piv + (k & 1) * q;
-        for (int j = t; j < q; j += T) sp[j] = __ldcg(pk + j);
+    int pkb = 0, pbk = 0;    // the previous step's panel (pbk = 0: none)
+    // the new values of the previous panel's row i (owned by this CTA) from T
+    auto restore = [&](int i, const double* Tp) {
+        const double* src = Tp + (size_t)(i - pkb) * q;
+        double* row = E + (size_t)i * q;
+        for (int j = t; j < q; j += NT) row[j] = __ldcg(src + j);
+    };
+    for (int kb = 0, step = 0; kb < q; kb += kInvPanel, ++step) {
+        const int bk = min(kInvPanel, q - kb);
+        const double* Tp = T + (size_t)((step + 1) & 1) * kInvPanel * q;
+        double* Tc = T + (size_t)(step & 1) * kInvPanel * q;
+        // P = E_KK^-1
+        const int pi = t / bk, pj = t - pi * bk;
+        const bool mine = t < bk * bk;
+        if (mine) Pm[pi][pj] = __ldcg(E + (size_t)(kb + pi) * q + kb + pj);
         __syncthreads();
-        const double p = 1.0 / sp[k];
-        for (int i = b; i < q; i += G) {
-            double* row = E + (size_t)i * q;
-            if (i == k) {
-                for (int j = t; j < q; j += T) row[j] = j == k ? p : sp[j] * p;
-            } else {
-                const double f = __ldcg(row + k);
-                __syncthreads();   // every thread has read row[k] before it changes
-                for (int j = t; j < q; j += T) row[j] = j == k ? -f * p : row[j] - f * (sp[j] * p);
+        for (int k = 0; k < bk; ++k) {
+            if (t == 0) piv = 1.0 / Pm[k][k];
+            __syncthreads();
+            const double p = piv;
+            double v = 0.0;
+            if (mine) {
+                if (pi == k) v = pj == k ? p : Pm[k][pj] * p;
+                else v = pj == k ? -Pm[pi][k] * p : Pm[pi][pj] - Pm[pi][k] * (Pm[k][pj] * p);
             }
-            if (i == k + 1) {
-                __syncthreads();
-                for (int j = t; j < q; j += T) piv[((k + 1) & 1) * q + j] = row[j];
-            }
+            __syncthreads();
+            if (mine) Pm[pi][pj] = v;
+            __syncthreads();
         }
+        for (int i = c; i < q; i += G) {
+            if (pbk && i >= pkb && i < pkb + pbk) {
+                restore(i, Tp);
+                __syncthreads();
+            }
+            double* row = E + (size_t)i * q;
+            if (i >= kb && i < kb + bk) {
+                // pivot row: (P E_K*)_r to T
+                const int r = i - kb;
+                double* dst = Tc + (size_t)r * q;
+                for (int j = t; j < q; j += NT) {
+                    double v;
+                    if (j >= kb && j < kb + bk) {
+                        v = Pm[r][j - kb];
+                    } else {
+                        v = 0.0;
+                        for (int m = 0; m < bk; ++m) v += Pm[r][m] * __ldcg(E + (size_t)(kb + m) * q + j);
+                    }
+                    dst[j] = v;
+                }
+            } else {
+                // g = -E_iK P, then E_iJ += g E_KJ
+                if (t < bk) fv[t] = __ldcg(row + kb + t);
+                __syncthreads();
+                if (t < bk) {
+                    double sum = 0.0;
+                    for (int m = 0; m < bk; ++m) sum += fv[m] * Pm[m][t];
+                    gv[t] = -sum;
+                }
+                __syncthreads();
+                for (int j = t; j < q; j += NT) {
+                    if (j >= kb && j < kb + bk) {
+                        row[j] = gv[j - kb];
+                    } else {
+                        double v = __ldcg(row + j);
+                        for (int m = 0; m < bk; ++m) v += gv[m] * __ldcg(E + (size_t)(kb + m) * q + j);
+                        row[j] = v;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        pkb = kb;
+        pbk = bk;
         if (!group_barrier(bar, G, epoch, budget, err, &ok)) return;
+        if (kb + kInvPanel >= q) {
+            // the last panel's rows
+            const double* Tl = T + (size_t)(step & 1) * kInvPanel * q;
+            for (int i = c; i < q; i += G)
+                if (i >= pkb && i < pkb + pbk) restore(i, Tl);
+        }
     }
 }
 
@@ -253,9 +392,11 @@ int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err,
         al((void**)&C.lab_c, (size_t)ld * 4) || al((void**)&C.crow, (size_t)ld * 4) ||
         al((void**)&C.boff, (size_t)(q + 1) * 4) || al((void**)&C.chunk_cnt, (size_t)nc * 4) ||
         al((void**)&C.chunk_off, (size_t)nc * 4) || al((void**)&C.cta_ptr, (size_t)(G + 1) * 4) ||
-        al((void**)&C.cta_lab, (size_t)q * 4) || al((void**)&C.Eacc, (size_t)q * q * 8) ||
-        al((void**)&C.Einv, (size_t)q * q * 8) || al((void**)&C.piv, (size_t)2 * q * 8) ||
-        al((void**)&C.tvec, (size_t)q * 8) || al((void**)&C.dmax, 8) || al((void**)&C.bar, 8)) {
+        al((void**)&C.cut, (size_t)(G + 1) * 4) || al((void**)&C.nzb, (size_t)q * 4) ||
+        al((void**)&C.piece, (size_t)3 * (G + q) * 4) || al((void**)&C.blk_ptr, (size_t)(q + 1) * 4) ||
+        al((void**)&C.tpiece, (size_t)(G + q) * 8) || al((void**)&C.Eacc, (size_t)q * q * 8) ||
+        al((void**)&C.Einv, (size_t)q * q * 8) || al((void**)&C.piv, (size_t)2 * kInvPanel * q * 8) ||
+        al((void**)&C.dmax, 8) || al((void**)&C.bar, 8)) {
         coarse_free(C);
         why = "coarse blocks: device allocation failed";
         return SDC_E_NOMEM;
@@ -269,6 +410,7 @@ int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err,
     }
     C.q = q;
     C.N = N;
+    C.Gmax = G;
     C.G = G;
     C.err = err;
     return SDC_OK;
@@ -276,56 +418,73 @@ int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err,
 
 void coarse_free(CoarseDev& C) {
     for (void* p : {(void*)C.lab, (void*)C.gperm, (void*)C.lab_c, (void*)C.crow, (void*)C.boff,
-                    (void*)C.chunk_cnt, (void*)C.chunk_off, (void*)C.cta_ptr, (void*)C.cta_lab,
-                    (void*)C.Eacc, (void*)C.Einv, (void*)C.piv, (void*)C.tvec, (void*)C.dmax,
+                    (void*)C.chunk_cnt, (void*)C.chunk_off, (void*)C.cta_ptr, (void*)C.piece,
+                    (void*)C.blk_ptr, (void*)C.tpiece, (void*)C.cut, (void*)C.nzb,
+                    (void*)C.Eacc, (void*)C.Einv, (void*)C.piv, (void*)C.dmax,
                     (void*)C.bar})
         if (p) cudaFree(p);
     C = CoarseDev{};
 }
 
-int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, int G, cudaStream_t s) {
+int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, const int* len, int G,
+                 cudaStream_t s) {
     const int N = C.N, q = C.q, nc = nb(N, kChunk);
     if (n < 1) return SDC_OK;
+    G = std::max(1, std::min({G, C.Gmax, (n + kRowsPerCta - 1) / kRowsPerCta}));
     k_coarse_labels<<<nb(n, 256), 256, 0, s>>>(n, act, C.lab, N, C.lab_c);
     k_coarse_count<<<nc, kChunk, 0, s>>>(N, C.gperm, pos, C.chunk_cnt);
     k_coarse_scan<<<1, 1024, 0, s>>>(nc, C.chunk_cnt, C.chunk_off);
     k_coarse_scatter<<<nc, kChunk, 0, s>>>(N, C.gperm, pos, C.chunk_off, n, C.crow);
     k_coarse_bounds<<<nb(q + 1, 256), 256, 0, s>>>(q, n, C.crow, C.lab_c, C.boff);
+    // CTA ranges of equal weight (the chunk scratch is free again after the scatter)
+    const int ncn = nb(n, kChunk);
+    k_coarse_wchunk<<<ncn, kChunk, 0, s>>>(n, C.crow, act, len, N, C.chunk_cnt);
+    k_coarse_scan<<<1, 1024, 0, s>>>(ncn, C.chunk_cnt, C.chunk_off);
+    if (G > 1)
+        k_coarse_cuts<<<G - 1, kChunk, 0, s>>>(n, G, C.crow, act, len, N, ncn, C.chunk_cnt,
+                                               C.chunk_off, C.cut);
     C.h_boff.resize(q + 1);
+    C.h_cut.assign(G + 1, 0);
     cudaMemcpyAsync(C.h_boff.data(), C.boff, (size_t)(q + 1) * 4, cudaMemcpyDeviceToHost, s);
+    if (G > 1) cudaMemcpyAsync(C.h_cut.data() + 1, C.cut + 1, (size_t)(G - 1) * 4,
+                               cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return SDC_E_CUDA;
     if (C.h_boff[q] != n) return SDC_E_INVALID;   // every active row carries a block
-    // blocks onto CTAs: largest first onto the least loaded (ties: lower index)
-    G = std::max(1, std::min(G, C.G));
-    std::vector<int> order(q);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return C.h_boff[a + 1] - C.h_boff[a] > C.h_boff[b + 1] - C.h_boff[b];
-    });
-    using Load = std::pair<long long, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int b = 0; b < G; ++b) heap.push({0, b});
-    std::vector<std::vector<int>> own(G);
-    for (int a : order) {
-        const int rows = C.h_boff[a + 1] - C.h_boff[a];
-        if (rows == 0) continue;
-        Load l = heap.top();
-        heap.pop();
-        own[l.second].push_back(a);
-        heap.push({l.first + rows, l.second});
-    }
+    C.h_cut[G] = n;
+    for (int b = 1; b <= G; ++b)
+        if (C.h_cut[b] < C.h_cut[b - 1] || C.h_cut[b] > n) return SDC_E_INVALID;
+    // the ranges cut at the block boundaries into pieces; pieces come in CTA order
+    // and, crow being sorted by block, in block order too
     C.h_cta_ptr.assign(G + 1, 0);
-    C.h_cta_lab.clear();
+    C.h_piece.clear();
+    C.h_blk_ptr.assign(q + 1, 0);
+    int a = 0, pmax = 0;
     for (int b = 0; b < G; ++b) {
-        std::sort(own[b].begin(), own[b].end());
-        C.h_cta_lab.insert(C.h_cta_lab.end(), own[b].begin(), own[b].end());
-        C.h_cta_ptr[b + 1] = (int)C.h_cta_lab.size();
+        const int k0 = C.h_cut[b], k1 = C.h_cut[b + 1];
+        for (int k = k0; k < k1;) {
+            while (C.h_boff[a + 1] <= k) ++a;
+            const int e = std::min(k1, C.h_boff[a + 1]);
+            C.h_piece.insert(C.h_piece.end(), {a, k, e});
+            ++C.h_blk_ptr[a + 1];
+            k = e;
+        }
+        C.h_cta_ptr[b + 1] = (int)(C.h_piece.size() / 3);
+        pmax = std::max(pmax, C.h_cta_ptr[b + 1] - C.h_cta_ptr[b]);
     }
+    C.h_nzb.clear();
+    for (int b = 0; b < q; ++b)
+        if (C.h_blk_ptr[b + 1]) C.h_nzb.push_back(b);
+    std::partial_sum(C.h_blk_ptr.begin(), C.h_blk_ptr.end(), C.h_blk_ptr.begin());
     cudaMemcpyAsync(C.cta_ptr, C.h_cta_ptr.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, s);
-    if (!C.h_cta_lab.empty())
-        cudaMemcpyAsync(C.cta_lab, C.h_cta_lab.data(), C.h_cta_lab.size() * 4,
-                        cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(C.blk_ptr, C.h_blk_ptr.data(), (size_t)(q + 1) * 4, cudaMemcpyHostToDevice, s);
+    if (!C.h_piece.empty())
+        cudaMemcpyAsync(C.piece, C.h_piece.data(), C.h_piece.size() * 4, cudaMemcpyHostToDevice,
+                        s);
+    if (!C.h_nzb.empty())
+        cudaMemcpyAsync(C.nzb, C.h_nzb.data(), C.h_nzb.size() * 4, cudaMemcpyHostToDevice, s);
     C.G = G;
+    C.qn = (int)C.h_nzb.size();
+    C.pmax = pmax;
     // the host vectors must outlive the copies
     return cudaStreamSynchronize(s) == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
@@ -338,7 +497,7 @@ int coarse_factor(CoarseDev& C, int n, const Ell& A, const double* mc, const dou
     k_coarse_dmax<<<nb(n, 256), 256, 0, s>>>(n, mc, J, kdc, c, C.dmax);
     k_coarse_E<<<nb(n, 128), 128, 0, s>>>(n, q, C.lab_c, A.val, A.col, A.len, A.ld, mc, J, kdc, c,
                                           C.dmax, C.Eacc);
-    k_coarse_convert<<<nb(q * q, 256), 256, 0, s>>>(q, C.Eacc, C.dmax, C.boff, C.Einv, C.piv);
+    k_coarse_convert<<<nb(q * q, 256), 256, 0, s>>>(q, C.Eacc, C.dmax, C.boff, C.Einv);
     cudaMemsetAsync(C.bar, 0, sizeof(unsigned), s);
     const int G = std::max(1, std::min(q, pcg_sm_count()));
     int nq = q;
@@ -348,7 +507,7 @@ int coarse_factor(CoarseDev& C, int n, const Ell& A, const double* mc, const dou
     int* err = C.err;
     void* args[] = {&nq, &E, &piv, &bar, &budget, &err};
     const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_coarse_invert, dim3(G),
-                                                      dim3(256), args, 0, s);
+                                                      dim3(kInvThreads), args, 0, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 

@@ -243,27 +243,37 @@ struct CoarseDev {
     int* boff = nullptr;                 // [q + 1] first position of each block in crow
     int* chunk_cnt = nullptr;            // compaction scratch: per-chunk counts and offsets
     int* chunk_off = nullptr;
-    int* cta_ptr = nullptr;              // [G + 1] blocks of each CTA of the CG launch ...
-    int* cta_lab = nullptr;              // [q]     ... in cta_lab[cta_ptr[b] .. cta_ptr[b+1])
+    // rows of the CG launch: CTA b takes the positions [cut[b], cut[b + 1]) of crow
+    // (equal shares of the row weight len + kRowWeight), cut at block boundaries into
+    // pieces cta_ptr[b] .. cta_ptr[b + 1]) (at most G + q)
+    int* cut = nullptr;                  // [G + 1]
+    int* cta_ptr = nullptr;              // [G + 1]
+    int* piece = nullptr;                // [3 (G + q)]: block, first and end position
+    int* blk_ptr = nullptr;              // [q + 1] pieces of each block (contiguous)
+    int* nzb = nullptr;                  // [q] the blocks with active rows, ascending
+    double* tpiece = nullptr;            // [G + q] partial coarse sums of each piece
     unsigned long long* Eacc = nullptr;  // [q * q] E in 64-bit fixed point
     double* Einv = nullptr;              // [q * q] E^-1, row-major
-    double* piv = nullptr;               // [2 q] pivot rows of the inversion
-    double* tvec = nullptr;              // [q] coarse residual of the current iteration
+    double* piv = nullptr;               // new pivot rows of the inversion (two panels)
     unsigned long long* dmax = nullptr;  // largest diagonal of the node operator (bits)
     unsigned* bar = nullptr;             // grid barrier counter of the inversion
     int* err = nullptr;                  // shared with the step's error word
-    std::vector<int> h_boff, h_cta_ptr, h_cta_lab;
-    int G = 0;                           // CTAs of the coarse CG launch
+    std::vector<int> h_boff, h_cut, h_cta_ptr, h_piece, h_blk_ptr, h_nzb;
+    int Gmax = 0;                        // CTAs of a full-size coarse CG launch (the SMs)
+    int G = 0;                           // CTAs of this sweep's coarse CG launch
+    int qn = 0;                          // blocks with active rows
+    int pmax = 0;                        // most pieces of one CTA
 };
 // labels: host, N entries in [0, q).  Allocates and uploads; returns an sdc_status.
 int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err, cudaStream_t s,
                  std::string& why);
 void coarse_free(CoarseDev& C);
 // Per sweep: block of each compact row, rows sorted by block, block ranges and the
-// assignment of blocks to the CTAs of the CG launch (balanced by rows).  pos: dof ->
-// compact row (-1 outside the active set).  Synchronises the stream (reads the block
-// ranges).
-int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, int G, cudaStream_t s);
+// pieces of the CG launch's CTAs (ranges of equal row weight cut at blocks).  pos: dof
+// -> compact row (-1 outside the active set); len: ELL row lengths of the dofs (the
+// row weights).  Synchronises the stream (reads the block ranges and the cuts).
+int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, const int* len, int G,
+                 cudaStream_t s);
 // Per node solve: E = Z' A Z of the operator diag(mc (1 + c J) + c kdc) + c A_off on the
 // active rows (exact fixed-point accumulation) and its inverse.
 int coarse_factor(CoarseDev& C, int n, const Ell& A, const double* mc, const double* J,

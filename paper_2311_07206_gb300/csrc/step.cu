@@ -1388,64 +1388,186 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
 // Batched form of the scaled classical arrangement (one group of blocks per instance).
 // ---- two-level preconditioner (cell-by-cell node solves, Sec. 6) ------------------
 // The classical scaled arrangement of pcgc_group_scaled with the preconditioned
-// residual u = r + Y E^-1 Y' r in place of u = r: in the scaled variables x = S x~
-// the block indicators Z become Y = S^-1 Z (Y_i = sqrt(d_i) on the rows of its block)
-// and D^-1 becomes the identity.  Every row of block a is handled by the CTA that owns
-// a (cta_lab), so a CTA forms the coarse residual t_a = sum_{i in a} Y_i r_i of its
-// blocks by exact sums in a fixed order, publishes it, and after one grid barrier
-// computes y_a = (E^-1 t)_a for its own blocks and u on their rows.  Per iteration:
-// the product and the two dot products (one grid sum), the update, the coarse
-// residual (one grid barrier), u (one grid barrier that also publishes it).
+// residual u = r + Y E^-1 t, t = Y' r, in place of u = r: in the scaled variables
+// x = S x~ the block indicators Z become Y = S^-1 Z (Y_i = sqrt(d_i) on the rows of its
+// block) and D^-1 becomes the identity.  The compact rows, sorted by block (crow), are
+// split into ranges of equal work per CTA, cut at the block boundaries into pieces;
+// each warp of a CTA takes a contiguous chunk of its range.
+// t is carried by the recurrences of the CG vectors it is a linear image of:
+//     Y' s <- Y' w + beta Y' s,   t <- t - alpha Y' s,
+// so an iteration needs Y' w only, taken per piece in the product and published by
+// the grid sum of the dot products.  Per iteration: the product, the dot products and
+// the pieces' Y' w (one grid sum); in every CTA the two recurrences over the blocks
+// with active rows (the same arithmetic in the same order in every CTA), then
+// y = E^-1 t for the blocks of its pieces (a warp per piece); the update of p, s, x,
+// r and u = r + Y y on its rows (one grid barrier, publishing u).  t starts as Y' r
+// of the initial residual.  Piece sums are exact: each warp sums its rows of a piece
+// in 128-bit fixed point when it leaves the piece, and the warps' records of a piece
+// are added as integers.  So are the rows of E^-1 t.
 struct CoarseParams {
     int q;
-    const int* lab_c;
+    int qn;                // blocks with active rows
+    int pmax;              // most pieces of one CTA
+    int ptot;              // pieces of all CTAs
     const int* crow;
-    const int* boff;
-    const int* cta_ptr;
-    const int* cta_lab;
+    const int* cta_ptr;    // [G + 1] pieces of each CTA
+    const int* piece;      // [3 ptot]: block, first and end position in crow
+    const int* blk_ptr;    // [q + 1] pieces of each block
+    const int* nzb;        // [qn] the blocks with active rows, ascending
     const double* Einv;
-    double* tvec;
+    double* tpiece;        // [ptot] sums of each piece
 };
 
-// exact block sums of (a, b) returned in every thread (tot: 2 doubles of shared memory)
-__device__ __forceinline__ void xs_block_total2(double a, double b, XsScratch& X, double* tot,
-                                                double& ta, double& tb) {
-    int fa, fb;
-    __int128 qa, qb;
-    xs_block_sum2(a, b, X, fa, fb, qa, qb);
-    if (threadIdx.x == 0) {
-        tot[0] = xs_to_double(qa, fa);
-        tot[1] = xs_to_double(qb, fb);
-    }
-    __syncthreads();
-    ta = tot[0];
-    tb = tot[1];
-    __syncthreads();
+// a warp's exact partial sum of one piece (shared memory)
+struct __align__(16) XsPieceRec {
+    __int128 q;
+    int f;
+    int tag;               // the piece it belongs to; -1: never written
+    int pad[2];
+};
+constexpr int kPieceRecSlack = 32;   // records: piece l of warp w at l + w (< pmax + 32)
+
+// dynamic shared memory of k_pcgcs_coarse
+inline size_t coarse_smem_bytes(int pmax, int qn, int ptot) {
+    return (size_t)(pmax + kPieceRecSlack) * sizeof(XsPieceRec) + (size_t)pmax * 8 +
+           (size_t)ptot * 8 + (size_t)pmax * 12 + (size_t)(2 * qn + 1) * 4;
 }
 
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarseParams C) {
     __shared__ CgShared S;
-    __shared__ double tot[2];
-    __shared__ double ysh[kMaxCoarseBlocks];
+    __shared__ double tr[kMaxCoarseBlocks];   // t = Y' r of every block with active rows
+    __shared__ double ts[kMaxCoarseBlocks];   // Y' s
+    extern __shared__ __align__(16) unsigned char dyn[];
     const int t = threadIdx.x, B = blockDim.x, G = gridDim.x, bidx = blockIdx.x;
+    const int lane = t & 31, wid = t >> 5, nw = B >> 5;
     const bool lead = bidx == 0 && t == 0;
-    const int ld = P.ld, n = P.n;
+    const int ld = P.ld, n = P.n, q = C.q, qn = C.qn;
     const double c = P.c;
     double* __restrict__ sg = P.sv;     // diag^-1/2
     double* __restrict__ yv = P.idA;    // diag^1/2: the block indicators in scaled variables
     double* __restrict__ sval = P.sval;
     XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
-    const int e0 = C.cta_ptr[bidx], e1 = C.cta_ptr[bidx + 1];
+    const int e0 = C.cta_ptr[bidx], np = C.cta_ptr[bidx + 1] - e0;
+    XsPieceRec* const recs = reinterpret_cast<XsPieceRec*>(dyn);           // [pmax + 32]
+    double* const ysh = reinterpret_cast<double*>(recs + C.pmax + kPieceRecSlack);  // [pmax]
+    double* const stp = ysh + C.pmax;                                       // [ptot]
+    int* const spc = reinterpret_cast<int*>(stp + C.ptot);                  // [3 pmax]
+    int* const snz = spc + 3 * C.pmax;                                      // [qn]
+    int* const sbp = snz + qn;                                              // [qn + 1]
+    for (int j = t; j < 3 * np; j += B) spc[j] = C.piece[3 * e0 + j];
+    for (int m = t; m < qn; m += B) {
+        const int a = sdc_idx(C.nzb[m], q, 73);
+        snz[m] = a;
+        sbp[m] = C.blk_ptr[a];
+    }
+    if (t == 0) sbp[qn] = C.blk_ptr[q];
+    for (int j = t; j < C.pmax + kPieceRecSlack; j += B) recs[j].tag = -1;
+    __syncthreads();
+    // this warp's chunk [cs, ce) of the CTA's positions and the piece holding cs
+    const int k0 = np ? spc[1] : 0, k1 = np ? spc[3 * np - 1] : 0;
+    const int rw = (k1 - k0 + nw - 1) / nw;
+    const int cs = min(k1, k0 + wid * rw), ce = min(k1, cs + rw);
+    int pf = 0;
+    while (pf < np - 1 && spc[3 * pf + 2] <= cs) ++pf;
     unsigned epoch = 0;
     int buf = 0;
-    // f(e, i) over the rows of this CTA: block cta_lab[e], compact row i
+    // f(l, i) over this thread's rows: piece l (of this CTA), compact row i
     auto for_rows = [&](auto&& f) {
-        for (int e = e0; e < e1; ++e) {
-            const int a = C.cta_lab[e];
-            const int k1 = C.boff[a + 1];
-            for (int k = C.boff[a] + t; k < k1; k += B) f(e, sdc_idx(C.crow[k], n, 70));
+        int l = pf;
+        for (int k = cs + lane; k < ce; k += 32) {
+            while (spc[3 * l + 2] <= k) ++l;
+            f(l, sdc_idx(C.crow[k], n, 70));
         }
+    };
+    // sum of g(i) = (a, b) -> a b over each piece of this CTA, exactly, into tpiece
+    auto piece_sums = [&](auto&& g) {
+        if (cs < ce) {
+            int l = pf, pend = spc[3 * pf + 2];
+            double acc = 0.0;
+            auto flush = [&]() {
+                const int F = __reduce_max_sync(0xffffffffu, xs_field(acc));
+                const __int128 qv = xs_warp_sum(xs_fixed(acc, F));
+                if (lane == 0) {
+                    XsPieceRec& R = recs[l + wid];
+                    R.q = qv;
+                    R.f = F;
+                    R.tag = l;
+                }
+            };
+            for (int base = cs; base < ce; base += 32) {
+                const int k = base + lane;
+                double2 v = make_double2(0.0, 0.0);
+                if (k < ce) v = g(sdc_idx(C.crow[k], n, 70));
+                if (__all_sync(0xffffffffu, k < pend)) {   // one piece: the common case
+                    acc = fma(v.x, v.y, acc);
+                    continue;
+                }
+                const double pv = v.x * v.y;
+                bool used = k >= ce;
+                while (true) {
+                    if (!used && k < pend) {
+                        acc += pv;
+                        used = true;
+                    }
+                    if (__all_sync(0xffffffffu, used)) break;
+                    flush();
+                    acc = 0.0;
+                    ++l;
+                    pend = spc[3 * l + 2];
+                }
+            }
+            flush();
+        }
+        __syncthreads();
+        for (int l = wid; l < np; l += nw) {
+            const XsPieceRec R = recs[l + lane];
+            const bool on = lane < nw && R.tag == l;
+            const int f = on ? R.f : 1;
+            const int F = __reduce_max_sync(0xffffffffu, f);
+            const int d = F - f;
+            __int128 qv = 0;
+            if (on) qv = d >= 127 ? (R.q < 0 ? (__int128)-1 : (__int128)0) : xs_sar(R.q, d);
+            qv = xs_warp_sum(qv);
+            if (lane == 0) C.tpiece[e0 + l] = xs_to_double(qv, F);
+        }
+    };
+    // the blocks' totals of the published piece sums; first: t = total, Y's = 0,
+    // else the recurrences
+    auto coarse_t = [&](bool first, double alpha, double beta) {
+        const int ptot = sbp[qn];
+        for (int e = t; e < ptot; e += B) stp[e] = __ldcg(C.tpiece + e);
+        __syncthreads();
+        for (int m = t; m < qn; m += B) {
+            const int a = snz[m];
+            double tw = 0.0;
+            for (int e = sbp[m]; e < sbp[m + 1]; ++e) tw += stp[e];
+            if (first) {
+                tr[a] = tw;
+                ts[a] = 0.0;
+            } else {
+                const double sa = tw + beta * ts[a];
+                ts[a] = sa;
+                tr[a] -= alpha * sa;
+            }
+        }
+        __syncthreads();
+    };
+    // y = E^-1 t on the blocks of this CTA's pieces, a warp per piece (t vanishes
+    // outside the blocks with active rows)
+    auto coarse_y = [&]() {
+        for (int l = wid; l < np; l += nw) {
+            const double* ra = C.Einv + (size_t)spc[3 * l] * q;
+            double pa = 0.0;
+            for (int m = lane; m < qn; m += 32) {
+                const int j = snz[m];
+                pa += __ldg(ra + j) * tr[j];
+            }
+            const int F = __reduce_max_sync(0xffffffffu, xs_field(pa));
+            const __int128 qv = xs_warp_sum(xs_fixed(pa, F));
+            if (lane == 0) ysh[l] = xs_to_double(qv, F);
+        }
+        __syncthreads();
     };
     for_rows([&](int, int i) {
         const double d = P.mc[i] * (1.0 + c * P.J[i]) + c * P.kdc[i];
@@ -1465,67 +1587,33 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
         const int len = P.alen[i];
         const double csi = c * sg[i];
         for (int k = 0; k < len; ++k) {
-            const size_t q = (size_t)k * ld + i;
-            sval[q] = csi * P.aval[q] * __ldcg(sg + sdc_idx(P.acol[q], n, 71));
+            const size_t qq = (size_t)k * ld + i;
+            sval[qq] = csi * P.aval[qq] * __ldcg(sg + sdc_idx(P.acol[qq], n, 71));
         }
     });
-    // u = r + Y E^-1 Y' r on this CTA's rows, published by the closing grid barrier
-    auto precondition = [&]() -> bool {
-        for (int e = e0; e < e1; e += 2) {
-            const int a = C.cta_lab[e], a2 = e + 1 < e1 ? C.cta_lab[e + 1] : -1;
-            double pa = 0.0, pb = 0.0;
-            for (int k = C.boff[a] + t; k < C.boff[a + 1]; k += B) {
-                const int i = C.crow[k];
-                pa += yv[i] * P.r[i];
-            }
-            if (a2 >= 0)
-                for (int k = C.boff[a2] + t; k < C.boff[a2 + 1]; k += B) {
-                    const int i = C.crow[k];
-                    pb += yv[i] * P.r[i];
-                }
-            double ta, tb;
-            xs_block_total2(pa, pb, S.xs, tot, ta, tb);
-            if (t == 0) {
-                C.tvec[a] = ta;
-                if (a2 >= 0) C.tvec[a2] = tb;
-            }
-        }
-        if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return false;
-        for (int e = e0; e < e1; e += 2) {
-            const int a = C.cta_lab[e], a2 = e + 1 < e1 ? C.cta_lab[e + 1] : -1;
-            double pa = 0.0, pb = 0.0;
-            for (int j = t; j < C.q; j += B) {
-                const double tj = __ldcg(C.tvec + j);
-                pa += __ldg(C.Einv + (size_t)a * C.q + j) * tj;
-                if (a2 >= 0) pb += __ldg(C.Einv + (size_t)a2 * C.q + j) * tj;
-            }
-            double ya, yb;
-            xs_block_total2(pa, pb, S.xs, tot, ya, yb);
-            if (t == 0) {
-                ysh[e - e0] = ya;
-                if (a2 >= 0) ysh[e + 1 - e0] = yb;
-            }
-        }
-        __syncthreads();
-        for_rows([&](int e, int i) { P.u[i] = P.r[i] + yv[i] * ysh[e - e0]; });
-        return group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok);
-    };
-    if (!precondition()) return;
+    // t = Y' r, y, u = r + Y y
+    piece_sums([&](int i) { return make_double2(yv[i], P.r[i]); });
+    if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return;
+    coarse_t(true, 0.0, 0.0);
+    coarse_y();
+    for_rows([&](int l, int i) { P.u[i] = P.r[i] + yv[i] * ysh[l]; });
+    if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return;
     int it = 0, nsum = 0;
     while (true) {
-        // w = (I + c S K_off S) u, r.u, w.u
+        // w = (I + c S K_off S) u, r.u, w.u, and Y' w per piece
         double ga = 0.0, de = 0.0;
-        for_rows([&](int, int i) {
+        piece_sums([&](int i) {
             const int len = P.alen[i];
             const double ui = __ldcg(P.u + i);
             double acc = ui;
             for (int k = 0; k < len; ++k) {
-                const size_t q = (size_t)k * ld + i;
-                acc += sval[q] * __ldcg(P.u + sdc_idx(P.acol[q], n, 72));
+                const size_t qq = (size_t)k * ld + i;
+                acc += sval[qq] * __ldcg(P.u + sdc_idx(P.acol[qq], n, 72));
             }
             P.w[i] = acc;
             ga += P.r[i] * ui;
             de += acc * ui;
+            return make_double2(yv[i], acc);
         });
         if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, bidx, epoch, P.budget, P.err))
             return;
@@ -1544,15 +1632,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
         }
         ++it;
         const double alpha = S.alpha, beta = S.beta;
-        for_rows([&](int, int i) {
+        coarse_t(false, alpha, beta);
+        coarse_y();
+        for_rows([&](int l, int i) {
             const double pi = P.u[i] + beta * P.p[i];
             const double si = P.w[i] + beta * P.s[i];
             P.p[i] = pi;
             P.s[i] = si;
             P.x[i] += alpha * pi;
-            P.r[i] -= alpha * si;
+            const double ri = P.r[i] - alpha * si;
+            P.r[i] = ri;
+            P.u[i] = ri + yv[i] * ysh[l];
         });
-        if (!precondition()) return;
+        if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return;
     }
     if (S.state == 2) {
         if (lead) raise_error(P.err, SDC_E_NONFINITE);
@@ -2268,7 +2360,9 @@ int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int
     P.x = role.x;
     set_cg_vectors(P, B);
     set_scaled_buffers(P, A, B);
-    if (!P.sv || !P.sval || role.epi_lo < role.epi_hi || C.G < 1 || C.q < 1) return SDC_E_INVALID;
+    if (!P.sv || !P.sval || role.epi_lo < role.epi_hi || C.G < 1 || C.q < 1 || C.qn > C.q ||
+        C.pmax > C.q + 1)
+        return SDC_E_INVALID;
     if (reinterpret_cast<uintptr_t>(P.part) % 16 != 0 || C.G > B.max_blocks) return SDC_E_INVALID;
     P.bar = &B.sc->bar;
     P.err = &B.sc->err;
@@ -2282,17 +2376,24 @@ int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int
     cudaMemsetAsync(&B.sc->bar, 0, sizeof(unsigned), s);
     CoarseParams CP;
     CP.q = C.q;
-    CP.lab_c = C.lab_c;
+    CP.qn = C.qn;
+    CP.pmax = C.pmax;
+    CP.ptot = C.h_blk_ptr.empty() ? 0 : C.h_blk_ptr[C.q];
     CP.crow = C.crow;
-    CP.boff = C.boff;
     CP.cta_ptr = C.cta_ptr;
-    CP.cta_lab = C.cta_lab;
+    CP.piece = C.piece;
+    CP.blk_ptr = C.blk_ptr;
+    CP.nzb = C.nzb;
     CP.Einv = C.Einv;
-    CP.tvec = C.tvec;
+    CP.tpiece = C.tpiece;
     void* args[] = {&P, &CP};
     const int blk = cfg.block > 512 ? 1024 : 512;
     const void* k = blk > 512 ? (const void*)k_pcgcs_coarse<1024> : (const void*)k_pcgcs_coarse<512>;
-    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(C.G), dim3(blk), args, 0, s);
+    const size_t smem = coarse_smem_bytes(C.pmax, C.qn, CP.ptot);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return SDC_E_CUDA;
+    cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(C.G), dim3(blk), args, smem, s);
     return e == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }
 

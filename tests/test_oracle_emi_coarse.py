@@ -141,3 +141,26 @@ def test_emi_step_with_two_level_preconditioner():
     it_j = sum(jac["stats"].cg_iters[k * 8 + m] for k in range(wl.sweeps) for m in range(wl.M))
     it_2 = sum(two["stats"].cg_iters[k * 8 + m] for k in range(wl.sweeps) for m in range(wl.M))
     assert it_2 < it_j, (it_2, it_j)
+
+
+def test_block_major_renumbering_is_a_relabelling():
+    """Numbering the dofs block by block (workloads.emi.block_major) permutes the
+    step's result and changes nothing else: the oracle's step of the renumbered
+    workload equals the permuted step of the original to rounding, with the same
+    active-set sizes."""
+    from workloads.emi import block_major, coarse_blocks, renumber
+    wl = emi_tiny("grid")
+    blocks = coarse_blocks(wl, split=(4, 2, 2))
+    order, b2 = block_major(wl, blocks)
+    assert np.array_equal(np.sort(order), np.arange(wl.n))
+    assert np.all(np.diff(b2) >= 0)                       # blocks contiguous
+    w2 = renumber(wl, order)
+    S1 = oracle.System.from_mesh(wl.mesh)
+    S2 = oracle.System.from_mesh(w2.mesh)
+    r1 = S1.step_emi(wl, wl.u0, wl.w0)
+    r2 = S2.step_emi(w2, w2.u0, w2.w0)
+    assert r1["status"] == r2["status"] == 0
+    scale = max(1.0, np.abs(r1["u"]).max())
+    assert np.abs(r1["u"][order] - r2["u"]).max() <= 1e-12 * scale
+    assert np.abs(r1["w"] - r2["w"]).max() <= 1e-12
+    assert list(r1["stats"].n_active) == list(r2["stats"].n_active)

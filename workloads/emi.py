@@ -369,6 +369,32 @@ def coarse_blocks(wl, split=(16, 4, 4), min_dofs=None) -> np.ndarray:
     return out.astype(np.int32)
 
 
+def renumber(wl, order) -> "EmiWorkload":
+    """The same workload with its dofs renumbered: new dof k is old dof order[k]
+    (mesh coordinates and elements, pair ends, Robin measures, labels, initial
+    potentials; per-pair data unchanged)."""
+    order = np.asarray(order, dtype=np.int64)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size)
+    mesh = Mesh(wl.mesh.dim, wl.mesh.xyz[order], inv[wl.mesh.elems].astype(np.int32),
+                wl.mesh.elem_sigma, dict(wl.mesh.meta))
+    out = EmiWorkload(wl.name, mesh, inv[wl.pair_k].astype(np.int32),
+                      inv[wl.pair_l].astype(np.int32), wl.pair_area, wl.pair_kind,
+                      wl.robin_area[order], wl.labels[order], wl.ionic, M=wl.M, dt=wl.dt,
+                      sweeps=wl.sweeps, tol=wl.tol, steps=wl.steps, u0=wl.u0[order], w0=wl.w0,
+                      robin_eps=wl.robin_eps, Cm=wl.Cm, g_gap=wl.g_gap, sigma_i=wl.sigma_i,
+                      sigma_e=wl.sigma_e, cg_rtol=wl.cg_rtol, alpha=wl.alpha,
+                      meta=dict(wl.meta, renumbered=True))
+    return out
+
+
+def block_major(wl, blocks):
+    """Dof order grouping each block's dofs (stable: the original order inside a
+    block), and the blocks in that order: (order, blocks[order])."""
+    order = np.argsort(np.asarray(blocks), kind="stable")
+    return order, np.asarray(blocks)[order]
+
+
 def emi_tiny(kind="pair"):
     """Small EMI problems for exact checks."""
     if kind == "two_cells":
