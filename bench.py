@@ -287,8 +287,8 @@ CG_SOURCES = ("step.cu", "device_common.cuh")
 # dram__bytes_write.sum) of the first node solve of a slab step, all 442,401 rows, scaled to
 # the average launch by algorithmic bytes.  `source_sha` is the hash of the CG sources the
 # capture was taken with (kernel_source_sha()); once they change, the figure is withheld.
-PCG_TRAFFIC = {"w1": {"dram_bytes": 64.38e6 + 10.77e6, "algorithmic_bytes": 1.735e9,
-                      "kernel": "k_pcg_scaled<1024>", "source_sha": "39f3eddd3007ffa6",
+PCG_TRAFFIC = {"w1": {"dram_bytes": 64.29e6 + 11.10e6, "algorithmic_bytes": 1.735e9,
+                      "kernel": "k_pcg_scaled<1024>", "source_sha": "d17d91028a67b582",
                       "capture": "profiles/pcg_scaled_w1_slab_full_solve.md"}}
 
 
@@ -302,33 +302,36 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def pcg_ops(st, M, sweeps):
+def pcg_ops(st, M, sweeps, extra_per_row=0.0):
     """Algorithmic FP64 operations (lane instructions) of the PCG solves of one
     step: per iteration and active row zbar + 8 (SpMV zbar + 1, p and q updates,
-    two dot products, x and r updates, z = r / diag)."""
+    two dot products, x and r updates, z = r / diag), plus extra_per_row (the
+    two-level preconditioner: 2, the piece sum of Y'w and u = r + Y y)."""
     ops = 0.0
     for k in range(st.sweeps_run):
         n = st.n_active[k]
         if n == 0:
             continue
         nnz = st.nnz_active[k] + n
-        per_iter = nnz + 8.0 * n
+        per_iter = nnz + (8.0 + extra_per_row) * n
         for m in range(M):
             ops += st.cg_iters[k][m] * per_iter
     return ops
 
 
-def pcg_bytes(st, M, sweeps):
+def pcg_bytes(st, M, sweeps, extra_per_row=0.0):
     """Algorithmic bytes of the restricted PCG solves of one step: per iteration
     and active row 12 zbar + 104 B (zbar = stored entries per row incl. the
-    diagonal; FP64 values, int32 indices, fused vector traffic)."""
+    diagonal; FP64 values, int32 indices, fused vector traffic), plus
+    extra_per_row (the two-level preconditioner: 20 B, the row's position in the
+    block order, Y_i, and the store of u)."""
     b = 0.0
     for k in range(st.sweeps_run):
         n = st.n_active[k]
         if n == 0:
             continue
         nnz = st.nnz_active[k] + n
-        per_iter = 12.0 * nnz + 104.0 * n
+        per_iter = 12.0 * nnz + (104.0 + extra_per_row) * n
         for m in range(M):
             b += st.cg_iters[k][m] * per_iter
     return b
@@ -766,8 +769,8 @@ def run_emi(args):
             agg["active_dof_sweeps"] += sum(st.n_active[:st.sweeps_run])
             agg["pcg_ms"] += st.phase_ms[1]
             agg["pcg_launches"] += st.phase_launches[1]
-            agg["pcg_bytes"] += pcg_bytes(st, wl.M, sweeps)
-            agg["pcg_ops"] += pcg_ops(st, wl.M, sweeps)
+            agg["pcg_bytes"] += pcg_bytes(st, wl.M, sweeps, 20.0 if blocks is not None else 0.0)
+            agg["pcg_ops"] += pcg_ops(st, wl.M, sweeps, 2.0 if blocks is not None else 0.0)
             agg["launches"] += st.kernel_launches
             agg["phase_ms"] += np.array(st.phase_ms[:5])
             for k in range(st.sweeps_run):
@@ -833,7 +836,9 @@ def run_emi(args):
     launches = max(1, agg_a["pcg_launches"])
     ach_ops = agg_a["pcg_ops"] / pcg_s / 1e9 if pcg_s > 0 else None
     ach_gbs = agg_a["pcg_bytes"] / pcg_s / 1e9 if pcg_s > 0 else None
-    roofline = {"kernel": "k_pcg* on the EMI node operator (K + membrane pair slots)",
+    kname = ("k_pcgcs_coarse (two-level: Jacobi + block coarse space)" if blocks is not None
+             else "k_pcg* (Jacobi)")
+    roofline = {"kernel": kname + " on the EMI node operator (K + membrane pair slots)",
                 "bound": "alu", "achieved": ach_ops, "peak": alu_peak,
                 "unit": "G FP64 lane-op/s", "frac": ach_ops / alu_peak if ach_ops else None,
                 "peak_source": "304 FP64 lanes/cycle (ncu dfma peak_sustained) x %.0f MHz max SM clock"
