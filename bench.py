@@ -80,6 +80,9 @@ def parse():
                     help="w2: two-level preconditioner of the node solves over blocks = the "
                          "cells and the extracellular space cut into this many boxes "
                          "(x,y,z); 'off' for Jacobi alone")
+    ap.add_argument("--emi-order", choices=["block", "natural"], default="block",
+                    help="w2 with coarse blocks: number the dofs block by block (block) or "
+                         "keep the mesh's numbering (natural)")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=None,
                     help="pick the node solves' launch shape with sdc_autotune before timing "
                          "(default: on for the batch w3, off otherwise)")
@@ -287,6 +290,9 @@ CG_SOURCES = ("step.cu", "device_common.cuh")
 # dram__bytes_write.sum) of the first node solve of a slab step, all 442,401 rows, scaled to
 # the average launch by algorithmic bytes.  `source_sha` is the hash of the CG sources the
 # capture was taken with (kernel_source_sha()); once they change, the figure is withheld.
+ERR_NORM = ("max over ten checkpoints evenly spaced in the window (the last step included) of "
+            "max_i |v_i(t) - v_ref,i(t)|")
+
 PCG_TRAFFIC = {"w1": {"dram_bytes": 64.29e6 + 11.10e6, "algorithmic_bytes": 1.735e9,
                       "kernel": "k_pcg_scaled<1024>", "source_sha": "d17d91028a67b582",
                       "capture": "profiles/pcg_scaled_w1_slab_full_solve.md"}}
@@ -412,9 +418,20 @@ def run_gb300(args):
     if args.autotune:
         tune = ctx.autotune(v0.clone(), w0.clone(), 0.0, wl.dt, wl.sweeps, wl.tol, trial_steps=3)
 
-    def trajectory(c, vs, ws, n0, steps, tol, sweeps, timed, table=None):
-        """`steps` steps of context c from (vs, ws) at step index n0 (inputs kept)."""
+    def checkpoints(steps):
+        """Step offsets after which errors are measured: ten, evenly spaced, the last
+        step included (a long window's final state alone can sit at rest)."""
+        return sorted({max(0, (j * steps) // 10 - 1) for j in range(1, 11)})
+
+    def trajectory(c, vs, ws, n0, steps, tol, sweeps, timed, table=None, ref=None,
+                   record=False):
+        """`steps` steps of context c from (vs, ws) at step index n0 (inputs kept).
+        record: also return v at the checkpoints (device copies, taken outside the
+        timed region); ref: such a record, against which the run's error (max over
+        the checkpoints of max |v - v_ref|) is returned instead."""
         v, w = vs.clone(), ws.clone()
+        ck = set(checkpoints(steps)) if (record or ref is not None) else set()
+        snaps, err = [], None
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)] if timed else None
         agg = {"active_dof_sweeps": 0, "pcg_ms": 0.0, "pcg_launches": 0, "pcg_bytes": 0.0,
@@ -437,8 +454,19 @@ def run_gb300(args):
             agg["phase_ms"] += np.array(st.phase_ms[:5])
             if table is not None:
                 table.add(st, wl.M)
+            if i in ck:
+                if record:
+                    snaps.append(v.clone())
+                else:
+                    e = (v - ref[len(snaps)]).abs().max()
+                    snaps.append(None)
+                    err = e if err is None else torch.maximum(err, e)
         torch.cuda.synchronize(dev)
         total_ms = sum(a.elapsed_time(b) for a, b in ev) if timed else None
+        if record:
+            return v, w, total_ms, agg, snaps
+        if ref is not None:
+            return v, w, total_ms, agg, float(err)
         return v, w, total_ms, agg
 
     def roofline_of(agg, ms_step_total):
@@ -485,8 +513,8 @@ def run_gb300(args):
                                        "capture (%s)" % (sha, tr["source_sha"]))
         return r
 
-    def max_err(v, ref):
-        return float(np.abs(v.cpu().numpy() - ref).max())
+    def err_of(snaps, ref):
+        return max(float((a - b).abs().max()) for a, b in zip(snaps, ref))
 
     def equal_error(vs, ws, n0, steps, ref, err_a, ms_a):
         """(fixed) adaptive with the workload's sweeps against plain SDC with the fewest
@@ -497,15 +525,16 @@ def run_gb300(args):
         same way.  All errors against plain SDC with 12 sweeps from the same state."""
         plain = {}
         for kp in range(1, wl.sweeps + 3):
-            v, _, ms, _ = trajectory(ctx, vs, ws, n0, steps, 0.0, kp, timed=True)
-            plain[kp] = (max_err(v, ref), ms)
+            _, _, ms, _, e = trajectory(ctx, vs, ws, n0, steps, 0.0, kp, timed=True, ref=ref)
+            plain[kp] = (e, ms)
         adapt = [(wl.tol, err_a, ms_a)]
         pick = None
         for j in range(6):
             if j > 0:
                 tol_j = wl.tol / 2 ** j
-                v, _, ms, _ = trajectory(ctx, vs, ws, n0, steps, tol_j, wl.sweeps, timed=True)
-                adapt.append((tol_j, max_err(v, ref), ms))
+                _, _, ms, _, e = trajectory(ctx, vs, ws, n0, steps, tol_j, wl.sweeps,
+                                            timed=True, ref=ref)
+                adapt.append((tol_j, e, ms))
             e_a = adapt[j][1]
             cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * e_a]
             kp = cands[0] if cands else max(plain)
@@ -543,14 +572,14 @@ def run_gb300(args):
                                        for t, e, m in adapt]}
         # energy-norm stop pair
         es_ctx = {a: new_ctx(alpha=a, energy_stop=1, sdc_rho=0.05) for a in (0.0, wl.alpha)}
-        v, _, ms0, agg0 = trajectory(es_ctx[0.0], vs, ws, n0, steps, wl.tol, 12, timed=True)
-        e0 = max_err(v, ref)
+        _, _, ms0, agg0, e0 = trajectory(es_ctx[0.0], vs, ws, n0, steps, wl.tol, 12,
+                                         timed=True, ref=ref)
         scan = []
         for j in range(5):
             tol_j = wl.tol / 2 ** j
-            v, _, ms1, agg1 = trajectory(es_ctx[wl.alpha], vs, ws, n0, steps, tol_j, 12,
-                                         timed=True)
-            scan.append({"TOL": tol_j, "err": max_err(v, ref), "ms_per_step": ms1 / steps,
+            _, _, ms1, agg1, e1 = trajectory(es_ctx[wl.alpha], vs, ws, n0, steps, tol_j, 12,
+                                             timed=True, ref=ref)
+            scan.append({"TOL": tol_j, "err": e1, "ms_per_step": ms1 / steps,
                          "mean_sweeps": agg1["sweeps"] / steps})
             if scan[-1]["err"] <= 1.1 * e0:
                 break
@@ -566,7 +595,7 @@ def run_gb300(args):
             c.close()
         return {"fixed_sweeps": fixed, "energy_stop": energy,
                 "reference": "plain SDC, %d sweeps, same dt, same start" % args.ref_sweeps,
-                "norm": "max |v(t_end) - v_ref(t_end)|"}
+                "norm": ERR_NORM}
 
     def window(vs, ws, n0, steps, extras, table):
         """Timed adaptive run of `steps` steps from (vs, ws) at step n0, then (extras) the
@@ -579,8 +608,10 @@ def run_gb300(args):
         barrier(world)
         torch.cuda.synchronize(dev)
         clocks = Clocks(dev_id)
-        va, wa, ms_a, agg_a = trajectory(ctx, vs, ws, n0, steps, wl.tol, wl.sweeps, timed=True,
-                                         table=table)
+        res = trajectory(ctx, vs, ws, n0, steps, wl.tol, wl.sweeps, timed=True, table=table,
+                         record=bool(extras))
+        va, wa, ms_a, agg_a = res[:4]
+        snaps_a = res[4] if extras else None
         torch.cuda.synchronize(dev)
         barrier(world)
         clk = clocks.stop()
@@ -589,17 +620,19 @@ def run_gb300(args):
                "active_dof_sweeps_per_s": world * agg_a["active_dof_sweeps"] / (ms_a / 1e3),
                "agg": agg_a, "clocks": clk, "va": va, "wa": wa}
         if extras:
-            vp, _, ms_p, agg_p = trajectory(ctx, vs, ws, n0, steps, 0.0, wl.sweeps, timed=True)
-            vr, _, _, _ = trajectory(ctx, vs, ws, n0, steps, 0.0, args.ref_sweeps, timed=False)
-            ref = vr.cpu().numpy()
-            err_a, err_p = max_err(va, ref), max_err(vp, ref)
+            _, _, _, _, ref = trajectory(ctx, vs, ws, n0, steps, 0.0, args.ref_sweeps,
+                                         timed=False, record=True)
+            _, _, ms_p, agg_p, err_p = trajectory(ctx, vs, ws, n0, steps, 0.0, wl.sweeps,
+                                                  timed=True, ref=ref)
+            err_a = err_of(snaps_a, ref)
+            del snaps_a
             out["plain"] = {"value": steps / (ms_p / 1e3), "unit": "steps/s",
                             "ms_per_step": ms_p / steps,
                             "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_p / 1e3)}
             out["speedup_vs_plain"] = ms_p / ms_a
             out["err_vs_ref"] = {"adaptive": err_a, "plain": err_p,
                                  "reference": "plain SDC, %d sweeps, same dt" % args.ref_sweeps,
-                                 "norm": "max |v(t_K) - v_ref(t_K)|"}
+                                 "norm": ERR_NORM}
             out["equal_error"] = equal_error(vs, ws, n0, steps, ref, err_a, ms_a)
         return out
 
@@ -739,11 +772,17 @@ def run_emi(args):
     stream = torch.cuda.current_stream(dev)
     opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, w_frozen=int(frozen),
                            cg_maxit=100000)
-    ctx = Context.from_emi(wl, options=opts, stream=stream.cuda_stream)
     blocks = None
     if args.emi_coarse != "off":
-        from workloads.emi import coarse_blocks
+        from workloads.emi import block_major, coarse_blocks, renumber
         blocks = coarse_blocks(wl, split=tuple(int(x) for x in args.emi_coarse.split(",")))
+        if args.emi_order == "block":
+            # the same problem with its dofs numbered block by block: each block's rows
+            # are contiguous in memory
+            order, blocks = block_major(wl, blocks)
+            wl = renumber(wl, order)
+    ctx = Context.from_emi(wl, options=opts, stream=stream.cuda_stream)
+    if blocks is not None:
         ctx.set_coarse_blocks(blocks)
     u0 = torch.tensor(wl.u0, dtype=torch.float64, device=dev)
     w0 = torch.tensor(wl.w0, dtype=torch.float64, device=dev)
@@ -865,6 +904,8 @@ def run_emi(args):
            "preconditioner": ("two-level: Jacobi + %d blocks (cells, extracellular space in "
                               "%s boxes)" % (int(blocks.max()) + 1, args.emi_coarse)
                               if blocks is not None else "Jacobi"),
+           "dof_order": ("block by block (workloads.emi.renumber)"
+                         if blocks is not None and args.emi_order == "block" else "mesh"),
            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",
            "autotune": tune}
     line = {"metric": "SDC steps/s & active-dof sweeps/s (cell-by-cell bricks), adaptive "

@@ -14,9 +14,10 @@
 //   - lab_c: the block of each compact row;
 //   - crow: the compact rows sorted by (block, row), a stable compaction of the dofs
 //     sorted by (block, dof) (set up once) by the active flag; boff: block ranges;
-//   - the rows of the CG launch: CTA b takes the positions [cut[b], cut[b + 1]) of
-//     crow, ranges of equal weight (ELL row length + kRowWeight: the product's work
-//     per row), cut at block boundaries into pieces (host).
+//   - the rows of the CG launch: the positions of crow in tiles of kCoarseTile, tile j
+//     on CTA j mod G (the whole grid sweeps one window of the vectors at a time, as the
+//     Jacobi kernels do); each tile cut at the block boundaries into pieces, numbered
+//     in position order, so that the pieces of a block are contiguous (host).
 // Work per node solve:
 //   - E = Z' A Z accumulated in 64-bit fixed point (terms rounded at 2^-41 of the
 //     largest diagonal entry; integer sums are exact, so E does not depend on the
@@ -41,9 +42,6 @@ namespace {
 
 constexpr int kChunk = 1024;    // dofs per compaction chunk (= threads per block)
 constexpr int kFracBits = 40;   // fixed-point fraction bits below the largest diagonal
-constexpr int kRowWeight = 4;   // per-row work of a CG iteration beside the row's slots
-constexpr int kRowsPerCta = 512;    // fewest active rows per CTA of the coarse CG launch:
-                                    // small active sets take fewer CTAs (cheaper grid syncs)
 
 inline int nb(int n, int b) { return (n + b - 1) / b; }
 
@@ -113,71 +111,6 @@ __global__ void k_coarse_scatter(int N, const int* __restrict__ gperm, const int
         const int at = off[blockIdx.x] + woff[wid] + __popc(bal & ((1u << lane) - 1u));
         crow[sdc_idx(at, n, 83)] = p;
     }
-}
-
-// weight of compact position k: the ELL length of its row plus kRowWeight
-__device__ __forceinline__ int row_weight(int k, int n, const int* __restrict__ crow,
-                                          const int* __restrict__ act, const int* __restrict__ len,
-                                          int N) {
-    if (k >= n) return 0;
-    const int p = sdc_idx(crow[k], n, 87);
-    return len[act ? sdc_idx(act[p], N, 88) : p] + kRowWeight;
-}
-
-// inclusive block scan of one int per thread (kChunk threads)
-__device__ __forceinline__ int block_incl_scan(int v, int* wsum) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    if (lane == 31) wsum[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int x = wsum[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += u;
-        }
-        wsum[lane] = x;
-    }
-    __syncthreads();
-    return v + (wid ? wsum[wid - 1] : 0);
-}
-
-// weight of each chunk of kChunk positions of crow
-__global__ void k_coarse_wchunk(int n, const int* __restrict__ crow, const int* __restrict__ act,
-                                const int* __restrict__ len, int N, int* __restrict__ wcnt) {
-    __shared__ int wsum[32];
-    const int k = blockIdx.x * kChunk + threadIdx.x;
-    const int v = block_incl_scan(row_weight(k, n, crow, act, len, N), wsum);
-    if (threadIdx.x == kChunk - 1) wcnt[blockIdx.x] = v;
-}
-
-// cut[b] (block b - 1 of the grid, 1 <= b < G): the first position whose inclusive
-// weight prefix exceeds W b / G (W: the total weight)
-__global__ void k_coarse_cuts(int n, int G, const int* __restrict__ crow, const int* __restrict__ act,
-                              const int* __restrict__ len, int N, int ncn,
-                              const int* __restrict__ wcnt, const int* __restrict__ woff,
-                              int* __restrict__ cut) {
-    __shared__ int wsum[32];
-    __shared__ int first;
-    const int b = blockIdx.x + 1;
-    const long long W = (long long)woff[ncn - 1] + wcnt[ncn - 1];
-    const long long T = W * b / G;
-    int lo = 0, hi = ncn - 1;   // the last chunk c with woff[c] <= T
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (woff[mid] <= T) lo = mid; else hi = mid - 1;
-    }
-    if (threadIdx.x == 0) first = n;
-    const int k = lo * kChunk + threadIdx.x;
-    const long long incl = woff[lo] + block_incl_scan(row_weight(k, n, crow, act, len, N), wsum);
-    if (k < n && incl > T) atomicMin(&first, k);
-    __syncthreads();
-    if (threadIdx.x == 0) cut[b] = first;
 }
 
 // boff[a] = first position k with lab_c[crow[k]] >= a (crow sorted by block)
@@ -387,14 +320,16 @@ int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err,
     for (int i = 0; i < N; ++i) gperm[cnt[h_lab[i]]++] = i;
     const int nc = nb(N, kChunk);
     const int G = pcg_sm_count();
+    const int P = (ld + kCoarseTile - 1) / kCoarseTile + q;   // pieces: tiles + block boundaries
     auto al = [&](void** p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 8)); };
     if (al((void**)&C.lab, (size_t)N * 4) || al((void**)&C.gperm, (size_t)N * 4) ||
         al((void**)&C.lab_c, (size_t)ld * 4) || al((void**)&C.crow, (size_t)ld * 4) ||
         al((void**)&C.boff, (size_t)(q + 1) * 4) || al((void**)&C.chunk_cnt, (size_t)nc * 4) ||
-        al((void**)&C.chunk_off, (size_t)nc * 4) || al((void**)&C.cta_ptr, (size_t)(G + 1) * 4) ||
-        al((void**)&C.cut, (size_t)(G + 1) * 4) || al((void**)&C.nzb, (size_t)q * 4) ||
-        al((void**)&C.piece, (size_t)3 * (G + q) * 4) || al((void**)&C.blk_ptr, (size_t)(q + 1) * 4) ||
-        al((void**)&C.tpiece, (size_t)(G + q) * 8) || al((void**)&C.Eacc, (size_t)q * q * 8) ||
+        al((void**)&C.chunk_off, (size_t)nc * 4) ||
+        al((void**)&C.tp, (size_t)((ld + kCoarseTile - 1) / kCoarseTile + 1) * 4) ||
+        al((void**)&C.nzb, (size_t)q * 4) || al((void**)&C.piece, (size_t)3 * P * 4) ||
+        al((void**)&C.blk_ptr, (size_t)(q + 1) * 4) || al((void**)&C.tpiece, (size_t)P * 8) ||
+        al((void**)&C.Eacc, (size_t)q * q * 8) ||
         al((void**)&C.Einv, (size_t)q * q * 8) || al((void**)&C.piv, (size_t)2 * kInvPanel * q * 8) ||
         al((void**)&C.dmax, 8) || al((void**)&C.bar, 8)) {
         coarse_free(C);
@@ -418,49 +353,36 @@ int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err,
 
 void coarse_free(CoarseDev& C) {
     for (void* p : {(void*)C.lab, (void*)C.gperm, (void*)C.lab_c, (void*)C.crow, (void*)C.boff,
-                    (void*)C.chunk_cnt, (void*)C.chunk_off, (void*)C.cta_ptr, (void*)C.piece,
-                    (void*)C.blk_ptr, (void*)C.tpiece, (void*)C.cut, (void*)C.nzb,
+                    (void*)C.chunk_cnt, (void*)C.chunk_off, (void*)C.tp, (void*)C.piece,
+                    (void*)C.blk_ptr, (void*)C.tpiece, (void*)C.nzb,
                     (void*)C.Eacc, (void*)C.Einv, (void*)C.piv, (void*)C.dmax,
                     (void*)C.bar})
         if (p) cudaFree(p);
     C = CoarseDev{};
 }
 
-int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, const int* len, int G,
-                 cudaStream_t s) {
+int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, int G, cudaStream_t s) {
     const int N = C.N, q = C.q, nc = nb(N, kChunk);
     if (n < 1) return SDC_OK;
-    G = std::max(1, std::min({G, C.Gmax, (n + kRowsPerCta - 1) / kRowsPerCta}));
+    const int T = kCoarseTile, ntiles = nb(n, T);
+    G = std::max(1, std::min({G, C.Gmax, ntiles}));
     k_coarse_labels<<<nb(n, 256), 256, 0, s>>>(n, act, C.lab, N, C.lab_c);
     k_coarse_count<<<nc, kChunk, 0, s>>>(N, C.gperm, pos, C.chunk_cnt);
     k_coarse_scan<<<1, 1024, 0, s>>>(nc, C.chunk_cnt, C.chunk_off);
     k_coarse_scatter<<<nc, kChunk, 0, s>>>(N, C.gperm, pos, C.chunk_off, n, C.crow);
     k_coarse_bounds<<<nb(q + 1, 256), 256, 0, s>>>(q, n, C.crow, C.lab_c, C.boff);
-    // CTA ranges of equal weight (the chunk scratch is free again after the scatter)
-    const int ncn = nb(n, kChunk);
-    k_coarse_wchunk<<<ncn, kChunk, 0, s>>>(n, C.crow, act, len, N, C.chunk_cnt);
-    k_coarse_scan<<<1, 1024, 0, s>>>(ncn, C.chunk_cnt, C.chunk_off);
-    if (G > 1)
-        k_coarse_cuts<<<G - 1, kChunk, 0, s>>>(n, G, C.crow, act, len, N, ncn, C.chunk_cnt,
-                                               C.chunk_off, C.cut);
     C.h_boff.resize(q + 1);
-    C.h_cut.assign(G + 1, 0);
     cudaMemcpyAsync(C.h_boff.data(), C.boff, (size_t)(q + 1) * 4, cudaMemcpyDeviceToHost, s);
-    if (G > 1) cudaMemcpyAsync(C.h_cut.data() + 1, C.cut + 1, (size_t)(G - 1) * 4,
-                               cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return SDC_E_CUDA;
     if (C.h_boff[q] != n) return SDC_E_INVALID;   // every active row carries a block
-    C.h_cut[G] = n;
-    for (int b = 1; b <= G; ++b)
-        if (C.h_cut[b] < C.h_cut[b - 1] || C.h_cut[b] > n) return SDC_E_INVALID;
-    // the ranges cut at the block boundaries into pieces; pieces come in CTA order
-    // and, crow being sorted by block, in block order too
-    C.h_cta_ptr.assign(G + 1, 0);
+    // pieces: the tiles cut at the block boundaries, in position order (so in block
+    // order too, crow being sorted by block)
+    C.h_tp.assign(ntiles + 1, 0);
     C.h_piece.clear();
     C.h_blk_ptr.assign(q + 1, 0);
-    int a = 0, pmax = 0;
-    for (int b = 0; b < G; ++b) {
-        const int k0 = C.h_cut[b], k1 = C.h_cut[b + 1];
+    int a = 0;
+    for (int j = 0; j < ntiles; ++j) {
+        const int k0 = j * T, k1 = std::min(n, k0 + T);
         for (int k = k0; k < k1;) {
             while (C.h_boff[a + 1] <= k) ++a;
             const int e = std::min(k1, C.h_boff[a + 1]);
@@ -468,23 +390,29 @@ int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, const int*
             ++C.h_blk_ptr[a + 1];
             k = e;
         }
-        C.h_cta_ptr[b + 1] = (int)(C.h_piece.size() / 3);
-        pmax = std::max(pmax, C.h_cta_ptr[b + 1] - C.h_cta_ptr[b]);
+        C.h_tp[j + 1] = (int)(C.h_piece.size() / 3);
+    }
+    int pmax = 0;
+    for (int b = 0; b < G; ++b) {
+        int np = 0;
+        for (int j = b; j < ntiles; j += G) np += C.h_tp[j + 1] - C.h_tp[j];
+        pmax = std::max(pmax, np);
     }
     C.h_nzb.clear();
     for (int b = 0; b < q; ++b)
         if (C.h_blk_ptr[b + 1]) C.h_nzb.push_back(b);
     std::partial_sum(C.h_blk_ptr.begin(), C.h_blk_ptr.end(), C.h_blk_ptr.begin());
-    cudaMemcpyAsync(C.cta_ptr, C.h_cta_ptr.data(), (size_t)(G + 1) * 4, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(C.tp, C.h_tp.data(), (size_t)(ntiles + 1) * 4, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(C.blk_ptr, C.h_blk_ptr.data(), (size_t)(q + 1) * 4, cudaMemcpyHostToDevice, s);
-    if (!C.h_piece.empty())
-        cudaMemcpyAsync(C.piece, C.h_piece.data(), C.h_piece.size() * 4, cudaMemcpyHostToDevice,
-                        s);
+    cudaMemcpyAsync(C.piece, C.h_piece.data(), C.h_piece.size() * 4, cudaMemcpyHostToDevice, s);
     if (!C.h_nzb.empty())
         cudaMemcpyAsync(C.nzb, C.h_nzb.data(), C.h_nzb.size() * 4, cudaMemcpyHostToDevice, s);
     C.G = G;
+    C.ntiles = ntiles;
+    C.tmax = nb(ntiles, G);
     C.qn = (int)C.h_nzb.size();
     C.pmax = pmax;
+    C.ptot = (int)(C.h_piece.size() / 3);
     // the host vectors must outlive the copies
     return cudaStreamSynchronize(s) == cudaSuccess ? SDC_OK : SDC_E_CUDA;
 }

@@ -427,8 +427,8 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
         if (a.coarse) {
             // the blocks of this sweep's active set: rows by block, CTA ownership
             int rc = SDC_OK;
-            run(SDC_PHASE_SELECT, 8, [&] { rc = coarse_sweep(*a.coarse, n, act, E.pos,
-                                                             A->len, a.pcg->sms, s); });
+            run(SDC_PHASE_SELECT, 5, [&] { rc = coarse_sweep(*a.coarse, n, act, E.pos,
+                                                             a.pcg->sms, s); });
             if (rc != SDC_OK) {
                 status = fail(rc, "two-level preconditioner: block ordering failed");
                 break;

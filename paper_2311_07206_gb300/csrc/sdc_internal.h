@@ -233,6 +233,7 @@ int launch_pcg_role(int n, const Ell& A, const PcgRole& role, double dt, int M, 
 // additive two-level preconditioner z = D^-1 r + Z E^-1 Z' r, E = Z' A Z, over the
 // blocks that hold active dofs.
 constexpr int kMaxCoarseBlocks = SDC_MAX_COARSE_BLOCKS;
+constexpr int kCoarseTile = 1024;   // positions per tile of the two-level CG (its block size)
 struct CoarseDev {
     int q = 0;                           // blocks
     int N = 0;
@@ -243,37 +244,37 @@ struct CoarseDev {
     int* boff = nullptr;                 // [q + 1] first position of each block in crow
     int* chunk_cnt = nullptr;            // compaction scratch: per-chunk counts and offsets
     int* chunk_off = nullptr;
-    // rows of the CG launch: CTA b takes the positions [cut[b], cut[b + 1]) of crow
-    // (equal shares of the row weight len + kRowWeight), cut at block boundaries into
-    // pieces cta_ptr[b] .. cta_ptr[b + 1]) (at most G + q)
-    int* cut = nullptr;                  // [G + 1]
-    int* cta_ptr = nullptr;              // [G + 1]
-    int* piece = nullptr;                // [3 (G + q)]: block, first and end position
+    // rows of the CG launch: the positions of crow in tiles of kCoarseTile, tile j on CTA
+    // j mod G; each tile cut at block boundaries into pieces, numbered in position order
+    int* tp = nullptr;                   // [ntiles + 1] pieces of each tile
+    int* piece = nullptr;                // [3 P]: block, first and end position
     int* blk_ptr = nullptr;              // [q + 1] pieces of each block (contiguous)
     int* nzb = nullptr;                  // [q] the blocks with active rows, ascending
-    double* tpiece = nullptr;            // [G + q] partial coarse sums of each piece
+    double* tpiece = nullptr;            // [P] partial coarse sums of each piece
     unsigned long long* Eacc = nullptr;  // [q * q] E in 64-bit fixed point
     double* Einv = nullptr;              // [q * q] E^-1, row-major
     double* piv = nullptr;               // new pivot rows of the inversion (two panels)
     unsigned long long* dmax = nullptr;  // largest diagonal of the node operator (bits)
     unsigned* bar = nullptr;             // grid barrier counter of the inversion
     int* err = nullptr;                  // shared with the step's error word
-    std::vector<int> h_boff, h_cut, h_cta_ptr, h_piece, h_blk_ptr, h_nzb;
+    std::vector<int> h_boff, h_tp, h_piece, h_blk_ptr, h_nzb;
     int Gmax = 0;                        // CTAs of a full-size coarse CG launch (the SMs)
     int G = 0;                           // CTAs of this sweep's coarse CG launch
     int qn = 0;                          // blocks with active rows
     int pmax = 0;                        // most pieces of one CTA
+    int ptot = 0;                        // pieces of the sweep
+    int ntiles = 0;                      // tiles of the sweep
+    int tmax = 0;                        // most tiles of one CTA
 };
 // labels: host, N entries in [0, q).  Allocates and uploads; returns an sdc_status.
 int coarse_setup(CoarseDev& C, const int* h_lab, int N, int q, int ld, int* err, cudaStream_t s,
                  std::string& why);
 void coarse_free(CoarseDev& C);
 // Per sweep: block of each compact row, rows sorted by block, block ranges and the
-// pieces of the CG launch's CTAs (ranges of equal row weight cut at blocks).  pos: dof
-// -> compact row (-1 outside the active set); len: ELL row lengths of the dofs (the
-// row weights).  Synchronises the stream (reads the block ranges and the cuts).
-int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, const int* len, int G,
-                 cudaStream_t s);
+// pieces of the CG launch (tiles of kCoarseTile positions, round robin over the CTAs,
+// cut at blocks).  pos: dof -> compact row (-1 outside the active set).  Synchronises
+// the stream (reads the block ranges).
+int coarse_sweep(CoarseDev& C, int n, const int* act, const int* pos, int G, cudaStream_t s);
 // Per node solve: E = Z' A Z of the operator diag(mc (1 + c J) + c kdc) + c A_off on the
 // active rows (exact fixed-point accumulation) and its inverse.
 int coarse_factor(CoarseDev& C, int n, const Ell& A, const double* mc, const double* J,

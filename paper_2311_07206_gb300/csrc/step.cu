@@ -420,16 +420,19 @@ __device__ __forceinline__ void pcg_group(const CgParams& P, CgShared& S, int ro
         double* mn = mbuf[nsum & 1];
         ga = de = 0.0;
         for (int i = c0 + t; i < c1; i += B) {
+            // every operand of the row loaded before the first store (the vectors may
+            // alias as far as the compiler knows)
             const double id = P.idA[i];
-            const double wi = P.w[i], ui = P.u[i];
-            const double zi = P.nv[i] + beta * P.z[i];
-            const double si = wi + beta * P.s[i];
-            const double pi = ui + beta * P.p[i];
+            const double wi = P.w[i], ui = P.u[i], ni = P.nv[i], z0 = P.z[i], s0 = P.s[i],
+                         p0 = P.p[i], xi = P.x[i], r0 = P.r[i];
+            const double zi = ni + beta * z0;
+            const double si = wi + beta * s0;
+            const double pi = ui + beta * p0;
             P.z[i] = zi;
             P.s[i] = si;
             P.p[i] = pi;
-            P.x[i] += alpha * pi;
-            const double r2 = P.r[i] - alpha * si;
+            P.x[i] = xi + alpha * pi;
+            const double r2 = r0 - alpha * si;
             const double w2 = wi - alpha * zi;
             const double u2 = id * r2;
             P.r[i] = r2;
@@ -557,14 +560,16 @@ __device__ __forceinline__ void pcg_group_scaled(const CgParams& P, CgShared& S,
         double* mn = mbuf[nsum & 1];
         ga = de = 0.0;
         for (int i = c0 + t; i < c1; i += B) {
-            const double wi = P.w[i], ri = P.r[i];
-            const double zi = P.nv[i] + beta * P.z[i];
-            const double si = wi + beta * P.s[i];
-            const double pi = ri + beta * P.p[i];
+            // every operand of the row loaded before the first store
+            const double wi = P.w[i], ri = P.r[i], ni = P.nv[i], z0 = P.z[i], s0 = P.s[i],
+                         p0 = P.p[i], xi = P.x[i];
+            const double zi = ni + beta * z0;
+            const double si = wi + beta * s0;
+            const double pi = ri + beta * p0;
             P.z[i] = zi;
             P.s[i] = si;
             P.p[i] = pi;
-            P.x[i] += alpha * pi;
+            P.x[i] = xi + alpha * pi;
             const double r2 = ri - alpha * si;
             const double w2 = wi - alpha * zi;
             P.r[i] = r2;
@@ -1230,14 +1235,17 @@ __device__ __forceinline__ void pcgc_group(const CgParams& P, CgShared& S, int r
         // phase 1: p, s, x, r, u
         const double alpha = S.alpha, beta = S.beta;
         for (int i = i0; i < row1; i += stride) {
-            const double pi = P.u[i] + beta * P.p[i];
-            const double si = P.w[i] + beta * P.s[i];
+            // every operand of the row loaded before the first store
+            const double ui = P.u[i], p0 = P.p[i], wi = P.w[i], s0 = P.s[i], xi = P.x[i],
+                         r0 = P.r[i], id = P.idA[i];
+            const double pi = ui + beta * p0;
+            const double si = wi + beta * s0;
+            const double r = r0 - alpha * si;
             P.p[i] = pi;
             P.s[i] = si;
-            P.x[i] += alpha * pi;
-            const double r = P.r[i] - alpha * si;
+            P.x[i] = xi + alpha * pi;
             P.r[i] = r;
-            P.u[i] = r * P.idA[i];
+            P.u[i] = r * id;
         }
         if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
     }
@@ -1344,12 +1352,13 @@ __device__ __forceinline__ void pcgc_group_scaled(const CgParams& P, CgShared& S
         ++it;
         const double alpha = S.alpha, beta = S.beta;
         for (int i = i0; i < n; i += stride) {
-            const double ri = P.r[i];
-            const double pi = ri + beta * P.p[i];
-            const double si = P.w[i] + beta * P.s[i];
+            // every operand of the row loaded before the first store
+            const double ri = P.r[i], p0 = P.p[i], wi = P.w[i], s0 = P.s[i], xi = P.x[i];
+            const double pi = ri + beta * p0;
+            const double si = wi + beta * s0;
             P.p[i] = pi;
             P.s[i] = si;
-            P.x[i] += alpha * pi;
+            P.x[i] = xi + alpha * pi;
             P.r[i] = ri - alpha * si;
         }
         if (!group_barrier(bar, nblk, epoch, P.budget, P.err, &S.ok)) return;
@@ -1390,9 +1399,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
 // The classical scaled arrangement of pcgc_group_scaled with the preconditioned
 // residual u = r + Y E^-1 t, t = Y' r, in place of u = r: in the scaled variables
 // x = S x~ the block indicators Z become Y = S^-1 Z (Y_i = sqrt(d_i) on the rows of its
-// block) and D^-1 becomes the identity.  The compact rows, sorted by block (crow), are
-// split into ranges of equal work per CTA, cut at the block boundaries into pieces;
-// each warp of a CTA takes a contiguous chunk of its range.
+// block) and D^-1 becomes the identity.  The compact rows, sorted by block (crow), run in
+// tiles of kCoarseTile positions, tile j on CTA j mod G and position j kCoarseTile + t on
+// thread t, so that the grid sweeps one window of the vectors at a time (the row order of
+// the Jacobi kernels); each tile is cut at the block boundaries into pieces.
 // t is carried by the recurrences of the CG vectors it is a linear image of:
 //     Y' s <- Y' w + beta Y' s,   t <- t - alpha Y' s,
 // so an iteration needs Y' w only, taken per piece in the product and published by
@@ -1402,16 +1412,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs(CgParams P) {
 // y = E^-1 t for the blocks of its pieces (a warp per piece); the update of p, s, x,
 // r and u = r + Y y on its rows (one grid barrier, publishing u).  t starts as Y' r
 // of the initial residual.  Piece sums are exact: each warp sums its rows of a piece
-// in 128-bit fixed point when it leaves the piece, and the warps' records of a piece
-// are added as integers.  So are the rows of E^-1 t.
+// in 128-bit fixed point, and the warps' records of a piece are added as integers.
+// So are the rows of E^-1 t.
 struct CoarseParams {
     int q;
     int qn;                // blocks with active rows
     int pmax;              // most pieces of one CTA
-    int ptot;              // pieces of all CTAs
+    int ptot;              // pieces of the sweep
+    int ntiles;            // tiles of the sweep
+    int tmax;              // most tiles of one CTA
+    int stage;             // 1: the CTA's rows of crow are staged in shared memory
     const int* crow;
-    const int* cta_ptr;    // [G + 1] pieces of each CTA
-    const int* piece;      // [3 ptot]: block, first and end position in crow
+    const int* tp;         // [ntiles + 1] pieces of each tile
+    const int* piece;      // [3 ptot]: block, first and end position in crow (position order)
     const int* blk_ptr;    // [q + 1] pieces of each block
     const int* nzb;        // [qn] the blocks with active rows, ascending
     const double* Einv;
@@ -1425,16 +1438,21 @@ struct __align__(16) XsPieceRec {
     int tag;               // the piece it belongs to; -1: never written
     int pad[2];
 };
-constexpr int kPieceRecSlack = 32;   // records: piece l of warp w at l + w (< pmax + 32)
 
-// dynamic shared memory of k_pcgcs_coarse
-inline size_t coarse_smem_bytes(int pmax, int qn, int ptot) {
-    return (size_t)(pmax + kPieceRecSlack) * sizeof(XsPieceRec) + (size_t)pmax * 8 +
-           (size_t)ptot * 8 + (size_t)pmax * 12 + (size_t)(2 * qn + 1) * 4;
+// dynamic shared memory of k_pcgcs_coarse: records (piece l of tile m, warp w at
+// l + 32 m + w), y, the staged piece sums, own pieces, their global ids, first piece of
+// each own tile, blocks with active rows and their first pieces, and (stage) the rows
+// of the own tiles
+inline size_t coarse_smem_bytes(int pmax, int qn, int ptot, int tmax, bool stage) {
+    return (size_t)(pmax + 32 * tmax) * sizeof(XsPieceRec) + (size_t)pmax * 8 +
+           (size_t)ptot * 8 + (size_t)pmax * 16 + (size_t)(tmax + 1) * 4 +
+           (size_t)(2 * qn + 1) * 4 + (stage ? (size_t)tmax * kCoarseTile * 4 : 0);
 }
+constexpr size_t kCoarseSmemMax = 200 * 1024;   // dynamic shared memory budget of the launch
 
 template <int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarseParams C) {
+    static_assert(MAXT == kCoarseTile, "one position of a tile per thread");
     __shared__ CgShared S;
     __shared__ double tr[kMaxCoarseBlocks];   // t = Y' r of every block with active rows
     __shared__ double ts[kMaxCoarseBlocks];   // Y' s
@@ -1448,80 +1466,105 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
     double* __restrict__ yv = P.idA;    // diag^1/2: the block indicators in scaled variables
     double* __restrict__ sval = P.sval;
     XsRecord* const rec = reinterpret_cast<XsRecord*>(P.part);
-    const int e0 = C.cta_ptr[bidx], np = C.cta_ptr[bidx + 1] - e0;
-    XsPieceRec* const recs = reinterpret_cast<XsPieceRec*>(dyn);           // [pmax + 32]
-    double* const ysh = reinterpret_cast<double*>(recs + C.pmax + kPieceRecSlack);  // [pmax]
-    double* const stp = ysh + C.pmax;                                       // [ptot]
-    int* const spc = reinterpret_cast<int*>(stp + C.ptot);                  // [3 pmax]
-    int* const snz = spc + 3 * C.pmax;                                      // [qn]
-    int* const sbp = snz + qn;                                              // [qn + 1]
-    for (int j = t; j < 3 * np; j += B) spc[j] = C.piece[3 * e0 + j];
+    const int ntl = C.ntiles > bidx ? (C.ntiles - bidx + G - 1) / G : 0;   // own tiles
+    XsPieceRec* const recs = reinterpret_cast<XsPieceRec*>(dyn);   // [pmax + 32 tmax]
+    double* const ysh = reinterpret_cast<double*>(recs + C.pmax + 32 * C.tmax);   // [pmax]
+    double* const stp = ysh + C.pmax;                                  // [ptot]
+    int* const spc = reinterpret_cast<int*>(stp + C.ptot);             // [3 pmax] own pieces
+    int* const sid = spc + 3 * C.pmax;                                 // [pmax] their ids
+    int* const stile = sid + C.pmax;                                   // [tmax + 1]
+    int* const snz = stile + C.tmax + 1;                               // [qn]
+    int* const sbp = snz + qn;                                         // [qn + 1]
+    int* const srow = sbp + qn + 1;                    // [tmax kCoarseTile] (stage) own rows
+    if (t == 0) {
+        int np = 0;
+        for (int m = 0; m < ntl; ++m) {
+            const int j = bidx + m * G;
+            stile[m] = np;
+            np += C.tp[j + 1] - C.tp[j];
+        }
+        stile[ntl] = np;
+    }
     for (int m = t; m < qn; m += B) {
         const int a = sdc_idx(C.nzb[m], q, 73);
         snz[m] = a;
         sbp[m] = C.blk_ptr[a];
     }
     if (t == 0) sbp[qn] = C.blk_ptr[q];
-    for (int j = t; j < C.pmax + kPieceRecSlack; j += B) recs[j].tag = -1;
+    for (int j = t; j < C.pmax + 32 * C.tmax; j += B) recs[j].tag = -1;
+    if (C.stage)
+        for (int m = 0; m < ntl; ++m) {
+            const int k = (bidx + m * G) * kCoarseTile + t;
+            srow[m * kCoarseTile + t] = k < n ? sdc_idx(C.crow[k], n, 70) : 0;
+        }
     __syncthreads();
-    // this warp's chunk [cs, ce) of the CTA's positions and the piece holding cs
-    const int k0 = np ? spc[1] : 0, k1 = np ? spc[3 * np - 1] : 0;
-    const int rw = (k1 - k0 + nw - 1) / nw;
-    const int cs = min(k1, k0 + wid * rw), ce = min(k1, cs + rw);
-    int pf = 0;
-    while (pf < np - 1 && spc[3 * pf + 2] <= cs) ++pf;
+    const int np = stile[ntl];
+    for (int m = 0; m < ntl; ++m) {
+        const int e0 = C.tp[bidx + m * G], l0 = stile[m], cnt = stile[m + 1] - l0;
+        for (int u = t; u < cnt; u += B) {
+            const int e = sdc_idx(e0 + u, C.ptot, 74);
+            sid[l0 + u] = e;
+            spc[3 * (l0 + u)] = C.piece[3 * e];
+            spc[3 * (l0 + u) + 1] = C.piece[3 * e + 1];
+            spc[3 * (l0 + u) + 2] = C.piece[3 * e + 2];
+        }
+    }
+    __syncthreads();
     unsigned epoch = 0;
     int buf = 0;
-    // f(l, i) over this thread's rows: piece l (of this CTA), compact row i
+    // compact row at position k of own tile m (thread t: k = tile start + t)
+    auto row_at = [&](int m, int k) {
+        return C.stage ? srow[m * kCoarseTile + t] : sdc_idx(C.crow[k], n, 70);
+    };
+    // f(l, i) over this thread's rows: own piece l, compact row i
     auto for_rows = [&](auto&& f) {
-        int l = pf;
-        for (int k = cs + lane; k < ce; k += 32) {
+        int l = 0;
+        for (int m = 0; m < ntl; ++m) {
+            const int k = (bidx + m * G) * kCoarseTile + t;
+            if (k >= n) break;
             while (spc[3 * l + 2] <= k) ++l;
-            f(l, sdc_idx(C.crow[k], n, 70));
+            f(l, row_at(m, k));
         }
     };
-    // sum of g(i) = (a, b) -> a b over each piece of this CTA, exactly, into tpiece
+    // sum of g(i) = (a, b) -> a b over each own piece, exactly, into tpiece
     auto piece_sums = [&](auto&& g) {
-        if (cs < ce) {
-            int l = pf, pend = spc[3 * pf + 2];
-            double acc = 0.0;
-            auto flush = [&]() {
-                const int F = __reduce_max_sync(0xffffffffu, xs_field(acc));
-                const __int128 qv = xs_warp_sum(xs_fixed(acc, F));
+        for (int m = 0; m < ntl; ++m) {
+            const int j = bidx + m * G;
+            const int base = j * kCoarseTile + 32 * wid, end = min(n, (j + 1) * kCoarseTile);
+            if (base >= end) continue;           // no rows of this warp in the tile
+            int l = stile[m];
+            while (spc[3 * l + 2] <= base) ++l;  // the piece holding the warp's first row
+            int pend = spc[3 * l + 2];
+            const int k = base + lane;
+            double v = 0.0;
+            if (k < end) {
+                const double2 ab = g(row_at(m, k));
+                v = ab.x * ab.y;
+            }
+            bool used = k >= end;
+            while (true) {
+                double part = 0.0;
+                if (!used && k < pend) {
+                    part = v;
+                    used = true;
+                }
+                const int F = __reduce_max_sync(0xffffffffu, xs_field(part));
+                const __int128 qv = xs_warp_sum(xs_fixed(part, F));
                 if (lane == 0) {
-                    XsPieceRec& R = recs[l + wid];
+                    XsPieceRec& R = recs[l + 32 * m + wid];
                     R.q = qv;
                     R.f = F;
                     R.tag = l;
                 }
-            };
-            for (int base = cs; base < ce; base += 32) {
-                const int k = base + lane;
-                double2 v = make_double2(0.0, 0.0);
-                if (k < ce) v = g(sdc_idx(C.crow[k], n, 70));
-                if (__all_sync(0xffffffffu, k < pend)) {   // one piece: the common case
-                    acc = fma(v.x, v.y, acc);
-                    continue;
-                }
-                const double pv = v.x * v.y;
-                bool used = k >= ce;
-                while (true) {
-                    if (!used && k < pend) {
-                        acc += pv;
-                        used = true;
-                    }
-                    if (__all_sync(0xffffffffu, used)) break;
-                    flush();
-                    acc = 0.0;
-                    ++l;
-                    pend = spc[3 * l + 2];
-                }
+                if (__all_sync(0xffffffffu, used)) break;
+                ++l;
+                pend = spc[3 * l + 2];
             }
-            flush();
         }
         __syncthreads();
         for (int l = wid; l < np; l += nw) {
-            const XsPieceRec R = recs[l + lane];
+            const int m = (spc[3 * l + 1] / kCoarseTile - bidx) / G;
+            const XsPieceRec R = recs[l + 32 * m + lane];
             const bool on = lane < nw && R.tag == l;
             const int f = on ? R.f : 1;
             const int F = __reduce_max_sync(0xffffffffu, f);
@@ -1529,7 +1572,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
             __int128 qv = 0;
             if (on) qv = d >= 127 ? (R.q < 0 ? (__int128)-1 : (__int128)0) : xs_sar(R.q, d);
             qv = xs_warp_sum(qv);
-            if (lane == 0) C.tpiece[e0 + l] = xs_to_double(qv, F);
+            if (lane == 0) C.tpiece[sid[l]] = xs_to_double(qv, F);
         }
     };
     // the blocks' totals of the published piece sums; first: t = total, Y's = 0,
@@ -1603,17 +1646,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
         // w = (I + c S K_off S) u, r.u, w.u, and Y' w per piece
         double ga = 0.0, de = 0.0;
         piece_sums([&](int i) {
+            // every operand of the row loaded before the first store (the vectors may
+            // alias as far as the compiler knows)
             const int len = P.alen[i];
-            const double ui = __ldcg(P.u + i);
+            const double ui = __ldcg(P.u + i), ri = P.r[i], yi = yv[i];
             double acc = ui;
             for (int k = 0; k < len; ++k) {
                 const size_t qq = (size_t)k * ld + i;
                 acc += sval[qq] * __ldcg(P.u + sdc_idx(P.acol[qq], n, 72));
             }
             P.w[i] = acc;
-            ga += P.r[i] * ui;
+            ga += ri * ui;
             de += acc * ui;
-            return make_double2(yv[i], acc);
+            return make_double2(yi, acc);
         });
         if (!cg_publish_arrive(ga, de, S, rec + buf * G, P.bar, G, bidx, epoch, P.budget, P.err))
             return;
@@ -1635,14 +1680,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_pcgcs_coarse(CgParams P, CoarsePara
         coarse_t(false, alpha, beta);
         coarse_y();
         for_rows([&](int l, int i) {
-            const double pi = P.u[i] + beta * P.p[i];
-            const double si = P.w[i] + beta * P.s[i];
+            const double ui = P.u[i], p0 = P.p[i], wi = P.w[i], s0 = P.s[i], xi = P.x[i],
+                         r0 = P.r[i], yi = yv[i];
+            const double pi = ui + beta * p0;
+            const double si = wi + beta * s0;
+            const double ri = r0 - alpha * si;
             P.p[i] = pi;
             P.s[i] = si;
-            P.x[i] += alpha * pi;
-            const double ri = P.r[i] - alpha * si;
+            P.x[i] = xi + alpha * pi;
             P.r[i] = ri;
-            P.u[i] = ri + yv[i] * ysh[l];
+            P.u[i] = ri + yi * ysh[l];
         });
         if (!group_barrier(P.bar, G, epoch, P.budget, P.err, &S.ok)) return;
     }
@@ -2361,7 +2408,7 @@ int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int
     set_cg_vectors(P, B);
     set_scaled_buffers(P, A, B);
     if (!P.sv || !P.sval || role.epi_lo < role.epi_hi || C.G < 1 || C.q < 1 || C.qn > C.q ||
-        C.pmax > C.q + 1)
+        C.ntiles < 1 || C.tmax < 1 || C.pmax < 1 || C.ptot < 1)
         return SDC_E_INVALID;
     if (reinterpret_cast<uintptr_t>(P.part) % 16 != 0 || C.G > B.max_blocks) return SDC_E_INVALID;
     P.bar = &B.sc->bar;
@@ -2378,18 +2425,22 @@ int launch_pcg_coarse(int n, const Ell& A, const PcgRole& role, double rtol, int
     CP.q = C.q;
     CP.qn = C.qn;
     CP.pmax = C.pmax;
-    CP.ptot = C.h_blk_ptr.empty() ? 0 : C.h_blk_ptr[C.q];
+    CP.ptot = C.ptot;
+    CP.ntiles = C.ntiles;
+    CP.tmax = C.tmax;
+    CP.stage = coarse_smem_bytes(C.pmax, C.qn, C.ptot, C.tmax, true) <= kCoarseSmemMax;
     CP.crow = C.crow;
-    CP.cta_ptr = C.cta_ptr;
+    CP.tp = C.tp;
     CP.piece = C.piece;
     CP.blk_ptr = C.blk_ptr;
     CP.nzb = C.nzb;
     CP.Einv = C.Einv;
     CP.tpiece = C.tpiece;
     void* args[] = {&P, &CP};
-    const int blk = cfg.block > 512 ? 1024 : 512;
-    const void* k = blk > 512 ? (const void*)k_pcgcs_coarse<1024> : (const void*)k_pcgcs_coarse<512>;
-    const size_t smem = coarse_smem_bytes(C.pmax, C.qn, CP.ptot);
+    const int blk = kCoarseTile;
+    const void* k = (const void*)k_pcgcs_coarse<kCoarseTile>;
+    const size_t smem = coarse_smem_bytes(C.pmax, C.qn, C.ptot, C.tmax, CP.stage != 0);
+    if (smem > kCoarseSmemMax) return SDC_E_INVALID;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return SDC_E_CUDA;
