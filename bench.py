@@ -293,8 +293,8 @@ CG_SOURCES = ("step.cu", "device_common.cuh")
 ERR_NORM = ("max over ten checkpoints evenly spaced in the window (the last step included) of "
             "max_i |v_i(t) - v_ref,i(t)|")
 
-PCG_TRAFFIC = {"w1": {"dram_bytes": 64.29e6 + 11.10e6, "algorithmic_bytes": 1.735e9,
-                      "kernel": "k_pcg_scaled<1024>", "source_sha": "d17d91028a67b582",
+PCG_TRAFFIC = {"w1": {"dram_bytes": 64.25e6 + 10.65e6, "algorithmic_bytes": 1.735e9,
+                      "kernel": "k_pcg_scaled<1024>", "source_sha": "f6df4e0ce07892df",
                       "capture": "profiles/pcg_scaled_w1_slab_full_solve.md"}}
 
 
