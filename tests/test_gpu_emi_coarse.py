@@ -193,3 +193,29 @@ def test_emi_two_level_full_size_bricks_properties(torch_dev):
     assert np.abs(outs[0][0] - outs[2][0]).max() <= wl.tol
     ctx.close()
     jac.close()
+
+
+@pytest.mark.parametrize("labels", ["spread", "one_block"])
+def test_emi_two_level_label_edge_cases(torch_dev, labels):
+    """Unused labels between the used ones (their blocks stay empty: unit rows of E)
+    and a single block holding every dof: one step against the oracle's step with
+    the same labels."""
+    torch, dev = torch_dev
+    wl = emi_tiny("grid")
+    blocks = coarse_blocks(wl, split=(4, 2, 2))
+    lab = 2 * blocks + 3 if labels == "spread" else np.zeros(wl.n, np.int32)
+    ctx = _ctx(wl, torch, dev, lab)
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    du, dw = t64(wl.u0), t64(wl.w0)
+    st = ctx.step(du, dw, 0.0, wl.dt, wl.sweeps, wl.tol)
+    r = oracle.System.from_mesh(wl.mesh).step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=lab)
+    assert r["status"] == 0
+    assert _relmax(du.cpu().numpy(), r["u"]) <= RTOL
+    assert _relmax(dw.cpu().numpy(), r["w"]) <= RTOL
+    for k in range(wl.sweeps):
+        if r["stats"].n_active[k]:
+            assert np.array_equal(ctx.active(k), r["active"][k]), "sweep %d" % k
+        for m in range(wl.M):
+            ref = r["stats"].cg_iters[k * 8 + m]
+            assert abs(st.cg_iters[k][m] - ref) <= max(2, 0.05 * ref), (k, m)
+    ctx.close()

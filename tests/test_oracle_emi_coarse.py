@@ -24,7 +24,7 @@ import scipy.sparse as sp
 import scipy.sparse.csgraph as csgraph
 
 import oracle
-from workloads.emi import emi_tiny
+from workloads.emi import coarse_blocks, emi_tiny
 
 
 def _node_system(wl, c=None, seed=0):
@@ -164,3 +164,23 @@ def test_block_major_renumbering_is_a_relabelling():
     assert np.abs(r1["u"][order] - r2["u"]).max() <= 1e-12 * scale
     assert np.abs(r1["w"] - r2["w"]).max() <= 1e-12
     assert list(r1["stats"].n_active) == list(r2["stats"].n_active)
+
+
+def test_block_labels_need_not_be_consecutive_and_one_block_is_allowed():
+    """Labels are only names: spreading them out (unused labels between) changes
+    nothing, bitwise; a single block (one coarse vector, every active dof) is a
+    valid coarse space whose step agrees with the Jacobi step within the solves'
+    tolerance."""
+    wl = emi_tiny("grid")
+    blocks = coarse_blocks(wl, split=(4, 2, 2))
+    S = oracle.System.from_mesh(wl.mesh)
+    a = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks)
+    b = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=2 * blocks + 3)
+    assert a["status"] == b["status"] == 0
+    assert np.array_equal(a["u"], b["u"]) and np.array_equal(a["w"], b["w"])
+    assert list(a["stats"].cg_iters) == list(b["stats"].cg_iters)
+    one = S.step_emi(wl, wl.u0, wl.w0, tol=0.0, cg_rtol=1e-13, coarse=np.zeros(wl.n, np.int32))
+    jac = S.step_emi(wl, wl.u0, wl.w0, tol=0.0, cg_rtol=1e-13)
+    assert one["status"] == jac["status"] == 0
+    scale = max(1.0, np.abs(jac["u"]).max())
+    assert np.abs(one["u"] - jac["u"]).max() <= 1e-10 * scale
