@@ -456,8 +456,13 @@ sdc_status sdc_create_emi(sdc_ctx** out, const sdc_mesh* mesh, const sdc_emi* em
  *   n_blocks      1 .. SDC_MAX_COARSE_BLOCKS; block_of_dof NULL or n_blocks 0
  *                 switches the two-level preconditioner off
  * Cell-by-cell contexts only (else SDC_E_INVALID); SDC_E_NOMEM when device memory
- * is short.  Each node solve then costs one more grid barrier per CG iteration, and
- * a factorisation of E (one grid barrier per block) per solve. */
+ * is short.  A CG iteration keeps the Jacobi solve's two grid synchronisations (the
+ * block sums of Y'r travel with the dot products); each solve adds the set-up of E
+ * and its inverse (one grid barrier per 16 blocks).  The solve's rows run in tiles
+ * of the active rows sorted by block: numbering the dofs block by block keeps each
+ * tile contiguous in memory.  A step returns SDC_E_INVALID if one CTA's share of the
+ * pieces (tile/block intersections) and the pieces' sums exceed the launch's shared
+ * memory (about 13 M active rows and more). */
 #define SDC_MAX_COARSE_BLOCKS 1024
 sdc_status sdc_set_coarse_blocks(sdc_ctx* ctx, const int* block_of_dof, int n_blocks);
 
