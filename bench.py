@@ -80,6 +80,9 @@ def parse():
                     help="w2: two-level preconditioner of the node solves over blocks = the "
                          "cells and the extracellular space cut into this many boxes "
                          "(x,y,z); 'off' for Jacobi alone")
+    ap.add_argument("--emi-coarse-min-rows", type=int, default=100000,
+                    help="w2 with coarse blocks: sweeps with fewer active rows solve with "
+                         "Jacobi alone (0: every sweep two-level)")
     ap.add_argument("--emi-order", choices=["block", "natural"], default="block",
                     help="w2 with coarse blocks: number the dofs block by block (block) or "
                          "keep the mesh's numbering (natural)")
@@ -771,7 +774,7 @@ def run_emi(args):
     K, Wm = args.steps, args.warmup
     stream = torch.cuda.current_stream(dev)
     opts = default_options(profile=1, cg_rtol=wl.cg_rtol, alpha=wl.alpha, w_frozen=int(frozen),
-                           cg_maxit=100000)
+                           cg_maxit=100000, coarse_min_rows=args.emi_coarse_min_rows)
     blocks = None
     if args.emi_coarse != "off":
         from workloads.emi import block_major, coarse_blocks, renumber
@@ -904,6 +907,7 @@ def run_emi(args):
            "preconditioner": ("two-level: Jacobi + %d blocks (cells, extracellular space in "
                               "%s boxes)" % (int(blocks.max()) + 1, args.emi_coarse)
                               if blocks is not None else "Jacobi"),
+           "coarse_min_rows": args.emi_coarse_min_rows if blocks is not None else None,
            "dof_order": ("block by block (workloads.emi.renumber)"
                          if blocks is not None and args.emi_order == "block" else "mesh"),
            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "replicas",

@@ -162,6 +162,11 @@ typedef struct {
                               off) as one CUDA graph and replayed, one host synchronisation per
                               step; 0 host-driven sweeps.  Bitwise the same results.
                               Default 1                                                      */
+    int coarse_min_rows;   /* cell-by-cell contexts with coarse blocks (sdc_set_coarse_blocks):
+                              node solves of sweeps with fewer active rows than this use Jacobi
+                              alone (small sets converge in few iterations, where the coarse
+                              space's set-up and per-iteration cost do not pay); default 0:
+                              every solve uses the two-level preconditioner                 */
 } sdc_options;
 
 /* Per-step statistics (valid when sdc_step returns).                              */

@@ -41,7 +41,7 @@ class _Opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int),
                 ("reaction_implicit", C.c_int), ("w_frozen", C.c_int),
                 ("energy_stop", C.c_int), ("rho", C.c_double), ("qhat", C.c_int),
-                ("drop_rule", C.c_int)]
+                ("drop_rule", C.c_int), ("coarse_min_rows", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -294,14 +294,15 @@ class System:
 
     def step_emi(self, wl, u, w, sweeps=None, tol=None, cg_rtol=None, w_frozen=False,
                  want_log=False, energy_stop=False, rho=0.0, alpha=None, drop_rule=0,
-                 coarse=False):
+                 coarse=False, coarse_min_rows=0):
         """One SDC step of a cell-by-cell workload (K of this system = the
         subdomain stiffness; pairs, Robin and membrane data from `wl`).
         `energy_stop` ends the sweeps by the energy-norm test of Sec. 3.2
         (`rho` given, or estimated from successive sweep energies when 0).
         `coarse` solves the node systems with the two-level preconditioner (Sec. 6)
         instead of Jacobi alone, over the workload's subdomain labels (True) or the
-        block labels given as an array."""
+        block labels given as an array; sweeps with fewer than `coarse_min_rows`
+        active dofs keep Jacobi alone."""
         n = self.n
         sweeps = wl.sweeps if sweeps is None else sweeps
         tol = wl.tol if tol is None else tol
@@ -310,7 +311,7 @@ class System:
         w = np.array(w, dtype=np.float64, copy=True)
         st = Stats()
         opts = _Opts(wl.alpha if alpha is None else alpha, cg_rtol, 100000, 1, int(w_frozen),
-                     int(energy_stop), rho, 0, int(drop_rule))
+                     int(energy_stop), rho, 0, int(drop_rule), int(coarse_min_rows))
         log = np.zeros(max(1, sweeps) * n, np.int32) if want_log else None
         rob = _f64(wl.robin)
         dom = None

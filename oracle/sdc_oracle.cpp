@@ -515,9 +515,11 @@ typedef struct { double ga, gs, a, eps, mu1, mu2, cw; } ora_ionic;
 // qhat: 0 LU trick, 1 implicit Euler (make_collocation)
 // drop_rule: 0 TOL_drop = alpha TOL; 1 the a priori drop tolerance of Sec. 4.1
 // (drop_tolerance below) with the given rho > 0 and c from the first sweep
+// coarse_min_rows: cell-by-cell steps with blocks: sweeps with fewer active dofs
+// solve with Jacobi alone
 typedef struct {
     double alpha; double cg_rtol; int cg_maxit; int reaction_implicit; int w_frozen;
-    int energy_stop; double rho; int qhat; int drop_rule;
+    int energy_stop; double rho; int qhat; int drop_rule; int coarse_min_rows;
 } ora_opts;
 #define ORA_MAX_SWEEPS 64
 #define ORA_MAX_M 8
@@ -994,11 +996,13 @@ int ora_step_emi(void* h, const ora_ionic* ip, double Cm, double g_gap, int M, i
             std::vector<double> x(N, 0.0);
             int iters = 0;
             double relres = 0.0;
-            // dom given: the two-level preconditioner over the subdomains of the active set
+            // dom given (and enough active dofs): the two-level preconditioner over the
+            // subdomains of the active set
+            const bool two = dom && (long long)act.size() >= o->coarse_min_rows;
             TwoLevel tl;
-            if (dom && !tl.build(N, dom, act, apply)) return ORA_DOMAIN;
+            if (two && !tl.build(N, dom, act, apply)) return ORA_DOMAIN;
             const int rc = pcg_op(N, apply, diag, act, b, x, o->cg_rtol, o->cg_maxit, iters, relres,
-                                  dom ? &tl : nullptr);
+                                  two ? &tl : nullptr);
             if (st) {
                 st->cg_iters[k * ORA_MAX_M + m] = iters;
                 st->cg_relres_max = std::max(st->cg_relres_max, relres);

@@ -48,7 +48,7 @@ class sdc_options(C.Structure):
                 ("profile", C.c_int), ("inject_fault", C.c_int), ("cg_pipelined", C.c_int),
                 ("energy_stop", C.c_int), ("sdc_rho", C.c_double), ("sdc_qhat", C.c_int),
                 ("reorder", C.c_int), ("drop_rule", C.c_int), ("cg_scaled", C.c_int),
-                ("batch_graph", C.c_int)]
+                ("batch_graph", C.c_int), ("coarse_min_rows", C.c_int)]
 
 
 class sdc_stats(C.Structure):

@@ -335,6 +335,7 @@ void sdc_default_options(sdc_options* o) {
     o->drop_rule = 0;
     o->batch_graph = 1;
     o->cg_scaled = 1;
+    o->coarse_min_rows = 0;
 }
 
 void sdc_default_ionic(sdc_ionic* p) {
@@ -456,7 +457,7 @@ sdc_status create_impl(sdc_ctx** out, const sdc_mesh* mesh, const sdc_ionic* ion
         o.energy_stop < 0 || o.energy_stop > 1 || !(o.sdc_rho >= 0.0) || !(o.sdc_rho < 1.0) ||
         o.sdc_qhat < 0 || o.sdc_qhat > 1 || o.reorder < 0 || o.reorder > 1 ||
         o.drop_rule < 0 || o.drop_rule > 1 || o.cg_scaled < 0 || o.cg_scaled > 1 ||
-        o.batch_graph < 0 || o.batch_graph > 1)
+        o.batch_graph < 0 || o.batch_graph > 1 || o.coarse_min_rows < 0)
         return fail(nullptr, SDC_E_INVALID, "invalid options");
     if (o.drop_rule == 1 && !(o.sdc_rho > 0.0))
         return fail(nullptr, SDC_E_INVALID, "drop_rule = 1 needs a given sdc_rho in (0, 1)");

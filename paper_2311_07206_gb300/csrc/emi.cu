@@ -424,10 +424,12 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             if (act) launch_pos_set(n, act, E.pos, 0, B.N, s);
             else k_pos_identity<<<nbk(N, 256), 256, 0, s>>>(N, E.pos, 0);
         });
-        if (a.coarse) {
+        // the two-level preconditioner on this sweep's solves (enough active rows)
+        CoarseDev* const coarse = a.coarse && n >= a.opt->coarse_min_rows ? a.coarse : nullptr;
+        if (coarse) {
             // the blocks of this sweep's active set: rows by block, CTA ownership
             int rc = SDC_OK;
-            run(SDC_PHASE_SELECT, 5, [&] { rc = coarse_sweep(*a.coarse, n, act, E.pos,
+            run(SDC_PHASE_SELECT, 5, [&] { rc = coarse_sweep(*coarse, n, act, E.pos,
                                                              a.pcg->sms, s); });
             if (rc != SDC_OK) {
                 status = fail(rc, "two-level preconditioner: block ordering failed");
@@ -469,9 +471,9 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
             role.iters_out = &B.sc->cg_iters[k * kMaxM + m];
             role.relres_out = &B.sc->cg_relres[k * kMaxM + m];
             role.energy_out = &B.sc->cg_energy[k * kMaxM + m];
-            if (a.coarse) {
+            if (coarse) {
                 run(SDC_PHASE_EXTRACT, 4, [&] {
-                    if (coarse_factor(*a.coarse, n, E.A, B.mc, role.J, B.kdc, c, pcg.budget, s) !=
+                    if (coarse_factor(*coarse, n, E.A, B.mc, role.J, B.kdc, c, pcg.budget, s) !=
                         SDC_OK)
                         status = fail(SDC_E_CUDA, std::string("coarse factorisation launch: ") +
                                                       cudaGetErrorString(cudaGetLastError()));
@@ -479,8 +481,8 @@ int emi_step(const EmiStepArgs& a, double* d_u, double* d_w, double dt, int swee
                 if (status != SDC_OK) break;
             }
             run(SDC_PHASE_PCG, 1, [&] {
-                const int rc = a.coarse ? launch_pcg_coarse(n, E.A, role, a.opt->cg_rtol,
-                                                            a.opt->cg_maxit, *a.coarse, pcg, B, s)
+                const int rc = coarse ? launch_pcg_coarse(n, E.A, role, a.opt->cg_rtol,
+                                                          a.opt->cg_maxit, *coarse, pcg, B, s)
                                         : launch_pcg_role(n, E.A, role, dt, M, a.opt->cg_rtol,
                                                           a.opt->cg_maxit, pcg, B, s);
                 if (rc != SDC_OK)

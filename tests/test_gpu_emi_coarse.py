@@ -219,3 +219,30 @@ def test_emi_two_level_label_edge_cases(torch_dev, labels):
             ref = r["stats"].cg_iters[k * 8 + m]
             assert abs(st.cg_iters[k][m] - ref) <= max(2, 0.05 * ref), (k, m)
     ctx.close()
+
+
+def test_emi_two_level_size_rule_parity(torch_dev):
+    """coarse_min_rows between the first and the second sweep's sizes: the first
+    sweep's solves use the two-level preconditioner, the later ones Jacobi; one step
+    against the oracle's step with the same rule."""
+    torch, dev = torch_dev
+    wl = emi_tiny("grid")
+    blocks = coarse_blocks(wl, split=(4, 2, 2))
+    S = oracle.System.from_mesh(wl.mesh)
+    two = S.step_emi(wl, wl.u0, wl.w0, coarse=blocks)
+    rule = two["stats"].n_active[1] + 1
+    ctx = _ctx(wl, torch, dev, blocks, coarse_min_rows=int(rule))
+    t64 = lambda a: torch.tensor(a, dtype=torch.float64, device=dev)
+    du, dw = t64(wl.u0), t64(wl.w0)
+    st = ctx.step(du, dw, 0.0, wl.dt, wl.sweeps, wl.tol)
+    r = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks, coarse_min_rows=int(rule))
+    assert r["status"] == 0
+    assert _relmax(du.cpu().numpy(), r["u"]) <= RTOL
+    assert _relmax(dw.cpu().numpy(), r["w"]) <= RTOL
+    for k in range(wl.sweeps):
+        if r["stats"].n_active[k]:
+            assert np.array_equal(ctx.active(k), r["active"][k]), "sweep %d" % k
+        for m in range(wl.M):
+            ref = r["stats"].cg_iters[k * 8 + m]
+            assert abs(st.cg_iters[k][m] - ref) <= max(2, 0.05 * ref), (k, m)
+    ctx.close()

@@ -184,3 +184,29 @@ def test_block_labels_need_not_be_consecutive_and_one_block_is_allowed():
     assert one["status"] == jac["status"] == 0
     scale = max(1.0, np.abs(jac["u"]).max())
     assert np.abs(one["u"] - jac["u"]).max() <= 1e-10 * scale
+
+
+def test_coarse_min_rows_chooses_the_preconditioner_per_sweep():
+    """coarse_min_rows: sweeps with fewer active dofs solve with Jacobi alone.  Above
+    every sweep's size it is the Jacobi step bitwise, at 0 the two-level step bitwise;
+    between the first and the second sweep's sizes the first sweep keeps the
+    two-level solves (same iteration counts, same next active set) and the step ends
+    within the solves' and the sweeps' tolerance of the two-level one."""
+    wl = emi_tiny("grid")
+    blocks = coarse_blocks(wl, split=(4, 2, 2))
+    S = oracle.System.from_mesh(wl.mesh)
+    jac = S.step_emi(wl, wl.u0, wl.w0, want_log=True)
+    two = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks)
+    off = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks, coarse_min_rows=10 ** 9)
+    on = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks, coarse_min_rows=0)
+    assert np.array_equal(off["u"], jac["u"]) and np.array_equal(off["w"], jac["w"])
+    assert np.array_equal(on["u"], two["u"]) and np.array_equal(on["w"], two["w"])
+    n0, n1 = two["stats"].n_active[0], two["stats"].n_active[1]
+    assert n1 < n0
+    mid = S.step_emi(wl, wl.u0, wl.w0, want_log=True, coarse=blocks, coarse_min_rows=n1 + 1)
+    assert mid["status"] == 0
+    assert [mid["stats"].cg_iters[m] for m in range(wl.M)] == \
+        [two["stats"].cg_iters[m] for m in range(wl.M)]
+    assert mid["stats"].n_active[1] == n1
+    scale = max(1.0, np.abs(two["u"]).max())
+    assert np.abs(mid["u"] - two["u"]).max() <= 10 * wl.tol * scale
