@@ -295,6 +295,7 @@ CG_SOURCES = ("step.cu", "device_common.cuh")
 # capture was taken with (kernel_source_sha()); once they change, the figure is withheld.
 ERR_NORM = ("max over ten checkpoints evenly spaced in the window (the last step included) of "
             "max_i |v_i(t) - v_ref,i(t)|")
+ERR_NORM_U = ERR_NORM.replace("|v_i(t) - v_ref,i(t)|", "|u_i(t) - u_ref,i(t)|")
 
 PCG_TRAFFIC = {"w1": {"dram_bytes": 64.25e6 + 10.65e6, "algorithmic_bytes": 1.735e9,
                       "kernel": "k_pcg_scaled<1024>", "source_sha": "f6df4e0ce07892df",
@@ -794,13 +795,18 @@ def run_emi(args):
         tune = ctx.autotune(u0.clone(), w0.clone(), 0.0, wl.dt, wl.sweeps, wl.tol, trial_steps=1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
-    def trajectory(tol, sweeps, steps, timed):
+    def trajectory(tol, sweeps, steps, timed, ref=None, record=False):
+        """record: also return u at ten checkpoints (outside the timed region); ref: such
+        a record, against which the run's error is returned instead."""
         u, w = u0.clone(), w0.clone()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(steps)] if timed else None
         agg = {"active_dof_sweeps": 0, "pcg_ms": 0.0, "pcg_launches": 0, "pcg_bytes": 0.0,
                "pcg_ops": 0.0, "launches": 0, "phase_ms": np.zeros(5), "row_iters": 0.0,
                "iters_max": 0}
+        ck = set(sorted({max(0, (j * steps) // 10 - 1) for j in range(1, 11)})) \
+            if (record or ref is not None) else set()
+        snaps, err = [], None
         for n in range(steps):
             if timed:
                 flush.fill_(n)
@@ -819,8 +825,19 @@ def run_emi(args):
                 for m in range(wl.M):
                     agg["row_iters"] += st.n_active[k] * st.cg_iters[k][m]
                     agg["iters_max"] = max(agg["iters_max"], st.cg_iters[k][m])
+            if n in ck:
+                if record:
+                    snaps.append(u.clone())
+                else:
+                    e = (u - ref[len(snaps)]).abs().max()
+                    snaps.append(None)
+                    err = e if err is None else torch.maximum(err, e)
         torch.cuda.synchronize(dev)
         total_ms = sum(a.elapsed_time(b) for a, b in ev) if timed else None
+        if record:
+            return u, w, total_ms, agg, snaps
+        if ref is not None:
+            return u, w, total_ms, agg, float(err)
         return u, w, total_ms, agg
 
     trajectory(wl.tol, wl.sweeps, Wm, timed=False)
@@ -831,7 +848,9 @@ def run_emi(args):
     barrier(world)
     torch.cuda.synchronize(dev)
     clocks = Clocks(dev_id)
-    ua, _, ms_adapt, agg_a = trajectory(wl.tol, wl.sweeps, K, timed=True)
+    res = trajectory(wl.tol, wl.sweeps, K, timed=True, record=not args.no_extras)
+    ua, _, ms_adapt, agg_a = res[:4]
+    snaps_a = res[4] if not args.no_extras else None
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop()
@@ -840,17 +859,67 @@ def run_emi(args):
 
     extras = {}
     if not args.no_extras:
-        up, _, ms_plain, agg_p = trajectory(0.0, wl.sweeps, K, timed=True)
-        ur, _, _, _ = trajectory(0.0, args.ref_sweeps, K, timed=False)
-        ref = ur.cpu().numpy()
+        _, _, _, _, ref = trajectory(0.0, args.ref_sweeps, K, timed=False, record=True)
+        _, _, ms_plain, agg_p, err_p = trajectory(0.0, wl.sweeps, K, timed=True, ref=ref)
+        err_a = max(float((a - b).abs().max()) for a, b in zip(snaps_a, ref))
+        del snaps_a
+        # equal error: adaptive against the plain run with the fewest fixed sweeps whose
+        # error is within 1.1x, the adaptive TOL halved (up to four times) until its error
+        # is within 1.1x of that partner's
+        plain = {}
+        for kp in range(1, wl.sweeps + 2):
+            _, _, ms_k, _, e_k = trajectory(0.0, kp, K, timed=True, ref=ref)
+            plain[kp] = (e_k, ms_k)
+        adapt = [(wl.tol, err_a, ms_adapt)]
+        pick = None
+        for j in range(5):
+            if j > 0:
+                tol_j = wl.tol / 2 ** j
+                _, _, ms_j, _, e_j = trajectory(tol_j, wl.sweeps, K, timed=True, ref=ref)
+                adapt.append((tol_j, e_j, ms_j))
+            cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * adapt[j][1]]
+            kp = cands[0] if cands else max(plain)
+            if adapt[j][1] <= 1.1 * plain[kp][0]:
+                pick = (j, kp)
+                break
+        matched = pick is not None
+        if pick is None:
+            pick = min(((j, kp) for j in range(len(adapt)) for kp in plain),
+                       key=lambda q: abs(np.log(max(adapt[q[0]][1], 1e-300)
+                                                / max(plain[q[1]][0], 1e-300))))
+        j, kp = pick
+        # plain time at the adaptive error, interpolated log-log between the fixed-sweep
+        # plain runs that bracket it (None outside their range)
+        pts = sorted((e, m) for e, m in plain.values() if e > 0)
+        interp = None
+        for (e_lo, m_lo), (e_hi, m_hi) in zip(pts, pts[1:]):
+            e = adapt[j][1]
+            if e_lo <= e <= e_hi and e_hi > e_lo:
+                f = np.log(e / e_lo) / np.log(e_hi / e_lo)
+                interp = float(np.exp(np.log(m_lo) + f * np.log(m_hi / m_lo)))
+                break
         extras = {"plain": {"value": K / (ms_plain / 1e3), "unit": "steps/s",
                             "ms_per_step": ms_plain / K,
                             "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_plain / 1e3)},
                   "speedup_vs_plain": ms_plain / ms_adapt,
-                  "err_vs_ref": {"adaptive": float(np.abs(ua.cpu().numpy() - ref).max()),
-                                 "plain": float(np.abs(up.cpu().numpy() - ref).max()),
+                  "err_vs_ref": {"adaptive": err_a, "plain": err_p,
                                  "reference": "plain SDC, %d sweeps, same dt" % args.ref_sweeps,
-                                 "norm": "max |u(t_K) - u_ref(t_K)|"}}
+                                 "norm": ERR_NORM_U},
+                  "equal_error": {"fixed_sweeps": {
+                      "adaptive": {"TOL": adapt[j][0], "sweeps": wl.sweeps, "err": adapt[j][1],
+                                   "ms_per_step": adapt[j][2] / K},
+                      "plain": {"sweeps": kp, "err": plain[kp][0], "ms_per_step": plain[kp][1] / K},
+                      "matched_within_1.1x": matched,
+                      "speedup": plain[kp][1] / adapt[j][2],
+                      "speedup_interpolated": interp / adapt[j][2] if interp else None,
+                      "interpolation": "plain ms/step at the adaptive error, log-log between "
+                                       "the two fixed-sweep plain runs whose errors bracket it",
+                      "plain_sweep_scan": {str(k): {"err": e, "ms_per_step": m / K}
+                                           for k, (e, m) in plain.items()},
+                      "adaptive_tol_scan": [{"TOL": t, "err": e, "ms_per_step": m / K}
+                                            for t, e, m in adapt]},
+                      "reference": "plain SDC, %d sweeps, same dt, same start" % args.ref_sweeps,
+                      "norm": ERR_NORM_U}}
 
     # end to end through the host-buffer entry point (pinned host u, w)
     hu_t = torch.tensor(wl.u0, dtype=torch.float64).pin_memory()
