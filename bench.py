@@ -297,6 +297,34 @@ ERR_NORM = ("max over ten checkpoints evenly spaced in the window (the last step
             "max_i |v_i(t) - v_ref,i(t)|")
 ERR_NORM_U = ERR_NORM.replace("|v_i(t) - v_ref,i(t)|", "|u_i(t) - u_ref,i(t)|")
 
+
+# ---- equal-error pairs (host logic) -----------------------------------------------
+# plain: {fixed sweeps: (err, ms)}; adapt: [(TOL, err, ms)] in the order run.
+
+def plain_partner(plain, err):
+    """The plain run with the fewest sweeps whose error is within 1.1x of err (the most
+    sweeps when none is)."""
+    cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * err]
+    return cands[0] if cands else max(plain)
+
+
+def closest_pair(plain, adapt):
+    """(j, kp) of the adaptive and plain runs whose errors are closest in log."""
+    return min(((j, kp) for j in range(len(adapt)) for kp in plain),
+               key=lambda q: abs(np.log(max(adapt[q[0]][1], 1e-300)
+                                        / max(plain[q[1]][0], 1e-300))))
+
+
+def interp_plain_ms(plain, err):
+    """Plain time at error err, log-log between the two plain runs whose errors bracket
+    it; None outside their range."""
+    pts = sorted((e, m) for e, m in plain.values() if e > 0)
+    for (e_lo, m_lo), (e_hi, m_hi) in zip(pts, pts[1:]):
+        if e_lo <= err <= e_hi and e_hi > e_lo:
+            f = np.log(err / e_lo) / np.log(e_hi / e_lo)
+            return float(np.exp(np.log(m_lo) + f * np.log(m_hi / m_lo)))
+    return None
+
 PCG_TRAFFIC = {"w1": {"dram_bytes": 64.25e6 + 10.65e6, "algorithmic_bytes": 1.735e9,
                       "kernel": "k_pcg_scaled<1024>", "source_sha": "f6df4e0ce07892df",
                       "capture": "profiles/pcg_scaled_w1_slab_full_solve.md"}}
@@ -540,27 +568,13 @@ def run_gb300(args):
                                             timed=True, ref=ref)
                 adapt.append((tol_j, e, ms))
             e_a = adapt[j][1]
-            cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * e_a]
-            kp = cands[0] if cands else max(plain)
+            kp = plain_partner(plain, e_a)
             if e_a <= 1.1 * plain[kp][0]:
                 pick = (j, kp)
                 break
         matched = pick is not None
-        if pick is None:
-            pick = min(((j, kp) for j in range(len(adapt)) for kp in plain),
-                       key=lambda q: abs(np.log(max(adapt[q[0]][1], 1e-300)
-                                                / max(plain[q[1]][0], 1e-300))))
-        j, kp = pick
-        # plain time at the adaptive error, interpolated log-log between the fixed-sweep runs
-        # that bracket it (None outside their range)
-        pts = sorted((e, m) for e, m in plain.values() if e > 0)
-        interp = None
-        for (e_lo, m_lo), (e_hi, m_hi) in zip(pts, pts[1:]):
-            e = adapt[j][1]
-            if e_lo <= e <= e_hi and e_hi > e_lo:
-                f = np.log(e / e_lo) / np.log(e_hi / e_lo)
-                interp = float(np.exp(np.log(m_lo) + f * np.log(m_hi / m_lo)))
-                break
+        j, kp = pick if matched else closest_pair(plain, adapt)
+        interp = interp_plain_ms(plain, adapt[j][1])
         fixed = {"adaptive": {"TOL": adapt[j][0], "sweeps": wl.sweeps, "err": adapt[j][1],
                               "ms_per_step": adapt[j][2] / steps},
                  "speedup_interpolated": interp / adapt[j][2] if interp else None,
@@ -877,27 +891,13 @@ def run_emi(args):
                 tol_j = wl.tol / 2 ** j
                 _, _, ms_j, _, e_j = trajectory(tol_j, wl.sweeps, K, timed=True, ref=ref)
                 adapt.append((tol_j, e_j, ms_j))
-            cands = [kp for kp in sorted(plain) if plain[kp][0] <= 1.1 * adapt[j][1]]
-            kp = cands[0] if cands else max(plain)
+            kp = plain_partner(plain, adapt[j][1])
             if adapt[j][1] <= 1.1 * plain[kp][0]:
                 pick = (j, kp)
                 break
         matched = pick is not None
-        if pick is None:
-            pick = min(((j, kp) for j in range(len(adapt)) for kp in plain),
-                       key=lambda q: abs(np.log(max(adapt[q[0]][1], 1e-300)
-                                                / max(plain[q[1]][0], 1e-300))))
-        j, kp = pick
-        # plain time at the adaptive error, interpolated log-log between the fixed-sweep
-        # plain runs that bracket it (None outside their range)
-        pts = sorted((e, m) for e, m in plain.values() if e > 0)
-        interp = None
-        for (e_lo, m_lo), (e_hi, m_hi) in zip(pts, pts[1:]):
-            e = adapt[j][1]
-            if e_lo <= e <= e_hi and e_hi > e_lo:
-                f = np.log(e / e_lo) / np.log(e_hi / e_lo)
-                interp = float(np.exp(np.log(m_lo) + f * np.log(m_hi / m_lo)))
-                break
+        j, kp = pick if matched else closest_pair(plain, adapt)
+        interp = interp_plain_ms(plain, adapt[j][1])
         extras = {"plain": {"value": K / (ms_plain / 1e3), "unit": "steps/s",
                             "ms_per_step": ms_plain / K,
                             "active_dof_sweeps_per_s": agg_p["active_dof_sweeps"] / (ms_plain / 1e3)},
